@@ -1,0 +1,272 @@
+"""Plain CPU oracle of the NHQ hybrid-query path (arXiv 2203.13601).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``; never by the product package.  It
+shares no code with the CUDA library.  The arithmetic lives in ``nhq_oracle.c``
+(plain serial C, see its header for the paper passage behind each function);
+this module only compiles it with gcc and marshals numpy arrays.
+
+Every function here follows a definition of the paper:
+
+* ``delta`` / ``chi`` / ``gamma``  Eq. 1, Eq. 4-5, Eq. 6 (weights of Sec. 3.2)
+* ``fused_topk``                   exact top-k by (Gamma, id) (Def. 2 with Gamma)
+* ``filtered_topk``                hybrid ground truth of Sec. 6.1
+* ``knn``                          candidate sets C(u) of Sec. 4.1 (exact K nearest)
+* ``edge_select``                  landing-zone edge selection (Sec. 4.1, Def. 6)
+* ``search``                       Alg. 2 joint pruning + two-stage routing (Sec. 4.2, 5.2)
+* ``graph_quality``                Eq. 7
+* ``recall`` / ``hybrid_recall``   Eq. 3 and its hybrid form (Sec. 6.1)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nhq_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+W_PROPORTIONAL = 0  # w_v = 1, w_l = delta / m  (Sec. 3.2, curve iv)
+W_CONSTANT = 1      # w_v, w_l given             (Eq. 6, curve v)
+F64 = 0
+F32 = 1
+ITER_LIMIT = 4
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.c_void_p
+            i64, i32, f64, u64 = C.c_int64, C.c_int, C.c_double, C.c_uint64
+            lib.or_mix64.restype = u64
+            lib.or_mix64.argtypes = [u64]
+            lib.or_splitmix64_at.restype = u64
+            lib.or_splitmix64_at.argtypes = [u64, u64]
+            lib.or_delta64.restype = f64
+            lib.or_delta64.argtypes = [P, P, i32]
+            lib.or_delta32.restype = C.c_float
+            lib.or_delta32.argtypes = [P, P, i32]
+            lib.or_chi.restype = i32
+            lib.or_chi.argtypes = [P, P, i32]
+            lib.or_gamma64.restype = f64
+            lib.or_gamma64.argtypes = [f64, i32, i32, i32, f64, f64]
+            lib.or_gamma32.restype = C.c_float
+            lib.or_gamma32.argtypes = [C.c_float, i32, i32, i32, C.c_float, C.c_float]
+            lib.or_fused_topk.restype = None
+            lib.or_fused_topk.argtypes = [P, P, i64, i32, i32, P, P, i64, i32, i32, f64, f64, i32,
+                                          P, P, P]
+            lib.or_filtered_topk.restype = None
+            lib.or_filtered_topk.argtypes = [P, P, i64, i32, i32, P, P, i64, i32, i32, P, P, P]
+            lib.or_knn.restype = None
+            lib.or_knn.argtypes = [P, P, i64, i32, i32, i32, i32, f64, f64, i32, P, i64, P, P]
+            lib.or_edge_select.restype = None
+            lib.or_edge_select.argtypes = [P, P, i64, i32, i32, P, i32, i32, i32, f64, f64, i32,
+                                           P, P]
+            lib.or_reverse_candidates.restype = None
+            lib.or_reverse_candidates.argtypes = [P, i64, i32, i32, P]
+            lib.or_graph_quality.restype = f64
+            lib.or_graph_quality.argtypes = [P, i64, i32, P, i32]
+            lib.or_search.restype = None
+            lib.or_search.argtypes = [P, P, i64, i32, i32, P, i32, P, P, i64, i32, i32, i32, u64,
+                                      i64, i32, f64, f64, i32, P, P, P, P, P, P]
+            _lib = lib
+    return _lib
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _u8(a):
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _i64(a):
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _mode(weights):
+    """weights: None / "proportional" -> Sec. 3.2 recommended form; (w_v, w_l) -> constant."""
+    if weights is None or weights == "proportional":
+        return W_PROPORTIONAL, 1.0, 0.0
+    wv, wl = weights
+    return W_CONSTANT, float(wv), float(wl)
+
+
+# ---------------------------------------------------------------- scalars
+def mix64(z: int) -> int:
+    return int(_L().or_mix64(C.c_uint64(z & (2**64 - 1))))
+
+
+def splitmix64_stream(state: int, n: int) -> list:
+    """First n outputs of splitmix64 started from ``state``."""
+    return [int(_L().or_splitmix64_at(C.c_uint64(state & (2**64 - 1)), j)) for j in range(n)]
+
+
+def delta(x, y, prec=F64) -> float:
+    x, y = _f32(x), _f32(y)
+    f = _L().or_delta32 if prec == F32 else _L().or_delta64
+    return float(f(_p(x), _p(y), x.shape[0]))
+
+
+def chi(a, b) -> int:
+    a, b = _u8(a), _u8(b)
+    return int(_L().or_chi(_p(a), _p(b), a.shape[0]))
+
+
+def gamma(delta_value, chi_value, m, weights=None, prec=F64) -> float:
+    mode, wv, wl = _mode(weights)
+    if prec == F32:
+        return float(_L().or_gamma32(delta_value, chi_value, m, mode, wv, wl))
+    return float(_L().or_gamma64(delta_value, chi_value, m, mode, wv, wl))
+
+
+# ---------------------------------------------------------------- batches
+def fused_topk(X, A, Qv, QA, k, weights=None, prec=F64):
+    """Exact top-k by (Gamma, id): returns ids [nq,k] int64, gamma [nq,k] f64, chi [nq,k]."""
+    X, A, Qv, QA = _f32(X), _u8(A), _f32(Qv), _u8(QA)
+    nq = Qv.shape[0]
+    ids = np.empty((nq, k), np.int64)
+    g = np.empty((nq, k), np.float64)
+    ch = np.empty((nq, k), np.int32)
+    mode, wv, wl = _mode(weights)
+    _L().or_fused_topk(_p(X), _p(A), X.shape[0], X.shape[1], A.shape[1], _p(Qv), _p(QA), nq, k,
+                       mode, wv, wl, prec, _p(ids), _p(g), _p(ch))
+    return ids, g, ch
+
+
+def filtered_topk(X, A, Qv, QA, k, prec=F64):
+    """Hybrid ground truth G: k nearest by delta among exact attribute matches.
+    Returns ids [nq,k] (-1 padded), delta [nq,k], |P| [nq]."""
+    X, A, Qv, QA = _f32(X), _u8(A), _f32(Qv), _u8(QA)
+    nq = Qv.shape[0]
+    ids = np.empty((nq, k), np.int64)
+    dl = np.empty((nq, k), np.float64)
+    P = np.empty(nq, np.int64)
+    _L().or_filtered_topk(_p(X), _p(A), X.shape[0], X.shape[1], A.shape[1], _p(Qv), _p(QA), nq,
+                          k, prec, _p(ids), _p(dl), _p(P))
+    return ids, dl, P
+
+
+def knn(X, A, K, weights=None, prec=F64, rows=None):
+    """Exact K nearest v != u by (Gamma, id) for every u (or the given rows)."""
+    X, A = _f32(X), _u8(A)
+    N = X.shape[0]
+    if rows is None:
+        rp, nr = None, N
+    else:
+        rows = _i64(rows)
+        rp, nr = _p(rows), rows.shape[0]
+    ids = np.empty((nr, K), np.int64)
+    g = np.empty((nr, K), np.float64)
+    mode, wv, wl = _mode(weights)
+    _L().or_knn(_p(X), _p(A), N, X.shape[1], A.shape[1], K, mode, wv, wl, prec, rp, nr, _p(ids),
+                _p(g))
+    return ids, g
+
+
+def edge_select(X, A, cand, R, weights=None, prec=F64):
+    """Landing-zone edge selection over candidate lists cand [N,K] -> nbr [N,R] (-1 pad), deg [N]."""
+    X, A, cand = _f32(X), _u8(A), _i64(cand)
+    N, K = cand.shape
+    nbr = np.empty((N, R), np.int64)
+    deg = np.empty(N, np.int32)
+    mode, wv, wl = _mode(weights)
+    _L().or_edge_select(_p(X), _p(A), N, X.shape[1], A.shape[1], _p(cand), K, R, mode, wv, wl,
+                        prec, _p(nbr), _p(deg))
+    return nbr, deg
+
+
+def reverse_candidates(nbr, cap=64):
+    """Rows N(v) + up to ``cap`` smallest reverse sources {u : v in N(u)} -> [N, R+cap]."""
+    nbr = _i64(nbr)
+    N, R = nbr.shape
+    out = np.empty((N, R + cap), np.int64)
+    _L().or_reverse_candidates(_p(nbr), N, R, cap, _p(out))
+    return out
+
+
+def build_graph(X, A, R=32, K=64, weights=None, prec=F32, reverse=True, rev_cap=64):
+    """The whole composite-index build: C(u) = exact K nearest, landing-zone
+    selection, then (reverse=True) the reverse-candidate second pass."""
+    cand, _ = knn(X, A, K, weights=weights, prec=prec)
+    nbr, deg = edge_select(X, A, cand, R, weights=weights, prec=prec)
+    if reverse:
+        nbr, deg = edge_select(X, A, reverse_candidates(nbr, rev_cap), R, weights=weights,
+                               prec=prec)
+    return nbr, deg, cand
+
+
+def graph_quality(nbr, knn_ids) -> float:
+    nbr, knn_ids = _i64(nbr), _i64(knn_ids)
+    return float(_L().or_graph_quality(_p(nbr), nbr.shape[0], nbr.shape[1], _p(knn_ids),
+                                       knn_ids.shape[1]))
+
+
+def search(X, A, nbr, Qv, QA, k, ef, h=1, seed=0, max_iters=1 << 30, weights=None, prec=F32):
+    """Serial Alg. 2 (+ two-stage routing when h > 1).  Returns a dict with
+    ids/gamma/chi [nq,k], ndc/expansions/status [nq]."""
+    X, A, nbr, Qv, QA = _f32(X), _u8(A), _i64(nbr), _f32(Qv), _u8(QA)
+    nq = Qv.shape[0]
+    ids = np.empty((nq, k), np.int64)
+    g = np.empty((nq, k), np.float64)
+    ch = np.empty((nq, k), np.int32)
+    ndc = np.empty(nq, np.int64)
+    ex = np.empty(nq, np.int64)
+    st = np.empty(nq, np.int32)
+    mode, wv, wl = _mode(weights)
+    _L().or_search(_p(X), _p(A), X.shape[0], X.shape[1], A.shape[1], _p(nbr), nbr.shape[1],
+                   _p(Qv), _p(QA), nq, k, ef, h, C.c_uint64(seed & (2**64 - 1)), max_iters,
+                   mode, wv, wl, prec, _p(ids), _p(g), _p(ch), _p(ndc), _p(ex), _p(st))
+    return dict(ids=ids, gamma=g, chi=ch, ndc=ndc, expansions=ex, status=st)
+
+
+# ---------------------------------------------------------------- metrics
+def recall(found, truth) -> float:
+    """Eq. 3: mean over queries of |D & G| / k."""
+    found, truth = np.asarray(found), np.asarray(truth)
+    k = truth.shape[1]
+    hits = [len(set(f[f >= 0].tolist()) & set(t[t >= 0].tolist())) for f, t in zip(found, truth)]
+    return float(np.mean(hits) / k) if len(hits) else 0.0
+
+
+def hybrid_recall(found, A, QA, truth, P):
+    """Recall of Sec. 6.1: only returned ids whose attributes equal the query's
+    count; the denominator is min(k, |P|); queries with |P| = 0 are excluded.
+    Returns (recall, n_excluded)."""
+    found, truth, A, QA = np.asarray(found), np.asarray(truth), np.asarray(A), np.asarray(QA)
+    k = truth.shape[1]
+    vals, excl = [], 0
+    for f, t, qa, p in zip(found, truth, QA, P):
+        if p == 0:
+            excl += 1
+            continue
+        f = f[f >= 0]
+        f = f[(A[f] == qa).all(axis=1)]
+        vals.append(len(set(f.tolist()) & set(t[t >= 0].tolist())) / min(k, int(p)))
+    return (float(np.mean(vals)) if vals else 0.0), excl

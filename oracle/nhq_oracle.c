@@ -1,0 +1,566 @@
+/*
+ * nhq_oracle.c -- plain, slow, serial CPU oracle of the NHQ hybrid-query path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or helper with the CUDA library; it is compiled with
+ * -ffp-contract=off so every float operation below is one IEEE rounding.
+ *
+ * What it computes (paper: arXiv 2203.13601):
+ *   Eq. 1        Euclidean distance delta                    or_delta64 / or_delta32
+ *   Eq. 4-5      attribute distance chi (mismatch count)     or_chi
+ *   Eq. 6        fusion distance Gamma = w_v*delta + w_l*chi or_gamma64 / or_gamma32
+ *   Sec. 3.2     recommended weights w_v = 1, w_l = delta/m  (mode OR_W_PROPORTIONAL)
+ *   Def. 2, 4    exact top-k by Gamma (brute force)          or_fused_topk
+ *   Sec. 6.1     hybrid ground truth (exact attribute match,
+ *                k nearest by delta)                         or_filtered_topk
+ *   Sec. 4.1     candidate set for edge selection: the exact
+ *                K nearest by Gamma                          or_knn
+ *   Sec. 4.1     landing-zone edge selection, Def. 6         or_edge_select
+ *   (reading)    reverse-edge candidates for a second pass   or_reverse_candidates
+ *   Alg. 2       joint pruning (ef-bounded best-first search)
+ *   Sec. 4.2/5.2 two-stage "random TOGG" routing             or_search
+ *   Eq. 7        graph quality Q_G                           or_graph_quality
+ *
+ * Precision: prec = OR_F64 computes delta in double (the truth used for error
+ * statements); prec = OR_F32 is the "canonical f32" form in which the kernels
+ * take their ordering decisions: squared differences summed in index order in
+ * float, sqrtf, then Eq. 6 as separately rounded float operations.  Ordering is
+ * always lexicographic by (Gamma, id).
+ *
+ * Readings where the paper is silent or ambiguous are the ones listed in the
+ * design notes: ef-bounded pool for Alg. 2, splitmix64-derived seeds and S1
+ * neighbour subsets, "local optimum" = an expansion that leaves the pool's
+ * membership unchanged, strict inequalities in the landing-zone test.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_W_PROPORTIONAL 0
+#define OR_W_CONSTANT 1
+#define OR_F64 0
+#define OR_F32 1
+
+#define OR_OK 0
+#define OR_ITER_LIMIT 4
+
+/* ------------------------------------------------------------------ */
+/* splitmix64 (S. Vigna's published generator): state advances by the  */
+/* golden-ratio increment and each output is the mix64 finaliser.      */
+/* ------------------------------------------------------------------ */
+static const uint64_t SM_GAMMA = 0x9E3779B97F4A7C15ULL;
+
+uint64_t or_mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* j-th output (j = 0, 1, ...) of a splitmix64 stream whose state starts at s0 */
+uint64_t or_splitmix64_at(uint64_t s0, uint64_t j)
+{
+    return or_mix64(s0 + (j + 1) * SM_GAMMA);
+}
+
+/* ------------------------------------------------------------------ */
+/* Distances                                                          */
+/* ------------------------------------------------------------------ */
+
+/* Eq. 1 in double */
+double or_delta64(const float *x, const float *y, int d)
+{
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double t = (double)x[i] - (double)y[i];
+        s += t * t;
+    }
+    return sqrt(s);
+}
+
+/* Eq. 1 in float, summed in index order */
+float or_delta32(const float *x, const float *y, int d)
+{
+    float s = 0.0f;
+    for (int i = 0; i < d; ++i) {
+        float t = x[i] - y[i];
+        float t2 = t * t;
+        s = s + t2;
+    }
+    return sqrtf(s);
+}
+
+/* Eq. 4-5: number of attribute positions whose codes differ */
+int or_chi(const uint8_t *a, const uint8_t *b, int m)
+{
+    int c = 0;
+    for (int i = 0; i < m; ++i)
+        c += (a[i] != b[i]) ? 1 : 0;
+    return c;
+}
+
+/* Eq. 6 in double.  Proportional mode: w_v = 1, w_l = delta / m (Sec. 3.2). */
+double or_gamma64(double delta, int chi, int m, int mode, double wv, double wl)
+{
+    if (mode == OR_W_PROPORTIONAL) {
+        double w_l = delta / (double)m;
+        return 1.0 * delta + w_l * (double)chi;
+    }
+    return wv * delta + wl * (double)chi;
+}
+
+/* Eq. 6 in float, each operation rounded once */
+float or_gamma32(float delta, int chi, int m, int mode, float wv, float wl)
+{
+    if (mode == OR_W_PROPORTIONAL) {
+        float w_l = delta / (float)m;
+        float t = w_l * (float)chi;
+        return delta + t;
+    }
+    float a = wv * delta;
+    float b = wl * (float)chi;
+    return a + b;
+}
+
+/* Gamma between row x (attrs ax) and row y (attrs ay) in the chosen precision */
+static double pair_gamma(const float *x, const uint8_t *ax, const float *y, const uint8_t *ay,
+                         int d, int m, int mode, double wv, double wl, int prec, int *chi_out)
+{
+    int chi = or_chi(ax, ay, m);
+    if (chi_out)
+        *chi_out = chi;
+    if (prec == OR_F32)
+        return (double)or_gamma32(or_delta32(x, y, d), chi, m, mode, (float)wv, (float)wl);
+    return or_gamma64(or_delta64(x, y, d), chi, m, mode, wv, wl);
+}
+
+/* ------------------------------------------------------------------ */
+/* (Gamma, id) records and their lexicographic order                  */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double g;
+    int64_t id;
+    int32_t chi;
+} rec_t;
+
+static int rec_cmp(const void *pa, const void *pb)
+{
+    const rec_t *a = (const rec_t *)pa, *b = (const rec_t *)pb;
+    if (a->g < b->g) return -1;
+    if (a->g > b->g) return 1;
+    if (a->id < b->id) return -1;
+    if (a->id > b->id) return 1;
+    return 0;
+}
+
+static int rec_less(double ga, int64_t ia, double gb, int64_t ib)
+{
+    return ga < gb || (ga == gb && ia < ib);
+}
+
+/* ------------------------------------------------------------------ */
+/* Def. 2 with Gamma in place of delta: exact top-k by (Gamma, id).    */
+/* Unfilled slots (k > N) get id -1 and Gamma +inf.                    */
+/* ------------------------------------------------------------------ */
+void or_fused_topk(const float *X, const uint8_t *A, int64_t N, int d, int m,
+                   const float *Qv, const uint8_t *QA, int64_t nq, int k,
+                   int mode, double wv, double wl, int prec,
+                   int64_t *out_ids, double *out_g, int32_t *out_chi)
+{
+    rec_t *all = (rec_t *)malloc(sizeof(rec_t) * (size_t)(N > 0 ? N : 1));
+    for (int64_t q = 0; q < nq; ++q) {
+        const float *qv = Qv + q * (int64_t)d;
+        const uint8_t *qa = QA + q * (int64_t)m;
+        for (int64_t v = 0; v < N; ++v) {
+            int chi;
+            all[v].g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m,
+                                  mode, wv, wl, prec, &chi);
+            all[v].id = v;
+            all[v].chi = chi;
+        }
+        qsort(all, (size_t)N, sizeof(rec_t), rec_cmp);
+        for (int j = 0; j < k; ++j) {
+            int64_t o = q * (int64_t)k + j;
+            if (j < N) {
+                out_ids[o] = all[j].id;
+                out_g[o] = all[j].g;
+                out_chi[o] = all[j].chi;
+            } else {
+                out_ids[o] = -1;
+                out_g[o] = INFINITY;
+                out_chi[o] = -1;
+            }
+        }
+    }
+    free(all);
+}
+
+/* Sec. 6.1: hybrid ground truth G = the k nearest by delta among the objects
+ * whose attributes all equal the query's (chi = 0); out_P[q] = |P|. */
+void or_filtered_topk(const float *X, const uint8_t *A, int64_t N, int d, int m,
+                      const float *Qv, const uint8_t *QA, int64_t nq, int k, int prec,
+                      int64_t *out_ids, double *out_delta, int64_t *out_P)
+{
+    rec_t *all = (rec_t *)malloc(sizeof(rec_t) * (size_t)(N > 0 ? N : 1));
+    for (int64_t q = 0; q < nq; ++q) {
+        const float *qv = Qv + q * (int64_t)d;
+        const uint8_t *qa = QA + q * (int64_t)m;
+        int64_t n = 0;
+        for (int64_t v = 0; v < N; ++v) {
+            if (or_chi(qa, A + v * (int64_t)m, m) != 0)
+                continue;
+            const float *x = X + v * (int64_t)d;
+            all[n].g = prec == OR_F32 ? (double)or_delta32(qv, x, d) : or_delta64(qv, x, d);
+            all[n].id = v;
+            all[n].chi = 0;
+            ++n;
+        }
+        qsort(all, (size_t)n, sizeof(rec_t), rec_cmp);
+        out_P[q] = n;
+        for (int j = 0; j < k; ++j) {
+            int64_t o = q * (int64_t)k + j;
+            out_ids[o] = j < n ? all[j].id : -1;
+            out_delta[o] = j < n ? all[j].g : INFINITY;
+        }
+    }
+    free(all);
+}
+
+/* Candidate set C(u) of Sec. 4.1 taken as the exact K nearest v != u by
+ * (Gamma, id).  rows == NULL means every row 0..N-1 (then nrows must be N). */
+void or_knn(const float *X, const uint8_t *A, int64_t N, int d, int m, int K,
+            int mode, double wv, double wl, int prec,
+            const int64_t *rows, int64_t nrows, int64_t *out_ids, double *out_g)
+{
+    rec_t *all = (rec_t *)malloc(sizeof(rec_t) * (size_t)(N > 0 ? N : 1));
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t u = rows ? rows[r] : r;
+        int64_t n = 0;
+        for (int64_t v = 0; v < N; ++v) {
+            if (v == u)
+                continue;
+            all[n].g = pair_gamma(X + u * (int64_t)d, A + u * (int64_t)m, X + v * (int64_t)d,
+                                  A + v * (int64_t)m, d, m, mode, wv, wl, prec, NULL);
+            all[n].id = v;
+            ++n;
+        }
+        qsort(all, (size_t)n, sizeof(rec_t), rec_cmp);
+        for (int j = 0; j < K; ++j) {
+            out_ids[r * (int64_t)K + j] = j < n ? all[j].id : -1;
+            out_g[r * (int64_t)K + j] = j < n ? all[j].g : INFINITY;
+        }
+    }
+    free(all);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 4.1 edge selection with the landing zone of Def. 6.           */
+/*   (1) candidates C(u) (ids < 0, u itself and repeats are dropped)  */
+/*   (2) sort C(u) ascending by (Gamma(p,u), id); the nearest becomes  */
+/*       the first neighbour                                           */
+/*   (3) each next p joins N(u) iff for every j in N(u) it lies in     */
+/*       L(u, j) = H(u, j) \ B(u, Gamma(u, j)):                        */
+/*         Gamma(p, u) < Gamma(p, j)   (u's side of the bisector)      */
+/*         Gamma(p, u) > Gamma(u, j)   (outside the ball)              */
+/*       until |N(u)| = R.  Unused slots get -1.                       */
+/* Gamma plays the role of delta for the composite index (Sec. 5.1).  */
+/* ------------------------------------------------------------------ */
+void or_edge_select(const float *X, const uint8_t *A, int64_t N, int d, int m,
+                    const int64_t *cand, int K, int R, int mode, double wv, double wl, int prec,
+                    int64_t *out_nbr, int32_t *out_deg)
+{
+    rec_t *c = (rec_t *)malloc(sizeof(rec_t) * (size_t)(K > 0 ? K : 1));
+    for (int64_t u = 0; u < N; ++u) {
+        const float *xu = X + u * (int64_t)d;
+        const uint8_t *au = A + u * (int64_t)m;
+        int n = 0;
+        for (int j = 0; j < K; ++j) {
+            int64_t p = cand[u * (int64_t)K + j];
+            if (p < 0 || p >= N || p == u)
+                continue;
+            int dup = 0;
+            for (int t = 0; t < n; ++t)
+                if (c[t].id == p)
+                    dup = 1;
+            if (dup)
+                continue;
+            c[n].g = pair_gamma(X + p * (int64_t)d, A + p * (int64_t)m, xu, au, d, m, mode, wv,
+                                wl, prec, NULL);
+            c[n].id = p;
+            ++n;
+        }
+        qsort(c, (size_t)n, sizeof(rec_t), rec_cmp);
+        int64_t *nb = out_nbr + u * (int64_t)R;
+        double *nbg = (double *)malloc(sizeof(double) * (size_t)(R > 0 ? R : 1));
+        int deg = 0;
+        for (int t = 0; t < n && deg < R; ++t) {
+            int64_t p = c[t].id;
+            int ok = 1;
+            for (int s = 0; s < deg && ok; ++s) {
+                int64_t j = nb[s];
+                double gpj = pair_gamma(X + p * (int64_t)d, A + p * (int64_t)m,
+                                        X + j * (int64_t)d, A + j * (int64_t)m, d, m, mode,
+                                        wv, wl, prec, NULL);
+                if (!(c[t].g < gpj && c[t].g > nbg[s]))
+                    ok = 0;
+            }
+            if (ok) {
+                nb[deg] = p;
+                nbg[deg] = c[t].g;
+                ++deg;
+            }
+        }
+        for (int s = deg; s < R; ++s)
+            nb[s] = -1;
+        out_deg[u] = deg;
+        free(nbg);
+    }
+    free(c);
+}
+
+/* Reverse-edge candidates (the paper is silent on reverse edges; this is the
+ * stated reading used by the second selection pass): for every v,
+ *   out[v] = N(v) (its selected neighbours, in slot order), followed by the
+ *            sources u with v in N(u) that are not already in N(v), taking the
+ *            `cap` smallest such ids in ascending order; -1 pads the row.
+ * Row width is R + cap.  The second pass runs or_edge_select on these rows. */
+void or_reverse_candidates(const int64_t *nbr, int64_t N, int R, int cap, int64_t *out)
+{
+    int W = R + cap;
+    for (int64_t v = 0; v < N; ++v) {
+        int64_t *row = out + v * (int64_t)W;
+        int n = 0;
+        for (int s = 0; s < R; ++s)
+            if (nbr[v * (int64_t)R + s] >= 0)
+                row[n++] = nbr[v * (int64_t)R + s];
+        int taken = 0;
+        /* ascending scan over u gives ascending source ids */
+        for (int64_t u = 0; u < N && taken < cap; ++u) {
+            int links = 0;
+            for (int s = 0; s < R; ++s)
+                if (nbr[u * (int64_t)R + s] == v)
+                    links = 1;
+            if (!links)
+                continue;
+            int dup = 0;
+            for (int t = 0; t < n; ++t)
+                if (row[t] == u)
+                    dup = 1;
+            if (dup)
+                continue;
+            row[n++] = u;
+            ++taken;
+        }
+        for (int t = n; t < W; ++t)
+            row[t] = -1;
+    }
+}
+
+/* Eq. 7: Q_G = mean over u of |N(u) & M(u)| / R, M(u) = the R nearest of u */
+double or_graph_quality(const int64_t *nbr, int64_t N, int R, const int64_t *knn, int K)
+{
+    double acc = 0.0;
+    int r = R < K ? R : K;
+    for (int64_t u = 0; u < N; ++u) {
+        int hit = 0;
+        for (int s = 0; s < R; ++s) {
+            int64_t v = nbr[u * (int64_t)R + s];
+            if (v < 0)
+                continue;
+            for (int t = 0; t < r; ++t)
+                if (knn[u * (int64_t)K + t] == v) {
+                    ++hit;
+                    break;
+                }
+        }
+        acc += (double)hit / (double)R;
+    }
+    return N > 0 ? acc / (double)N : 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Alg. 2 (joint pruning), ef-bounded, with the two-stage routing of   */
+/* Sec. 4.2 / Sec. 5.2.                                                */
+/*                                                                     */
+/* pool  : at most ef records sorted by (Gamma, id), each with an      */
+/*         "expanded" flag; it is R of Alg. 2 and its unexpanded part  */
+/*         is C.                                                       */
+/* seeds : B = the first min(ef, 32) distinct ids among the splitmix64 */
+/*         stream s0 = seed ^ mix64(q), id_j = out_j mod N, j < 64.    */
+/* step  : take the smallest unexpanded record u (line 3), mark it     */
+/*         expanded; evaluate each not-yet-evaluated neighbour v of u  */
+/*         in adjacency order (lines 4-5); insert v if the pool holds  */
+/*         fewer than ef records or (Gamma, v) is below the last       */
+/*         record, dropping the last one (lines 6-8).                  */
+/* stop  : no unexpanded record is left ("R is updated" read as "C is  */
+/*         not exhausted").  Output the first k records.               */
+/* S1    : while h > 1, only the ceil(R/h) valid neighbours with the    */
+/*         smallest keys mix64(s_u + (slot+1)*GAMMA), s_u = mix64(s0 ^ */
+/*         mix64(u+1)), are evaluated.  S1 ends at a local optimum: an */
+/*         expansion after which the pool holds the same records (or   */
+/*         when C is exhausted).  S2 sets C = C u R (every record       */
+/*         unexpanded) and continues with all neighbours.  Neighbours  */
+/*         skipped in S1 are not marked evaluated.                     */
+/* max_iters caps the number of expansions; hitting it ends the query  */
+/* with status OR_ITER_LIMIT and its current pool.                     */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double g;
+    int64_t id;
+    int expanded;
+} pool_t;
+
+static int pool_insert(pool_t *pool, int *n, int ef, double g, int64_t id)
+{
+    if (*n == ef && !rec_less(g, id, pool[ef - 1].g, pool[ef - 1].id))
+        return 0;
+    int pos = *n < ef ? *n : ef - 1;
+    while (pos > 0 && rec_less(g, id, pool[pos - 1].g, pool[pos - 1].id)) {
+        pool[pos] = pool[pos - 1];
+        --pos;
+    }
+    pool[pos].g = g;
+    pool[pos].id = id;
+    pool[pos].expanded = 0;
+    if (*n < ef)
+        ++*n;
+    return 1;
+}
+
+void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
+               const int64_t *nbr, int R, const float *Qv, const uint8_t *QA, int64_t nq,
+               int k, int ef, int h, uint64_t seed, int64_t max_iters,
+               int mode, double wv, double wl, int prec,
+               int64_t *out_ids, double *out_g, int32_t *out_chi,
+               int64_t *out_ndc, int64_t *out_exp, int32_t *out_status)
+{
+    pool_t *pool = (pool_t *)malloc(sizeof(pool_t) * (size_t)ef);
+    int64_t *before = (int64_t *)malloc(sizeof(int64_t) * (size_t)ef);
+    uint8_t *evaluated = (uint8_t *)malloc((size_t)(N > 0 ? N : 1));
+    int *sel = (int *)malloc(sizeof(int) * (size_t)(R > 0 ? R : 1));
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(R > 0 ? R : 1));
+    int *rank_buf = (int *)malloc(sizeof(int) * (size_t)(R > 0 ? R : 1));
+    int s1_take = h > 1 ? (R + h - 1) / h : R;
+
+    for (int64_t q = 0; q < nq; ++q) {
+        const float *qv = Qv + q * (int64_t)d;
+        const uint8_t *qa = QA + q * (int64_t)m;
+        memset(evaluated, 0, (size_t)N);
+        int n = 0;
+        int64_t ndc = 0, iters = 0;
+        int32_t status = OR_OK;
+        uint64_t s0 = seed ^ or_mix64((uint64_t)q);
+
+        /* seed set B */
+        int want = ef < 32 ? ef : 32, got = 0;
+        for (uint64_t j = 0; j < 64 && got < want && N > 0; ++j) {
+            int64_t v = (int64_t)(or_splitmix64_at(s0, j) % (uint64_t)N);
+            if (evaluated[v])
+                continue;
+            evaluated[v] = 1;
+            ++ndc;
+            ++got;
+            double g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m, mode,
+                                  wv, wl, prec, NULL);
+            pool_insert(pool, &n, ef, g, v);
+        }
+
+        int stage = h > 1 ? 1 : 2;
+        for (;;) {
+            int i = 0;
+            while (i < n && pool[i].expanded)
+                ++i;
+            if (i == n) {
+                if (stage == 1) {
+                    stage = 2;
+                    for (int t = 0; t < n; ++t)
+                        pool[t].expanded = 0;
+                    continue;
+                }
+                break;
+            }
+            if (iters >= max_iters) {
+                status = OR_ITER_LIMIT;
+                break;
+            }
+            ++iters;
+            pool[i].expanded = 1;
+            int64_t u = pool[i].id;
+            const int64_t *nu = nbr + u * (int64_t)R;
+
+            /* neighbour slots to evaluate, in adjacency order */
+            int ns = 0;
+            for (int s = 0; s < R; ++s)
+                if (nu[s] >= 0)
+                    sel[ns++] = s;
+            if (stage == 1 && ns > s1_take) {
+                uint64_t su = or_mix64(s0 ^ or_mix64((uint64_t)u + 1));
+                for (int t = 0; t < ns; ++t)
+                    key[t] = or_splitmix64_at(su, (uint64_t)sel[t]);
+                /* keep the s1_take slots of smallest (key, slot), in slot order */
+                for (int t = 0; t < ns; ++t) {
+                    int rank = 0;
+                    for (int o = 0; o < ns; ++o)
+                        if (key[o] < key[t] || (key[o] == key[t] && sel[o] < sel[t]))
+                            ++rank;
+                    rank_buf[t] = rank;
+                }
+                int w = 0;
+                for (int t = 0; t < ns; ++t)
+                    if (rank_buf[t] < s1_take)
+                        sel[w++] = sel[t];
+                ns = w;
+            }
+
+            for (int t = 0; t < n; ++t)
+                before[t] = pool[t].id;
+            int n_before = n;
+            for (int t = 0; t < ns; ++t) {
+                int64_t v = nu[sel[t]];
+                if (evaluated[v])
+                    continue;
+                evaluated[v] = 1;
+                ++ndc;
+                double g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m,
+                                      mode, wv, wl, prec, NULL);
+                pool_insert(pool, &n, ef, g, v);
+            }
+            if (stage == 1) {
+                int same = (n == n_before);
+                for (int t = 0; t < n && same; ++t)
+                    if (before[t] != pool[t].id)
+                        same = 0;
+                if (same) {
+                    stage = 2;
+                    for (int t = 0; t < n; ++t)
+                        pool[t].expanded = 0;
+                }
+            }
+        }
+
+        for (int j = 0; j < k; ++j) {
+            int64_t o = q * (int64_t)k + j;
+            if (j < n) {
+                int64_t v = pool[j].id;
+                out_ids[o] = v;
+                out_g[o] = pool[j].g;
+                out_chi[o] = or_chi(qa, A + v * (int64_t)m, m);
+            } else {
+                out_ids[o] = -1;
+                out_g[o] = INFINITY;
+                out_chi[o] = -1;
+            }
+        }
+        out_ndc[q] = ndc;
+        out_exp[q] = iters;
+        out_status[q] = status;
+    }
+    free(pool);
+    free(before);
+    free(evaluated);
+    free(sel);
+    free(key);
+    free(rank_buf);
+}

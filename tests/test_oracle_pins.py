@@ -1,0 +1,360 @@
+"""Pins for the CPU oracle: each test checks the oracle against something the
+paper or mathematics fixes (closed forms, published generator outputs,
+hand-derived geometry, textbook routines, invariants), never against itself."""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ------------------------------------------------------------------ generator
+def test_splitmix64_published_outputs(oracle_mod):
+    want = [int(r[0]) for r in _golden_rows("splitmix64_seed1234567.txt")]
+    assert oracle_mod.splitmix64_stream(1234567, 5) == want
+
+
+def test_mix64_zero_and_bijective_sample(oracle_mod):
+    assert oracle_mod.mix64(0) == 0  # every step of the finaliser maps 0 to 0
+    outs = {oracle_mod.mix64(i) for i in range(2000)}
+    assert len(outs) == 2000  # a bijection has no collisions
+
+
+# ------------------------------------------------------------------ Eq. 1
+def test_delta_closed_forms(oracle_mod):
+    O = oracle_mod
+    for prec in (O.F64, O.F32):
+        assert O.delta([0, 0], [3, 4], prec) == 5.0
+        assert O.delta([1, 2, 3], [1, 2, 3], prec) == 0.0
+        e = np.zeros(17, np.float32)
+        e[9] = -2.5
+        assert O.delta(np.zeros(17), e, prec) == 2.5
+    # f64 against an independent textbook routine
+    r = np.random.default_rng(0)
+    for d in (1, 7, 128, 960):
+        x, y = r.standard_normal(d).astype(np.float32), r.standard_normal(d).astype(np.float32)
+        ref = float(np.linalg.norm(x.astype(np.float64) - y.astype(np.float64)))
+        assert O.delta(x, y, O.F64) == pytest.approx(ref, rel=1e-14)
+        assert O.delta(x, y, O.F32) == pytest.approx(ref, rel=1e-5)
+
+
+def test_delta32_exact_on_integer_vectors(oracle_mod):
+    # integer components 0..255 and d <= 256: the squared distance is an integer
+    # below 2^24, so f32 is exact and sqrtf is the correctly rounded sqrt
+    r = np.random.default_rng(1)
+    for _ in range(50):
+        x = r.integers(0, 256, 128).astype(np.float32)
+        y = r.integers(0, 256, 128).astype(np.float32)
+        s = int(((x.astype(np.int64) - y.astype(np.int64)) ** 2).sum())
+        assert oracle_mod.delta(x, y, oracle_mod.F32) == float(np.sqrt(np.float32(s)))
+
+
+# ------------------------------------------------------------------ Eq. 4-5
+def test_chi_hand_cases(oracle_mod):
+    O = oracle_mod
+    assert O.chi([1, 2, 3], [1, 2, 3]) == 0
+    assert O.chi([1, 2, 3], [0, 2, 3]) == 1
+    assert O.chi([1, 2, 3], [1, 0, 0]) == 2
+    assert O.chi([1, 2, 3], [3, 1, 2]) == 3
+    assert O.chi([255, 0, 7, 9], [255, 1, 7, 8]) == 2
+    assert O.chi([4], [4]) == 0
+
+
+def test_chi_is_a_metric(oracle_mod):
+    r = np.random.default_rng(2)
+    for _ in range(300):
+        a, b, c = (r.integers(0, 3, 4).astype(np.uint8) for _ in range(3))
+        ab, bc, ac = oracle_mod.chi(a, b), oracle_mod.chi(b, c), oracle_mod.chi(a, c)
+        assert ab == oracle_mod.chi(b, a)
+        assert 0 <= ab <= 4
+        assert ac <= ab + bc
+
+
+# ------------------------------------------------------------------ Eq. 6 / Sec. 3.2
+def test_gamma_recommended_weights_bounds(oracle_mod):
+    O = oracle_mod
+    for m in (1, 2, 3, 4):
+        for dl in (0.0, 0.5, 1.0, 3.7, 1234.5):
+            g = [O.gamma(dl, c, m) for c in range(m + 1)]
+            assert g[0] == dl  # chi = 0: no change
+            assert g[m] == pytest.approx(2 * dl, rel=1e-15, abs=0)  # chi = m: doubled
+            assert all(dl <= x <= 2 * dl * (1 + 1e-15) for x in g)
+            assert all(g[i] <= g[i + 1] for i in range(m))
+
+
+def test_gamma_constant_weights_literals(oracle_mod):
+    O = oracle_mod
+    assert O.gamma(2.5, 2, 3, weights=(2.0, 10.0)) == 25.0
+    assert O.gamma(2.5, 2, 3, weights=(2.0, 10.0), prec=O.F32) == 25.0
+    assert O.gamma(7.25, 3, 3, weights=(1.0, 0.0)) == 7.25  # w_l = 0: plain delta
+    assert O.gamma(7.25, 3, 3, weights=(0.0, 1.0)) == 3.0  # w_v = 0: attributes only
+
+
+# ------------------------------------------------------------------ Def. 2 / Sec. 6.1
+def test_fused_topk_plain_l2_matches_torch_cdist(oracle_mod):
+    O = oracle_mod
+    w = synth.c1(N=700, nq=25, d=32, seed=5)
+    ids, g, _ = O.fused_topk(w.X, w.A, w.Qv, w.QA, 10, weights=(1.0, 0.0))
+    D = torch.cdist(torch.from_numpy(w.Qv).double(), torch.from_numpy(w.X).double())
+    ref = torch.topk(D, 10, largest=False)
+    assert np.allclose(g, ref.values.numpy(), rtol=1e-12)
+    assert (ids == ref.indices.numpy()).mean() > 0.999  # exact ties are possible only in theory
+
+
+def test_fused_topk_attribute_dominant_equals_filtered(oracle_mod):
+    O = oracle_mod
+    w = synth.int_valued(1500, 40, 16, cards=(2, 3), seed=11)
+    f_ids, f_dl, P = O.filtered_topk(w.X, w.A, w.Qv, w.QA, 10)
+    # w_l larger than any delta (<= 255 * sqrt(16)) puts every match first
+    ids, g, ch = O.fused_topk(w.X, w.A, w.Qv, w.QA, 10, weights=(1.0, 10000.0))
+    for q in range(w.nq):
+        n = min(10, P[q])
+        assert (ids[q, :n] == f_ids[q, :n]).all()
+        assert (ch[q, :n] == 0).all()
+        assert np.allclose(g[q, :n], f_dl[q, :n], rtol=1e-15)
+
+
+def test_filtered_topk_counts_and_order(oracle_mod):
+    O = oracle_mod
+    w = synth.c1(N=900, nq=20, d=8, cards=(2, 2), seed=3)
+    ids, dl, P = O.filtered_topk(w.X, w.A, w.Qv, w.QA, 5)
+    for q in range(w.nq):
+        match = np.nonzero((w.A == w.QA[q]).all(axis=1))[0]
+        assert P[q] == len(match)
+        dd = np.linalg.norm(w.X[match].astype(np.float64) - w.Qv[q], axis=1)
+        order = match[np.lexsort((match, dd))][:5]
+        assert (ids[q, : len(order)] == order).all()
+
+
+def test_fused_topk_hand_enumeration(oracle_mod):
+    O = oracle_mod
+    # 1-D points at 0..5, query at 2.2 with attribute 1; objects 1 and 4 mismatch
+    X = np.arange(6, dtype=np.float32)[:, None]
+    A = np.array([[1], [0], [1], [1], [0], [1]], np.uint8)
+    ids, g, ch = O.fused_topk(X, A, np.array([[2.2]], np.float32), np.array([[1]], np.uint8), 6)
+    # proportional weights, m = 1: Gamma = delta * (1 + chi)
+    want = sorted(((abs(i - 2.2) * (1 + int(A[i, 0] != 1)), i) for i in range(6)))
+    assert list(ids[0]) == [i for _, i in want]
+    assert list(ch[0]) == [int(A[i, 0] != 1) for _, i in want]
+    assert list(ids[0]) == [2, 3, 0, 1, 5, 4]  # Gamma: .2 .8 2.2 2.4 2.8 3.6
+
+
+# ------------------------------------------------------------------ Sec. 4.1 candidates
+def test_knn_excludes_self_and_matches_cdist(oracle_mod):
+    O = oracle_mod
+    w = synth.c1(N=400, nq=1, d=24, seed=8)
+    ids, g = O.knn(w.X, w.A, 12, weights=(1.0, 0.0))
+    D = torch.cdist(torch.from_numpy(w.X).double(), torch.from_numpy(w.X).double())
+    D.fill_diagonal_(float("inf"))
+    ref = torch.topk(D, 12, largest=False)
+    assert not (ids == np.arange(400)[:, None]).any()
+    assert np.allclose(g, ref.values.numpy(), rtol=1e-12)
+    assert (ids == ref.indices.numpy()).mean() > 0.999
+
+
+def test_graph_quality_of_exact_knn_is_one(oracle_mod):
+    O = oracle_mod
+    w = synth.c1(N=300, nq=1, d=16, seed=9)
+    ids, _ = O.knn(w.X, w.A, 20)
+    assert O.graph_quality(ids[:, :8], ids) == 1.0  # Eq. 7 with N(u) = M(u)
+    r = np.random.default_rng(0)
+    rnd = r.integers(0, 300, (300, 8))
+    assert O.graph_quality(rnd, ids) < 0.2
+
+
+# ------------------------------------------------------------------ Sec. 4.1 edge selection
+def _lz_points():
+    rows = _golden_rows("landing_zone_2d.txt")
+    return np.array([[float(r[1]), float(r[2])] for r in rows], np.float32)
+
+
+def _half_plane_landing(p, u, j):
+    """p in L(u, j) by the geometry of Def. 6: the side of the perpendicular
+    bisector of u-j that holds u, minus the closed ball around u of radius |u-j|."""
+    mid = (u + j) / 2.0
+    side = float(np.dot(p - mid, u - j)) > 0.0
+    outside = float(np.linalg.norm(p - u)) > float(np.linalg.norm(j - u))
+    return side and outside
+
+
+def test_landing_zone_2d_hand_case(oracle_mod):
+    O = oracle_mod
+    X = _lz_points()
+    A = np.zeros((len(X), 1), np.uint8)
+    for cands, R, want in (([1, 2, 3, 4, 5, 6], 8, [1, 2, 3, 5]),
+                           ([1, 2, 3, 4, 5, 6], 3, [1, 2, 3]),
+                           ([1, 2, 3, 4, 5, 6, 7], 8, [1, 2, 3, 5])):
+        cand = -np.ones((len(X), len(cands)), np.int64)
+        cand[0] = cands
+        nbr, deg = O.edge_select(X, A, cand, R, weights=(1.0, 0.0))
+        got = [int(v) for v in nbr[0] if v >= 0]
+        assert got == want
+        assert deg[0] == len(want)
+
+
+def test_landing_zone_matches_geometry_on_random_2d(oracle_mod):
+    O = oracle_mod
+    r = np.random.default_rng(4)
+    for trial in range(30):
+        X = r.standard_normal((40, 2)).astype(np.float32)
+        A = np.zeros((40, 1), np.uint8)
+        cand = -np.ones((40, 39), np.int64)
+        cand[0] = np.arange(1, 40)
+        nbr, _ = O.edge_select(X, A, cand, 10, weights=(1.0, 0.0))
+        # rebuild N(0) with the half-plane geometry and the paper's steps
+        Xd = X.astype(np.float64)
+        order = sorted(range(1, 40), key=lambda i: (float(np.linalg.norm(Xd[i] - Xd[0])), i))
+        sel = [order[0]]
+        for p in order[1:]:
+            if len(sel) == 10:
+                break
+            if all(_half_plane_landing(Xd[p], Xd[0], Xd[j]) for j in sel):
+                sel.append(p)
+        assert [int(v) for v in nbr[0] if v >= 0] == sel
+
+
+def test_edge_select_invariants(oracle_mod):
+    O = oracle_mod
+    w = synth.int_valued(600, 1, 16, seed=12)
+    cand, g = O.knn(w.X, w.A, 24, prec=O.F32)
+    nbr, deg = O.edge_select(w.X, w.A, cand, 8, prec=O.F32)
+    for u in range(0, 600, 7):
+        row = [int(v) for v in nbr[u] if v >= 0]
+        assert len(row) == deg[u] <= 8
+        assert row[0] == cand[u, 0]  # step (2): the nearest candidate always joins
+        assert len(set(row)) == len(row) and u not in row
+        # every later neighbour p is closer to u than to any earlier neighbour j
+        for a in range(len(row)):
+            for b in range(a):
+                p, j = row[a], row[b]
+                gpu_ = O.gamma(O.delta(w.X[p], w.X[u], O.F32), O.chi(w.A[p], w.A[u]), w.m, prec=O.F32)
+                gpj = O.gamma(O.delta(w.X[p], w.X[j], O.F32), O.chi(w.A[p], w.A[j]), w.m, prec=O.F32)
+                assert gpu_ < gpj
+
+
+def test_reverse_candidates_hand_case(oracle_mod):
+    nbr = np.array([[1, 2, -1], [2, -1, -1], [0, 1, -1], [1, 0, 2]])
+    out = oracle_mod.reverse_candidates(nbr, cap=2)
+    assert out.tolist() == [[1, 2, 3, -1, -1], [2, 0, 3, -1, -1], [0, 1, 3, -1, -1],
+                            [1, 0, 2, -1, -1]]
+
+
+# ------------------------------------------------------------------ Alg. 2
+def _complete_graph(n):
+    return np.array([[j for j in range(n) if j != i] for i in range(n)], np.int64)
+
+
+def test_search_complete_graph_is_exact(oracle_mod):
+    O = oracle_mod
+    w = synth.c1(N=30, nq=12, d=8, cards=(2, 3), seed=13)
+    G = _complete_graph(30)
+    ref, rg, _ = O.fused_topk(w.X, w.A, w.Qv, w.QA, 5, prec=O.F32)
+    for h in (1, 2, 29):
+        for ef in (5, 8, 30):
+            r = O.search(w.X, w.A, G, w.Qv, w.QA, 5, ef, h=h, seed=3)
+            assert (r["ids"] == ref).all(), (h, ef)
+            assert np.array_equal(r["gamma"], rg)
+            assert (r["status"] == 0).all()
+
+
+def _reachable(nbr, seeds):
+    seen, stack = set(seeds), list(seeds)
+    while stack:
+        u = stack.pop()
+        for v in nbr[u]:
+            if v >= 0 and v not in seen:
+                seen.add(int(v))
+                stack.append(int(v))
+    return seen
+
+
+def _seed_ids(O, seed, q, N, want=32):
+    """Seed set B of the stated reading: first distinct ids of the splitmix64
+    stream started at seed ^ mix64(q), reduced mod N, at most 64 draws."""
+    seeds = []
+    for x in O.splitmix64_stream(seed ^ O.mix64(q), 64):
+        v = x % N
+        if v not in seeds:
+            seeds.append(v)
+        if len(seeds) == want:
+            break
+    return seeds
+
+
+def test_search_ef_ge_N_equals_brute_force_on_reachable_set(oracle_mod):
+    O = oracle_mod
+    w = synth.int_valued(250, 15, 16, seed=14)
+    nbr, _, _ = O.build_graph(w.X, w.A, R=6, K=12)
+    N, k = 250, 7
+    r = O.search(w.X, w.A, nbr, w.Qv, w.QA, k, N, h=1, seed=99)
+    for q in range(w.nq):
+        reach = np.array(sorted(_reachable(nbr, _seed_ids(O, 99, q, N))))
+        ids, _, _ = O.fused_topk(w.X[reach], w.A[reach], w.Qv[q:q + 1], w.QA[q:q + 1], k,
+                                 prec=O.F32)
+        assert list(r["ids"][q]) == list(reach[ids[0]])
+
+
+def test_search_greedy_path_graph(oracle_mod):
+    O = oracle_mod
+    # 1-D chain 0-1-...-9 with x_i = i; ef = 1 greedy walk must end at the vertex
+    # nearest the query, whatever the seed
+    X = np.arange(10, dtype=np.float32)[:, None]
+    A = np.zeros((10, 1), np.uint8)
+    nbr = np.array([[i - 1 if i > 0 else -1, i + 1 if i < 9 else -1] for i in range(10)])
+    for qx in (0.1, 3.4, 8.9):
+        r = O.search(X, A, nbr, np.array([[qx]], np.float32), np.zeros((1, 1), np.uint8), 1, 1,
+                     seed=7)
+        assert r["ids"][0, 0] == int(round(qx))
+
+
+def test_search_iteration_cap_reports_status(oracle_mod):
+    O = oracle_mod
+    w = synth.c1(N=200, nq=3, d=8, seed=15)
+    nbr, _, _ = O.build_graph(w.X, w.A, R=8, K=16)
+    r = O.search(w.X, w.A, nbr, w.Qv, w.QA, 4, 16, max_iters=0)
+    assert (r["status"] == O.ITER_LIMIT).all() and (r["expansions"] == 0).all()
+    assert (r["ndc"] == 16).all()  # only the seeds were evaluated
+    r = O.search(w.X, w.A, nbr, w.Qv, w.QA, 4, 16, max_iters=1 << 20)
+    assert (r["status"] == 0).all()
+
+
+def test_search_recall_grows_with_ef(oracle_mod):
+    O = oracle_mod
+    w = synth.int_valued(2000, 60, 32, seed=16)
+    nbr, _, _ = O.build_graph(w.X, w.A, R=16, K=32, weights=(1.0, 10000.0))
+    ref, _, _ = O.fused_topk(w.X, w.A, w.Qv, w.QA, 10, weights=(1.0, 10000.0), prec=O.F32)
+    rec = [O.recall(O.search(w.X, w.A, nbr, w.Qv, w.QA, 10, ef, weights=(1.0, 10000.0))["ids"],
+                    ref) for ef in (10, 40, 160)]
+    assert rec[0] <= rec[1] + 0.02 and rec[1] <= rec[2] + 0.02
+    assert rec[2] > 0.9
+
+
+# ------------------------------------------------------------------ Eq. 3
+def test_recall_definitions(oracle_mod):
+    O = oracle_mod
+    assert O.recall([[1, 2, 3]], [[3, 2, 9]]) == pytest.approx(2 / 3)
+    A = np.array([[0], [1], [0], [0]], np.uint8)
+    QA = np.array([[0], [0]], np.uint8)
+    found = np.array([[0, 1], [2, 3]])
+    truth = np.array([[0, 2], [2, -1]])
+    r, excl = O.hybrid_recall(found, A, QA, truth, np.array([3, 1]))
+    # q0: matching returned {0}; hits {0} of min(2,3)=2 -> 0.5; q1: {2,3} & {2} -> 1/1
+    assert r == pytest.approx(0.75) and excl == 0
+    r, excl = O.hybrid_recall(found, A, QA, truth, np.array([0, 1]))
+    assert excl == 1 and r == 1.0
+    assert math.isfinite(r)
