@@ -1,0 +1,223 @@
+/*
+ * nhq.h -- C ABI of the GB300 (sm_103a) native hybrid-query library.
+ *
+ * The library answers hybrid queries (Def. 4 of arXiv 2203.13601): top-k objects
+ * that are near a query vector AND share its structured attributes, by searching
+ * a composite proximity-graph index under the fusion distance (Eq. 6).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Plain pointers and sizes only.  A pointer argument may be device memory
+ *   (including memory allocated by another runtime such as PyTorch's caching
+ *   allocator) or host memory, except where a call says "device".  The library
+ *   detects which with cudaPointerGetAttributes.  Calls that receive host input
+ *   or output pointers copy through library-owned device staging and return
+ *   only after host outputs are written (the call synchronises `stream`).
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  With device
+ *   pointers every call only enqueues work and returns; outputs are valid once
+ *   the stream has been synchronised.
+ * - Ownership: the caller owns every array it passes.  An nhq_index owns its
+ *   device copies (vectors, packed attributes, graph) and its scratch buffers;
+ *   it is released by nhq_free.  Indices are not thread-safe: one host thread
+ *   per index at a time.
+ * - Errors: every call returns nhq_status; nothing aborts or throws across the
+ *   ABI.  nhq_last_error() returns a message for the last failing call on the
+ *   calling thread.  Invalid sizes or values return NHQ_ERR_ARG before any
+ *   work is enqueued; a failing CUDA call returns NHQ_ERR_CUDA; a failed
+ *   device allocation returns NHQ_ERR_OOM.
+ * - Notation (paper): N objects, d vector dimension, m attributes (1..4, each an
+ *   ordinal code 0..255, Sec. 3.2 "ordinal encoding"), R graph out-degree
+ *   (the paper's k in Sec. 4), k results, ef search-pool size.
+ * - Result order: ascending by (Gamma, id).  `dists` hold Gamma (Eq. 6), not
+ *   delta.  Missing results (fewer than k reachable) have id 0xFFFFFFFF,
+ *   Gamma +inf and chi 255.
+ */
+#ifndef NHQ_H
+#define NHQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum nhq_status {
+    NHQ_OK = 0,
+    NHQ_ERR_ARG = 1,
+    NHQ_ERR_OOM = 2,
+    NHQ_ERR_CUDA = 3,
+    NHQ_ERR_ITER_LIMIT = 4, /* per-query status only: expansion cap reached */
+    NHQ_ERR_IO = 5
+} nhq_status;
+
+/* Weights of the fusion distance Gamma = w_v * delta + w_l * chi (Eq. 6). */
+typedef enum nhq_weight_mode {
+    NHQ_W_PROPORTIONAL = 0, /* w_v = 1, w_l = delta / m: the recommended setting of Sec. 3.2 */
+    NHQ_W_CONSTANT = 1,     /* w_v, w_l as given (Sec. 6.5, curve v)                         */
+    NHQ_W_FILTER = 2        /* brute force only: Gamma = delta if chi = 0, else excluded; the
+                               hybrid ground truth of Sec. 6.1                               */
+} nhq_weight_mode;
+
+typedef struct nhq_weights {
+    int32_t mode; /* nhq_weight_mode */
+    float w_v;
+    float w_l;
+} nhq_weights;
+
+/* Element type of the vector copy used to score candidates during search. */
+typedef enum nhq_vec_dtype { NHQ_VEC_F32 = 0, NHQ_VEC_BF16 = 1 } nhq_vec_dtype;
+
+typedef struct nhq_build_params {
+    int32_t K;           /* candidate-set size l of Sec. 4.1 (exact K nearest by Gamma); 0 -> 64 */
+    int32_t reverse;     /* 1: second selection pass over N(v) plus reverse sources (default)   */
+    int32_t reverse_cap; /* at most this many reverse sources per vertex; 0 -> 64               */
+    int32_t reserved;
+} nhq_build_params;
+
+typedef struct nhq_search_params {
+    uint64_t seed;           /* seeds B and S1 neighbour subsets derive from splitmix64(seed) */
+    int32_t h;               /* two-stage routing: S1 visits ceil(R/h) neighbours; 1 = off     */
+    int32_t max_iters;       /* expansion cap per query; 0 -> 1<<20                             */
+    int32_t warps_per_block; /* 0 -> auto                                                      */
+    int32_t hash_bits;       /* visited-filter size 2^hash_bits per query; 0 -> auto          */
+    int32_t vec_dtype;       /* nhq_vec_dtype used for candidate scoring                       */
+    int32_t rerank;          /* with BF16 scoring: recompute Gamma of the final pool in f32    */
+} nhq_search_params;
+
+typedef struct nhq_index nhq_index;
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *nhq_last_error(void);
+
+/* ABI version of this header (1). */
+int32_t nhq_version(void);
+
+/*
+ * Object set S of Def. 1: copies vectors[N][d] (f32, row-major) into index-owned
+ * HBM (rows padded to a multiple of 4 floats) and packs attributes[N][m] (u8
+ * ordinal codes, Sec. 3.2) into one u32 per object.  `w` fixes the fusion
+ * distance (Eq. 6) used by build and search.  The graph is empty until
+ * nhq_index_build / nhq_index_set_graph.  Errors: N < 1, d < 1, m outside 1..4,
+ * a non-finite vector component, or w_v/w_l negative or non-finite -> NHQ_ERR_ARG.
+ */
+nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
+                            int32_t m, nhq_weights w, void *stream, nhq_index **out);
+
+/* Releases the index and all its device memory.  NULL is a no-op. */
+void nhq_free(nhq_index *index);
+
+/* Shape of an index (any output pointer may be NULL).  R = 0 before a graph exists. */
+nhq_status nhq_index_info(const nhq_index *index, int64_t *N, int32_t *d, int32_t *m, int32_t *R);
+
+/*
+ * Ordinal attribute packing (Sec. 3.2): packed[i] = sum_j attributes[i][j] << 8j for
+ * n rows of m (1..4) u8 codes.  Device pointers only.
+ */
+nhq_status nhq_pack_attributes(const uint8_t *attributes, int64_t n, int32_t m, uint32_t *packed,
+                               void *stream);
+
+/*
+ * Candidate sets C(u) of Sec. 4.1 (the paper refines random candidates by
+ * NN-descent; this computes their limit, the exact K nearest): for every object
+ * u, the K objects v != u with smallest (Gamma(u, v), v).  cand_ids[N][K] u32,
+ * cand_dist[N][K] f32 (may be NULL).  Errors: K outside 1..256 or K >= N.
+ */
+nhq_status nhq_knn(const nhq_index *index, int32_t K, uint32_t *cand_ids, float *cand_dist,
+                   void *stream);
+
+/*
+ * Landing-zone edge selection (Sec. 4.1, Def. 6) for every vertex u over the
+ * candidate list cand_ids[N][L] (0xFFFFFFFF, u itself and repeats are skipped):
+ * candidates are sorted by (Gamma(p, u), p); the nearest joins N(u); each next p
+ * joins iff for every j already in N(u): Gamma(p, u) < Gamma(p, j) and
+ * Gamma(p, u) > Gamma(u, j); stop at R.  Writes nbr_out[N][R], unused slots
+ * 0xFFFFFFFF.  Errors: L outside 1..128, R outside 1..64.
+ */
+nhq_status nhq_edge_select(const nhq_index *index, const uint32_t *cand_ids, int32_t L, int32_t R,
+                           uint32_t *nbr_out, void *stream);
+
+/*
+ * Reverse-edge candidates for a second selection pass (the paper states no
+ * reverse-edge step; this is the library's reading): out[v] (width R + cap) =
+ * N(v) in slot order, then the `cap` smallest ids u with v in N(u) and u not in
+ * N(v), ascending; 0xFFFFFFFF pads.  nbr[N][R] as written by nhq_edge_select.
+ * Errors: R outside 1..64, cap outside 0..64.
+ */
+nhq_status nhq_reverse_candidates(const nhq_index *index, const uint32_t *nbr, int32_t R,
+                                  int32_t cap, uint32_t *out, void *stream);
+
+/* Installs a graph nbr[N][R] (copied) as the index's composite-index adjacency. */
+nhq_status nhq_index_set_graph(nhq_index *index, const uint32_t *nbr, int32_t R, void *stream);
+
+/* Copies the index's adjacency into nbr[N][R]. */
+nhq_status nhq_index_get_graph(const nhq_index *index, uint32_t *nbr, void *stream);
+
+/*
+ * Composite-index build (Sec. 5.1 with the NPG_kgraph recipe of Sec. 4.3):
+ * exact candidate sets (nhq_knn, K), landing-zone selection to degree R, then
+ * (params->reverse) a second selection over nhq_reverse_candidates.  params may
+ * be NULL for the defaults.  Errors: as nhq_knn / nhq_edge_select.
+ */
+nhq_status nhq_index_build(nhq_index *index, int32_t degree, const nhq_build_params *params,
+                           void *stream);
+
+/* build(vectors, attributes, degree, weights): nhq_index_create + nhq_index_build. */
+nhq_status nhq_build(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
+                     int32_t m, int32_t degree, nhq_weights w, const nhq_build_params *params,
+                     void *stream, nhq_index **out);
+
+/*
+ * Exact top-k by (Gamma, id) over all N objects (Def. 2 with Gamma in place of
+ * delta).  queries[Q][d] f32, query_attributes[Q][m] u8.  `w` overrides the
+ * index weights when not NULL (NHQ_W_FILTER gives the hybrid ground truth of
+ * Sec. 6.1).  ids[Q][k] u32, dists[Q][k] f32, chi[Q][k] u8 (may be NULL).
+ * Errors: k outside 1..256.
+ */
+nhq_status nhq_brute_force(const nhq_index *index, const float *queries,
+                           const uint8_t *query_attributes, int64_t Q, int32_t k,
+                           const nhq_weights *w, uint32_t *ids, float *dists, uint8_t *chi,
+                           void *stream);
+
+/*
+ * search(queries, query_attributes, k, ef): joint pruning (Alg. 2) on the
+ * composite index, ef-bounded, with the two-stage routing of Sec. 4.2 / 5.2
+ * when params->h > 1.  Per query: a pool of ef records sorted by (Gamma, id);
+ * repeatedly expand the nearest unexpanded record and evaluate its neighbours
+ * not evaluated before; stop when every record is expanded; return the first k.
+ * Seeds: the first min(ef, 32) distinct ids of the splitmix64 stream started at
+ * seed ^ mix64(q) (q = row index within this call), reduced mod N, at most 64 draws.
+ * Outputs: ids/dists/chi [Q][k]; status[Q] (NHQ_OK or NHQ_ERR_ITER_LIMIT) and
+ * ndc[Q] (vector-distance evaluations) may be NULL.  Errors: no graph, k < 1,
+ * ef < k, ef > 1024, Q < 0.  Q = 0 is a no-op.
+ */
+nhq_status nhq_search(const nhq_index *index, const float *queries,
+                      const uint8_t *query_attributes, int64_t Q, int32_t k, int32_t ef,
+                      const nhq_search_params *params, uint32_t *ids, float *dists, uint8_t *chi,
+                      int32_t *status, int32_t *ndc, void *stream);
+
+/*
+ * Heterogeneous batch in one launch: query q uses k_arr[q] and ef_arr[q]
+ * (device or host int32 arrays); outputs are [Q][k_max] with row q holding
+ * k_arr[q] results followed by padding.  Same semantics as nhq_search per
+ * query.  Errors: any k_arr[q] outside 1..k_max, ef_arr[q] outside
+ * k_arr[q]..1024.
+ */
+nhq_status nhq_search_batched(const nhq_index *index, const float *queries,
+                              const uint8_t *query_attributes, int64_t Q, const int32_t *k_arr,
+                              const int32_t *ef_arr, int32_t k_max,
+                              const nhq_search_params *params, uint32_t *ids, float *dists,
+                              uint8_t *chi, int32_t *status, int32_t *ndc, void *stream);
+
+/*
+ * Index persistence: header {magic "NHQIDX01", version, N, d, m, R, weights}
+ * then vectors (f32, unpadded rows), packed attributes (u32) and the graph (u32).
+ * Errors: unreadable/unwritable file or bad header -> NHQ_ERR_IO.
+ */
+nhq_status nhq_save(const nhq_index *index, const char *path);
+nhq_status nhq_load(const char *path, void *stream, nhq_index **out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NHQ_H */

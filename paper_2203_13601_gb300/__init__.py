@@ -1,0 +1,359 @@
+"""GB300-native hybrid-query search (NHQ, arXiv 2203.13601) -- Python binding.
+
+Every function below forwards to the C ABI of ``include/nhq.h`` with the same
+name; this module only checks shapes/dtypes and passes pointers.  All compute
+runs in the CUDA library ``_build/libnhq.so`` (built by ``build.py`` for
+sm_103a).  Importing this module does not need a GPU; calling a function does
+need the library, and a missing library raises ``RuntimeError``: there is no
+CPU fallback.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; host arrays are
+copied through the library's staging buffers and the call then synchronises.
+``stream`` defaults to torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "NHQError", "Index", "load_library", "library_path",
+    "W_PROPORTIONAL", "W_CONSTANT", "W_FILTER", "VEC_F32", "VEC_BF16",
+    "nhq_last_error", "nhq_version", "nhq_index_create", "nhq_free", "nhq_index_info",
+    "nhq_pack_attributes", "nhq_knn", "nhq_edge_select", "nhq_reverse_candidates",
+    "nhq_index_set_graph", "nhq_index_get_graph", "nhq_index_build", "nhq_build",
+    "nhq_brute_force", "nhq_search", "nhq_search_batched", "nhq_save", "nhq_load",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libnhq.so")
+
+W_PROPORTIONAL, W_CONSTANT, W_FILTER = 0, 1, 2
+VEC_F32, VEC_BF16 = 0, 1
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_ITER_LIMIT, ERR_IO = range(6)
+NONE_ID = 0xFFFFFFFF
+
+
+class NHQError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"nhq status {status}: {message}")
+        self.status = status
+
+
+class _Weights(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("w_v", C.c_float), ("w_l", C.c_float)]
+
+
+class _BuildParams(C.Structure):
+    _fields_ = [("K", C.c_int32), ("reverse", C.c_int32), ("reverse_cap", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class _SearchParams(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("h", C.c_int32), ("max_iters", C.c_int32),
+                ("warps_per_block", C.c_int32), ("hash_bits", C.c_int32),
+                ("vec_dtype", C.c_int32), ("rerank", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libnhq.so (build it first with ``build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: run paper_2203_13601_gb300.build.build()"
+                               " (the CUDA library is required; there is no CPU fallback)")
+        lib = C.CDLL(_LIB_PATH)
+        P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        S = C.c_int  # nhq_status
+        sig = {
+            "nhq_last_error": (C.c_char_p, []),
+            "nhq_version": (i32, []),
+            "nhq_index_create": (S, [P, i64, i32, P, i32, _Weights, P, C.POINTER(P)]),
+            "nhq_free": (None, [P]),
+            "nhq_index_info": (S, [P, P, P, P, P]),
+            "nhq_pack_attributes": (S, [P, i64, i32, P, P]),
+            "nhq_knn": (S, [P, i32, P, P, P]),
+            "nhq_edge_select": (S, [P, P, i32, i32, P, P]),
+            "nhq_reverse_candidates": (S, [P, P, i32, i32, P, P]),
+            "nhq_index_set_graph": (S, [P, P, i32, P]),
+            "nhq_index_get_graph": (S, [P, P, P]),
+            "nhq_index_build": (S, [P, i32, C.POINTER(_BuildParams), P]),
+            "nhq_build": (S, [P, i64, i32, P, i32, i32, _Weights, C.POINTER(_BuildParams), P,
+                              C.POINTER(P)]),
+            "nhq_brute_force": (S, [P, P, P, i64, i32, C.POINTER(_Weights), P, P, P, P]),
+            "nhq_search": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P, P, P, P, P,
+                               P]),
+            "nhq_search_batched": (S, [P, P, P, i64, P, P, i32, C.POINTER(_SearchParams), P, P, P,
+                                       P, P, P]),
+            "nhq_save": (S, [P, C.c_char_p]),
+            "nhq_load": (S, [C.c_char_p, P, C.POINTER(P)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+# ------------------------------------------------------------------ marshalling
+def _ptr(a, dtype, shape=None, name="array"):
+    """Data pointer of a contiguous torch tensor / numpy array with the given dtype."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(dtype):
+            raise TypeError(f"{name}: dtype {a.dtype}, expected {np.dtype(dtype)}")
+        if not a.flags.c_contiguous:
+            raise ValueError(f"{name} must be C-contiguous")
+        shp = a.shape
+        p = a.ctypes.data
+    else:  # torch tensor
+        import torch
+
+        want = {np.float32: torch.float32, np.uint8: torch.uint8, np.int32: torch.int32,
+                np.uint32: torch.uint32}[dtype]
+        if a.dtype != want:
+            raise TypeError(f"{name}: dtype {a.dtype}, expected {want}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        shp = tuple(a.shape)
+        p = a.data_ptr()
+    if shape is not None and tuple(shp) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(shp)}, expected {tuple(shape)}")
+    return p
+
+
+def _shape(a):
+    return tuple(a.shape)
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+def _weights(weights):
+    if weights is None or weights == "proportional":
+        return _Weights(W_PROPORTIONAL, 1.0, 0.0)
+    if weights == "filter":
+        return _Weights(W_FILTER, 1.0, 0.0)
+    wv, wl = weights
+    return _Weights(W_CONSTANT, float(wv), float(wl))
+
+
+def _check(status):
+    if status != OK:
+        raise NHQError(status, load_library().nhq_last_error().decode())
+
+
+# ------------------------------------------------------------------ ABI mirror
+def nhq_last_error() -> str:
+    return load_library().nhq_last_error().decode()
+
+
+def nhq_version() -> int:
+    return int(load_library().nhq_version())
+
+
+def nhq_index_create(vectors, attributes, weights=None, stream=None) -> int:
+    N, d = _shape(vectors)
+    m = _shape(attributes)[1]
+    out = C.c_void_p()
+    _check(load_library().nhq_index_create(_ptr(vectors, np.float32, (N, d), "vectors"), N, d,
+                                           _ptr(attributes, np.uint8, (N, m), "attributes"), m,
+                                           _weights(weights), _stream(stream), C.byref(out)))
+    return out.value
+
+
+def nhq_free(index) -> None:
+    if index:
+        load_library().nhq_free(index)
+
+
+def nhq_index_info(index):
+    N, d, m, R = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load_library().nhq_index_info(index, C.byref(N), C.byref(d), C.byref(m), C.byref(R)))
+    return N.value, d.value, m.value, R.value
+
+
+def nhq_pack_attributes(attributes, packed, stream=None) -> None:
+    n, m = _shape(attributes)
+    _check(load_library().nhq_pack_attributes(_ptr(attributes, np.uint8, (n, m), "attributes"),
+                                              n, m, _ptr(packed, np.uint32, (n,), "packed"),
+                                              _stream(stream)))
+
+
+def nhq_knn(index, K, cand_ids, cand_dist=None, stream=None) -> None:
+    N = nhq_index_info(index)[0]
+    _check(load_library().nhq_knn(index, K, _ptr(cand_ids, np.uint32, (N, K), "cand_ids"),
+                                  _ptr(cand_dist, np.float32, (N, K), "cand_dist"),
+                                  _stream(stream)))
+
+
+def nhq_edge_select(index, cand_ids, R, nbr_out, stream=None) -> None:
+    N = nhq_index_info(index)[0]
+    L = _shape(cand_ids)[1]
+    _check(load_library().nhq_edge_select(index, _ptr(cand_ids, np.uint32, (N, L), "cand_ids"),
+                                          L, R, _ptr(nbr_out, np.uint32, (N, R), "nbr_out"),
+                                          _stream(stream)))
+
+
+def nhq_reverse_candidates(index, nbr, cap, out, stream=None) -> None:
+    N = nhq_index_info(index)[0]
+    R = _shape(nbr)[1]
+    _check(load_library().nhq_reverse_candidates(index, _ptr(nbr, np.uint32, (N, R), "nbr"), R,
+                                                 cap, _ptr(out, np.uint32, (N, R + cap), "out"),
+                                                 _stream(stream)))
+
+
+def nhq_index_set_graph(index, nbr, stream=None) -> None:
+    N = nhq_index_info(index)[0]
+    R = _shape(nbr)[1]
+    _check(load_library().nhq_index_set_graph(index, _ptr(nbr, np.uint32, (N, R), "nbr"), R,
+                                              _stream(stream)))
+
+
+def nhq_index_get_graph(index, nbr, stream=None) -> None:
+    N, _, _, R = nhq_index_info(index)
+    _check(load_library().nhq_index_get_graph(index, _ptr(nbr, np.uint32, (N, R), "nbr"),
+                                              _stream(stream)))
+
+
+def _build_params(K, reverse, reverse_cap):
+    return _BuildParams(int(K), int(reverse), int(reverse_cap), 0)
+
+
+def nhq_index_build(index, degree, K=64, reverse=1, reverse_cap=64, stream=None) -> None:
+    p = _build_params(K, reverse, reverse_cap)
+    _check(load_library().nhq_index_build(index, degree, C.byref(p), _stream(stream)))
+
+
+def nhq_build(vectors, attributes, degree, weights=None, K=64, reverse=1, reverse_cap=64,
+              stream=None) -> int:
+    N, d = _shape(vectors)
+    m = _shape(attributes)[1]
+    p = _build_params(K, reverse, reverse_cap)
+    out = C.c_void_p()
+    _check(load_library().nhq_build(_ptr(vectors, np.float32, (N, d), "vectors"), N, d,
+                                     _ptr(attributes, np.uint8, (N, m), "attributes"), m, degree,
+                                     _weights(weights), C.byref(p), _stream(stream),
+                                     C.byref(out)))
+    return out.value
+
+
+def nhq_brute_force(index, queries, query_attributes, k, ids, dists=None, chi=None,
+                    weights="index", stream=None) -> None:
+    Q, d = _shape(queries)
+    m = _shape(query_attributes)[1]
+    w = None if weights == "index" else C.byref(_weights(weights))
+    _check(load_library().nhq_brute_force(
+        index, _ptr(queries, np.float32, (Q, d), "queries"),
+        _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, w,
+        _ptr(ids, np.uint32, (Q, k), "ids"), _ptr(dists, np.float32, (Q, k), "dists"),
+        _ptr(chi, np.uint8, (Q, k), "chi"), _stream(stream)))
+
+
+def _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank):
+    return _SearchParams(int(seed) & (2**64 - 1), int(h), int(max_iters), int(warps_per_block),
+                         int(hash_bits), int(vec_dtype), int(rerank))
+
+
+def nhq_search(index, queries, query_attributes, k, ef, ids, dists=None, chi=None, status=None,
+               ndc=None, h=1, seed=0, max_iters=0, warps_per_block=0, hash_bits=0,
+               vec_dtype=VEC_F32, rerank=0, stream=None) -> None:
+    Q, d = _shape(queries)
+    m = _shape(query_attributes)[1]
+    p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank)
+    _check(load_library().nhq_search(
+        index, _ptr(queries, np.float32, (Q, d), "queries"),
+        _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, ef, C.byref(p),
+        _ptr(ids, np.uint32, (Q, k), "ids"), _ptr(dists, np.float32, (Q, k), "dists"),
+        _ptr(chi, np.uint8, (Q, k), "chi"), _ptr(status, np.int32, (Q,), "status"),
+        _ptr(ndc, np.int32, (Q,), "ndc"), _stream(stream)))
+
+
+def nhq_search_batched(index, queries, query_attributes, k_arr, ef_arr, k_max, ids, dists=None,
+                       chi=None, status=None, ndc=None, h=1, seed=0, max_iters=0,
+                       warps_per_block=0, hash_bits=0, vec_dtype=VEC_F32, rerank=0,
+                       stream=None) -> None:
+    Q, d = _shape(queries)
+    m = _shape(query_attributes)[1]
+    p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank)
+    _check(load_library().nhq_search_batched(
+        index, _ptr(queries, np.float32, (Q, d), "queries"),
+        _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q,
+        _ptr(k_arr, np.int32, (Q,), "k_arr"), _ptr(ef_arr, np.int32, (Q,), "ef_arr"), k_max,
+        C.byref(p), _ptr(ids, np.uint32, (Q, k_max), "ids"),
+        _ptr(dists, np.float32, (Q, k_max), "dists"), _ptr(chi, np.uint8, (Q, k_max), "chi"),
+        _ptr(status, np.int32, (Q,), "status"), _ptr(ndc, np.int32, (Q,), "ndc"),
+        _stream(stream)))
+
+
+def nhq_save(index, path) -> None:
+    _check(load_library().nhq_save(index, os.fsencode(path)))
+
+
+def nhq_load(path, stream=None) -> int:
+    out = C.c_void_p()
+    _check(load_library().nhq_load(os.fsencode(path), _stream(stream), C.byref(out)))
+    return out.value
+
+
+class Index:
+    """Owning wrapper around an nhq_index handle (freed on close / context exit)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    @classmethod
+    def create(cls, vectors, attributes, weights=None, stream=None):
+        return cls(nhq_index_create(vectors, attributes, weights, stream))
+
+    @classmethod
+    def build(cls, vectors, attributes, degree=32, weights=None, K=64, reverse=1,
+              reverse_cap=64, stream=None):
+        return cls(nhq_build(vectors, attributes, degree, weights, K, reverse, reverse_cap,
+                             stream))
+
+    @property
+    def info(self):
+        return nhq_index_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            nhq_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,562 @@
+// k_search.cu -- joint pruning (Alg. 2) on the composite index, ef-bounded,
+// with the two-stage "random TOGG" routing of Sec. 4.2 / Sec. 5.2.
+//
+// One warp owns one query at a time; warps pull query indices from a global
+// counter (persistent grid sized to the device).  Per warp, shared memory holds
+//   pool  [ef]  u64 records (Gamma bits << 32 | id << 1 | expanded), sorted
+//   cand  [64]  candidate records of the current expansion
+//   hash  [H]   visited filter (open addressing)
+//   qv    [d]   the query vector
+// Each expansion: pick the smallest unexpanded record (ballot scan), read the
+// parent's neighbour ids and their attribute words (one coalesced row each),
+// drop already-evaluated ids through the visited filter, prune by the
+// attribute lower bound w_l * chi when the weights are constant (a candidate
+// whose bound already exceeds the pool's last record cannot enter), evaluate
+// the rest with teams of 8 lanes (128-bit loads, shuffle reduction), and merge
+// them into the pool (warp bitonic sort + rank-based in-place merge).
+//
+// The pool after every expansion equals the serial algorithm's: inserting a
+// batch and keeping the ef smallest equals inserting the batch one record at a
+// time.  When the visited filter fills it is rebuilt from the pool's ids; an
+// id forgotten that way either is in the pool (and re-inserted) or was rejected
+// or evicted while the pool was full, so re-evaluating it rejects it again (its
+// record is above the pool's last record, which only decreases).
+#include "nhq_internal.cuh"
+
+namespace nhq {
+
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr int TEAM = 8;
+constexpr int CAND = 64;
+
+__device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
+__device__ __forceinline__ uint32_t hash_slot(uint32_t v, int bits) {
+    return (v * 0x9E3779B1u) >> (32 - bits);
+}
+
+// true if v was not present (and is now)
+__device__ __forceinline__ bool hash_insert(uint32_t *h, int bits, uint32_t v) {
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t s = hash_slot(v, bits);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        uint32_t old = atomicCAS(&h[s], kNone, v);
+        if (old == kNone)
+            return true;
+        if (old == v)
+            return false;
+        s = (s + 1) & mask;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool hash_contains(const uint32_t *h, int bits, uint32_t v) {
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t s = hash_slot(v, bits);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        uint32_t x = h[s];
+        if (x == v)
+            return true;
+        if (x == kNone)
+            return false;
+        s = (s + 1) & mask;
+    }
+    return false;
+}
+
+__device__ __forceinline__ unsigned long long warp_sort_asc(unsigned long long x, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            unsigned long long y = __shfl_xor_sync(FULL, x, j);
+            bool up = (lane & k) == 0;
+            bool lower = (lane & j) == 0;
+            unsigned long long lo = x < y ? x : y, hi = x < y ? y : x;
+            x = (lower == up) ? lo : hi;
+        }
+    }
+    return x;
+}
+
+// number of pool records whose (Gamma, id) is below key c (flag bits ignored)
+__device__ __forceinline__ int pool_lower_bound(const unsigned long long *pool, int n,
+                                                unsigned long long c) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((pool[mid] & ~1ull) < c)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int sorted_count_less(const unsigned long long *s, int n,
+                                                 unsigned long long x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (s[mid] < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+struct Row4 {
+    float4 v;
+};
+
+template <typename VT>
+__device__ __forceinline__ void accum_chunk(float &acc, const float4 &q0, const float4 &q1,
+                                            const VT *row, int c, bool live);
+
+// f32 rows: chunk c = 4 floats; one float4 of the query
+template <>
+__device__ __forceinline__ void accum_chunk<float>(float &acc, const float4 &q0, const float4 &,
+                                                   const float *row, int c, bool live) {
+    if (!live)
+        return;
+    float4 x = __ldg(reinterpret_cast<const float4 *>(row) + c);
+    float t;
+    t = q0.x - x.x; acc = fmaf(t, t, acc);
+    t = q0.y - x.y; acc = fmaf(t, t, acc);
+    t = q0.z - x.z; acc = fmaf(t, t, acc);
+    t = q0.w - x.w; acc = fmaf(t, t, acc);
+}
+
+// bf16 rows: chunk c = 8 values (16 bytes); two float4 of the query
+template <>
+__device__ __forceinline__ void accum_chunk<__nv_bfloat16>(float &acc, const float4 &q0,
+                                                           const float4 &q1,
+                                                           const __nv_bfloat16 *row, int c,
+                                                           bool live) {
+    if (!live)
+        return;
+    uint4 raw = __ldg(reinterpret_cast<const uint4 *>(row) + c);
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&raw);
+    float2 x0 = __bfloat1622float2(h[0]), x1 = __bfloat1622float2(h[1]);
+    float2 x2 = __bfloat1622float2(h[2]), x3 = __bfloat1622float2(h[3]);
+    float t;
+    t = q0.x - x0.x; acc = fmaf(t, t, acc);
+    t = q0.y - x0.y; acc = fmaf(t, t, acc);
+    t = q0.z - x1.x; acc = fmaf(t, t, acc);
+    t = q0.w - x1.y; acc = fmaf(t, t, acc);
+    t = q1.x - x2.x; acc = fmaf(t, t, acc);
+    t = q1.y - x2.y; acc = fmaf(t, t, acc);
+    t = q1.z - x3.x; acc = fmaf(t, t, acc);
+    t = q1.w - x3.y; acc = fmaf(t, t, acc);
+}
+
+template <typename VT>
+struct VecTraits;
+template <>
+struct VecTraits<float> {
+    static constexpr int kPerChunk = 4;
+};
+template <>
+struct VecTraits<__nv_bfloat16> {
+    static constexpr int kPerChunk = 8;
+};
+
+// Gamma of cnt candidates cid[0..cnt) (chi precomputed in cchi) -> cand[0..cnt).
+// Teams of 8 lanes; each team carries two rows per pass so 8 rows are in flight.
+template <typename VT>
+__device__ __forceinline__ void eval_candidates(const VT *__restrict__ X, int xstride,
+                                                const float *qv, const uint32_t *cid,
+                                                const int *cchi, unsigned long long *cand,
+                                                int cnt, const Fusion &w, int lane) {
+    constexpr int PC = VecTraits<VT>::kPerChunk;
+    const int team = lane / TEAM, tl = lane % TEAM;
+    const int nchunk = xstride / PC;
+    for (int base = 0; base < cnt; base += 8) {
+        const int j0 = base + team, j1 = base + 4 + team;
+        const bool h0 = j0 < cnt, h1 = j1 < cnt;
+        const VT *r0 = X + (int64_t)cid[h0 ? j0 : 0] * xstride;
+        const VT *r1 = X + (int64_t)cid[h1 ? j1 : 0] * xstride;
+        float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll 4
+        for (int c = tl; c < nchunk; c += TEAM) {
+            float4 qa = reinterpret_cast<const float4 *>(qv)[c * PC / 4];
+            float4 qb = PC == 8 ? reinterpret_cast<const float4 *>(qv)[c * PC / 4 + 1] : qa;
+            accum_chunk<VT>(acc0, qa, qb, r0, c, h0);
+            accum_chunk<VT>(acc1, qa, qb, r1, c, h1);
+        }
+        acc0 += __shfl_xor_sync(FULL, acc0, 1);
+        acc1 += __shfl_xor_sync(FULL, acc1, 1);
+        acc0 += __shfl_xor_sync(FULL, acc0, 2);
+        acc1 += __shfl_xor_sync(FULL, acc1, 2);
+        acc0 += __shfl_xor_sync(FULL, acc0, 4);
+        acc1 += __shfl_xor_sync(FULL, acc1, 4);
+        if (tl == 0) {
+            if (h0)
+                cand[j0] = make_key(fusion_gamma(__fsqrt_rn(acc0), cchi[j0], w), cid[j0]);
+            if (h1)
+                cand[j1] = make_key(fusion_gamma(__fsqrt_rn(acc1), cchi[j1], w), cid[j1]);
+        }
+    }
+    __syncwarp();
+}
+
+// Merge cand[0..cnt) into the pool; returns true if any candidate entered it.
+__device__ bool merge_into_pool(unsigned long long *pool, int &n, int ef,
+                                unsigned long long *cand, int cnt, int &cursor, int lane) {
+    bool any = false;
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        unsigned long long c = i < cnt ? cand[i] : kInfKey;
+        if (c != kInfKey && n == ef && c > (pool[ef - 1] & ~1ull))
+            c = kInfKey;  // cannot beat the last record of a full pool
+        if (c != kInfKey) {
+            int lb = pool_lower_bound(pool, n, c);
+            if (lb < n && (pool[lb] & ~1ull) == c)
+                c = kInfKey;  // already pooled
+        }
+        c = warp_sort_asc(c, lane);
+        const int nv = __popc(__ballot_sync(FULL, c != kInfKey));
+        if (nv == 0)
+            continue;
+        __syncwarp();
+        cand[base + lane] = c;  // sorted candidates of this round
+        __syncwarp();
+        const unsigned long long *cs = cand + base;
+        const int pos = lane < nv ? lane + pool_lower_bound(pool, n, c) : ef;
+        const int p0 = __shfl_sync(FULL, pos, 0);
+        if (p0 >= ef)
+            continue;  // nothing enters
+        for (int b = (n - 1) & ~31; n > 0 && b >= (p0 & ~31); b -= 32) {
+            const int e = b + lane;
+            const bool mv = e >= p0 && e < n;
+            unsigned long long val = 0;
+            int dst = ef;
+            if (mv) {
+                val = pool[e];
+                dst = e + sorted_count_less(cs, nv, val & ~1ull);
+            }
+            __syncwarp();
+            if (mv && dst < ef)
+                pool[dst] = val;
+            __syncwarp();
+        }
+        if (lane < nv && pos < ef)
+            pool[pos] = c;
+        __syncwarp();
+        n = min(ef, n + nv);
+        any = true;
+        cursor = min(cursor, p0);
+    }
+    return any;
+}
+
+__device__ __forceinline__ void clear_expanded(unsigned long long *pool, int n, int lane) {
+    __syncwarp();
+    for (int i = lane; i < n; i += 32)
+        pool[i] &= ~1ull;
+    __syncwarp();
+}
+
+struct WarpLayout {
+    size_t pool, cand, cid, cchi, hash, qv, total;
+};
+
+__host__ __device__ inline WarpLayout warp_layout(int ef_cap, int hash_bits, int xstride) {
+    WarpLayout L;
+    size_t o = 0;
+    L.pool = o;
+    o += sizeof(unsigned long long) * ef_cap;
+    L.cand = o;
+    o += sizeof(unsigned long long) * CAND;
+    L.cid = o;
+    o += sizeof(uint32_t) * CAND;
+    L.cchi = o;
+    o += sizeof(int) * CAND;
+    L.hash = o;
+    o += sizeof(uint32_t) * ((size_t)1 << hash_bits);
+    o = (o + 15) & ~(size_t)15;
+    L.qv = o;
+    o += sizeof(float) * xstride;
+    o = (o + 15) & ~(size_t)15;
+    L.total = o;
+    return L;
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(256) search_kernel(SearchArgs a, const VT *__restrict__ Xs,
+                                                     int ef_cap) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const WarpLayout L = warp_layout(ef_cap, a.hash_bits, a.xstride);
+    unsigned char *base = smem + wib * L.total;
+    unsigned long long *pool = reinterpret_cast<unsigned long long *>(base + L.pool);
+    unsigned long long *cand = reinterpret_cast<unsigned long long *>(base + L.cand);
+    uint32_t *cid = reinterpret_cast<uint32_t *>(base + L.cid);
+    int *cchi = reinterpret_cast<int *>(base + L.cchi);
+    uint32_t *hash = reinterpret_cast<uint32_t *>(base + L.hash);
+    float *qv = reinterpret_cast<float *>(base + L.qv);
+    const int H = 1 << a.hash_bits;
+    const int R = a.R;
+    const uint32_t amask = a.w.mask;
+
+    for (;;) {
+        unsigned long long qq = 0;
+        if (lane == 0)
+            qq = atomicAdd(a.counter, 1ull);
+        qq = __shfl_sync(FULL, qq, 0);
+        if (qq >= (unsigned long long)a.nq)
+            break;
+        const int64_t q = (int64_t)qq;
+        const int k = a.k_arr ? a.k_arr[q] : a.k;
+        const int ef = a.ef_arr ? a.ef_arr[q] : a.ef;
+
+        for (int i = lane; i < a.xstride; i += 32)
+            qv[i] = i < a.d ? a.Q[q * a.qstride + i] : 0.f;
+        uint32_t qa = 0;
+        for (int j = 0; j < a.w.m; ++j)
+            qa |= (uint32_t)a.qattr[q * a.w.m + j] << (8 * j);
+        for (int i = lane; i < H; i += 32)
+            hash[i] = kNone;
+        __syncwarp();
+
+        int n = 0, cursor = 0, hcount = 0, iters = 0, ndc = 0;
+        int stage = a.h > 1 ? 1 : 2;
+        int status = NHQ_OK;
+        const uint64_t s0 = a.seed ^ mix64((uint64_t)q);
+
+        // ---- seed set B: first min(ef, 32) distinct ids of the stream, <= 64 draws
+        const int want = min(ef, 32);
+        int got = 0;
+        for (int r = 0; r < 2 && got < want; ++r) {
+            const uint32_t v = (uint32_t)(splitmix_at(s0, (uint64_t)(32 * r + lane)) %
+                                          (unsigned long long)a.N);
+            const unsigned same = __match_any_sync(FULL, v);
+            bool first = (__ffs(same) - 1) == lane;
+            if (r == 1 && first)
+                first = !hash_contains(hash, a.hash_bits, v);
+            const unsigned fb = __ballot_sync(FULL, first);
+            const bool keep = first && __popc(fb & lanemask_lt(lane)) < want - got;
+            const unsigned kb = __ballot_sync(FULL, keep);
+            if (keep) {
+                hash_insert(hash, a.hash_bits, v);
+                const int p = __popc(kb & lanemask_lt(lane));
+                cid[p] = v;
+                cchi[p] = chi_packed(a.attr[v], qa, amask);
+            }
+            __syncwarp();
+            const int cnt = __popc(kb);
+            got += cnt;
+            hcount += cnt;
+            ndc += cnt;
+            eval_candidates<VT>(Xs, a.xstride, qv, cid, cchi, cand, cnt, a.w, lane);
+            merge_into_pool(pool, n, ef, cand, cnt, cursor, lane);
+        }
+        cursor = 0;
+
+        // ---- expansions
+        for (;;) {
+            int pidx = -1;
+            while (cursor < n) {
+                const int i = cursor + lane;
+                const bool un = i < n && !(pool[i] & 1ull);
+                const unsigned b = __ballot_sync(FULL, un);
+                if (b) {
+                    pidx = cursor + __ffs(b) - 1;
+                    break;
+                }
+                cursor += 32;
+            }
+            if (pidx < 0) {
+                if (stage == 1) {  // S1 exhausted C: S2 with C = C u R
+                    stage = 2;
+                    clear_expanded(pool, n, lane);
+                    cursor = 0;
+                    continue;
+                }
+                break;
+            }
+            if (iters >= a.max_iters) {
+                status = NHQ_ERR_ITER_LIMIT;
+                break;
+            }
+            ++iters;
+            const unsigned long long pk = pool[pidx];
+            __syncwarp();
+            if (lane == 0)
+                pool[pidx] = pk | 1ull;
+            cursor = pidx + 1;
+            const uint32_t u = key_id(pk);
+
+            if (hcount + R > (H >> 1)) {  // rebuild the visited filter from the pool
+                __syncwarp();
+                for (int i = lane; i < H; i += 32)
+                    hash[i] = kNone;
+                __syncwarp();
+                for (int i = lane; i < n; i += 32)
+                    hash_insert(hash, a.hash_bits, key_id(pool[i]));
+                __syncwarp();
+                hcount = n;
+            }
+
+            uint32_t v0 = kNone, v1 = kNone, at0 = 0, at1 = 0;
+            if (lane < R) {
+                v0 = a.nbr[(int64_t)u * R + lane];
+                at0 = a.nbr_attr[(int64_t)u * R + lane];
+            }
+            if (lane + 32 < R) {
+                v1 = a.nbr[(int64_t)u * R + lane + 32];
+                at1 = a.nbr_attr[(int64_t)u * R + lane + 32];
+            }
+            bool ok0 = v0 != kNone, ok1 = v1 != kNone;
+
+            if (stage == 1) {  // S1: ceil(R/h) valid neighbours of smallest key
+                const unsigned b0 = __ballot_sync(FULL, ok0), b1 = __ballot_sync(FULL, ok1);
+                const int take = (R + a.h - 1) / a.h;
+                if (__popc(b0) + __popc(b1) > take) {
+                    const uint64_t su = mix64(s0 ^ mix64((uint64_t)u + 1));
+                    const uint64_t k0 = splitmix_at(su, (uint64_t)lane);
+                    const uint64_t k1 = splitmix_at(su, (uint64_t)(lane + 32));
+                    int r0 = 0, r1 = 0;
+                    for (int t = 0; t < R; ++t) {
+                        const uint64_t kt = __shfl_sync(FULL, t < 32 ? k0 : k1, t & 31);
+                        const bool okt = t < 32 ? ((b0 >> t) & 1u) : ((b1 >> (t - 32)) & 1u);
+                        if (!okt)
+                            continue;
+                        r0 += (kt < k0 || (kt == k0 && t < lane)) ? 1 : 0;
+                        r1 += (kt < k1 || (kt == k1 && t < lane + 32)) ? 1 : 0;
+                    }
+                    ok0 = ok0 && r0 < take;
+                    ok1 = ok1 && r1 < take;
+                }
+            }
+
+            bool nw0 = ok0 && hash_insert(hash, a.hash_bits, v0);
+            bool nw1 = ok1 && hash_insert(hash, a.hash_bits, v1);
+            hcount += __popc(__ballot_sync(FULL, nw0)) + __popc(__ballot_sync(FULL, nw1));
+            const int c0 = chi_packed(at0, qa, amask), c1 = chi_packed(at1, qa, amask);
+            if (a.w.mode == NHQ_W_CONSTANT && n == ef) {
+                // Gamma >= w_l * chi in f32 (w_v * delta >= 0 and rounding is monotone)
+                const unsigned long long worst = pool[ef - 1] & ~1ull;
+                if (nw0 && make_key(__fmul_rn(a.w.wl, (float)c0), v0) > worst)
+                    nw0 = false;
+                if (nw1 && make_key(__fmul_rn(a.w.wl, (float)c1), v1) > worst)
+                    nw1 = false;
+            }
+            const unsigned e0 = __ballot_sync(FULL, nw0), e1 = __ballot_sync(FULL, nw1);
+            if (nw0) {
+                const int p = __popc(e0 & lanemask_lt(lane));
+                cid[p] = v0;
+                cchi[p] = c0;
+            }
+            if (nw1) {
+                const int p = __popc(e0) + __popc(e1 & lanemask_lt(lane));
+                cid[p] = v1;
+                cchi[p] = c1;
+            }
+            __syncwarp();
+            const int cnt = __popc(e0) + __popc(e1);
+            ndc += cnt;
+            bool changed = false;
+            if (cnt > 0) {
+                eval_candidates<VT>(Xs, a.xstride, qv, cid, cchi, cand, cnt, a.w, lane);
+                changed = merge_into_pool(pool, n, ef, cand, cnt, cursor, lane);
+            }
+            if (stage == 1 && !changed) {  // local optimum ends S1
+                stage = 2;
+                clear_expanded(pool, n, lane);
+                cursor = 0;
+            }
+        }
+
+        __syncwarp();
+        for (int j = lane; j < a.k_out; j += 32) {
+            const int64_t o = q * a.k_out + j;
+            uint32_t id = kNone;
+            float g = __int_as_float(0x7f800000);
+            if (j < k && j < n) {
+                id = key_id(pool[j]);
+                g = key_gamma(pool[j]);
+            }
+            a.ids[o] = id;
+            if (a.dists)
+                a.dists[o] = g;
+            if (a.chi)
+                a.chi[o] = id == kNone ? (uint8_t)255 : (uint8_t)chi_packed(a.attr[id], qa, amask);
+        }
+        if (lane == 0) {
+            if (a.status)
+                a.status[q] = status;
+            if (a.ndc)
+                a.ndc[q] = ndc;
+        }
+        __syncwarp();
+    }
+}
+
+int auto_hash_bits(int ef_cap, int R) {
+    int need = 4 * (ef_cap + R);
+    int bits = 11;  // 2048 slots
+    while ((1 << bits) < need)
+        ++bits;
+    return bits;
+}
+
+}  // namespace
+
+size_t search_scratch_bytes() { return 256; }
+
+cudaError_t launch_search(SearchArgs a, void *scratch, int sm_count, size_t smem_optin,
+                          cudaStream_t s) {
+    if (a.nq <= 0)
+        return cudaSuccess;
+    a.counter = reinterpret_cast<unsigned long long *>(scratch);
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess)
+        return e;
+    const int ef_cap = (a.ef + 31) & ~31;
+    if (a.hash_bits <= 0)
+        a.hash_bits = auto_hash_bits(ef_cap, a.R);
+    if ((1 << a.hash_bits) < 2 * (ef_cap + a.R) + 64)
+        return cudaErrorInvalidValue;
+    const WarpLayout L = warp_layout(ef_cap, a.hash_bits, a.xstride);
+    int wpb = a.warps_per_block > 0 ? a.warps_per_block : 4;
+    while (wpb > 1 && L.total * wpb > smem_optin)
+        wpb >>= 1;
+    if (L.total * wpb > smem_optin)
+        return cudaErrorInvalidValue;
+    const size_t smem = L.total * wpb;
+    int per_sm = 0;
+    if (a.vec_dtype == NHQ_VEC_BF16) {
+        auto kfn = search_kernel<__nv_bfloat16>;
+        if ((e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * wpb, smem)) !=
+            cudaSuccess)
+            return e;
+    } else {
+        auto kfn = search_kernel<float>;
+        if ((e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * wpb, smem)) !=
+            cudaSuccess)
+            return e;
+    }
+    if (per_sm < 1)
+        per_sm = 1;
+    int64_t blocks = (int64_t)per_sm * sm_count;
+    int64_t need = (a.nq + wpb - 1) / wpb;
+    if (blocks > need)
+        blocks = need;
+    if (a.vec_dtype == NHQ_VEC_BF16)
+        search_kernel<__nv_bfloat16><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a, a.Xh, ef_cap);
+    else
+        search_kernel<float><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a, a.X, ef_cap);
+    return cudaGetLastError();
+}
+
+}  // namespace nhq

@@ -1,0 +1,101 @@
+// k_util.cu -- data-layout kernels: ordinal attribute packing (Sec. 3.2),
+// padded row copies of the object vectors, the BF16 scoring copy, and the
+// per-edge attribute words stored beside the adjacency.
+#include "nhq_internal.cuh"
+
+namespace nhq {
+
+namespace {
+
+__global__ void pack_attr_kernel(const uint8_t *__restrict__ a, int64_t n, int m,
+                                 uint32_t *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t w = 0;
+        for (int j = 0; j < m; ++j)
+            w |= (uint32_t)a[i * m + j] << (8 * j);
+        out[i] = w;
+    }
+}
+
+// dst[r][0..xstride) = src[r][0..d) followed by zeros; flags non-finite input.
+__global__ void copy_rows_kernel(const float *__restrict__ src, int64_t N, int d, int xstride,
+                                 float *__restrict__ dst, int *__restrict__ bad) {
+    int64_t total = N * (int64_t)xstride;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = i / xstride;
+        int c = (int)(i - r * xstride);
+        float v = c < d ? src[r * d + c] : 0.0f;
+        if (!isfinite(v))
+            *bad = 1;
+        dst[i] = v;
+    }
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ src, int64_t n,
+                               __nv_bfloat16 *__restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// Also validates the adjacency: an id that is neither kNone nor < N sets *bad.
+__global__ void gather_nbr_attr_kernel(const uint32_t *__restrict__ nbr,
+                                       const uint32_t *__restrict__ attr, int64_t N,
+                                       int64_t total, uint32_t *__restrict__ out,
+                                       int *__restrict__ bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t v = nbr[i];
+        if (v != kNone && (int64_t)v >= N) {
+            *bad = 1;
+            v = kNone;
+        }
+        out[i] = v == kNone ? 0u : attr[v];
+    }
+}
+
+inline int grid_for(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    return (int)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
+}
+
+}  // namespace
+
+cudaError_t launch_pack_attributes(const uint8_t *a, int64_t n, int m, uint32_t *out,
+                                   cudaStream_t s) {
+    if (n <= 0)
+        return cudaSuccess;
+    pack_attr_kernel<<<grid_for(n), 256, 0, s>>>(a, n, m, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_rows(const float *src, int64_t N, int d, int xstride, float *dst,
+                             int *bad, cudaStream_t s) {
+    copy_rows_kernel<<<grid_for(N * xstride), 256, 0, s>>>(src, N, d, xstride, dst, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_to_bf16(const float *src, int64_t n, __nv_bfloat16 *dst, cudaStream_t s) {
+    to_bf16_kernel<<<grid_for(n), 256, 0, s>>>(src, n, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_nbr_attr(const uint32_t *nbr, const uint32_t *attr, int64_t N, int R,
+                                   uint32_t *out, int *bad, cudaStream_t s) {
+    gather_nbr_attr_kernel<<<grid_for(N * R), 256, 0, s>>>(nbr, attr, N, N * (int64_t)R, out, bad);
+    return cudaGetLastError();
+}
+
+Fusion make_fusion(const nhq_weights &w, int m) {
+    Fusion f;
+    f.mode = w.mode;
+    f.wv = w.w_v;
+    f.wl = w.w_l;
+    f.m = m;
+    f.mask = m >= 4 ? 0xFFFFFFFFu : ((1u << (8 * m)) - 1u);
+    return f;
+}
+
+}  // namespace nhq

@@ -1,0 +1,720 @@
+// nhq_api.cu -- the C ABI declared in include/nhq.h: argument checks, index
+// ownership, host/device pointer handling, and the launches of the kernels in
+// k_util.cu, k_bruteforce.cu, k_edge.cu and k_search.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nhq_internal.cuh"
+
+using namespace nhq;
+
+namespace {
+
+thread_local std::string g_err;
+
+nhq_status fail(nhq_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+nhq_status fail_cuda(cudaError_t e, const char *what) {
+    nhq_status s = e == cudaErrorMemoryAllocation ? NHQ_ERR_OOM : NHQ_ERR_CUDA;
+    return fail(s, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail_cuda(e_, #call);                                                           \
+    } while (0)
+
+#define CKS(expr)                                                                                  \
+    do {                                                                                           \
+        nhq_status s_ = (expr);                                                                    \
+        if (s_ != NHQ_OK)                                                                          \
+            return s_;                                                                             \
+    } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool is_device_ptr(const void *p) {
+    if (p == nullptr)
+        return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+nhq_status grow(void **buf, size_t *cap, size_t need) {
+    if (*cap >= need)
+        return NHQ_OK;
+    if (*buf) {
+        CK(cudaDeviceSynchronize());
+        CK(cudaFree(*buf));
+        *buf = nullptr;
+        *cap = 0;
+    }
+    size_t sz = need < 4096 ? 4096 : need;
+    CK(cudaMalloc(buf, sz));
+    *cap = sz;
+    return NHQ_OK;
+}
+
+// Host pointers are copied through one device staging allocation per call.
+struct Stager {
+    struct Req {
+        void *user;
+        size_t bytes;
+        bool input;
+        bool host;
+        size_t off;
+    };
+    std::vector<Req> reqs;
+    void *base = nullptr;
+    bool any_host = false;
+
+    int add(const void *p, size_t bytes, bool input) {
+        Req r{const_cast<void *>(p), bytes, input, p != nullptr && !is_device_ptr(p), 0};
+        any_host = any_host || r.host;
+        reqs.push_back(r);
+        return (int)reqs.size() - 1;
+    }
+    nhq_status commit(void **arena, size_t *cap, cudaStream_t s) {
+        size_t off = 0;
+        for (auto &r : reqs)
+            if (r.host) {
+                r.off = off;
+                off += (r.bytes + 255) & ~(size_t)255;
+            }
+        if (off == 0)
+            return NHQ_OK;
+        CKS(grow(arena, cap, off));
+        base = *arena;
+        for (auto &r : reqs)
+            if (r.host && r.input && r.bytes)
+                CK(cudaMemcpyAsync((char *)base + r.off, r.user, r.bytes, cudaMemcpyHostToDevice, s));
+        return NHQ_OK;
+    }
+    void *dev(int i) const {
+        const Req &r = reqs[i];
+        if (r.user == nullptr)
+            return nullptr;
+        return r.host ? (char *)base + r.off : r.user;
+    }
+    nhq_status finish(cudaStream_t s) {
+        if (!any_host)
+            return NHQ_OK;
+        for (auto &r : reqs)
+            if (r.host && !r.input && r.bytes)
+                CK(cudaMemcpyAsync(r.user, (char *)base + r.off, r.bytes, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return NHQ_OK;
+    }
+};
+
+nhq_status check_weights(const nhq_weights &w, bool allow_filter) {
+    if (w.mode != NHQ_W_PROPORTIONAL && w.mode != NHQ_W_CONSTANT &&
+        !(allow_filter && w.mode == NHQ_W_FILTER))
+        return fail(NHQ_ERR_ARG, "unknown weight mode %d", w.mode);
+    if (w.mode == NHQ_W_CONSTANT &&
+        (!std::isfinite(w.w_v) || !std::isfinite(w.w_l) || w.w_v < 0.f || w.w_l < 0.f))
+        return fail(NHQ_ERR_ARG, "constant weights must be finite and >= 0");
+    return NHQ_OK;
+}
+
+nhq_status scratch(nhq_index *ix, size_t need) { return grow(&ix->scratch, &ix->scratch_bytes, need); }
+
+struct StageArena {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+thread_local StageArena g_stage;  // host-pointer staging (per host thread)
+
+nhq_status install_graph(nhq_index *ix, const uint32_t *nbr_dev, int R, cudaStream_t s) {
+    const size_t bytes = sizeof(uint32_t) * (size_t)ix->N * R;
+    if (ix->R != R || ix->nbr == nullptr) {
+        if (ix->nbr)
+            CK(cudaFree(ix->nbr));
+        if (ix->nbr_attr)
+            CK(cudaFree(ix->nbr_attr));
+        ix->nbr = ix->nbr_attr = nullptr;
+        CK(cudaMalloc(&ix->nbr, bytes));
+        CK(cudaMalloc(&ix->nbr_attr, bytes));
+    }
+    if (nbr_dev != ix->nbr)
+        CK(cudaMemcpyAsync(ix->nbr, nbr_dev, bytes, cudaMemcpyDeviceToDevice, s));
+    CKS(scratch(ix, 256));
+    int *bad = reinterpret_cast<int *>(ix->scratch);
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    CK(launch_gather_nbr_attr(ix->nbr, ix->attr, ix->N, R, ix->nbr_attr, bad, s));
+    int hbad = 0;
+    CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ix->R = R;
+    if (hbad)
+        return fail(NHQ_ERR_ARG, "graph holds an id that is neither 0xFFFFFFFF nor < N");
+    return NHQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *nhq_last_error(void) { return g_err.c_str(); }
+
+int32_t nhq_version(void) { return 1; }
+
+nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
+                            int32_t m, nhq_weights w, void *stream, nhq_index **out) {
+    if (out == nullptr)
+        return fail(NHQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (N < 1 || N > 0x7FFFFFFE)
+        return fail(NHQ_ERR_ARG, "N must be in 1..2^31-2 (got %lld)", (long long)N);
+    if (d < 1 || d > 16384)
+        return fail(NHQ_ERR_ARG, "d must be in 1..16384 (got %d)", d);
+    if (m < 1 || m > 4)
+        return fail(NHQ_ERR_ARG, "m must be in 1..4 (got %d)", m);
+    if (vectors == nullptr || attributes == nullptr)
+        return fail(NHQ_ERR_ARG, "vectors and attributes are required");
+    CKS(check_weights(w, false));
+    cudaStream_t s = as_stream(stream);
+    nhq_index *ix = new nhq_index();
+    ix->N = N;
+    ix->d = d;
+    ix->m = m;
+    ix->xstride = (d + 7) & ~7;
+    ix->w = w;
+    auto bail = [&](nhq_status st) {
+        nhq_free(ix);
+        return st;
+    };
+    cudaError_t e;
+    if ((e = cudaGetDevice(&ix->device)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaGetDevice"));
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, ix->device)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaGetDeviceProperties"));
+    ix->sm_count = prop.multiProcessorCount;
+    ix->smem_optin = prop.sharedMemPerBlockOptin;
+    if ((e = cudaMalloc(&ix->X, sizeof(float) * (size_t)N * ix->xstride)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaMalloc(vectors)"));
+    if ((e = cudaMalloc(&ix->attr, sizeof(uint32_t) * (size_t)N)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaMalloc(attributes)"));
+    Stager st;
+    int iv = st.add(vectors, sizeof(float) * (size_t)N * d, true);
+    int ia = st.add(attributes, (size_t)N * m, true);
+    nhq_status rs = st.commit(&g_stage.p, &g_stage.cap, s);
+    if (rs != NHQ_OK)
+        return bail(rs);
+    if ((rs = scratch(ix, 256)) != NHQ_OK)
+        return bail(rs);
+    int *bad = reinterpret_cast<int *>(ix->scratch);
+    if ((e = cudaMemsetAsync(bad, 0, sizeof(int), s)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaMemsetAsync"));
+    if ((e = launch_copy_rows((const float *)st.dev(iv), N, d, ix->xstride, ix->X, bad, s)) !=
+        cudaSuccess)
+        return bail(fail_cuda(e, "copy_rows"));
+    if ((e = launch_pack_attributes((const uint8_t *)st.dev(ia), N, m, ix->attr, s)) != cudaSuccess)
+        return bail(fail_cuda(e, "pack_attributes"));
+    int hbad = 0;
+    if ((e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaMemcpyAsync"));
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaStreamSynchronize"));
+    if (hbad)
+        return bail(fail(NHQ_ERR_ARG, "vectors contain a non-finite component"));
+    *out = ix;
+    return NHQ_OK;
+}
+
+void nhq_free(nhq_index *ix) {
+    if (ix == nullptr)
+        return;
+    cudaDeviceSynchronize();
+    cudaFree(ix->X);
+    cudaFree(ix->Xh);
+    cudaFree(ix->attr);
+    cudaFree(ix->nbr);
+    cudaFree(ix->nbr_attr);
+    cudaFree(ix->scratch);
+    delete ix;
+}
+
+nhq_status nhq_index_info(const nhq_index *ix, int64_t *N, int32_t *d, int32_t *m, int32_t *R) {
+    if (ix == nullptr)
+        return fail(NHQ_ERR_ARG, "index is NULL");
+    if (N)
+        *N = ix->N;
+    if (d)
+        *d = ix->d;
+    if (m)
+        *m = ix->m;
+    if (R)
+        *R = ix->R;
+    return NHQ_OK;
+}
+
+nhq_status nhq_pack_attributes(const uint8_t *attributes, int64_t n, int32_t m, uint32_t *packed,
+                               void *stream) {
+    if (n < 0 || m < 1 || m > 4)
+        return fail(NHQ_ERR_ARG, "n must be >= 0 and m in 1..4");
+    if (n == 0)
+        return NHQ_OK;
+    if (!is_device_ptr(attributes) || !is_device_ptr(packed))
+        return fail(NHQ_ERR_ARG, "nhq_pack_attributes takes device pointers");
+    CK(launch_pack_attributes(attributes, n, m, packed, as_stream(stream)));
+    return NHQ_OK;
+}
+
+nhq_status nhq_knn(const nhq_index *cix, int32_t K, uint32_t *cand_ids, float *cand_dist,
+                   void *stream) {
+    nhq_index *ix = const_cast<nhq_index *>(cix);
+    if (ix == nullptr || cand_ids == nullptr)
+        return fail(NHQ_ERR_ARG, "index and cand_ids are required");
+    if (K < 1 || K > kMaxK || K >= ix->N)
+        return fail(NHQ_ERR_ARG, "K must be in 1..min(256, N-1) (got %d)", K);
+    cudaStream_t s = as_stream(stream);
+    Stager st;
+    int io = st.add(cand_ids, sizeof(uint32_t) * (size_t)ix->N * K, false);
+    int id = st.add(cand_dist, sizeof(float) * (size_t)ix->N * K, false);
+    CKS(st.commit(&g_stage.p, &g_stage.cap, s));
+    TopkArgs a;
+    a.X = ix->X;
+    a.xstride = ix->xstride;
+    a.d = ix->d;
+    a.N = ix->N;
+    a.attr = ix->attr;
+    a.Q = ix->X;
+    a.qstride = ix->xstride;
+    a.qattr = ix->attr;
+    a.nq = ix->N;
+    a.k = K;
+    a.exclude_self = 1;
+    a.w = make_fusion(ix->w, ix->m);
+    a.ids = (uint32_t *)st.dev(io);
+    a.dists = (float *)st.dev(id);
+    a.chi = nullptr;
+    size_t need = topk_scratch_bytes(a, ix->sm_count);
+    CKS(scratch(ix, need + 256));
+    CK(launch_topk(a, ix->scratch, ix->scratch_bytes, ix->sm_count, s));
+    return st.finish(s);
+}
+
+nhq_status nhq_edge_select(const nhq_index *cix, const uint32_t *cand_ids, int32_t L, int32_t R,
+                           uint32_t *nbr_out, void *stream) {
+    const nhq_index *ix = cix;
+    if (ix == nullptr || cand_ids == nullptr || nbr_out == nullptr)
+        return fail(NHQ_ERR_ARG, "index, cand_ids and nbr_out are required");
+    if (L < 1 || L > kMaxCand)
+        return fail(NHQ_ERR_ARG, "L must be in 1..128 (got %d)", L);
+    if (R < 1 || R > kMaxDegree)
+        return fail(NHQ_ERR_ARG, "R must be in 1..64 (got %d)", R);
+    cudaStream_t s = as_stream(stream);
+    Stager st;
+    int ic = st.add(cand_ids, sizeof(uint32_t) * (size_t)ix->N * L, true);
+    int io = st.add(nbr_out, sizeof(uint32_t) * (size_t)ix->N * R, false);
+    CKS(st.commit(&g_stage.p, &g_stage.cap, s));
+    CK(launch_edge_select(ix, (const uint32_t *)st.dev(ic), L, R, (uint32_t *)st.dev(io), s));
+    return st.finish(s);
+}
+
+nhq_status nhq_reverse_candidates(const nhq_index *cix, const uint32_t *nbr, int32_t R, int32_t cap,
+                                  uint32_t *out, void *stream) {
+    nhq_index *ix = const_cast<nhq_index *>(cix);
+    if (ix == nullptr || nbr == nullptr || out == nullptr)
+        return fail(NHQ_ERR_ARG, "index, nbr and out are required");
+    if (R < 1 || R > kMaxDegree || cap < 0 || cap > kMaxDegree)
+        return fail(NHQ_ERR_ARG, "R must be in 1..64 and cap in 0..64");
+    cudaStream_t s = as_stream(stream);
+    Stager st;
+    int in = st.add(nbr, sizeof(uint32_t) * (size_t)ix->N * R, true);
+    int io = st.add(out, sizeof(uint32_t) * (size_t)ix->N * (R + cap), false);
+    CKS(st.commit(&g_stage.p, &g_stage.cap, s));
+    CKS(scratch(ix, reverse_scratch_bytes(ix->N, R)));
+    CK(launch_reverse_candidates((const uint32_t *)st.dev(in), ix->N, R, cap,
+                                 (uint32_t *)st.dev(io), ix->scratch, s));
+    return st.finish(s);
+}
+
+nhq_status nhq_index_set_graph(nhq_index *ix, const uint32_t *nbr, int32_t R, void *stream) {
+    if (ix == nullptr || nbr == nullptr)
+        return fail(NHQ_ERR_ARG, "index and nbr are required");
+    if (R < 1 || R > kMaxDegree)
+        return fail(NHQ_ERR_ARG, "R must be in 1..64 (got %d)", R);
+    cudaStream_t s = as_stream(stream);
+    Stager st;
+    int in = st.add(nbr, sizeof(uint32_t) * (size_t)ix->N * R, true);
+    CKS(st.commit(&g_stage.p, &g_stage.cap, s));
+    return install_graph(ix, (const uint32_t *)st.dev(in), R, s);
+}
+
+nhq_status nhq_index_get_graph(const nhq_index *ix, uint32_t *nbr, void *stream) {
+    if (ix == nullptr || nbr == nullptr)
+        return fail(NHQ_ERR_ARG, "index and nbr are required");
+    if (ix->nbr == nullptr)
+        return fail(NHQ_ERR_ARG, "the index has no graph");
+    cudaStream_t s = as_stream(stream);
+    Stager st;
+    int io = st.add(nbr, sizeof(uint32_t) * (size_t)ix->N * ix->R, false);
+    CKS(st.commit(&g_stage.p, &g_stage.cap, s));
+    CK(cudaMemcpyAsync(st.dev(io), ix->nbr, sizeof(uint32_t) * (size_t)ix->N * ix->R,
+                       cudaMemcpyDeviceToDevice, s));
+    return st.finish(s);
+}
+
+nhq_status nhq_index_build(nhq_index *ix, int32_t degree, const nhq_build_params *p,
+                           void *stream) {
+    if (ix == nullptr)
+        return fail(NHQ_ERR_ARG, "index is NULL");
+    if (degree < 1 || degree > kMaxDegree)
+        return fail(NHQ_ERR_ARG, "degree must be in 1..64 (got %d)", degree);
+    if (ix->N < 2)
+        return fail(NHQ_ERR_ARG, "a graph needs N >= 2");
+    int K = p && p->K > 0 ? p->K : 64;
+    int rev = p ? p->reverse : 1;
+    int cap = p && p->reverse_cap > 0 ? p->reverse_cap : 64;
+    if (K > kMaxCand)
+        return fail(NHQ_ERR_ARG, "K must be in 1..128 for the build (got %d)", K);
+    if (cap > kMaxDegree)
+        return fail(NHQ_ERR_ARG, "reverse_cap must be in 1..64");
+    if (K >= ix->N)
+        K = (int)(ix->N - 1);
+    if (rev && degree + cap > kMaxCand)
+        cap = kMaxCand - degree;
+    cudaStream_t s = as_stream(stream);
+    uint32_t *cand = nullptr, *nbr = nullptr, *rc = nullptr;
+    const size_t N = (size_t)ix->N;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(s);
+        cudaFree(cand);
+        cudaFree(nbr);
+        cudaFree(rc);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&cand, sizeof(uint32_t) * N * K)) != cudaSuccess ||
+        (e = cudaMalloc(&nbr, sizeof(uint32_t) * N * degree)) != cudaSuccess) {
+        cleanup();
+        return fail_cuda(e, "cudaMalloc(build buffers)");
+    }
+    nhq_status st = nhq_knn(ix, K, cand, nullptr, stream);
+    if (st == NHQ_OK)
+        st = nhq_edge_select(ix, cand, K, degree, nbr, stream);
+    if (st == NHQ_OK && rev) {
+        if ((e = cudaMalloc(&rc, sizeof(uint32_t) * N * (degree + cap))) != cudaSuccess) {
+            cleanup();
+            return fail_cuda(e, "cudaMalloc(reverse candidates)");
+        }
+        st = nhq_reverse_candidates(ix, nbr, degree, cap, rc, stream);
+        if (st == NHQ_OK)
+            st = nhq_edge_select(ix, rc, degree + cap, degree, nbr, stream);
+    }
+    if (st == NHQ_OK)
+        st = install_graph(ix, nbr, degree, s);
+    cleanup();
+    return st;
+}
+
+nhq_status nhq_build(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
+                     int32_t m, int32_t degree, nhq_weights w, const nhq_build_params *params,
+                     void *stream, nhq_index **out) {
+    nhq_index *ix = nullptr;
+    CKS(nhq_index_create(vectors, N, d, attributes, m, w, stream, &ix));
+    nhq_status st = nhq_index_build(ix, degree, params, stream);
+    if (st != NHQ_OK) {
+        std::string keep = g_err;
+        nhq_free(ix);
+        g_err = keep;
+        *out = nullptr;
+        return st;
+    }
+    *out = ix;
+    return NHQ_OK;
+}
+
+nhq_status nhq_brute_force(const nhq_index *cix, const float *queries,
+                           const uint8_t *query_attributes, int64_t Q, int32_t k,
+                           const nhq_weights *w, uint32_t *ids, float *dists, uint8_t *chi,
+                           void *stream) {
+    nhq_index *ix = const_cast<nhq_index *>(cix);
+    if (ix == nullptr)
+        return fail(NHQ_ERR_ARG, "index is NULL");
+    if (Q < 0)
+        return fail(NHQ_ERR_ARG, "Q must be >= 0");
+    if (k < 1 || k > kMaxK)
+        return fail(NHQ_ERR_ARG, "k must be in 1..256 (got %d)", k);
+    if (Q == 0)
+        return NHQ_OK;
+    if (queries == nullptr || query_attributes == nullptr || ids == nullptr)
+        return fail(NHQ_ERR_ARG, "queries, query_attributes and ids are required");
+    nhq_weights ww = w ? *w : ix->w;
+    CKS(check_weights(ww, true));
+    cudaStream_t s = as_stream(stream);
+    Stager st;
+    int iq = st.add(queries, sizeof(float) * (size_t)Q * ix->d, true);
+    int ia = st.add(query_attributes, (size_t)Q * ix->m, true);
+    int io = st.add(ids, sizeof(uint32_t) * (size_t)Q * k, false);
+    int id = st.add(dists, sizeof(float) * (size_t)Q * k, false);
+    int ic = st.add(chi, (size_t)Q * k, false);
+    CKS(st.commit(&g_stage.p, &g_stage.cap, s));
+    TopkArgs a;
+    a.X = ix->X;
+    a.xstride = ix->xstride;
+    a.d = ix->d;
+    a.N = ix->N;
+    a.attr = ix->attr;
+    a.Q = (const float *)st.dev(iq);
+    a.qstride = ix->d;
+    a.nq = Q;
+    a.k = k;
+    a.exclude_self = 0;
+    a.w = make_fusion(ww, ix->m);
+    a.ids = (uint32_t *)st.dev(io);
+    a.dists = (float *)st.dev(id);
+    a.chi = (uint8_t *)st.dev(ic);
+    size_t qa_bytes = ((sizeof(uint32_t) * (size_t)Q) + 255) & ~(size_t)255;
+    size_t need = qa_bytes + topk_scratch_bytes(a, ix->sm_count);
+    CKS(scratch(ix, need));
+    uint32_t *qa = reinterpret_cast<uint32_t *>(ix->scratch);
+    CK(launch_pack_attributes((const uint8_t *)st.dev(ia), Q, ix->m, qa, s));
+    a.qattr = qa;
+    CK(launch_topk(a, (char *)ix->scratch + qa_bytes, ix->scratch_bytes - qa_bytes, ix->sm_count,
+                   s));
+    return st.finish(s);
+}
+
+static nhq_status search_common(const nhq_index *cix, const float *queries,
+                                const uint8_t *query_attributes, int64_t Q, const int32_t *k_arr,
+                                const int32_t *ef_arr, int32_t k, int32_t ef, int32_t k_out,
+                                const nhq_search_params *p, uint32_t *ids, float *dists,
+                                uint8_t *chi, int32_t *status, int32_t *ndc, void *stream) {
+    nhq_index *ix = const_cast<nhq_index *>(cix);
+    cudaStream_t s = as_stream(stream);
+    nhq_search_params P{};
+    if (p)
+        P = *p;
+    if (P.h < 1)
+        P.h = 1;
+    if (P.h > kMaxDegree)
+        return fail(NHQ_ERR_ARG, "h must be in 1..64");
+    if (P.max_iters <= 0)
+        P.max_iters = 1 << 20;
+    if (P.vec_dtype != NHQ_VEC_F32 && P.vec_dtype != NHQ_VEC_BF16)
+        return fail(NHQ_ERR_ARG, "unknown vec_dtype %d", P.vec_dtype);
+    if (P.hash_bits < 0 || P.hash_bits > 16)
+        return fail(NHQ_ERR_ARG, "hash_bits must be in 0..16");
+    if (P.warps_per_block < 0 || P.warps_per_block > 8)
+        return fail(NHQ_ERR_ARG, "warps_per_block must be in 0..8");
+    if (P.vec_dtype == NHQ_VEC_BF16 && ix->Xh == nullptr) {
+        CK(cudaMalloc(&ix->Xh, sizeof(__nv_bfloat16) * (size_t)ix->N * ix->xstride));
+        CK(launch_rows_to_bf16(ix->X, (int64_t)ix->N * ix->xstride, ix->Xh, s));
+    }
+    Stager st;
+    int iq = st.add(queries, sizeof(float) * (size_t)Q * ix->d, true);
+    int ia = st.add(query_attributes, (size_t)Q * ix->m, true);
+    int ik = st.add(k_arr, sizeof(int32_t) * (size_t)Q, true);
+    int ie = st.add(ef_arr, sizeof(int32_t) * (size_t)Q, true);
+    int io = st.add(ids, sizeof(uint32_t) * (size_t)Q * k_out, false);
+    int id = st.add(dists, sizeof(float) * (size_t)Q * k_out, false);
+    int ic = st.add(chi, (size_t)Q * k_out, false);
+    int is = st.add(status, sizeof(int32_t) * (size_t)Q, false);
+    int in = st.add(ndc, sizeof(int32_t) * (size_t)Q, false);
+    CKS(st.commit(&g_stage.p, &g_stage.cap, s));
+    SearchArgs a{};
+    a.X = ix->X;
+    a.Xh = ix->Xh;
+    a.xstride = ix->xstride;
+    a.d = ix->d;
+    a.N = ix->N;
+    a.attr = ix->attr;
+    a.nbr = ix->nbr;
+    a.nbr_attr = ix->nbr_attr;
+    a.R = ix->R;
+    a.w = make_fusion(ix->w, ix->m);
+    a.Q = (const float *)st.dev(iq);
+    a.qstride = ix->d;
+    a.qattr = (const uint8_t *)st.dev(ia);
+    a.nq = Q;
+    a.k_arr = (const int32_t *)st.dev(ik);
+    a.ef_arr = (const int32_t *)st.dev(ie);
+    a.k = k;
+    a.ef = ef;
+    a.k_out = k_out;
+    a.h = P.h;
+    a.seed = P.seed;
+    a.max_iters = P.max_iters;
+    a.vec_dtype = P.vec_dtype;
+    a.rerank = P.rerank;
+    a.ids = (uint32_t *)st.dev(io);
+    a.dists = (float *)st.dev(id);
+    a.chi = (uint8_t *)st.dev(ic);
+    a.status = (int32_t *)st.dev(is);
+    a.ndc = (int32_t *)st.dev(in);
+    a.warps_per_block = P.warps_per_block;
+    a.hash_bits = P.hash_bits;
+    CKS(scratch(ix, search_scratch_bytes()));
+    cudaError_t e = launch_search(a, ix->scratch, ix->sm_count, ix->smem_optin, s);
+    if (e == cudaErrorInvalidValue)
+        return fail(NHQ_ERR_ARG, "search launch: ef/hash_bits/warps_per_block do not fit shared memory");
+    if (e != cudaSuccess)
+        return fail_cuda(e, "search kernel launch");
+    return st.finish(s);
+}
+
+nhq_status nhq_search(const nhq_index *ix, const float *queries, const uint8_t *query_attributes,
+                      int64_t Q, int32_t k, int32_t ef, const nhq_search_params *params,
+                      uint32_t *ids, float *dists, uint8_t *chi, int32_t *status, int32_t *ndc,
+                      void *stream) {
+    if (ix == nullptr)
+        return fail(NHQ_ERR_ARG, "index is NULL");
+    if (ix->nbr == nullptr)
+        return fail(NHQ_ERR_ARG, "the index has no graph (build or set one first)");
+    if (Q < 0)
+        return fail(NHQ_ERR_ARG, "Q must be >= 0");
+    if (k < 1 || k > kMaxK)
+        return fail(NHQ_ERR_ARG, "k must be in 1..256 (got %d)", k);
+    if (ef < k || ef > kMaxEf)
+        return fail(NHQ_ERR_ARG, "ef must be in k..1024 (got %d)", ef);
+    if (Q == 0)
+        return NHQ_OK;
+    if (queries == nullptr || query_attributes == nullptr || ids == nullptr)
+        return fail(NHQ_ERR_ARG, "queries, query_attributes and ids are required");
+    return search_common(ix, queries, query_attributes, Q, nullptr, nullptr, k, ef, k, params, ids,
+                         dists, chi, status, ndc, stream);
+}
+
+nhq_status nhq_search_batched(const nhq_index *ix, const float *queries,
+                              const uint8_t *query_attributes, int64_t Q, const int32_t *k_arr,
+                              const int32_t *ef_arr, int32_t k_max,
+                              const nhq_search_params *params, uint32_t *ids, float *dists,
+                              uint8_t *chi, int32_t *status, int32_t *ndc, void *stream) {
+    if (ix == nullptr)
+        return fail(NHQ_ERR_ARG, "index is NULL");
+    if (ix->nbr == nullptr)
+        return fail(NHQ_ERR_ARG, "the index has no graph (build or set one first)");
+    if (Q < 0)
+        return fail(NHQ_ERR_ARG, "Q must be >= 0");
+    if (k_max < 1 || k_max > kMaxK)
+        return fail(NHQ_ERR_ARG, "k_max must be in 1..256 (got %d)", k_max);
+    if (Q == 0)
+        return NHQ_OK;
+    if (queries == nullptr || query_attributes == nullptr || ids == nullptr || k_arr == nullptr ||
+        ef_arr == nullptr)
+        return fail(NHQ_ERR_ARG, "queries, query_attributes, k_arr, ef_arr and ids are required");
+    // the per-query values bound the pool size, so they are read on the host
+    std::vector<int32_t> hk((size_t)Q), he((size_t)Q);
+    cudaStream_t s = as_stream(stream);
+    CK(cudaMemcpyAsync(hk.data(), k_arr, sizeof(int32_t) * Q, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(he.data(), ef_arr, sizeof(int32_t) * Q, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    int ef_max = 1;
+    for (int64_t i = 0; i < Q; ++i) {
+        if (hk[i] < 1 || hk[i] > k_max)
+            return fail(NHQ_ERR_ARG, "k_arr[%lld] = %d outside 1..k_max", (long long)i, hk[i]);
+        if (he[i] < hk[i] || he[i] > kMaxEf)
+            return fail(NHQ_ERR_ARG, "ef_arr[%lld] = %d outside k..1024", (long long)i, he[i]);
+        ef_max = he[i] > ef_max ? he[i] : ef_max;
+    }
+    return search_common(ix, queries, query_attributes, Q, k_arr, ef_arr, k_max, ef_max, k_max,
+                         params, ids, dists, chi, status, ndc, stream);
+}
+
+static const char kMagic[8] = {'N', 'H', 'Q', 'I', 'D', 'X', '0', '1'};
+
+nhq_status nhq_save(const nhq_index *ix, const char *path) {
+    if (ix == nullptr || path == nullptr)
+        return fail(NHQ_ERR_ARG, "index and path are required");
+    FILE *f = fopen(path, "wb");
+    if (!f)
+        return fail(NHQ_ERR_IO, "cannot open %s for writing", path);
+    const size_t N = (size_t)ix->N;
+    std::vector<float> row((size_t)ix->xstride * 4096);
+    std::vector<uint32_t> attr(N), nbr(N * (size_t)ix->R);
+    int32_t hdr[8] = {1, (int32_t)(ix->N & 0x7FFFFFFF), ix->d, ix->m, ix->R, ix->w.mode, 0, 0};
+    float wts[2] = {ix->w.w_v, ix->w.w_l};
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              fwrite(wts, sizeof(wts), 1, f) == 1;
+    cudaError_t e = cudaSuccess;
+    for (size_t r0 = 0; ok && r0 < N; r0 += 4096) {
+        size_t nr = N - r0 < 4096 ? N - r0 : 4096;
+        e = cudaMemcpy(row.data(), ix->X + r0 * ix->xstride, sizeof(float) * nr * ix->xstride,
+                       cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            break;
+        for (size_t r = 0; ok && r < nr; ++r)
+            ok = fwrite(row.data() + r * ix->xstride, sizeof(float), ix->d, f) == (size_t)ix->d;
+    }
+    if (e == cudaSuccess && ok)
+        e = cudaMemcpy(attr.data(), ix->attr, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && ok && ix->R > 0)
+        e = cudaMemcpy(nbr.data(), ix->nbr, sizeof(uint32_t) * nbr.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && ok)
+        ok = fwrite(attr.data(), sizeof(uint32_t), N, f) == N &&
+             fwrite(nbr.data(), sizeof(uint32_t), nbr.size(), f) == nbr.size();
+    bool closed = fclose(f) == 0;
+    if (e != cudaSuccess)
+        return fail_cuda(e, "nhq_save copy");
+    if (!ok || !closed)
+        return fail(NHQ_ERR_IO, "write to %s failed", path);
+    return NHQ_OK;
+}
+
+nhq_status nhq_load(const char *path, void *stream, nhq_index **out) {
+    if (path == nullptr || out == nullptr)
+        return fail(NHQ_ERR_ARG, "path and out are required");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f)
+        return fail(NHQ_ERR_IO, "cannot open %s", path);
+    char magic[8];
+    int32_t hdr[8];
+    float wts[2];
+    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kMagic, 8) != 0 ||
+        fread(hdr, sizeof(hdr), 1, f) != 1 || fread(wts, sizeof(wts), 1, f) != 1 || hdr[0] != 1 ||
+        hdr[1] < 1 || hdr[2] < 1 || hdr[3] < 1 || hdr[3] > 4 || hdr[4] < 0 ||
+        hdr[4] > kMaxDegree) {
+        fclose(f);
+        return fail(NHQ_ERR_IO, "%s is not an index file of version 1", path);
+    }
+    const size_t N = (size_t)hdr[1], d = (size_t)hdr[2], m = (size_t)hdr[3], R = (size_t)hdr[4];
+    std::vector<float> X(N * d);
+    std::vector<uint32_t> attr(N), nbr(N * R);
+    bool ok = fread(X.data(), sizeof(float), X.size(), f) == X.size() &&
+              fread(attr.data(), sizeof(uint32_t), N, f) == N &&
+              fread(nbr.data(), sizeof(uint32_t), nbr.size(), f) == nbr.size();
+    fclose(f);
+    if (!ok)
+        return fail(NHQ_ERR_IO, "%s is truncated", path);
+    std::vector<uint8_t> a8(N * m);
+    for (size_t i = 0; i < N; ++i)
+        for (size_t j = 0; j < m; ++j)
+            a8[i * m + j] = (uint8_t)(attr[i] >> (8 * j));
+    nhq_weights w{hdr[5], wts[0], wts[1]};
+    nhq_index *ix = nullptr;
+    CKS(nhq_index_create(X.data(), (int64_t)N, (int32_t)d, a8.data(), (int32_t)m, w, stream, &ix));
+    if (R > 0) {
+        nhq_status st = nhq_index_set_graph(ix, nbr.data(), (int32_t)R, stream);
+        if (st != NHQ_OK) {
+            nhq_free(ix);
+            return st;
+        }
+    }
+    *out = ix;
+    return NHQ_OK;
+}
+
+}  // extern "C"

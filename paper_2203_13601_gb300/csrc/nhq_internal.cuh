@@ -1,0 +1,168 @@
+// nhq_internal.cuh -- device helpers and launch declarations shared by the
+// library's translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/nhq.h"
+
+namespace nhq {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;                 // empty id / hash slot
+constexpr unsigned long long kInfKey = ~0ull;           // key larger than any record
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;      // splitmix64 increment
+constexpr int kMaxDegree = 64;
+constexpr int kMaxK = 256;
+constexpr int kMaxEf = 1024;
+constexpr int kMaxCand = 128;
+
+// Fusion-distance weights (Eq. 6) as the kernels see them.
+struct Fusion {
+    int mode;  // nhq_weight_mode
+    float wv, wl;
+    int m;
+    uint32_t mask;  // low 8*m bits set
+};
+
+// ---- splitmix64 (Vigna): the finaliser and the j-th output of a stream ----
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t splitmix_at(uint64_t s0, uint64_t j) {
+    return mix64(s0 + (j + 1) * kGolden);
+}
+
+// chi (Eq. 4-5) on packed attribute words: number of differing bytes among the m used.
+__device__ __forceinline__ int chi_packed(uint32_t a, uint32_t b, uint32_t mask) {
+    return __popc(__vcmpne4((a ^ b) & mask, 0u)) >> 3;
+}
+
+// Gamma (Eq. 6) from delta and chi, each operation rounded once (round-to-nearest),
+// so it equals the canonical f32 evaluation of the formula.
+__device__ __forceinline__ float fusion_gamma(float delta, int chi, const Fusion &w) {
+    if (w.mode == NHQ_W_PROPORTIONAL) {
+        float wl = __fdiv_rn(delta, (float)w.m);
+        return __fadd_rn(delta, __fmul_rn(wl, (float)chi));
+    }
+    if (w.mode == NHQ_W_CONSTANT)
+        return __fadd_rn(__fmul_rn(w.wv, delta), __fmul_rn(w.wl, (float)chi));
+    return chi == 0 ? delta : __int_as_float(0x7f800000);  // NHQ_W_FILTER
+}
+
+// A record (Gamma, id) as one u64 whose unsigned order is the lexicographic
+// order on (Gamma, id) for Gamma >= 0 (+inf included).  Bit 0 is a free flag.
+__device__ __forceinline__ unsigned long long make_key(float g, uint32_t id) {
+    return ((unsigned long long)__float_as_uint(g) << 32) | ((unsigned long long)id << 1);
+}
+__device__ __forceinline__ uint32_t key_id(unsigned long long k) {
+    return (uint32_t)(k >> 1) & 0x7FFFFFFFu;
+}
+__device__ __forceinline__ float key_gamma(unsigned long long k) {
+    return __uint_as_float((uint32_t)(k >> 32));
+}
+
+}  // namespace nhq
+
+// ---------------------------------------------------------------- host side
+struct nhq_index {
+    int64_t N = 0;
+    int d = 0, m = 0, R = 0;
+    int xstride = 0;  // floats per stored row (d rounded up to a multiple of 4)
+    nhq_weights w{};
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    float *X = nullptr;            // [N][xstride] f32
+    __nv_bfloat16 *Xh = nullptr;   // [N][xstride] bf16 copy (built on first BF16 search)
+    uint32_t *attr = nullptr;      // [N] packed attributes
+    uint32_t *nbr = nullptr;       // [N][R] adjacency, kNone padded
+    uint32_t *nbr_attr = nullptr;  // [N][R] packed attributes of each neighbour
+    // scratch arena (grown on demand, owned by the index)
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+namespace nhq {
+
+nhq::Fusion make_fusion(const nhq_weights &w, int m);
+
+// k_util.cu
+cudaError_t launch_pack_attributes(const uint8_t *a, int64_t n, int m, uint32_t *out, cudaStream_t s);
+cudaError_t launch_copy_rows(const float *src, int64_t N, int d, int xstride, float *dst,
+                             int *nonfinite_flag, cudaStream_t s);
+cudaError_t launch_rows_to_bf16(const float *src, int64_t n_elems, __nv_bfloat16 *dst, cudaStream_t s);
+cudaError_t launch_gather_nbr_attr(const uint32_t *nbr, const uint32_t *attr, int64_t N, int R,
+                                   uint32_t *out, int *bad, cudaStream_t s);
+
+// k_bruteforce.cu -- exact top-k by (Gamma, id); also the exact candidate sets
+struct TopkArgs {
+    const float *X;
+    int xstride;
+    int d;
+    int64_t N;
+    const uint32_t *attr;
+    const float *Q;
+    int qstride;
+    const uint32_t *qattr;
+    int64_t nq;
+    int k;
+    int exclude_self;  // query q is object q (candidate sets)
+    Fusion w;
+    uint32_t *ids;     // [nq][k]
+    float *dists;      // [nq][k] or null
+    uint8_t *chi;      // [nq][k] or null
+};
+size_t topk_scratch_bytes(const TopkArgs &a, int sm_count);
+cudaError_t launch_topk(const TopkArgs &a, void *scratch, size_t scratch_bytes, int sm_count,
+                        cudaStream_t s);
+
+// k_edge.cu
+cudaError_t launch_edge_select(const nhq_index *ix, const uint32_t *cand, int L, int R,
+                               uint32_t *out, cudaStream_t s);
+size_t reverse_scratch_bytes(int64_t N, int R);
+cudaError_t launch_reverse_candidates(const uint32_t *nbr, int64_t N, int R, int cap,
+                                      uint32_t *out, void *scratch, cudaStream_t s);
+
+// k_search.cu
+struct SearchArgs {
+    const float *X;
+    const __nv_bfloat16 *Xh;
+    int xstride;
+    int d;
+    int64_t N;
+    const uint32_t *attr;
+    const uint32_t *nbr;
+    const uint32_t *nbr_attr;
+    int R;
+    Fusion w;
+    const float *Q;
+    int qstride;
+    const uint8_t *qattr;  // [nq][m] u8
+    int64_t nq;
+    const int32_t *k_arr;  // per-query k or null
+    const int32_t *ef_arr;
+    int k, ef;             // uniform values (or maxima when arrays are given)
+    int k_out;             // row width of the outputs
+    int h;
+    uint64_t seed;
+    int max_iters;
+    int vec_dtype;
+    int rerank;
+    uint32_t *ids;
+    float *dists;
+    uint8_t *chi;
+    int32_t *status;
+    int32_t *ndc;
+    unsigned long long *counter;  // scratch work counter (zeroed by the launcher)
+    int warps_per_block;
+    int hash_bits;
+};
+size_t search_scratch_bytes();
+cudaError_t launch_search(SearchArgs a, void *scratch, int sm_count, size_t smem_optin,
+                          cudaStream_t s);
+
+}  // namespace nhq

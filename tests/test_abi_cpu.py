@@ -1,0 +1,107 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol declared in include/*.h, and rejects bad arguments before any CUDA work."""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2203_13601_gb300 import build as B
+
+    B.build()
+    import paper_2203_13601_gb300 as nhq
+
+    return nhq.load_library()
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(nhq_[a-z_0-9]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("nhq_build", "nhq_search", "nhq_search_batched", "nhq_brute_force",
+                     "nhq_knn", "nhq_edge_select", "nhq_save", "nhq_load", "nhq_free"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_mirrors_the_abi():
+    import paper_2203_13601_gb300 as nhq
+
+    missing = [n for n in _declared_functions() if not hasattr(nhq, n)]
+    assert not missing, missing
+
+
+def test_version_and_empty_error(lib):
+    import paper_2203_13601_gb300 as nhq
+
+    assert nhq.nhq_version() == 1
+    assert isinstance(nhq.nhq_last_error(), str)
+
+
+def test_argument_errors_before_cuda(lib):
+    import paper_2203_13601_gb300 as nhq
+
+    out = C.c_void_p()
+    w = nhq._Weights(0, 1.0, 0.0)
+    x = np.zeros((4, 3), np.float32)
+    a = np.zeros((4, 5), np.uint8)
+    # m = 5 attributes is outside 1..4
+    st = lib.nhq_index_create(x.ctypes.data, 4, 3, a.ctypes.data, 5, w, None, C.byref(out))
+    assert st == nhq.ERR_ARG and out.value is None
+    assert "m must be" in nhq.nhq_last_error()
+    # N = 0
+    st = lib.nhq_index_create(x.ctypes.data, 0, 3, a.ctypes.data, 2, w, None, C.byref(out))
+    assert st == nhq.ERR_ARG
+    # negative constant weight
+    st = lib.nhq_index_create(x.ctypes.data, 4, 3, a.ctypes.data, 2, nhq._Weights(1, -1.0, 1.0),
+                              None, C.byref(out))
+    assert st == nhq.ERR_ARG
+    # NULL index everywhere
+    p = nhq._SearchParams()
+    assert lib.nhq_search(None, None, None, 1, 10, 10, C.byref(p), None, None, None, None, None,
+                          None) == nhq.ERR_ARG
+    assert lib.nhq_brute_force(None, None, None, 1, 10, None, None, None, None, None) == nhq.ERR_ARG
+    assert lib.nhq_index_build(None, 32, None, None) == nhq.ERR_ARG
+    assert lib.nhq_save(None, b"/tmp/x") == nhq.ERR_ARG
+    lib.nhq_free(None)  # no-op
+
+
+def test_load_rejects_missing_and_corrupt_files(lib, tmp_path):
+    import paper_2203_13601_gb300 as nhq
+
+    out = C.c_void_p()
+    assert lib.nhq_load(str(tmp_path / "absent.idx").encode(), None, C.byref(out)) == nhq.ERR_IO
+    bad = tmp_path / "bad.idx"
+    bad.write_bytes(b"NOTANIDX" + b"\0" * 64)
+    assert lib.nhq_load(str(bad).encode(), None, C.byref(out)) == nhq.ERR_IO
+    assert "not an index file" in nhq.nhq_last_error()
+
+
+def test_binding_type_checks():
+    import paper_2203_13601_gb300 as nhq
+
+    with pytest.raises(TypeError):
+        nhq._ptr(np.zeros(3, np.float64), np.float32)
+    with pytest.raises(ValueError):
+        nhq._ptr(np.zeros((3, 4), np.float32).T, np.float32)
+    with pytest.raises(ValueError):
+        nhq._ptr(np.zeros((3, 4), np.float32), np.float32, (4, 3))
