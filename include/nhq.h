@@ -74,14 +74,28 @@ typedef struct nhq_build_params {
     int32_t reserved;
 } nhq_build_params;
 
+/* How the seed set B of Alg. 2 is chosen (the paper draws it at random). */
+typedef enum nhq_seed_mode {
+    NHQ_SEED_RANDOM = 0,    /* first min(ef, 32) distinct ids of splitmix64(seed ^ mix64(q)) mod N,
+                               at most 64 draws                                              */
+    NHQ_SEED_ATTRIBUTE = 1, /* P = objects whose attributes all equal the query's, ascending id;
+                               c = |P| >= 1: S = min(ef, 32, c), B = {P[floor(j*c/S)] : j < S};
+                               c = 0: as NHQ_SEED_RANDOM                                     */
+    NHQ_SEED_GIVEN = 2      /* B = the valid distinct ids of seeds[q][0..n_seeds)            */
+} nhq_seed_mode;
+
 typedef struct nhq_search_params {
-    uint64_t seed;           /* seeds B and S1 neighbour subsets derive from splitmix64(seed) */
+    uint64_t seed;           /* random seeds and S1 neighbour subsets derive from splitmix64(seed) */
     int32_t h;               /* two-stage routing: S1 visits ceil(R/h) neighbours; 1 = off     */
     int32_t max_iters;       /* expansion cap per query; 0 -> 1<<20                             */
     int32_t warps_per_block; /* 0 -> auto                                                      */
     int32_t hash_bits;       /* visited-filter size 2^hash_bits per query; 0 -> auto          */
     int32_t vec_dtype;       /* nhq_vec_dtype used for candidate scoring                       */
     int32_t rerank;          /* with BF16 scoring: recompute Gamma of the final pool in f32    */
+    int32_t seed_mode;       /* nhq_seed_mode                                                   */
+    int32_t n_seeds;         /* NHQ_SEED_GIVEN: row width of `seeds`, 1..64                     */
+    const uint32_t *seeds;   /* NHQ_SEED_GIVEN: [Q][n_seeds] ids (device or host), 0xFFFFFFFF
+                                entries are skipped                                           */
 } nhq_search_params;
 
 typedef struct nhq_index nhq_index;
@@ -184,16 +198,16 @@ nhq_status nhq_brute_force(const nhq_index *index, const float *queries,
  * when params->h > 1.  Per query: a pool of ef records sorted by (Gamma, id);
  * repeatedly expand the nearest unexpanded record and evaluate its neighbours
  * not evaluated before; stop when every record is expanded; return the first k.
- * Seeds: the first min(ef, 32) distinct ids of the splitmix64 stream started at
- * seed ^ mix64(q) (q = row index within this call), reduced mod N, at most 64 draws.
- * Outputs: ids/dists/chi [Q][k]; status[Q] (NHQ_OK or NHQ_ERR_ITER_LIMIT) and
- * ndc[Q] (vector-distance evaluations) may be NULL.  Errors: no graph, k < 1,
- * ef < k, ef > 1024, Q < 0.  Q = 0 is a no-op.
+ * Seeds: params->seed_mode (nhq_seed_mode; q = row index within this call).
+ * Outputs: ids/dists/chi [Q][k]; status[Q] (NHQ_OK or NHQ_ERR_ITER_LIMIT),
+ * ndc[Q] (vector-distance evaluations) and expansions[Q] (expanded vertices)
+ * may be NULL.  Errors: no graph, k < 1, ef < k, ef > 1024, Q < 0.  Q = 0 is a
+ * no-op.
  */
 nhq_status nhq_search(const nhq_index *index, const float *queries,
                       const uint8_t *query_attributes, int64_t Q, int32_t k, int32_t ef,
                       const nhq_search_params *params, uint32_t *ids, float *dists, uint8_t *chi,
-                      int32_t *status, int32_t *ndc, void *stream);
+                      int32_t *status, int32_t *ndc, int32_t *expansions, void *stream);
 
 /*
  * Heterogeneous batch in one launch: query q uses k_arr[q] and ef_arr[q]
@@ -206,7 +220,8 @@ nhq_status nhq_search_batched(const nhq_index *index, const float *queries,
                               const uint8_t *query_attributes, int64_t Q, const int32_t *k_arr,
                               const int32_t *ef_arr, int32_t k_max,
                               const nhq_search_params *params, uint32_t *ids, float *dists,
-                              uint8_t *chi, int32_t *status, int32_t *ndc, void *stream);
+                              uint8_t *chi, int32_t *status, int32_t *ndc, int32_t *expansions,
+                              void *stream);
 
 /*
  * Index persistence: header {magic "NHQIDX01", version, N, d, m, R, weights}

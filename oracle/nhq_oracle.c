@@ -387,8 +387,8 @@ double or_graph_quality(const int64_t *nbr, int64_t N, int R, const int64_t *knn
 /* pool  : at most ef records sorted by (Gamma, id), each with an      */
 /*         "expanded" flag; it is R of Alg. 2 and its unexpanded part  */
 /*         is C.                                                       */
-/* seeds : B = the first min(ef, 32) distinct ids among the splitmix64 */
-/*         stream s0 = seed ^ mix64(q), id_j = out_j mod N, j < 64.    */
+/* seeds : B, see or_search below (random stream, attribute entry or  */
+/*         given ids).                                                 */
 /* step  : take the smallest unexpanded record u (line 3), mark it     */
 /*         expanded; evaluate each not-yet-evaluated neighbour v of u  */
 /*         in adjacency order (lines 4-5); insert v if the pool holds  */
@@ -429,10 +429,18 @@ static int pool_insert(pool_t *pool, int *n, int ef, double g, int64_t id)
     return 1;
 }
 
+/* Seed set B (Alg. 2 takes it as an input):
+ *   seed_mode 0  random: the first min(ef, 32) distinct ids of the splitmix64
+ *                stream s0 = seed ^ mix64(q), id_j = out_j mod N, j < 64
+ *   seed_mode 1  attribute entry: P = the objects whose attributes all equal the
+ *                query's, in ascending id; with c = |P| >= 1 and S = min(ef, 32, c),
+ *                B = { P[floor(j * c / S)] : j < S }; with c = 0, as mode 0
+ *   seed_mode 2  given: the valid distinct ids of seeds_in[q][0..n_seeds), in order */
 void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                const int64_t *nbr, int R, const float *Qv, const uint8_t *QA, int64_t nq,
                int k, int ef, int h, uint64_t seed, int64_t max_iters,
-               int mode, double wv, double wl, int prec,
+               int mode, double wv, double wl, int prec, int seed_mode,
+               const int64_t *seeds_in, int n_seeds,
                int64_t *out_ids, double *out_g, int32_t *out_chi,
                int64_t *out_ndc, int64_t *out_exp, int32_t *out_status)
 {
@@ -454,17 +462,52 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
         uint64_t s0 = seed ^ or_mix64((uint64_t)q);
 
         /* seed set B */
-        int want = ef < 32 ? ef : 32, got = 0;
-        for (uint64_t j = 0; j < 64 && got < want && N > 0; ++j) {
-            int64_t v = (int64_t)(or_splitmix64_at(s0, j) % (uint64_t)N);
-            if (evaluated[v])
-                continue;
-            evaluated[v] = 1;
-            ++ndc;
-            ++got;
-            double g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m, mode,
-                                  wv, wl, prec, NULL);
-            pool_insert(pool, &n, ef, g, v);
+        int want = ef < 32 ? ef : 32;
+        int64_t c = 0;
+        if (seed_mode == 1)
+            for (int64_t v = 0; v < N; ++v)
+                c += or_chi(qa, A + v * (int64_t)m, m) == 0 ? 1 : 0;
+        if (seed_mode == 2) {
+            for (int j = 0; j < n_seeds; ++j) {
+                int64_t v = seeds_in[q * (int64_t)n_seeds + j];
+                if (v < 0 || v >= N || evaluated[v])
+                    continue;
+                evaluated[v] = 1;
+                ++ndc;
+                double g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m,
+                                      mode, wv, wl, prec, NULL);
+                pool_insert(pool, &n, ef, g, v);
+            }
+        } else if (seed_mode == 1 && c > 0) {
+            int S = (int64_t)want < c ? want : (int)c;
+            int64_t rank = 0;  /* position of v within P */
+            int j = 0;
+            for (int64_t v = 0; v < N && j < S; ++v) {
+                if (or_chi(qa, A + v * (int64_t)m, m) != 0)
+                    continue;
+                if (rank == ((int64_t)j * c) / S) {
+                    evaluated[v] = 1;
+                    ++ndc;
+                    double g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m,
+                                          mode, wv, wl, prec, NULL);
+                    pool_insert(pool, &n, ef, g, v);
+                    ++j;
+                }
+                ++rank;
+            }
+        } else {
+            int got = 0;
+            for (uint64_t j = 0; j < 64 && got < want && N > 0; ++j) {
+                int64_t v = (int64_t)(or_splitmix64_at(s0, j) % (uint64_t)N);
+                if (evaluated[v])
+                    continue;
+                evaluated[v] = 1;
+                ++ndc;
+                ++got;
+                double g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m,
+                                      mode, wv, wl, prec, NULL);
+                pool_insert(pool, &n, ef, g, v);
+            }
         }
 
         int stage = h > 1 ? 1 : 2;

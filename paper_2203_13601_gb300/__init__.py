@@ -22,6 +22,7 @@ import numpy as np
 __all__ = [
     "NHQError", "Index", "load_library", "library_path",
     "W_PROPORTIONAL", "W_CONSTANT", "W_FILTER", "VEC_F32", "VEC_BF16",
+    "SEED_RANDOM", "SEED_ATTRIBUTE", "SEED_GIVEN",
     "nhq_last_error", "nhq_version", "nhq_index_create", "nhq_free", "nhq_index_info",
     "nhq_pack_attributes", "nhq_knn", "nhq_edge_select", "nhq_reverse_candidates",
     "nhq_index_set_graph", "nhq_index_get_graph", "nhq_index_build", "nhq_build",
@@ -33,6 +34,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libnhq.so")
 
 W_PROPORTIONAL, W_CONSTANT, W_FILTER = 0, 1, 2
 VEC_F32, VEC_BF16 = 0, 1
+SEED_RANDOM, SEED_ATTRIBUTE, SEED_GIVEN = 0, 1, 2
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_ITER_LIMIT, ERR_IO = range(6)
 NONE_ID = 0xFFFFFFFF
 
@@ -55,7 +57,8 @@ class _BuildParams(C.Structure):
 class _SearchParams(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("h", C.c_int32), ("max_iters", C.c_int32),
                 ("warps_per_block", C.c_int32), ("hash_bits", C.c_int32),
-                ("vec_dtype", C.c_int32), ("rerank", C.c_int32)]
+                ("vec_dtype", C.c_int32), ("rerank", C.c_int32), ("seed_mode", C.c_int32),
+                ("n_seeds", C.c_int32), ("seeds", C.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -95,9 +98,9 @@ def load_library():
                               C.POINTER(P)]),
             "nhq_brute_force": (S, [P, P, P, i64, i32, C.POINTER(_Weights), P, P, P, P]),
             "nhq_search": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P, P, P, P, P,
-                               P]),
+                               P, P]),
             "nhq_search_batched": (S, [P, P, P, i64, P, P, i32, C.POINTER(_SearchParams), P, P, P,
-                                       P, P, P]),
+                                       P, P, P, P]),
             "nhq_save": (S, [P, C.c_char_p]),
             "nhq_load": (S, [C.c_char_p, P, C.POINTER(P)]),
         }
@@ -275,32 +278,44 @@ def nhq_brute_force(index, queries, query_attributes, k, ids, dists=None, chi=No
         _ptr(chi, np.uint8, (Q, k), "chi"), _stream(stream)))
 
 
-def _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank):
+def _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
+                   seed_mode=SEED_RANDOM, seeds=None, Q=None):
+    """Search parameters; ``seeds`` ([Q][n] uint32, 0xFFFFFFFF = none) selects SEED_GIVEN."""
+    n_seeds, sp = 0, None
+    if seeds is not None:
+        seed_mode = SEED_GIVEN
+        n_seeds = _shape(seeds)[1]
+        sp = _ptr(seeds, np.uint32, (Q, n_seeds), "seeds")
     return _SearchParams(int(seed) & (2**64 - 1), int(h), int(max_iters), int(warps_per_block),
-                         int(hash_bits), int(vec_dtype), int(rerank))
+                         int(hash_bits), int(vec_dtype), int(rerank), int(seed_mode),
+                         int(n_seeds), sp)
 
 
 def nhq_search(index, queries, query_attributes, k, ef, ids, dists=None, chi=None, status=None,
-               ndc=None, h=1, seed=0, max_iters=0, warps_per_block=0, hash_bits=0,
-               vec_dtype=VEC_F32, rerank=0, stream=None) -> None:
+               ndc=None, expansions=None, h=1, seed=0, max_iters=0, warps_per_block=0,
+               hash_bits=0, vec_dtype=VEC_F32, rerank=0, seed_mode=SEED_RANDOM, seeds=None,
+               stream=None) -> None:
     Q, d = _shape(queries)
     m = _shape(query_attributes)[1]
-    p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank)
+    p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
+                       seed_mode, seeds, Q)
     _check(load_library().nhq_search(
         index, _ptr(queries, np.float32, (Q, d), "queries"),
         _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, ef, C.byref(p),
         _ptr(ids, np.uint32, (Q, k), "ids"), _ptr(dists, np.float32, (Q, k), "dists"),
         _ptr(chi, np.uint8, (Q, k), "chi"), _ptr(status, np.int32, (Q,), "status"),
-        _ptr(ndc, np.int32, (Q,), "ndc"), _stream(stream)))
+        _ptr(ndc, np.int32, (Q,), "ndc"), _ptr(expansions, np.int32, (Q,), "expansions"),
+        _stream(stream)))
 
 
 def nhq_search_batched(index, queries, query_attributes, k_arr, ef_arr, k_max, ids, dists=None,
-                       chi=None, status=None, ndc=None, h=1, seed=0, max_iters=0,
-                       warps_per_block=0, hash_bits=0, vec_dtype=VEC_F32, rerank=0,
-                       stream=None) -> None:
+                       chi=None, status=None, ndc=None, expansions=None, h=1, seed=0,
+                       max_iters=0, warps_per_block=0, hash_bits=0, vec_dtype=VEC_F32, rerank=0,
+                       seed_mode=SEED_RANDOM, seeds=None, stream=None) -> None:
     Q, d = _shape(queries)
     m = _shape(query_attributes)[1]
-    p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank)
+    p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
+                       seed_mode, seeds, Q)
     _check(load_library().nhq_search_batched(
         index, _ptr(queries, np.float32, (Q, d), "queries"),
         _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q,
@@ -308,7 +323,7 @@ def nhq_search_batched(index, queries, query_attributes, k_arr, ef_arr, k_max, i
         C.byref(p), _ptr(ids, np.uint32, (Q, k_max), "ids"),
         _ptr(dists, np.float32, (Q, k_max), "dists"), _ptr(chi, np.uint8, (Q, k_max), "chi"),
         _ptr(status, np.int32, (Q,), "status"), _ptr(ndc, np.int32, (Q,), "ndc"),
-        _stream(stream)))
+        _ptr(expansions, np.int32, (Q,), "expansions"), _stream(stream)))
 
 
 def nhq_save(index, path) -> None:

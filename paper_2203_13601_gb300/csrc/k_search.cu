@@ -327,8 +327,30 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a, const VT *__r
         int status = NHQ_OK;
         const uint64_t s0 = a.seed ^ mix64((uint64_t)q);
 
-        // ---- seed set B: first min(ef, 32) distinct ids of the stream, <= 64 draws
-        const int want = min(ef, 32);
+        // ---- seed set B, given: the valid distinct ids of the row, all evaluated
+        for (int r = 0; a.seeds != nullptr && 32 * r < a.n_seeds; ++r) {
+            const int j = 32 * r + lane;
+            const uint32_t v = j < a.n_seeds ? a.seeds[q * a.n_seeds + j] : kNone;
+            const bool valid = v != kNone && (int64_t)v < a.N;
+            const unsigned same = __match_any_sync(FULL, v);
+            bool take = valid && (__ffs(same) - 1) == lane;
+            if (take)
+                take = hash_insert(hash, a.hash_bits, v);  // false if an earlier round had it
+            const unsigned kb = __ballot_sync(FULL, take);
+            if (take) {
+                const int p = __popc(kb & lanemask_lt(lane));
+                cid[p] = v;
+                cchi[p] = chi_packed(a.attr[v], qa, amask);
+            }
+            __syncwarp();
+            const int cnt = __popc(kb);
+            hcount += cnt;
+            ndc += cnt;
+            eval_candidates<VT>(Xs, a.xstride, qv, cid, cchi, cand, cnt, a.w, lane);
+            merge_into_pool(pool, n, ef, cand, cnt, cursor, lane);
+        }
+        // ---- seed set B, random: first min(ef, 32) distinct ids of the stream, <= 64 draws
+        const int want = a.seeds != nullptr ? 0 : min(ef, 32);
         int got = 0;
         for (int r = 0; r < 2 && got < want; ++r) {
             const uint32_t v = (uint32_t)(splitmix_at(s0, (uint64_t)(32 * r + lane)) %
@@ -491,6 +513,8 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a, const VT *__r
                 a.status[q] = status;
             if (a.ndc)
                 a.ndc[q] = ndc;
+            if (a.expansions)
+                a.expansions[q] = iters;
         }
         __syncwarp();
     }
@@ -506,7 +530,7 @@ int auto_hash_bits(int ef_cap, int R) {
 
 }  // namespace
 
-size_t search_scratch_bytes() { return 256; }
+size_t search_scratch_bytes(int64_t nq) { return 256 + sizeof(uint32_t) * 32 * (size_t)nq; }
 
 cudaError_t launch_search(SearchArgs a, void *scratch, int sm_count, size_t smem_optin,
                           cudaStream_t s) {

@@ -251,6 +251,8 @@ void nhq_free(nhq_index *ix) {
     cudaFree(ix->attr);
     cudaFree(ix->nbr);
     cudaFree(ix->nbr_attr);
+    cudaFree(ix->attr_sorted);
+    cudaFree(ix->id_sorted);
     cudaFree(ix->scratch);
     delete ix;
 }
@@ -501,7 +503,8 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
                                 const uint8_t *query_attributes, int64_t Q, const int32_t *k_arr,
                                 const int32_t *ef_arr, int32_t k, int32_t ef, int32_t k_out,
                                 const nhq_search_params *p, uint32_t *ids, float *dists,
-                                uint8_t *chi, int32_t *status, int32_t *ndc, void *stream) {
+                                uint8_t *chi, int32_t *status, int32_t *ndc, int32_t *expansions,
+                                void *stream) {
     nhq_index *ix = const_cast<nhq_index *>(cix);
     cudaStream_t s = as_stream(stream);
     nhq_search_params P{};
@@ -519,6 +522,17 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         return fail(NHQ_ERR_ARG, "hash_bits must be in 0..16");
     if (P.warps_per_block < 0 || P.warps_per_block > 8)
         return fail(NHQ_ERR_ARG, "warps_per_block must be in 0..8");
+    if (P.seed_mode < NHQ_SEED_RANDOM || P.seed_mode > NHQ_SEED_GIVEN)
+        return fail(NHQ_ERR_ARG, "unknown seed_mode %d", P.seed_mode);
+    if (P.seed_mode == NHQ_SEED_GIVEN && (P.seeds == nullptr || P.n_seeds < 1 || P.n_seeds > 64))
+        return fail(NHQ_ERR_ARG, "NHQ_SEED_GIVEN needs seeds and n_seeds in 1..64");
+    if (P.seed_mode == NHQ_SEED_ATTRIBUTE && ix->attr_sorted == nullptr) {
+        CK(cudaMalloc(&ix->attr_sorted, sizeof(uint32_t) * (size_t)ix->N));
+        CK(cudaMalloc(&ix->id_sorted, sizeof(uint32_t) * (size_t)ix->N));
+        CKS(scratch(ix, attribute_sort_scratch_bytes(ix->N)));
+        CK(launch_attribute_sort(ix->attr, ix->N, ix->attr_sorted, ix->id_sorted, ix->scratch,
+                                 ix->scratch_bytes, s));
+    }
     if (P.vec_dtype == NHQ_VEC_BF16 && ix->Xh == nullptr) {
         CK(cudaMalloc(&ix->Xh, sizeof(__nv_bfloat16) * (size_t)ix->N * ix->xstride));
         CK(launch_rows_to_bf16(ix->X, (int64_t)ix->N * ix->xstride, ix->Xh, s));
@@ -533,6 +547,10 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     int ic = st.add(chi, (size_t)Q * k_out, false);
     int is = st.add(status, sizeof(int32_t) * (size_t)Q, false);
     int in = st.add(ndc, sizeof(int32_t) * (size_t)Q, false);
+    int ix_ = st.add(expansions, sizeof(int32_t) * (size_t)Q, false);
+    int isd = st.add(P.seed_mode == NHQ_SEED_GIVEN ? P.seeds : nullptr,
+                     sizeof(uint32_t) * (size_t)Q * (P.seed_mode == NHQ_SEED_GIVEN ? P.n_seeds : 0),
+                     true);
     CKS(st.commit(&g_stage.p, &g_stage.cap, s));
     SearchArgs a{};
     a.X = ix->X;
@@ -564,9 +582,21 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     a.chi = (uint8_t *)st.dev(ic);
     a.status = (int32_t *)st.dev(is);
     a.ndc = (int32_t *)st.dev(in);
+    a.expansions = (int32_t *)st.dev(ix_);
     a.warps_per_block = P.warps_per_block;
     a.hash_bits = P.hash_bits;
-    CKS(scratch(ix, search_scratch_bytes()));
+    CKS(scratch(ix, search_scratch_bytes(Q)));
+    a.seeds = nullptr;
+    a.n_seeds = 0;
+    if (P.seed_mode == NHQ_SEED_GIVEN) {
+        a.seeds = (const uint32_t *)st.dev(isd);
+        a.n_seeds = P.n_seeds;
+    } else if (P.seed_mode == NHQ_SEED_ATTRIBUTE) {
+        uint32_t *sd = reinterpret_cast<uint32_t *>((char *)ix->scratch + 256);
+        CK(launch_attribute_seeds(a, ix->attr_sorted, ix->id_sorted, sd, s));
+        a.seeds = sd;
+        a.n_seeds = 32;
+    }
     cudaError_t e = launch_search(a, ix->scratch, ix->sm_count, ix->smem_optin, s);
     if (e == cudaErrorInvalidValue)
         return fail(NHQ_ERR_ARG, "search launch: ef/hash_bits/warps_per_block do not fit shared memory");
@@ -578,7 +608,7 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
 nhq_status nhq_search(const nhq_index *ix, const float *queries, const uint8_t *query_attributes,
                       int64_t Q, int32_t k, int32_t ef, const nhq_search_params *params,
                       uint32_t *ids, float *dists, uint8_t *chi, int32_t *status, int32_t *ndc,
-                      void *stream) {
+                      int32_t *expansions, void *stream) {
     if (ix == nullptr)
         return fail(NHQ_ERR_ARG, "index is NULL");
     if (ix->nbr == nullptr)
@@ -594,14 +624,15 @@ nhq_status nhq_search(const nhq_index *ix, const float *queries, const uint8_t *
     if (queries == nullptr || query_attributes == nullptr || ids == nullptr)
         return fail(NHQ_ERR_ARG, "queries, query_attributes and ids are required");
     return search_common(ix, queries, query_attributes, Q, nullptr, nullptr, k, ef, k, params, ids,
-                         dists, chi, status, ndc, stream);
+                         dists, chi, status, ndc, expansions, stream);
 }
 
 nhq_status nhq_search_batched(const nhq_index *ix, const float *queries,
                               const uint8_t *query_attributes, int64_t Q, const int32_t *k_arr,
                               const int32_t *ef_arr, int32_t k_max,
                               const nhq_search_params *params, uint32_t *ids, float *dists,
-                              uint8_t *chi, int32_t *status, int32_t *ndc, void *stream) {
+                              uint8_t *chi, int32_t *status, int32_t *ndc, int32_t *expansions,
+                              void *stream) {
     if (ix == nullptr)
         return fail(NHQ_ERR_ARG, "index is NULL");
     if (ix->nbr == nullptr)
@@ -630,7 +661,7 @@ nhq_status nhq_search_batched(const nhq_index *ix, const float *queries,
         ef_max = he[i] > ef_max ? he[i] : ef_max;
     }
     return search_common(ix, queries, query_attributes, Q, k_arr, ef_arr, k_max, ef_max, k_max,
-                         params, ids, dists, chi, status, ndc, stream);
+                         params, ids, dists, chi, status, ndc, expansions, stream);
 }
 
 static const char kMagic[8] = {'N', 'H', 'Q', 'I', 'D', 'X', '0', '1'};

@@ -81,6 +81,8 @@ struct nhq_index {
     uint32_t *attr = nullptr;      // [N] packed attributes
     uint32_t *nbr = nullptr;       // [N][R] adjacency, kNone padded
     uint32_t *nbr_attr = nullptr;  // [N][R] packed attributes of each neighbour
+    uint32_t *attr_sorted = nullptr;  // [N] packed attributes, ascending (stable radix sort)
+    uint32_t *id_sorted = nullptr;    // [N] object ids in that order
     // scratch arena (grown on demand, owned by the index)
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -157,11 +159,21 @@ struct SearchArgs {
     uint8_t *chi;
     int32_t *status;
     int32_t *ndc;
+    int32_t *expansions;
+    const uint32_t *seeds;  // [nq][n_seeds] given seed ids or null (random stream)
+    int n_seeds;
     unsigned long long *counter;  // scratch work counter (zeroed by the launcher)
     int warps_per_block;
     int hash_bits;
 };
-size_t search_scratch_bytes();
+size_t search_scratch_bytes(int64_t nq);
+cudaError_t launch_attribute_sort(const uint32_t *attr, int64_t N, uint32_t *attr_sorted,
+                                  uint32_t *id_sorted, void *scratch, size_t scratch_bytes,
+                                  cudaStream_t s);
+size_t attribute_sort_scratch_bytes(int64_t N);
+// Seeds of NHQ_SEED_ATTRIBUTE into seeds[nq][32] (rows padded with kNone).
+cudaError_t launch_attribute_seeds(const SearchArgs &a, const uint32_t *attr_sorted,
+                                   const uint32_t *id_sorted, uint32_t *seeds, cudaStream_t s);
 cudaError_t launch_search(SearchArgs a, void *scratch, int sm_count, size_t smem_optin,
                           cudaStream_t s);
 

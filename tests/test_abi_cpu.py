@@ -78,7 +78,7 @@ def test_argument_errors_before_cuda(lib):
     # NULL index everywhere
     p = nhq._SearchParams()
     assert lib.nhq_search(None, None, None, 1, 10, 10, C.byref(p), None, None, None, None, None,
-                          None) == nhq.ERR_ARG
+                          None, None) == nhq.ERR_ARG
     assert lib.nhq_brute_force(None, None, None, 1, 10, None, None, None, None, None) == nhq.ERR_ARG
     assert lib.nhq_index_build(None, 32, None, None) == nhq.ERR_ARG
     assert lib.nhq_save(None, b"/tmp/x") == nhq.ERR_ARG

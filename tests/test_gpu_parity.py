@@ -366,3 +366,47 @@ def test_save_load_roundtrip(nhq, graph_case, tmp_path):
         nhq.nhq_search(ix2.handle, dev(w.Qv), dev(w.QA), 10, 40, *b, seed=3)
         torch.cuda.synchronize()
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+# ------------------------------------------------------------------ seed sets B
+@pytest.mark.parametrize("wname", ["prop", "const"])
+@pytest.mark.parametrize("ef", [10, 20, 64])
+def test_search_attribute_entry_seeds_exact(nhq, graph_case, wname, ef):
+    w, graphs = graph_case
+    wts, nbr = graphs[wname]
+    QA = w.QA.copy()
+    QA[::7, 0] = 200  # tuples that no object has: the random stream is used for them
+    ref = O.search(w.X, w.A, nbr, w.Qv, QA, 10, ef, seed=21, weights=wts,
+                   seed_mode=O.SEED_ATTRIBUTE)
+    with _index(nhq, w, wts) as ix:
+        nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
+        ids, g, chi = empty_out(w.nq, 10)
+        ndc = torch.empty(w.nq, dtype=torch.int32, device="cuda:0")
+        nhq.nhq_search(ix.handle, dev(w.Qv), dev(QA), 10, ef, ids, g, chi, ndc=ndc, seed=21,
+                       seed_mode=nhq.SEED_ATTRIBUTE)
+        torch.cuda.synchronize()
+    assert (ids_i64(ids) == ref["ids"]).all()
+    assert np.array_equal(g.cpu().numpy().astype(np.float64), ref["gamma"])
+
+
+def test_search_given_seeds_exact(nhq, graph_case):
+    w, graphs = graph_case
+    wts, nbr = graphs["const"]
+    r = np.random.default_rng(3)
+    seeds = r.integers(0, w.N, (w.nq, 64)).astype(np.int64)
+    seeds[:, 5] = seeds[:, 0]           # repeats
+    seeds[r.random(seeds.shape) < 0.3] = -1
+    ref = O.search(w.X, w.A, nbr, w.Qv, w.QA, 10, 40, weights=wts, seeds=seeds)
+    with _index(nhq, w, wts) as ix:
+        nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
+        ids, g, chi = empty_out(w.nq, 10)
+        nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 40, ids, g, chi,
+                       seeds=dev(to_u32_graph(seeds)))
+        torch.cuda.synchronize()
+        # host seed array through the same call
+        ids2, g2, chi2 = empty_out(w.nq, 10)
+        nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 40, ids2, g2, chi2,
+                       seeds=to_u32_graph(seeds))
+        torch.cuda.synchronize()
+    assert (ids_i64(ids) == ref["ids"]).all()
+    assert torch.equal(ids, ids2)
