@@ -302,7 +302,7 @@ def main():
                 ms = time_once(ef, h, vec)
                 sweep.append({"ef": ef, "h": h, "vec": ["f32", "bf16"][vec], "recall": rec,
                               "ms": ms})
-                if rec >= a.target:
+                if rec >= a.target or cand_list:
                     found = (ef, h, vec, rec, ms)
                     break
             if found:
