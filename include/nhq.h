@@ -224,6 +224,30 @@ nhq_status nhq_search_batched(const nhq_index *index, const float *queries,
                               void *stream);
 
 /*
+ * Allocation-free brute-force top-k.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they call the
+ * library (their memory is owned by another allocator or pool, or their hot path
+ * must not touch an allocator).  It computes the same result as nhq_brute_force
+ * but takes raw arrays instead of an index and allocates nothing:
+ *   vectors[N][d] f32 (d a multiple of 4, 16-byte aligned), packed_attributes[N]
+ *   and packed_query_attributes[Q] (u32 words as written by nhq_pack_attributes),
+ *   queries[Q][d] f32, outputs ids/dists/chi[Q][k] (dists, chi may be NULL);
+ *   every pointer must be device memory.
+ * Its working memory is a fixed 16 MiB array inside the library, present on every
+ * GPU that loads the library until the process exits.  The first call on a device
+ * looks up that array's device address (make it before any stream capture).
+ * A call whose split lists would need more than 16 MiB (about Q * 32 * k * 8
+ * bytes for small batches) returns NHQ_ERR_ARG with the required size; nothing
+ * is written then.  Calls share the array: calls that overlap on the GPU (other
+ * streams or host threads) race and must be serialised by the caller.
+ */
+nhq_status nhq_brute_force_noalloc(const float *vectors, const uint32_t *packed_attributes,
+                                   int64_t N, int32_t d, int32_t m, const float *queries,
+                                   const uint32_t *packed_query_attributes, int64_t Q, int32_t k,
+                                   nhq_weights w, uint32_t *ids, float *dists, uint8_t *chi,
+                                   void *stream);
+
+/*
  * Index persistence: header {magic "NHQIDX01", version, N, d, m, R, weights}
  * then vectors (f32, unpadded rows), packed attributes (u32) and the graph (u32).
  * Errors: unreadable/unwritable file or bad header -> NHQ_ERR_IO.

@@ -27,6 +27,7 @@ __all__ = [
     "nhq_pack_attributes", "nhq_knn", "nhq_edge_select", "nhq_reverse_candidates",
     "nhq_index_set_graph", "nhq_index_get_graph", "nhq_index_build", "nhq_build",
     "nhq_brute_force", "nhq_search", "nhq_search_batched", "nhq_save", "nhq_load",
+    "nhq_brute_force_noalloc",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -101,6 +102,8 @@ def load_library():
                                P, P]),
             "nhq_search_batched": (S, [P, P, P, i64, P, P, i32, C.POINTER(_SearchParams), P, P, P,
                                        P, P, P, P]),
+            "nhq_brute_force_noalloc": (S, [P, P, i64, i32, i32, P, P, i64, i32, _Weights, P, P,
+                                            P, P]),
             "nhq_save": (S, [P, C.c_char_p]),
             "nhq_load": (S, [C.c_char_p, P, C.POINTER(P)]),
         }
@@ -324,6 +327,23 @@ def nhq_search_batched(index, queries, query_attributes, k_arr, ef_arr, k_max, i
         _ptr(dists, np.float32, (Q, k_max), "dists"), _ptr(chi, np.uint8, (Q, k_max), "chi"),
         _ptr(status, np.int32, (Q,), "status"), _ptr(ndc, np.int32, (Q,), "ndc"),
         _ptr(expansions, np.int32, (Q,), "expansions"), _stream(stream)))
+
+
+def nhq_brute_force_noalloc(vectors, packed_attributes, m, queries, packed_query_attributes, k,
+                            ids, dists=None, chi=None, weights=None, stream=None) -> None:
+    """Allocation-free brute-force top-k for callers that cannot allocate device
+    memory at call time; every array is a device tensor and ``m`` is the number of
+    attributes packed into each u32 word (see include/nhq.h)."""
+    N, d = _shape(vectors)
+    Q = _shape(queries)[0]
+    _check(load_library().nhq_brute_force_noalloc(
+        _ptr(vectors, np.float32, (N, d), "vectors"),
+        _ptr(packed_attributes, np.uint32, (N,), "packed_attributes"), N, d, int(m),
+        _ptr(queries, np.float32, (Q, d), "queries"),
+        _ptr(packed_query_attributes, np.uint32, (Q,), "packed_query_attributes"), Q, k,
+        _weights(weights), _ptr(ids, np.uint32, (Q, k), "ids"),
+        _ptr(dists, np.float32, (Q, k), "dists"), _ptr(chi, np.uint8, (Q, k), "chi"),
+        _stream(stream)))
 
 
 def nhq_save(index, path) -> None:

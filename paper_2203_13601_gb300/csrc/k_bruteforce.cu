@@ -10,6 +10,10 @@
 // survivors into a sorted per-query list in shared memory.  With several slices
 // (small query batches) the per-slice lists go to scratch and a warp-per-query
 // k-way merge writes the final rows.
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
 #include "nhq_internal.cuh"
 
 namespace nhq {
@@ -295,3 +299,139 @@ cudaError_t launch_topk(const TopkArgs &a, void *scratch, size_t scratch_bytes, 
 }
 
 }  // namespace nhq
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the brute-force top-k (nhq_brute_force_noalloc).
+//
+// Some callers cannot allocate device memory when they call the library: code
+// that runs under a memory budget owned by another allocator (a framework's
+// caching pool, an embedded or real-time service that reserves all memory at
+// start-up), or code that must not touch the allocator on its hot path.  For
+// them the split path's only scratch -- the per-slice sorted lists that
+// topk_tile_kernel writes and topk_merge_kernel reads -- lives in the
+// file-scope array below.  It is kNoAllocScratchBytes (16 MiB) on every GPU
+// that loads the library and stays there until the process exits.  Every call
+// on a device shares it: each call fully rewrites the entries it later reads,
+// so nothing has to start at zero, but calls whose kernels overlap on the GPU
+// (different streams, or different host threads) race on it.
+// ---------------------------------------------------------------------------
+namespace nhq {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+struct NoAllocDevice {
+    bool ready = false;
+    void *scratch = nullptr;  // device address of g_noalloc_scratch on this device
+    int sm_count = 0;
+};
+constexpr int kNoAllocMaxDevices = 64;
+NoAllocDevice g_noalloc_devices[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes at;
+    if (p == nullptr || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Per-device set-up, done by the first call on the current device.  In host code
+// g_noalloc_scratch names a host-side shadow, not device memory, so the device
+// address is looked up with cudaGetSymbolAddress while this device is current.
+nhq_status noalloc_setup(NoAllocDevice **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return report_error(NHQ_ERR_CUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocDevice &d = g_noalloc_devices[dev];
+    if (!d.ready) {
+        void *ptr = nullptr;
+        if ((e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch)) != cudaSuccess)
+            return report_error(NHQ_ERR_CUDA, cudaGetErrorString(e));
+        int sms = 0;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
+            cudaSuccess)
+            return report_error(NHQ_ERR_CUDA, cudaGetErrorString(e));
+        d.scratch = ptr;
+        d.sm_count = sms;
+        d.ready = true;
+    }
+    *out = &d;
+    return NHQ_OK;
+}
+
+}  // namespace
+
+}  // namespace nhq
+
+extern "C" nhq_status nhq_brute_force_noalloc(const float *vectors,
+                                              const uint32_t *packed_attributes, int64_t N,
+                                              int32_t d, int32_t m, const float *queries,
+                                              const uint32_t *packed_query_attributes,
+                                              int64_t Q, int32_t k, nhq_weights w, uint32_t *ids,
+                                              float *dists, uint8_t *chi, void *stream) {
+    using namespace nhq;
+    if (N < 1 || N > 0x7FFFFFFE || d < 1 || m < 1 || m > 4 || Q < 0 || k < 1 || k > kMaxK)
+        return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: need N >= 1, d >= 1, m in "
+                                         "1..4, Q >= 0, k in 1..256");
+    if (d % 4 != 0)
+        return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: d must be a multiple of 4");
+    if (w.mode != NHQ_W_PROPORTIONAL && w.mode != NHQ_W_CONSTANT && w.mode != NHQ_W_FILTER)
+        return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: unknown weight mode");
+    if (w.mode == NHQ_W_CONSTANT &&
+        (!std::isfinite(w.w_v) || !std::isfinite(w.w_l) || w.w_v < 0.f || w.w_l < 0.f))
+        return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: weights must be finite, >= 0");
+    if (Q == 0)
+        return NHQ_OK;
+    if (!is_device_pointer(vectors) || !is_device_pointer(packed_attributes) ||
+        !is_device_pointer(queries) || !is_device_pointer(packed_query_attributes) ||
+        !is_device_pointer(ids) || (dists && !is_device_pointer(dists)) ||
+        (chi && !is_device_pointer(chi)))
+        return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: every array must be device "
+                                         "memory (NULL allowed for dists and chi)");
+    if ((reinterpret_cast<uintptr_t>(vectors) & 15) != 0)
+        return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: vectors must be 16-byte "
+                                         "aligned");
+    NoAllocDevice *dv = nullptr;
+    nhq_status st = noalloc_setup(&dv);
+    if (st != NHQ_OK)
+        return st;
+    TopkArgs a;
+    a.X = vectors;
+    a.xstride = d;
+    a.d = d;
+    a.N = N;
+    a.attr = packed_attributes;
+    a.Q = queries;
+    a.qstride = d;
+    a.qattr = packed_query_attributes;
+    a.nq = Q;
+    a.k = k;
+    a.exclude_self = 0;
+    a.w = make_fusion(w, m);
+    a.ids = ids;
+    a.dists = dists;
+    a.chi = chi;
+    const size_t need = topk_scratch_bytes(a, dv->sm_count);
+    if (need > kNoAllocScratchBytes) {
+        char msg[256];
+        snprintf(msg, sizeof(msg),
+                 "nhq_brute_force_noalloc: Q = %lld, k = %d needs %zu scratch bytes, above the "
+                 "fixed %zu (use nhq_brute_force, or fewer queries per call)",
+                 (long long)Q, k, need, kNoAllocScratchBytes);
+        return report_error(NHQ_ERR_ARG, msg);
+    }
+    cudaError_t e = launch_topk(a, dv->scratch, kNoAllocScratchBytes, dv->sm_count,
+                                reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return report_error(NHQ_ERR_CUDA, cudaGetErrorString(e));
+    return NHQ_OK;
+}

@@ -172,6 +172,14 @@ nhq_status install_graph(nhq_index *ix, const uint32_t *nbr_dev, int R, cudaStre
 
 }  // namespace
 
+namespace nhq {
+// Lets other translation units of the library report an error through nhq_last_error.
+nhq_status report_error(nhq_status s, const char *message) {
+    g_err = message;
+    return s;
+}
+}  // namespace nhq
+
 extern "C" {
 
 const char *nhq_last_error(void) { return g_err.c_str(); }

@@ -91,6 +91,7 @@ struct nhq_index {
 namespace nhq {
 
 nhq::Fusion make_fusion(const nhq_weights &w, int m);
+nhq_status report_error(nhq_status s, const char *message);  // nhq_api.cu
 
 // k_util.cu
 cudaError_t launch_pack_attributes(const uint8_t *a, int64_t n, int m, uint32_t *out, cudaStream_t s);
