@@ -7,13 +7,16 @@
 //   cand  [64]  candidate records of the current expansion
 //   hash  [H]   visited filter (open addressing)
 //   qv    [d]   the query vector
-// Each expansion: pick the smallest unexpanded record (ballot scan), read the
-// parent's neighbour ids and their attribute words (one coalesced row each),
-// drop already-evaluated ids through the visited filter, prune by the
-// attribute lower bound w_l * chi when the weights are constant (a candidate
-// whose bound already exceeds the pool's last record cannot enter), evaluate
-// the rest with teams of 8 lanes (128-bit loads, shuffle reduction), and merge
-// them into the pool (warp bitonic sort + rank-based in-place merge).
+// Each expansion: take the smallest unexpanded record, read the parent's
+// neighbour ids and their attribute words (one coalesced row each, issued one
+// expansion ahead), drop already-evaluated ids through the visited filter,
+// prune by the attribute lower bound w_l * chi when the weights are constant
+// (a candidate whose bound already exceeds the pool's last record cannot
+// enter), accumulate squared distances with teams of 8 lanes (128-bit loads,
+// shuffle reduction), finish every candidate's Gamma in one warp-wide step
+// (lane j holds candidate j's record in a register), and merge the survivors
+// into the pool (rank by broadcast compares for up to 8, warp bitonic sort
+// beyond).
 //
 // The pool after every expansion equals the serial algorithm's: inserting a
 // batch and keeping the ef smallest equals inserting the batch one record at a
@@ -37,16 +40,21 @@ __device__ __forceinline__ uint32_t hash_slot(uint32_t v, int bits) {
     return (v * 0x9E3779B1u) >> (32 - bits);
 }
 
-// true if v was not present (and is now)
+// true if v was not present (and is now); a plain read first, the atomic only on an empty slot
 __device__ __forceinline__ bool hash_insert(uint32_t *h, int bits, uint32_t v) {
     const uint32_t mask = (1u << bits) - 1u;
     uint32_t s = hash_slot(v, bits);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
-        uint32_t old = atomicCAS(&h[s], kNone, v);
-        if (old == kNone)
-            return true;
-        if (old == v)
+        uint32_t x = h[s];
+        if (x == v)
             return false;
+        if (x == kNone) {
+            x = atomicCAS(&h[s], kNone, v);
+            if (x == kNone)
+                return true;
+            if (x == v)
+                return false;
+        }
         s = (s + 1) & mask;
     }
     return false;
@@ -108,10 +116,6 @@ __device__ __forceinline__ int sorted_count_less(const unsigned long long *s, in
     return lo;
 }
 
-struct Row4 {
-    float4 v;
-};
-
 template <typename VT>
 __device__ __forceinline__ void accum_chunk(float &acc, const float4 &q0, const float4 &q1,
                                             const VT *row, int c, bool live);
@@ -164,13 +168,13 @@ struct VecTraits<__nv_bfloat16> {
     static constexpr int kPerChunk = 8;
 };
 
-// Gamma of cnt candidates cid[0..cnt) (chi precomputed in cchi) -> cand[0..cnt).
-// Teams of 8 lanes; each team carries two rows per pass so 8 rows are in flight.
-template <typename VT>
-__device__ __forceinline__ void eval_candidates(const VT *__restrict__ X, int xstride,
-                                                const float *qv, const uint32_t *cid,
-                                                const int *cchi, unsigned long long *cand,
-                                                int cnt, const Fusion &w, int lane) {
+// Squared distances of cnt candidates cid[0..cnt) into d2s[0..cnt).  Teams of 8
+// lanes, two rows per team per pass (8 rows in flight per warp).  CPL > 0: each
+// lane covers at most CPL chunks of a row (EXACT: exactly CPL, no bounds test);
+// CPL == 0: a strided loop for wide rows.
+template <typename VT, int CPL, bool EXACT>
+__device__ __forceinline__ void eval_dist2(const VT *__restrict__ X, int xstride, const float *qv,
+                                           const uint32_t *cid, float *d2s, int cnt, int lane) {
     constexpr int PC = VecTraits<VT>::kPerChunk;
     const int team = lane / TEAM, tl = lane % TEAM;
     const int nchunk = xstride / PC;
@@ -180,55 +184,138 @@ __device__ __forceinline__ void eval_candidates(const VT *__restrict__ X, int xs
         const VT *r0 = X + (int64_t)cid[h0 ? j0 : 0] * xstride;
         const VT *r1 = X + (int64_t)cid[h1 ? j1 : 0] * xstride;
         float acc0 = 0.f, acc1 = 0.f;
+        if (CPL > 0) {
+#pragma unroll
+            for (int i = 0; i < (CPL > 0 ? CPL : 1); ++i) {
+                const int c = tl + i * TEAM;
+                const bool live = EXACT || c < nchunk;
+                const int cc = EXACT ? c : (live ? c : 0);
+                const float4 qa = reinterpret_cast<const float4 *>(qv)[cc * PC / 4];
+                const float4 qb =
+                    PC == 8 ? reinterpret_cast<const float4 *>(qv)[cc * PC / 4 + 1] : qa;
+                accum_chunk<VT>(acc0, qa, qb, r0, cc, h0 && live);
+                accum_chunk<VT>(acc1, qa, qb, r1, cc, h1 && live);
+            }
+        } else {
 #pragma unroll 4
-        for (int c = tl; c < nchunk; c += TEAM) {
-            float4 qa = reinterpret_cast<const float4 *>(qv)[c * PC / 4];
-            float4 qb = PC == 8 ? reinterpret_cast<const float4 *>(qv)[c * PC / 4 + 1] : qa;
-            accum_chunk<VT>(acc0, qa, qb, r0, c, h0);
-            accum_chunk<VT>(acc1, qa, qb, r1, c, h1);
+            for (int c = tl; c < nchunk; c += TEAM) {
+                const float4 qa = reinterpret_cast<const float4 *>(qv)[c * PC / 4];
+                const float4 qb =
+                    PC == 8 ? reinterpret_cast<const float4 *>(qv)[c * PC / 4 + 1] : qa;
+                accum_chunk<VT>(acc0, qa, qb, r0, c, h0);
+                accum_chunk<VT>(acc1, qa, qb, r1, c, h1);
+            }
         }
-        acc0 += __shfl_xor_sync(FULL, acc0, 1);
-        acc1 += __shfl_xor_sync(FULL, acc1, 1);
-        acc0 += __shfl_xor_sync(FULL, acc0, 2);
-        acc1 += __shfl_xor_sync(FULL, acc1, 2);
-        acc0 += __shfl_xor_sync(FULL, acc0, 4);
-        acc1 += __shfl_xor_sync(FULL, acc1, 4);
-        if (tl == 0) {
-            if (h0)
-                cand[j0] = make_key(fusion_gamma(__fsqrt_rn(acc0), cchi[j0], w), cid[j0]);
-            if (h1)
-                cand[j1] = make_key(fusion_gamma(__fsqrt_rn(acc1), cchi[j1], w), cid[j1]);
-        }
+        // reduce both rows over the team: the first level swaps halves so that
+        // lanes tl < 4 carry row j0 and lanes tl >= 4 row j1
+        const bool upper = (tl & 4) != 0;
+        const float send = upper ? acc0 : acc1;
+        const float keep = upper ? acc1 : acc0;
+        float acc = keep + __shfl_xor_sync(FULL, send, 4);
+        acc += __shfl_xor_sync(FULL, acc, 2);
+        acc += __shfl_xor_sync(FULL, acc, 1);
+        if (tl == 0 && h0)
+            d2s[j0] = acc;
+        if (tl == 4 && h1)
+            d2s[j1] = acc;
     }
     __syncwarp();
 }
 
-// Merge cand[0..cnt) into the pool; returns true if any candidate entered it.
-__device__ bool merge_into_pool(unsigned long long *pool, int &n, int ef,
-                                unsigned long long *cand, int cnt, int &cursor, int lane) {
-    bool any = false;
-    for (int base = 0; base < cnt; base += 32) {
-        const int i = base + lane;
-        unsigned long long c = i < cnt ? cand[i] : kInfKey;
-        if (c != kInfKey && n == ef && c > (pool[ef - 1] & ~1ull))
-            c = kInfKey;  // cannot beat the last record of a full pool
-        if (c != kInfKey) {
-            int lb = pool_lower_bound(pool, n, c);
-            if (lb < n && (pool[lb] & ~1ull) == c)
-                c = kInfKey;  // already pooled
+// Record (Gamma, id) of candidate j, or kInfKey when j >= cnt (one lane per candidate).
+__device__ __forceinline__ unsigned long long candidate_key(int j, int cnt, const float *d2s,
+                                                            const uint32_t *cid, const int *cchi,
+                                                            const Fusion &w) {
+    if (j >= cnt)
+        return kInfKey;
+    return make_key(fusion_gamma(__fsqrt_rn(d2s[j]), cchi[j], w), cid[j]);
+}
+
+// smallest record over the warp from two 32-bit reductions (Gamma bits, then ids of ties)
+__device__ __forceinline__ unsigned long long warp_min_key(unsigned long long x) {
+    const unsigned hi = __reduce_min_sync(FULL, (unsigned)(x >> 32));
+    const unsigned lo = __reduce_min_sync(FULL, (unsigned)(x >> 32) == hi ? (unsigned)x : ~0u);
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// number of pool records below c, every lane passing the same c (ballot count)
+__device__ __forceinline__ int pool_rank_uniform(const unsigned long long *pool, int n,
+                                                 unsigned long long c, int lane) {
+    int r = 0;
+    for (int b = 0; b < n; b += 32) {
+        const int i = b + lane;
+        const unsigned m = __ballot_sync(FULL, i < n && (pool[i] & ~1ull) < c);
+        r += __popc(m);
+        if (m != FULL)
+            break;  // sorted: the first record not below c ends the run
+    }
+    return r;
+}
+
+// Drop a candidate that cannot enter: above the last record of a full pool, or,
+// after the visited filter was rebuilt, a record already in the pool.
+__device__ __forceinline__ unsigned long long filter_key(unsigned long long c,
+                                                         const unsigned long long *pool, int n,
+                                                         int ef, bool dup_check) {
+    if (c == kInfKey)
+        return c;
+    if (n == ef && c > (pool[ef - 1] & ~1ull))
+        return kInfKey;
+    if (dup_check) {
+        const int lb = pool_lower_bound(pool, n, c);
+        if (lb < n && (pool[lb] & ~1ull) == c)
+            return kInfKey;
+    }
+    return c;
+}
+
+// Inserts the candidate records held one per lane (kInfKey = none) into the pool,
+// keeping its ef smallest records; equals inserting them one at a time.
+__device__ void merge_round(unsigned long long *pool, int &n, int ef, unsigned long long c,
+                            unsigned long long *sorted32, int lane) {
+    if (c != kInfKey && n == ef && c > (pool[ef - 1] & ~1ull))
+        c = kInfKey;
+    const unsigned vb = __ballot_sync(FULL, c != kInfKey);
+    if (vb == 0)
+        return;
+    const int nv = __popc(vb);
+    if (nv <= 8) {
+        int rank = 0;
+        for (unsigned mm = vb; mm; mm &= mm - 1) {
+            const unsigned long long cj = __shfl_sync(FULL, c, __ffs(mm) - 1);
+            rank += cj < c ? 1 : 0;
         }
-        c = warp_sort_asc(c, lane);
-        const int nv = __popc(__ballot_sync(FULL, c != kInfKey));
-        if (nv == 0)
-            continue;
-        __syncwarp();
-        cand[base + lane] = c;  // sorted candidates of this round
-        __syncwarp();
-        const unsigned long long *cs = cand + base;
-        const int pos = lane < nv ? lane + pool_lower_bound(pool, n, c) : ef;
-        const int p0 = __shfl_sync(FULL, pos, 0);
-        if (p0 >= ef)
-            continue;  // nothing enters
+        const int pos = c != kInfKey ? rank + pool_lower_bound(pool, n, c) : ef;
+        const int p0 = (int)__reduce_min_sync(FULL, (unsigned)pos);
+        if (p0 < ef) {
+            for (int b = (n - 1) & ~31; n > 0 && b >= (p0 & ~31); b -= 32) {
+                const int e = b + lane;
+                const bool mv = e >= p0 && e < n;
+                const unsigned long long val = mv ? pool[e] : 0ull;
+                int sh = 0;
+                for (unsigned mm = vb; mm; mm &= mm - 1) {
+                    const unsigned long long cj = __shfl_sync(FULL, c, __ffs(mm) - 1);
+                    sh += cj < (val & ~1ull) ? 1 : 0;
+                }
+                __syncwarp();
+                if (mv && e + sh < ef)
+                    pool[e + sh] = val;
+                __syncwarp();
+            }
+            if (c != kInfKey && pos < ef)
+                pool[pos] = c;
+            __syncwarp();
+            n = min(ef, n + nv);
+        }
+        return;
+    }
+    c = warp_sort_asc(c, lane);
+    __syncwarp();
+    sorted32[lane] = c;
+    __syncwarp();
+    const int pos = lane < nv ? lane + pool_lower_bound(pool, n, c) : ef;
+    const int p0 = __shfl_sync(FULL, pos, 0);
+    if (p0 < ef) {
         for (int b = (n - 1) & ~31; n > 0 && b >= (p0 & ~31); b -= 32) {
             const int e = b + lane;
             const bool mv = e >= p0 && e < n;
@@ -236,7 +323,7 @@ __device__ bool merge_into_pool(unsigned long long *pool, int &n, int ef,
             int dst = ef;
             if (mv) {
                 val = pool[e];
-                dst = e + sorted_count_less(cs, nv, val & ~1ull);
+                dst = e + sorted_count_less(sorted32, nv, val & ~1ull);
             }
             __syncwarp();
             if (mv && dst < ef)
@@ -247,10 +334,38 @@ __device__ bool merge_into_pool(unsigned long long *pool, int &n, int ef,
             pool[pos] = c;
         __syncwarp();
         n = min(ef, n + nv);
-        any = true;
-        cursor = min(cursor, p0);
     }
-    return any;
+}
+
+// index of the first unexpanded record at or after `from`, or -1
+__device__ __forceinline__ int first_unexpanded(const unsigned long long *pool, int n, int from,
+                                                int lane) {
+    for (int c = from; c < n; c += 32) {
+        const int i = c + lane;
+        const unsigned b = __ballot_sync(FULL, i < n && !(pool[i] & 1ull));
+        if (b)
+            return c + __ffs(b) - 1;
+    }
+    return -1;
+}
+
+// the neighbour ids and their attribute words of vertex u (slots lane, lane + 32)
+struct Adjacency {
+    uint32_t v0, v1, at0, at1;
+};
+template <bool TWO>
+__device__ __forceinline__ Adjacency load_adjacency(const SearchArgs &a, uint32_t u, int lane) {
+    Adjacency r{kNone, kNone, 0u, 0u};
+    const int64_t row = (int64_t)u * a.R;
+    if (lane < a.R) {
+        r.v0 = __ldg(a.nbr + row + lane);
+        r.at0 = __ldg(a.nbr_attr + row + lane);
+    }
+    if (TWO && lane + 32 < a.R) {
+        r.v1 = __ldg(a.nbr + row + lane + 32);
+        r.at1 = __ldg(a.nbr_attr + row + lane + 32);
+    }
+    return r;
 }
 
 __device__ __forceinline__ void clear_expanded(unsigned long long *pool, int n, int lane) {
@@ -261,7 +376,7 @@ __device__ __forceinline__ void clear_expanded(unsigned long long *pool, int n, 
 }
 
 struct WarpLayout {
-    size_t pool, cand, cid, cchi, hash, qv, total;
+    size_t pool, sorted, d2s, cid, cchi, hash, qv, total;
 };
 
 __host__ __device__ inline WarpLayout warp_layout(int ef_cap, int hash_bits, int xstride) {
@@ -269,12 +384,15 @@ __host__ __device__ inline WarpLayout warp_layout(int ef_cap, int hash_bits, int
     size_t o = 0;
     L.pool = o;
     o += sizeof(unsigned long long) * ef_cap;
-    L.cand = o;
-    o += sizeof(unsigned long long) * CAND;
+    L.sorted = o;
+    o += sizeof(unsigned long long) * 32;
+    L.d2s = o;
+    o += sizeof(float) * CAND;
     L.cid = o;
     o += sizeof(uint32_t) * CAND;
     L.cchi = o;
     o += sizeof(int) * CAND;
+    o = (o + 15) & ~(size_t)15;
     L.hash = o;
     o += sizeof(uint32_t) * ((size_t)1 << hash_bits);
     o = (o + 15) & ~(size_t)15;
@@ -285,15 +403,16 @@ __host__ __device__ inline WarpLayout warp_layout(int ef_cap, int hash_bits, int
     return L;
 }
 
-template <typename VT>
-__global__ void __launch_bounds__(256) search_kernel(SearchArgs a, const VT *__restrict__ Xs,
-                                                     int ef_cap) {
+template <typename VT, int CPL, bool EXACT, bool TWO>
+__global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *__restrict__ Xs,
+                                                        int ef_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const WarpLayout L = warp_layout(ef_cap, a.hash_bits, a.xstride);
     unsigned char *base = smem + wib * L.total;
     unsigned long long *pool = reinterpret_cast<unsigned long long *>(base + L.pool);
-    unsigned long long *cand = reinterpret_cast<unsigned long long *>(base + L.cand);
+    unsigned long long *sorted32 = reinterpret_cast<unsigned long long *>(base + L.sorted);
+    float *d2s = reinterpret_cast<float *>(base + L.d2s);
     uint32_t *cid = reinterpret_cast<uint32_t *>(base + L.cid);
     int *cchi = reinterpret_cast<int *>(base + L.cchi);
     uint32_t *hash = reinterpret_cast<uint32_t *>(base + L.hash);
@@ -318,11 +437,12 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a, const VT *__r
         uint32_t qa = 0;
         for (int j = 0; j < a.w.m; ++j)
             qa |= (uint32_t)a.qattr[q * a.w.m + j] << (8 * j);
-        for (int i = lane; i < H; i += 32)
-            hash[i] = kNone;
+        for (int i = lane; i < H / 4; i += 32)
+            reinterpret_cast<uint4 *>(hash)[i] = make_uint4(kNone, kNone, kNone, kNone);
         __syncwarp();
 
         int n = 0, cursor = 0, hcount = 0, iters = 0, ndc = 0;
+        bool rebuilt = false;  // the visited filter forgot ids at least once
         int stage = a.h > 1 ? 1 : 2;
         int status = NHQ_OK;
         const uint64_t s0 = a.seed ^ mix64((uint64_t)q);
@@ -346,8 +466,11 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a, const VT *__r
             const int cnt = __popc(kb);
             hcount += cnt;
             ndc += cnt;
-            eval_candidates<VT>(Xs, a.xstride, qv, cid, cchi, cand, cnt, a.w, lane);
-            merge_into_pool(pool, n, ef, cand, cnt, cursor, lane);
+            if (cnt > 0) {
+                eval_dist2<VT, CPL, EXACT>(Xs, a.xstride, qv, cid, d2s, cnt, lane);
+                merge_round(pool, n, ef, candidate_key(lane, cnt, d2s, cid, cchi, a.w), sorted32,
+                            lane);
+            }
         }
         // ---- seed set B, random: first min(ef, 32) distinct ids of the stream, <= 64 draws
         const int want = a.seeds != nullptr ? 0 : min(ef, 32);
@@ -373,29 +496,30 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a, const VT *__r
             got += cnt;
             hcount += cnt;
             ndc += cnt;
-            eval_candidates<VT>(Xs, a.xstride, qv, cid, cchi, cand, cnt, a.w, lane);
-            merge_into_pool(pool, n, ef, cand, cnt, cursor, lane);
-        }
-        cursor = 0;
-
-        // ---- expansions
-        for (;;) {
-            int pidx = -1;
-            while (cursor < n) {
-                const int i = cursor + lane;
-                const bool un = i < n && !(pool[i] & 1ull);
-                const unsigned b = __ballot_sync(FULL, un);
-                if (b) {
-                    pidx = cursor + __ffs(b) - 1;
-                    break;
-                }
-                cursor += 32;
+            if (cnt > 0) {
+                eval_dist2<VT, CPL, EXACT>(Xs, a.xstride, qv, cid, d2s, cnt, lane);
+                merge_round(pool, n, ef, candidate_key(lane, cnt, d2s, cid, cchi, a.w), sorted32,
+                            lane);
             }
+        }
+
+        // ---- expansions.  The parent of the next expansion is known before the merge
+        // (the smaller of the first unexpanded record and the smallest surviving new
+        // candidate), so its adjacency loads are issued before the merge runs.
+        cursor = 0;
+        int pidx = first_unexpanded(pool, n, 0, lane);
+        Adjacency adj{kNone, kNone, 0u, 0u};
+        if (pidx >= 0)
+            adj = load_adjacency<TWO>(a, key_id(pool[pidx]), lane);
+        for (;;) {
             if (pidx < 0) {
                 if (stage == 1) {  // S1 exhausted C: S2 with C = C u R
                     stage = 2;
                     clear_expanded(pool, n, lane);
                     cursor = 0;
+                    pidx = n > 0 ? 0 : -1;
+                    if (pidx >= 0)
+                        adj = load_adjacency<TWO>(a, key_id(pool[0]), lane);
                     continue;
                 }
                 break;
@@ -409,13 +533,15 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a, const VT *__r
             __syncwarp();
             if (lane == 0)
                 pool[pidx] = pk | 1ull;
+            __syncwarp();
             cursor = pidx + 1;
             const uint32_t u = key_id(pk);
 
             if (hcount + R > (H >> 1)) {  // rebuild the visited filter from the pool
+                rebuilt = true;
                 __syncwarp();
-                for (int i = lane; i < H; i += 32)
-                    hash[i] = kNone;
+                for (int i = lane; i < H / 4; i += 32)
+                    reinterpret_cast<uint4 *>(hash)[i] = make_uint4(kNone, kNone, kNone, kNone);
                 __syncwarp();
                 for (int i = lane; i < n; i += 32)
                     hash_insert(hash, a.hash_bits, key_id(pool[i]));
@@ -423,16 +549,8 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a, const VT *__r
                 hcount = n;
             }
 
-            uint32_t v0 = kNone, v1 = kNone, at0 = 0, at1 = 0;
-            if (lane < R) {
-                v0 = a.nbr[(int64_t)u * R + lane];
-                at0 = a.nbr_attr[(int64_t)u * R + lane];
-            }
-            if (lane + 32 < R) {
-                v1 = a.nbr[(int64_t)u * R + lane + 32];
-                at1 = a.nbr_attr[(int64_t)u * R + lane + 32];
-            }
-            bool ok0 = v0 != kNone, ok1 = v1 != kNone;
+            const uint32_t v0 = adj.v0, v1 = adj.v1, at0 = adj.at0, at1 = adj.at1;
+            bool ok0 = v0 != kNone, ok1 = TWO && v1 != kNone;
 
             if (stage == 1) {  // S1: ceil(R/h) valid neighbours of smallest key
                 const unsigned b0 = __ballot_sync(FULL, ok0), b1 = __ballot_sync(FULL, ok1);
@@ -456,24 +574,27 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a, const VT *__r
             }
 
             bool nw0 = ok0 && hash_insert(hash, a.hash_bits, v0);
-            bool nw1 = ok1 && hash_insert(hash, a.hash_bits, v1);
-            hcount += __popc(__ballot_sync(FULL, nw0)) + __popc(__ballot_sync(FULL, nw1));
-            const int c0 = chi_packed(at0, qa, amask), c1 = chi_packed(at1, qa, amask);
+            bool nw1 = TWO && ok1 && hash_insert(hash, a.hash_bits, v1);
+            // newly inserted ids fill the filter, pruned or not (they count as evaluated)
+            hcount += __popc(__ballot_sync(FULL, nw0)) + (TWO ? __popc(__ballot_sync(FULL, nw1)) : 0);
+            const int c0 = chi_packed(at0, qa, amask);
+            const int c1 = TWO ? chi_packed(at1, qa, amask) : 0;
             if (a.w.mode == NHQ_W_CONSTANT && n == ef) {
                 // Gamma >= w_l * chi in f32 (w_v * delta >= 0 and rounding is monotone)
                 const unsigned long long worst = pool[ef - 1] & ~1ull;
                 if (nw0 && make_key(__fmul_rn(a.w.wl, (float)c0), v0) > worst)
                     nw0 = false;
-                if (nw1 && make_key(__fmul_rn(a.w.wl, (float)c1), v1) > worst)
+                if (TWO && nw1 && make_key(__fmul_rn(a.w.wl, (float)c1), v1) > worst)
                     nw1 = false;
             }
-            const unsigned e0 = __ballot_sync(FULL, nw0), e1 = __ballot_sync(FULL, nw1);
+            const unsigned e0 = __ballot_sync(FULL, nw0);
+            const unsigned e1 = TWO ? __ballot_sync(FULL, nw1) : 0u;
             if (nw0) {
                 const int p = __popc(e0 & lanemask_lt(lane));
                 cid[p] = v0;
                 cchi[p] = c0;
             }
-            if (nw1) {
+            if (TWO && nw1) {
                 const int p = __popc(e0) + __popc(e1 & lanemask_lt(lane));
                 cid[p] = v1;
                 cchi[p] = c1;
@@ -481,15 +602,45 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a, const VT *__r
             __syncwarp();
             const int cnt = __popc(e0) + __popc(e1);
             ndc += cnt;
-            bool changed = false;
+            unsigned long long k0 = kInfKey, k1 = kInfKey;
             if (cnt > 0) {
-                eval_candidates<VT>(Xs, a.xstride, qv, cid, cchi, cand, cnt, a.w, lane);
-                changed = merge_into_pool(pool, n, ef, cand, cnt, cursor, lane);
+                eval_dist2<VT, CPL, EXACT>(Xs, a.xstride, qv, cid, d2s, cnt, lane);
+                k0 = filter_key(candidate_key(lane, cnt, d2s, cid, cchi, a.w), pool, n, ef,
+                                rebuilt);
+                if (TWO)
+                    k1 = filter_key(candidate_key(lane + 32, cnt, d2s, cid, cchi, a.w), pool, n,
+                                    ef, rebuilt);
             }
-            if (stage == 1 && !changed) {  // local optimum ends S1
+            const unsigned long long cmin = warp_min_key(k0 < k1 ? k0 : k1);
+            // next parent and its adjacency, before the merge
+            const int uo = first_unexpanded(pool, n, cursor, lane);
+            const unsigned long long uo_key = uo >= 0 ? (pool[uo] & ~1ull) : kInfKey;
+            int next = -1;
+            uint32_t next_id = kNone;
+            const int cpos = cmin != kInfKey ? pool_rank_uniform(pool, n, cmin, lane) : n;
+            if (cmin != kInfKey && cmin < uo_key) {
+                next = cpos;
+                next_id = key_id(cmin);
+            } else if (uo >= 0) {
+                next = uo;
+                next_id = key_id(uo_key);
+            }
+            if (next >= 0)
+                adj = load_adjacency<TWO>(a, next_id, lane);
+            if (cmin != kInfKey) {
+                merge_round(pool, n, ef, k0, sorted32, lane);
+                if (TWO)
+                    merge_round(pool, n, ef, k1, sorted32, lane);
+                cursor = min(cursor, cpos);
+            }
+            pidx = next;
+            if (stage == 1 && cmin == kInfKey) {  // local optimum ends S1
                 stage = 2;
                 clear_expanded(pool, n, lane);
                 cursor = 0;
+                pidx = n > 0 ? 0 : -1;
+                if (pidx >= 0 && key_id(pool[0]) != next_id)
+                    adj = load_adjacency<TWO>(a, key_id(pool[0]), lane);
             }
         }
 
@@ -522,10 +673,54 @@ __global__ void __launch_bounds__(256) search_kernel(SearchArgs a, const VT *__r
 
 int auto_hash_bits(int ef_cap, int R) {
     int need = 4 * (ef_cap + R);
-    int bits = 11;  // 2048 slots
+    int bits = 10;  // 1024 slots: small enough for 32 resident warps per SM at small ef
     while ((1 << bits) < need)
         ++bits;
     return bits;
+}
+
+template <typename VT, int CPL, bool EXACT, bool TWO>
+cudaError_t launch_variant(const SearchArgs &a, const VT *X, int ef_cap, int wpb, size_t smem,
+                           int sm_count, cudaStream_t s) {
+    auto kfn = search_kernel<VT, CPL, EXACT, TWO>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * wpb, smem)) !=
+        cudaSuccess)
+        return e;
+    if (per_sm < 1)
+        per_sm = 1;
+    int64_t blocks = (int64_t)per_sm * sm_count;
+    const int64_t need = (a.nq + wpb - 1) / wpb;
+    if (blocks > need)
+        blocks = need;
+    kfn<<<(unsigned)blocks, 32 * wpb, smem, s>>>(a, X, ef_cap);
+    return cudaGetLastError();
+}
+
+template <typename VT, bool TWO>
+cudaError_t launch_shape(const SearchArgs &a, const VT *X, int ef_cap, int wpb, size_t smem,
+                         int sm_count, cudaStream_t s) {
+    constexpr int PC = VecTraits<VT>::kPerChunk;
+    const int nchunk = a.xstride / PC;
+    if (nchunk == 2 * TEAM)
+        return launch_variant<VT, 2, true, TWO>(a, X, ef_cap, wpb, smem, sm_count, s);
+    if (nchunk == 4 * TEAM)
+        return launch_variant<VT, 4, true, TWO>(a, X, ef_cap, wpb, smem, sm_count, s);
+    if (nchunk < 4 * TEAM)
+        return launch_variant<VT, 4, false, TWO>(a, X, ef_cap, wpb, smem, sm_count, s);
+    return launch_variant<VT, 0, false, TWO>(a, X, ef_cap, wpb, smem, sm_count, s);
+}
+
+template <typename VT>
+cudaError_t launch_dtype(const SearchArgs &a, const VT *X, int ef_cap, int wpb, size_t smem,
+                         int sm_count, cudaStream_t s) {
+    if (a.R > 32)
+        return launch_shape<VT, true>(a, X, ef_cap, wpb, smem, sm_count, s);
+    return launch_shape<VT, false>(a, X, ef_cap, wpb, smem, sm_count, s);
 }
 
 }  // namespace
@@ -546,41 +741,15 @@ cudaError_t launch_search(SearchArgs a, void *scratch, int sm_count, size_t smem
     if ((1 << a.hash_bits) < 2 * (ef_cap + a.R) + 64)
         return cudaErrorInvalidValue;
     const WarpLayout L = warp_layout(ef_cap, a.hash_bits, a.xstride);
-    int wpb = a.warps_per_block > 0 ? a.warps_per_block : 4;
+    int wpb = a.warps_per_block > 0 ? a.warps_per_block : 8;
     while (wpb > 1 && L.total * wpb > smem_optin)
         wpb >>= 1;
     if (L.total * wpb > smem_optin)
         return cudaErrorInvalidValue;
     const size_t smem = L.total * wpb;
-    int per_sm = 0;
-    if (a.vec_dtype == NHQ_VEC_BF16) {
-        auto kfn = search_kernel<__nv_bfloat16>;
-        if ((e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem)) != cudaSuccess)
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * wpb, smem)) !=
-            cudaSuccess)
-            return e;
-    } else {
-        auto kfn = search_kernel<float>;
-        if ((e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem)) != cudaSuccess)
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * wpb, smem)) !=
-            cudaSuccess)
-            return e;
-    }
-    if (per_sm < 1)
-        per_sm = 1;
-    int64_t blocks = (int64_t)per_sm * sm_count;
-    int64_t need = (a.nq + wpb - 1) / wpb;
-    if (blocks > need)
-        blocks = need;
     if (a.vec_dtype == NHQ_VEC_BF16)
-        search_kernel<__nv_bfloat16><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a, a.Xh, ef_cap);
-    else
-        search_kernel<float><<<(unsigned)blocks, 32 * wpb, smem, s>>>(a, a.X, ef_cap);
-    return cudaGetLastError();
+        return launch_dtype<__nv_bfloat16>(a, a.Xh, ef_cap, wpb, smem, sm_count, s);
+    return launch_dtype<float>(a, a.X, ef_cap, wpb, smem, sm_count, s);
 }
 
 }  // namespace nhq
