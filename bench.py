@@ -35,6 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "QPS at Recall@10 >= 0.95 (hybrid recall, Sec. 6.1) on 1 GB300"
+VEC_NAMES = {0: "f32", 1: "bf16", 2: "fp8e4m3"}
 CONST_W = (1.0, 10000.0)
 
 
@@ -263,9 +264,12 @@ def main():
     exps = torch.empty(w.nq, dtype=torch.int32, device=dev)
 
     def run(ef, h, vec, diag=False):
+        # the reduced-precision copies are re-ranked in f32 (vec 2 = fp8 needs it; bf16 is
+        # exact on this integer data and runs without)
         nhq.nhq_search(ix.handle, Qv, QA, a.k, ef, ids, dists, chi,
                        ndc=ndc if diag else None, expansions=exps if diag else None,
-                       h=h, seed=12345, vec_dtype=vec, seed_mode=a.seed_mode, stream=stream)
+                       h=h, seed=12345, vec_dtype=vec, rerank=int(vec == nhq.VEC_FP8E4M3),
+                       seed_mode=a.seed_mode, stream=stream)
 
     def time_once(ef, h, vec, reps=2):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -280,7 +284,7 @@ def main():
     # sweep: smallest ef reaching the target per (h, scoring copy); keep the fastest
     sweep = []
     choices = []
-    vecs = [nhq.VEC_F32, nhq.VEC_BF16]
+    vecs = [nhq.VEC_F32, nhq.VEC_BF16, nhq.VEC_FP8E4M3]
     if a.fixed:
         ef, h, vec = (int(x) for x in a.fixed.split(","))
         cand_list = [(ef, h, vec)]
@@ -300,7 +304,7 @@ def main():
                 torch.cuda.synchronize()
                 rec, excl = hybrid_recall(ids.cpu().numpy(), w.A, w.QA, gt_h, P, a.k)
                 ms = time_once(ef, h, vec)
-                sweep.append({"ef": ef, "h": h, "vec": ["f32", "bf16"][vec], "recall": rec,
+                sweep.append({"ef": ef, "h": h, "vec": VEC_NAMES[vec], "recall": rec,
                               "ms": ms})
                 if rec >= a.target or cand_list:
                     found = (ef, h, vec, rec, ms)
@@ -318,8 +322,10 @@ def main():
     run(ef, h, vec, diag=True)
     torch.cuda.synchronize()
     ndc_h, exp_h = ndc.cpu().numpy().astype(np.float64), exps.cpu().numpy().astype(np.float64)
-    row_bytes = (2 if vec == nhq.VEC_BF16 else 4) * a.d
+    row_bytes = {nhq.VEC_F32: 4, nhq.VEC_BF16: 2, nhq.VEC_FP8E4M3: 1}[vec] * a.d
     bytes_per_query = ndc_h * (row_bytes + 4) + exp_h * a.R * 4 + a.d * 4 + a.k * 9
+    if vec == nhq.VEC_FP8E4M3:  # the f32 re-rank reads every pool member's f32 row once
+        bytes_per_query = bytes_per_query + ef * 4 * a.d
     alg_bytes = float(bytes_per_query.sum())
 
     # timed region: K steps of one search over the whole batch, device-resident inputs
@@ -366,7 +372,8 @@ def main():
 
     def run_host():
         nhq.nhq_search(ix.handle, Qh, QAh, a.k, ef, ids_h, d_h, c_h, h=h, seed=12345,
-                       vec_dtype=vec, seed_mode=a.seed_mode, stream=stream)
+                       vec_dtype=vec, rerank=int(vec == nhq.VEC_FP8E4M3),
+                       seed_mode=a.seed_mode, stream=stream)
 
     for _ in range(max(3, a.warmup)):
         run_host()
@@ -383,10 +390,11 @@ def main():
         "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world,
         "steps": a.steps, "warmup": max(3, a.warmup), "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if vec == nhq.VEC_BF16 else "f32", "data": "synthetic",
+        "dtype": VEC_NAMES[vec], "data": "synthetic",
         "config": {"workload": workload_name(a), "ef": ef, "h": h,
                    "seed_set": ["random (Sec. 3.2)", "attribute entry"][a.seed_mode],
-                   "scoring_copy": ["f32", "bf16"][vec], "recall": rec,
+                   "scoring_copy": VEC_NAMES[vec] + (" + f32 re-rank" if vec == 2 else ""),
+                   "recall": rec,
                    "recall_kind": "hybrid Recall@10 vs filter-mode brute force",
                    "l2": "inputs larger than L2 (vectors 512 MB + adjacency 256 MB)",
                    "build_s": t_build, "gen_s": t_gen, "ground_truth_s": t_gt,

@@ -64,8 +64,12 @@ typedef struct nhq_weights {
     float w_l;
 } nhq_weights;
 
-/* Element type of the vector copy used to score candidates during search. */
-typedef enum nhq_vec_dtype { NHQ_VEC_F32 = 0, NHQ_VEC_BF16 = 1 } nhq_vec_dtype;
+/* Element type of the vector copy used to score candidates during search (a
+ * project addition; the paper scores in f32).  Each component of the object
+ * vectors is rounded to nearest-even into the copy (FP8 saturates at +-448); the
+ * query stays f32 and distances accumulate in f32.  With `rerank` the final pool
+ * is re-scored with the f32 vectors and the first k of that order are returned. */
+typedef enum nhq_vec_dtype { NHQ_VEC_F32 = 0, NHQ_VEC_BF16 = 1, NHQ_VEC_FP8E4M3 = 2 } nhq_vec_dtype;
 
 typedef struct nhq_build_params {
     int32_t K;           /* candidate-set size l of Sec. 4.1 (exact K nearest by Gamma); 0 -> 64 */
@@ -91,7 +95,7 @@ typedef struct nhq_search_params {
     int32_t warps_per_block; /* 0 -> auto                                                      */
     int32_t hash_bits;       /* visited-filter size 2^hash_bits per query; 0 -> auto          */
     int32_t vec_dtype;       /* nhq_vec_dtype used for candidate scoring                       */
-    int32_t rerank;          /* with BF16 scoring: recompute Gamma of the final pool in f32    */
+    int32_t rerank;          /* with BF16/FP8 scoring: re-score the final pool in f32          */
     int32_t seed_mode;       /* nhq_seed_mode                                                   */
     int32_t n_seeds;         /* NHQ_SEED_GIVEN: row width of `seeds`, 1..64                     */
     const uint32_t *seeds;   /* NHQ_SEED_GIVEN: [Q][n_seeds] ids (device or host), 0xFFFFFFFF
@@ -108,7 +112,7 @@ int32_t nhq_version(void);
 
 /*
  * Object set S of Def. 1: copies vectors[N][d] (f32, row-major) into index-owned
- * HBM (rows padded to a multiple of 4 floats) and packs attributes[N][m] (u8
+ * HBM (rows padded to a multiple of 16 elements) and packs attributes[N][m] (u8
  * ordinal codes, Sec. 3.2) into one u32 per object.  `w` fixes the fusion
  * distance (Eq. 6) used by build and search.  The graph is empty until
  * nhq_index_build / nhq_index_set_graph.  Errors: N < 1, d < 1, m outside 1..4,

@@ -89,7 +89,12 @@ def _L():
             lib.or_graph_quality.argtypes = [P, i64, i32, P, i32]
             lib.or_search.restype = None
             lib.or_search.argtypes = [P, P, i64, i32, i32, P, i32, P, P, i64, i32, i32, i32, u64,
-                                      i64, i32, f64, f64, i32, i32, P, i32, P, P, P, P, P, P]
+                                      i64, i32, f64, f64, i32, i32, P, i32, i32, i32, P, P, P, P,
+                                      P, P]
+            lib.or_round_bf16.restype = C.c_float
+            lib.or_round_bf16.argtypes = [C.c_float]
+            lib.or_round_e4m3.restype = C.c_float
+            lib.or_round_e4m3.argtypes = [C.c_float]
             _lib = lib
     return _lib
 
@@ -231,11 +236,24 @@ def graph_quality(nbr, knn_ids) -> float:
 SEED_RANDOM, SEED_ATTRIBUTE, SEED_GIVEN = 0, 1, 2
 
 
+ROUND_NONE, ROUND_BF16, ROUND_E4M3 = 0, 1, 2
+
+
+def round_bf16(x) -> float:
+    return float(_L().or_round_bf16(float(x)))
+
+
+def round_e4m3(x) -> float:
+    return float(_L().or_round_e4m3(float(x)))
+
+
 def search(X, A, nbr, Qv, QA, k, ef, h=1, seed=0, max_iters=1 << 30, weights=None, prec=F32,
-           seed_mode=SEED_RANDOM, seeds=None):
+           seed_mode=SEED_RANDOM, seeds=None, vec_round=ROUND_NONE, rerank=False):
     """Serial Alg. 2 (+ two-stage routing when h > 1).  ``seed_mode`` picks the
     seed set B (random stream / attribute entry / the rows of ``seeds``, -1 =
-    none).  Returns a dict with ids/gamma/chi [nq,k], ndc/expansions/status [nq]."""
+    none).  ``vec_round`` scores candidates with X rounded to bf16 / fp8 e4m3;
+    ``rerank`` re-scores the final pool with X itself before returning the first k.
+    Returns a dict with ids/gamma/chi [nq,k], ndc/expansions/status [nq]."""
     X, A, nbr, Qv, QA = _f32(X), _u8(A), _i64(nbr), _f32(Qv), _u8(QA)
     if seeds is not None:
         seeds = _i64(seeds)
@@ -253,8 +271,8 @@ def search(X, A, nbr, Qv, QA, k, ef, h=1, seed=0, max_iters=1 << 30, weights=Non
     mode, wv, wl = _mode(weights)
     _L().or_search(_p(X), _p(A), X.shape[0], X.shape[1], A.shape[1], _p(nbr), nbr.shape[1],
                    _p(Qv), _p(QA), nq, k, ef, h, C.c_uint64(seed & (2**64 - 1)), max_iters,
-                   mode, wv, wl, prec, seed_mode, sp, ns, _p(ids), _p(g), _p(ch), _p(ndc),
-                   _p(ex), _p(st))
+                   mode, wv, wl, prec, seed_mode, sp, ns, int(vec_round), int(bool(rerank)),
+                   _p(ids), _p(g), _p(ch), _p(ndc), _p(ex), _p(st))
     return dict(ids=ids, gamma=g, chi=ch, ndc=ndc, expansions=ex, status=st)
 
 

@@ -101,6 +101,40 @@ int or_chi(const uint8_t *a, const uint8_t *b, int m)
     return c;
 }
 
+/* Reduced-precision copies used for scoring (a project addition, not in the
+ * paper): each object component rounded to nearest, ties to even.
+ *   bf16      : 8 significant bits (the upper half of the f32 encoding)
+ *   fp8 e4m3  : 4 exponent bits (bias 7), 3 mantissa bits, subnormals down to
+ *               2^-9, largest finite 448; magnitudes beyond saturate to 448 */
+float or_round_bf16(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    u &= 0xFFFF0000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+float or_round_e4m3(float x)
+{
+    double a = fabs((double)x);
+    if (a == 0.0)
+        return x;
+    int e;
+    frexp(a, &e);          /* a = f * 2^e with f in [0.5, 1): leading bit 2^(e-1) */
+    int lead = e - 1;
+    if (lead < -6)
+        lead = -6;         /* subnormal range shares the quantum of 2^-6 normals */
+    double quantum = ldexp(1.0, lead - 3);
+    double r = nearbyint(a / quantum) * quantum;  /* default rounding: to nearest even */
+    if (r > 448.0)
+        r = 448.0;
+    return (float)(x < 0 ? -r : r);
+}
+
 /* Eq. 6 in double.  Proportional mode: w_v = 1, w_l = delta / m (Sec. 3.2). */
 double or_gamma64(double delta, int chi, int m, int mode, double wv, double wl)
 {
@@ -440,10 +474,21 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                const int64_t *nbr, int R, const float *Qv, const uint8_t *QA, int64_t nq,
                int k, int ef, int h, uint64_t seed, int64_t max_iters,
                int mode, double wv, double wl, int prec, int seed_mode,
-               const int64_t *seeds_in, int n_seeds,
+               const int64_t *seeds_in, int n_seeds, int vec_round, int rerank,
                int64_t *out_ids, double *out_g, int32_t *out_chi,
                int64_t *out_ndc, int64_t *out_exp, int32_t *out_status)
 {
+    /* vec_round: 0 scores with X itself, 1 with X rounded to bf16, 2 to fp8 e4m3.
+     * rerank: the final pool is re-scored with X in the chosen precision prec and
+     * re-sorted by (Gamma, id) before the first k are returned. */
+    const float *Xs = X;
+    float *Xr = NULL;
+    if (vec_round != 0) {
+        Xr = (float *)malloc(sizeof(float) * (size_t)(N > 0 ? N : 1) * (size_t)d);
+        for (int64_t i = 0; i < N * (int64_t)d; ++i)
+            Xr[i] = vec_round == 1 ? or_round_bf16(X[i]) : or_round_e4m3(X[i]);
+        Xs = Xr;
+    }
     pool_t *pool = (pool_t *)malloc(sizeof(pool_t) * (size_t)ef);
     int64_t *before = (int64_t *)malloc(sizeof(int64_t) * (size_t)ef);
     uint8_t *evaluated = (uint8_t *)malloc((size_t)(N > 0 ? N : 1));
@@ -474,7 +519,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                     continue;
                 evaluated[v] = 1;
                 ++ndc;
-                double g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m,
+                double g = pair_gamma(qv, qa, Xs + v * (int64_t)d, A + v * (int64_t)m, d, m,
                                       mode, wv, wl, prec, NULL);
                 pool_insert(pool, &n, ef, g, v);
             }
@@ -488,7 +533,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                 if (rank == ((int64_t)j * c) / S) {
                     evaluated[v] = 1;
                     ++ndc;
-                    double g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m,
+                    double g = pair_gamma(qv, qa, Xs + v * (int64_t)d, A + v * (int64_t)m, d, m,
                                           mode, wv, wl, prec, NULL);
                     pool_insert(pool, &n, ef, g, v);
                     ++j;
@@ -504,7 +549,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                 evaluated[v] = 1;
                 ++ndc;
                 ++got;
-                double g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m,
+                double g = pair_gamma(qv, qa, Xs + v * (int64_t)d, A + v * (int64_t)m, d, m,
                                       mode, wv, wl, prec, NULL);
                 pool_insert(pool, &n, ef, g, v);
             }
@@ -566,7 +611,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                     continue;
                 evaluated[v] = 1;
                 ++ndc;
-                double g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m,
+                double g = pair_gamma(qv, qa, Xs + v * (int64_t)d, A + v * (int64_t)m, d, m,
                                       mode, wv, wl, prec, NULL);
                 pool_insert(pool, &n, ef, g, v);
             }
@@ -583,6 +628,21 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
             }
         }
 
+        if (rerank && n > 0) {
+            rec_t *rr = (rec_t *)malloc(sizeof(rec_t) * (size_t)n);
+            for (int t = 0; t < n; ++t) {
+                int64_t v = pool[t].id;
+                rr[t].g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m, mode,
+                                     wv, wl, prec, NULL);
+                rr[t].id = v;
+            }
+            qsort(rr, (size_t)n, sizeof(rec_t), rec_cmp);
+            for (int t = 0; t < n; ++t) {
+                pool[t].g = rr[t].g;
+                pool[t].id = rr[t].id;
+            }
+            free(rr);
+        }
         for (int j = 0; j < k; ++j) {
             int64_t o = q * (int64_t)k + j;
             if (j < n) {
@@ -606,4 +666,5 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
     free(sel);
     free(key);
     free(rank_buf);
+    free(Xr);
 }

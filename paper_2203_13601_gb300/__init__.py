@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "NHQError", "Index", "load_library", "library_path",
-    "W_PROPORTIONAL", "W_CONSTANT", "W_FILTER", "VEC_F32", "VEC_BF16",
+    "W_PROPORTIONAL", "W_CONSTANT", "W_FILTER", "VEC_F32", "VEC_BF16", "VEC_FP8E4M3",
     "SEED_RANDOM", "SEED_ATTRIBUTE", "SEED_GIVEN",
     "nhq_last_error", "nhq_version", "nhq_index_create", "nhq_free", "nhq_index_info",
     "nhq_pack_attributes", "nhq_knn", "nhq_edge_select", "nhq_reverse_candidates",
@@ -34,7 +34,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libnhq.so")
 
 W_PROPORTIONAL, W_CONSTANT, W_FILTER = 0, 1, 2
-VEC_F32, VEC_BF16 = 0, 1
+VEC_F32, VEC_BF16, VEC_FP8E4M3 = 0, 1, 2
 SEED_RANDOM, SEED_ATTRIBUTE, SEED_GIVEN = 0, 1, 2
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_ITER_LIMIT, ERR_IO = range(6)
 NONE_ID = 0xFFFFFFFF

@@ -24,6 +24,8 @@
 // id forgotten that way either is in the pool (and re-inserted) or was rejected
 // or evicted while the pool was full, so re-evaluating it rejects it again (its
 // record is above the pool's last record, which only decreases).
+#include <type_traits>
+
 #include "nhq_internal.cuh"
 
 namespace nhq {
@@ -117,56 +119,87 @@ __device__ __forceinline__ int sorted_count_less(const unsigned long long *s, in
 }
 
 template <typename VT>
-__device__ __forceinline__ void accum_chunk(float &acc, const float4 &q0, const float4 &q1,
+struct VecTraits;
+template <>
+struct VecTraits<float> {
+    static constexpr int kPerChunk = 4;  // 16-byte chunk = 4 f32
+};
+template <>
+struct VecTraits<__nv_bfloat16> {
+    static constexpr int kPerChunk = 8;  // 8 bf16
+};
+template <>
+struct VecTraits<__nv_fp8_e4m3> {
+    static constexpr int kPerChunk = 16;  // 16 fp8 e4m3
+};
+
+// the query values matching one 16-byte chunk of a stored row
+template <int PC>
+struct QChunk {
+    float4 v[PC / 4];
+};
+
+template <int PC>
+__device__ __forceinline__ QChunk<PC> load_qchunk(const float *qv, int c) {
+    QChunk<PC> q;
+#pragma unroll
+    for (int i = 0; i < PC / 4; ++i)
+        q.v[i] = reinterpret_cast<const float4 *>(qv)[c * (PC / 4) + i];
+    return q;
+}
+
+__device__ __forceinline__ void sq4(float &acc, const float4 &q, float x0, float x1, float x2,
+                                    float x3) {
+    float t;
+    t = q.x - x0; acc = fmaf(t, t, acc);
+    t = q.y - x1; acc = fmaf(t, t, acc);
+    t = q.z - x2; acc = fmaf(t, t, acc);
+    t = q.w - x3; acc = fmaf(t, t, acc);
+}
+
+template <typename VT>
+__device__ __forceinline__ void accum_chunk(float &acc, const QChunk<VecTraits<VT>::kPerChunk> &q,
                                             const VT *row, int c, bool live);
 
-// f32 rows: chunk c = 4 floats; one float4 of the query
 template <>
-__device__ __forceinline__ void accum_chunk<float>(float &acc, const float4 &q0, const float4 &,
+__device__ __forceinline__ void accum_chunk<float>(float &acc, const QChunk<4> &q,
                                                    const float *row, int c, bool live) {
     if (!live)
         return;
-    float4 x = __ldg(reinterpret_cast<const float4 *>(row) + c);
-    float t;
-    t = q0.x - x.x; acc = fmaf(t, t, acc);
-    t = q0.y - x.y; acc = fmaf(t, t, acc);
-    t = q0.z - x.z; acc = fmaf(t, t, acc);
-    t = q0.w - x.w; acc = fmaf(t, t, acc);
+    const float4 x = __ldg(reinterpret_cast<const float4 *>(row) + c);
+    sq4(acc, q.v[0], x.x, x.y, x.z, x.w);
 }
 
-// bf16 rows: chunk c = 8 values (16 bytes); two float4 of the query
 template <>
-__device__ __forceinline__ void accum_chunk<__nv_bfloat16>(float &acc, const float4 &q0,
-                                                           const float4 &q1,
+__device__ __forceinline__ void accum_chunk<__nv_bfloat16>(float &acc, const QChunk<8> &q,
                                                            const __nv_bfloat16 *row, int c,
                                                            bool live) {
     if (!live)
         return;
-    uint4 raw = __ldg(reinterpret_cast<const uint4 *>(row) + c);
+    const uint4 raw = __ldg(reinterpret_cast<const uint4 *>(row) + c);
     const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&raw);
-    float2 x0 = __bfloat1622float2(h[0]), x1 = __bfloat1622float2(h[1]);
-    float2 x2 = __bfloat1622float2(h[2]), x3 = __bfloat1622float2(h[3]);
-    float t;
-    t = q0.x - x0.x; acc = fmaf(t, t, acc);
-    t = q0.y - x0.y; acc = fmaf(t, t, acc);
-    t = q0.z - x1.x; acc = fmaf(t, t, acc);
-    t = q0.w - x1.y; acc = fmaf(t, t, acc);
-    t = q1.x - x2.x; acc = fmaf(t, t, acc);
-    t = q1.y - x2.y; acc = fmaf(t, t, acc);
-    t = q1.z - x3.x; acc = fmaf(t, t, acc);
-    t = q1.w - x3.y; acc = fmaf(t, t, acc);
+    const float2 x0 = __bfloat1622float2(h[0]), x1 = __bfloat1622float2(h[1]);
+    const float2 x2 = __bfloat1622float2(h[2]), x3 = __bfloat1622float2(h[3]);
+    sq4(acc, q.v[0], x0.x, x0.y, x1.x, x1.y);
+    sq4(acc, q.v[1], x2.x, x2.y, x3.x, x3.y);
 }
 
-template <typename VT>
-struct VecTraits;
 template <>
-struct VecTraits<float> {
-    static constexpr int kPerChunk = 4;
-};
-template <>
-struct VecTraits<__nv_bfloat16> {
-    static constexpr int kPerChunk = 8;
-};
+__device__ __forceinline__ void accum_chunk<__nv_fp8_e4m3>(float &acc, const QChunk<16> &q,
+                                                           const __nv_fp8_e4m3 *row, int c,
+                                                           bool live) {
+    if (!live)
+        return;
+    const uint4 raw = __ldg(reinterpret_cast<const uint4 *>(row) + c);
+    const __nv_fp8x2_storage_t *p2 = reinterpret_cast<const __nv_fp8x2_storage_t *>(&raw);
+    float2 f[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)  // e4m3 -> f16 -> f32 are exact
+        f[i] = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(p2[i], __NV_E4M3)));
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        sq4(acc, q.v[i], f[2 * i].x, f[2 * i].y, f[2 * i + 1].x, f[2 * i + 1].y);
+}
 
 // Squared distances of cnt candidates cid[0..cnt) into d2s[0..cnt).  Teams of 8
 // lanes, two rows per team per pass (8 rows in flight per warp).  CPL > 0: each
@@ -190,20 +223,16 @@ __device__ __forceinline__ void eval_dist2(const VT *__restrict__ X, int xstride
                 const int c = tl + i * TEAM;
                 const bool live = EXACT || c < nchunk;
                 const int cc = EXACT ? c : (live ? c : 0);
-                const float4 qa = reinterpret_cast<const float4 *>(qv)[cc * PC / 4];
-                const float4 qb =
-                    PC == 8 ? reinterpret_cast<const float4 *>(qv)[cc * PC / 4 + 1] : qa;
-                accum_chunk<VT>(acc0, qa, qb, r0, cc, h0 && live);
-                accum_chunk<VT>(acc1, qa, qb, r1, cc, h1 && live);
+                const QChunk<PC> qc = load_qchunk<PC>(qv, cc);
+                accum_chunk<VT>(acc0, qc, r0, cc, h0 && live);
+                accum_chunk<VT>(acc1, qc, r1, cc, h1 && live);
             }
         } else {
 #pragma unroll 4
             for (int c = tl; c < nchunk; c += TEAM) {
-                const float4 qa = reinterpret_cast<const float4 *>(qv)[c * PC / 4];
-                const float4 qb =
-                    PC == 8 ? reinterpret_cast<const float4 *>(qv)[c * PC / 4 + 1] : qa;
-                accum_chunk<VT>(acc0, qa, qb, r0, c, h0);
-                accum_chunk<VT>(acc1, qa, qb, r1, c, h1);
+                const QChunk<PC> qc = load_qchunk<PC>(qv, c);
+                accum_chunk<VT>(acc0, qc, r0, c, h0);
+                accum_chunk<VT>(acc1, qc, r1, c, h1);
             }
         }
         // reduce both rows over the team: the first level swaps halves so that
@@ -645,7 +674,52 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
         }
 
         __syncwarp();
-        for (int j = lane; j < a.k_out; j += 32) {
+        int first_pad = 0;
+        if (!std::is_same<VT, float>::value && a.rerank) {
+            // re-score the final pool with the f32 vectors ...
+            for (int b0 = 0; b0 < n; b0 += CAND) {
+                const int cb = min(CAND, n - b0);
+                for (int j = lane; j < cb; j += 32) {
+                    const uint32_t id = key_id(pool[b0 + j]);
+                    cid[j] = id;
+                    cchi[j] = chi_packed(a.attr[id], qa, amask);
+                }
+                __syncwarp();
+                eval_dist2<float, 0, false>(a.X, a.xstride, qv, cid, d2s, cb, lane);
+                for (int j = lane; j < cb; j += 32)
+                    pool[b0 + j] = candidate_key(j, cb, d2s, cid, cchi, a.w);
+                __syncwarp();
+            }
+            // ... and return its k smallest records by (Gamma, id), one minimum at a time
+            const int kk = min(k, n);
+            for (int j = 0; j < kk; ++j) {
+                unsigned long long best = kInfKey;
+                int bi = -1;
+                for (int i = lane; i < n; i += 32) {
+                    const unsigned long long v = pool[i];
+                    if (v < best) {
+                        best = v;
+                        bi = i;
+                    }
+                }
+                const unsigned long long m = warp_min_key(best);
+                __syncwarp();
+                if (bi >= 0 && best == m)
+                    pool[bi] = kInfKey;
+                if (lane == 0) {
+                    const int64_t o = q * a.k_out + j;
+                    const uint32_t id = key_id(m);
+                    a.ids[o] = id;
+                    if (a.dists)
+                        a.dists[o] = key_gamma(m);
+                    if (a.chi)
+                        a.chi[o] = (uint8_t)chi_packed(a.attr[id], qa, amask);
+                }
+                __syncwarp();
+            }
+            first_pad = kk;
+        }
+        for (int j = first_pad + lane; j < a.k_out; j += 32) {
             const int64_t o = q * a.k_out + j;
             uint32_t id = kNone;
             float g = __int_as_float(0x7f800000);
@@ -749,6 +823,8 @@ cudaError_t launch_search(SearchArgs a, void *scratch, int sm_count, size_t smem
     const size_t smem = L.total * wpb;
     if (a.vec_dtype == NHQ_VEC_BF16)
         return launch_dtype<__nv_bfloat16>(a, a.Xh, ef_cap, wpb, smem, sm_count, s);
+    if (a.vec_dtype == NHQ_VEC_FP8E4M3)
+        return launch_dtype<__nv_fp8_e4m3>(a, a.X8, ef_cap, wpb, smem, sm_count, s);
     return launch_dtype<float>(a, a.X, ef_cap, wpb, smem, sm_count, s);
 }
 

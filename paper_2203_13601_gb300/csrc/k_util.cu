@@ -40,6 +40,16 @@ __global__ void to_bf16_kernel(const float *__restrict__ src, int64_t n,
         dst[i] = __float2bfloat16_rn(src[i]);
 }
 
+__global__ void to_fp8_kernel(const float *__restrict__ src, int64_t n,
+                              __nv_fp8_e4m3 *__restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        __nv_fp8_e4m3 v;
+        v.__x = __nv_cvt_float_to_fp8(src[i], __NV_SATFINITE, __NV_E4M3);
+        dst[i] = v;
+    }
+}
+
 // Also validates the adjacency: an id that is neither kNone nor < N sets *bad.
 __global__ void gather_nbr_attr_kernel(const uint32_t *__restrict__ nbr,
                                        const uint32_t *__restrict__ attr, int64_t N,
@@ -79,6 +89,11 @@ cudaError_t launch_copy_rows(const float *src, int64_t N, int d, int xstride, fl
 
 cudaError_t launch_rows_to_bf16(const float *src, int64_t n, __nv_bfloat16 *dst, cudaStream_t s) {
     to_bf16_kernel<<<grid_for(n), 256, 0, s>>>(src, n, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_to_fp8(const float *src, int64_t n, __nv_fp8_e4m3 *dst, cudaStream_t s) {
+    to_fp8_kernel<<<grid_for(n), 256, 0, s>>>(src, n, dst);
     return cudaGetLastError();
 }
 

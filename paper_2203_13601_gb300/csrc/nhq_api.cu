@@ -205,7 +205,7 @@ nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const ui
     ix->N = N;
     ix->d = d;
     ix->m = m;
-    ix->xstride = (d + 7) & ~7;
+    ix->xstride = (d + 15) & ~15;
     ix->w = w;
     auto bail = [&](nhq_status st) {
         nhq_free(ix);
@@ -256,6 +256,7 @@ void nhq_free(nhq_index *ix) {
     cudaDeviceSynchronize();
     cudaFree(ix->X);
     cudaFree(ix->Xh);
+    cudaFree(ix->X8);
     cudaFree(ix->attr);
     cudaFree(ix->nbr);
     cudaFree(ix->nbr_attr);
@@ -524,7 +525,8 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         return fail(NHQ_ERR_ARG, "h must be in 1..64");
     if (P.max_iters <= 0)
         P.max_iters = 1 << 20;
-    if (P.vec_dtype != NHQ_VEC_F32 && P.vec_dtype != NHQ_VEC_BF16)
+    if (P.vec_dtype != NHQ_VEC_F32 && P.vec_dtype != NHQ_VEC_BF16 &&
+        P.vec_dtype != NHQ_VEC_FP8E4M3)
         return fail(NHQ_ERR_ARG, "unknown vec_dtype %d", P.vec_dtype);
     if (P.hash_bits < 0 || P.hash_bits > 16)
         return fail(NHQ_ERR_ARG, "hash_bits must be in 0..16");
@@ -545,6 +547,10 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         CK(cudaMalloc(&ix->Xh, sizeof(__nv_bfloat16) * (size_t)ix->N * ix->xstride));
         CK(launch_rows_to_bf16(ix->X, (int64_t)ix->N * ix->xstride, ix->Xh, s));
     }
+    if (P.vec_dtype == NHQ_VEC_FP8E4M3 && ix->X8 == nullptr) {
+        CK(cudaMalloc(&ix->X8, sizeof(__nv_fp8_e4m3) * (size_t)ix->N * ix->xstride));
+        CK(launch_rows_to_fp8(ix->X, (int64_t)ix->N * ix->xstride, ix->X8, s));
+    }
     Stager st;
     int iq = st.add(queries, sizeof(float) * (size_t)Q * ix->d, true);
     int ia = st.add(query_attributes, (size_t)Q * ix->m, true);
@@ -563,6 +569,7 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     SearchArgs a{};
     a.X = ix->X;
     a.Xh = ix->Xh;
+    a.X8 = ix->X8;
     a.xstride = ix->xstride;
     a.d = ix->d;
     a.N = ix->N;
@@ -584,7 +591,7 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     a.seed = P.seed;
     a.max_iters = P.max_iters;
     a.vec_dtype = P.vec_dtype;
-    a.rerank = P.rerank;
+    a.rerank = P.vec_dtype != NHQ_VEC_F32 && P.rerank != 0;
     a.ids = (uint32_t *)st.dev(io);
     a.dists = (float *)st.dev(id);
     a.chi = (uint8_t *)st.dev(ic);

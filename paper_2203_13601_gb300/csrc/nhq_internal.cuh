@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 #include "nhq.h"
@@ -71,13 +72,14 @@ __device__ __forceinline__ float key_gamma(unsigned long long k) {
 struct nhq_index {
     int64_t N = 0;
     int d = 0, m = 0, R = 0;
-    int xstride = 0;  // floats per stored row (d rounded up to a multiple of 4)
+    int xstride = 0;  // elements per stored row (d rounded up to a multiple of 16)
     nhq_weights w{};
     int device = 0;
     int sm_count = 0;
     size_t smem_optin = 0;
     float *X = nullptr;            // [N][xstride] f32
     __nv_bfloat16 *Xh = nullptr;   // [N][xstride] bf16 copy (built on first BF16 search)
+    __nv_fp8_e4m3 *X8 = nullptr;   // [N][xstride] fp8 e4m3 copy (built on first FP8 search)
     uint32_t *attr = nullptr;      // [N] packed attributes
     uint32_t *nbr = nullptr;       // [N][R] adjacency, kNone padded
     uint32_t *nbr_attr = nullptr;  // [N][R] packed attributes of each neighbour
@@ -98,6 +100,7 @@ cudaError_t launch_pack_attributes(const uint8_t *a, int64_t n, int m, uint32_t 
 cudaError_t launch_copy_rows(const float *src, int64_t N, int d, int xstride, float *dst,
                              int *nonfinite_flag, cudaStream_t s);
 cudaError_t launch_rows_to_bf16(const float *src, int64_t n_elems, __nv_bfloat16 *dst, cudaStream_t s);
+cudaError_t launch_rows_to_fp8(const float *src, int64_t n_elems, __nv_fp8_e4m3 *dst, cudaStream_t s);
 cudaError_t launch_gather_nbr_attr(const uint32_t *nbr, const uint32_t *attr, int64_t N, int R,
                                    uint32_t *out, int *bad, cudaStream_t s);
 
@@ -134,6 +137,7 @@ cudaError_t launch_reverse_candidates(const uint32_t *nbr, int64_t N, int R, int
 struct SearchArgs {
     const float *X;
     const __nv_bfloat16 *Xh;
+    const __nv_fp8_e4m3 *X8;
     int xstride;
     int d;
     int64_t N;

@@ -410,3 +410,49 @@ def test_search_given_seeds_exact(nhq, graph_case):
         torch.cuda.synchronize()
     assert (ids_i64(ids) == ref["ids"]).all()
     assert torch.equal(ids, ids2)
+
+
+# ------------------------------------------------------------------ reduced-precision scoring
+@pytest.mark.parametrize("vec,rnd", [(1, 1), (2, 2)])
+@pytest.mark.parametrize("rerank", [False, True])
+def test_search_reduced_precision_exact_on_integer_data(nhq, graph_case, vec, rnd, rerank):
+    # 0..255 components round to integers in bf16 and fp8 e4m3, so the scoring
+    # distances stay exact in f32 and the search must equal the oracle's bit for bit
+    w, graphs = graph_case
+    wts, nbr = graphs["const"]
+    ref = O.search(w.X, w.A, nbr, w.Qv, w.QA, 10, 40, seed=5, weights=wts, vec_round=rnd,
+                   rerank=rerank, seed_mode=O.SEED_ATTRIBUTE)
+    with _index(nhq, w, wts) as ix:
+        nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
+        ids, g, chi = empty_out(w.nq, 10)
+        nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 40, ids, g, chi, seed=5,
+                       vec_dtype=vec, rerank=int(rerank), seed_mode=nhq.SEED_ATTRIBUTE)
+        torch.cuda.synchronize()
+    assert (ids_i64(ids) == ref["ids"]).all()
+    assert np.array_equal(g.cpu().numpy().astype(np.float64), ref["gamma"])
+    assert (chi.cpu().numpy().astype(np.int32) == ref["chi"]).all()
+
+
+def test_search_rerank_on_float_data(nhq):
+    # unit-normalised float rows: bf16 / fp8 scoring with an f32 re-rank; values must
+    # be the exact f32 Gamma of the returned ids and ids equal up to near-ties
+    w = synth.c3(N=3000, nq=40, d=96, cards=(2, 5), n_comp=20, seed=45)
+    nbr, _, _ = O.build_graph(w.X, w.A, R=16, K=32, prec=O.F32)
+    for vec, rnd in ((1, O.ROUND_BF16), (2, O.ROUND_E4M3)):
+        ref = O.search(w.X, w.A, nbr, w.Qv, w.QA, 10, 48, seed=2, vec_round=rnd, rerank=True)
+        with _index(nhq, w) as ix:
+            nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
+            ids, g, chi = empty_out(w.nq, 10)
+            nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 48, ids, g, chi, seed=2,
+                           vec_dtype=vec, rerank=1)
+            torch.cuda.synchronize()
+        got, gg = ids_i64(ids), g.cpu().numpy()
+        for q in range(w.nq):
+            exact = [O.gamma(O.delta(w.Qv[q], w.X[i], O.F64), O.chi(w.QA[q], w.A[i]), w.m)
+                     for i in got[q]]
+            assert np.allclose(gg[q], exact, rtol=1e-5, atol=0)
+            assert (np.diff(gg[q]) >= 0).all()
+        # the pool decisions use the rounded copy; ids may differ only where the
+        # rounded Gammas nearly tie, so require a high overlap with the oracle
+        overlap = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(got, ref["ids"])])
+        assert overlap > 0.97, (vec, overlap)

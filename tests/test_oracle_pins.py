@@ -358,3 +358,47 @@ def test_recall_definitions(oracle_mod):
     r, excl = O.hybrid_recall(found, A, QA, truth, np.array([0, 1]))
     assert excl == 1 and r == 1.0
     assert math.isfinite(r)
+
+
+# ------------------------------------------------------------------ reduced-precision copies
+def test_bf16_rounding_follows_the_format(oracle_mod):
+    O = oracle_mod
+    for x in (0.0, 1.0, -2.5, 255.0, 0.15625, 3.0e38):
+        # values with at most 8 significant bits are representable and unchanged
+        if x in (0.0, 1.0, -2.5, 255.0, 0.15625):
+            assert O.round_bf16(x) == x
+    assert O.round_bf16(1 + 2**-8) == 1.0                  # halfway: to even (1.0)
+    assert O.round_bf16(1 + 3 * 2**-8) == 1 + 2**-6        # halfway: to even (1 + 2^-6)
+    assert O.round_bf16(1 + 2**-8 + 2**-12) == 1 + 2**-7   # above halfway: up
+    assert O.round_bf16(-(1 + 2**-8 + 2**-12)) == -(1 + 2**-7)
+
+
+def test_e4m3_rounding_follows_the_format(oracle_mod):
+    O = oracle_mod
+    for x in (0.0, 1.0, 1.125, 16.0, 18.0, 448.0, -240.0, 2**-6, 2**-9, 3 * 2**-9):
+        assert O.round_e4m3(x) == x                        # representable values
+    assert O.round_e4m3(17.0) == 16.0                      # halfway 16|18: to even
+    assert O.round_e4m3(19.0) == 20.0                      # halfway 18|20: to even
+    assert O.round_e4m3(1.0625) == 1.0                     # halfway 1|1.125: to even
+    assert O.round_e4m3(470.0) == 448.0 and O.round_e4m3(-1e6) == -448.0   # saturation
+    assert O.round_e4m3(2**-10) == 0.0                     # half the smallest subnormal: even
+    assert O.round_e4m3(3 * 2**-10) == 2**-8               # halfway 2^-9|2^-8: to even
+    assert O.round_e4m3(2**-10 + 2**-14) == 2**-9          # above halfway: up
+
+
+def test_reduced_precision_search_equals_plain_on_exact_data(oracle_mod):
+    O = oracle_mod
+    # integer components 0..255 are exact in bf16: scoring with the copy changes nothing
+    w = synth.int_valued(600, 20, 16, seed=17)
+    nbr, _, _ = O.build_graph(w.X, w.A, R=8, K=16)
+    a = O.search(w.X, w.A, nbr, w.Qv, w.QA, 5, 20, seed=3)
+    b = O.search(w.X, w.A, nbr, w.Qv, w.QA, 5, 20, seed=3, vec_round=O.ROUND_BF16)
+    c = O.search(w.X, w.A, nbr, w.Qv, w.QA, 5, 20, seed=3, vec_round=O.ROUND_BF16, rerank=True)
+    assert (a["ids"] == b["ids"]).all() and (a["ids"] == c["ids"]).all()
+    # fp8 scoring differs, and the re-rank returns exact Gamma values for its ids
+    d = O.search(w.X, w.A, nbr, w.Qv, w.QA, 5, 20, seed=3, vec_round=O.ROUND_E4M3, rerank=True)
+    for q in range(w.nq):
+        for j, i in enumerate(d["ids"][q]):
+            g = O.gamma(O.delta(w.Qv[q], w.X[i], O.F32), O.chi(w.QA[q], w.A[i]), w.m, prec=O.F32)
+            assert d["gamma"][q, j] == g
+        assert all(np.diff(d["gamma"][q]) >= 0)
