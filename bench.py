@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--R", type=int, default=32)
     ap.add_argument("--target", type=float, default=0.95)
+    ap.add_argument("--target2", type=float, default=0.98,
+                    help="a second recall level at which the forms are also compared")
     ap.add_argument("--efs", default="10,12,16,20,24,32,40,48,64,80,96,128,160,200,256,320,400,500")
     ap.add_argument("--hs", default="1,2")
     ap.add_argument("--cpu-sample", type=int, default=40, help="queries in the oracle sample")
@@ -58,6 +60,9 @@ def parse():
     ap.add_argument("--fixed", default=None, help="skip the sweep: ef,h,vec (e.g. 64,1,1)")
     ap.add_argument("--seed-mode", type=int, default=1,
                     help="seed set B: 0 random (the paper's), 1 attribute entry")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned early stop")
+    ap.add_argument("--learned-efs", default="16,24,32,48,64")
+    ap.add_argument("--taus", default="0.7,0.8,0.9,0.95")
     return ap.parse_args()
 
 
@@ -66,11 +71,11 @@ def workload_name(a):
             f"Zipf s=1, {a.nq:,} queries, k={a.k}, R={a.R}, weights w_v=1 w_l=10000")
 
 
-def make_workload(a):
+def make_workload(a, query_stream=0):
     import synth
 
     n_comp = 1000 if a.n >= 100_000 else max(10, a.n // 100)
-    return synth.c2(N=a.n, nq=a.nq, d=a.d, n_comp=n_comp)
+    return synth.c2(N=a.n, nq=a.nq, d=a.d, n_comp=n_comp, query_stream=query_stream)
 
 
 # ---------------------------------------------------------------- clocks
@@ -263,13 +268,16 @@ def main():
     ndc = torch.empty(w.nq, dtype=torch.int32, device=dev)
     exps = torch.empty(w.nq, dtype=torch.int32, device=dev)
 
+    sel = {"model": None, "tau": 0.5}
+
     def run(ef, h, vec, diag=False):
         # the reduced-precision copies are re-ranked in f32 (vec 2 = fp8 needs it; bf16 is
         # exact on this integer data and runs without)
         nhq.nhq_search(ix.handle, Qv, QA, a.k, ef, ids, dists, chi,
                        ndc=ndc if diag else None, expansions=exps if diag else None,
                        h=h, seed=12345, vec_dtype=vec, rerank=int(vec == nhq.VEC_FP8E4M3),
-                       seed_mode=a.seed_mode, stream=stream)
+                       seed_mode=a.seed_mode, stop_model=sel["model"],
+                       stop_threshold=sel["tau"], stop_min=4, stop_every=2, stream=stream)
 
     def time_once(ef, h, vec, reps=2):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -300,24 +308,92 @@ def main():
                     continue
                 efs = [cand_list[0][0]]
             for ef in efs:
-                run(ef, h, vec)
+                run(ef, h, vec, diag=True)
                 torch.cuda.synchronize()
                 rec, excl = hybrid_recall(ids.cpu().numpy(), w.A, w.QA, gt_h, P, a.k)
                 ms = time_once(ef, h, vec)
                 sweep.append({"ef": ef, "h": h, "vec": VEC_NAMES[vec], "recall": rec,
-                              "ms": ms})
-                if rec >= a.target or cand_list:
+                              "ms": ms, "mean_expansions": float(exps.float().mean().item())})
+                if found is None and (rec >= a.target or cand_list):
                     found = (ef, h, vec, rec, ms)
+                if rec >= a.target2 or cand_list:
                     break
             if found:
                 choices.append(found)
                 if vec == nhq.VEC_F32 and (plain is None or found[4] < plain[4]):
                     plain = found
+    # learned early stop: traces of training queries (same mixture, independent
+    # stream), the MLP trained on the GPU, then a sweep of (ef, threshold)
+    learned = None
+    stop_model = None
+    if not a.no_learned and not a.fixed:
+        t0 = time.perf_counter()
+        wtr = make_workload(a, query_stream=1)
+        Qtr = torch.from_numpy(wtr.Qv).to(dev)
+        QAtr = torch.from_numpy(wtr.QA).to(dev)
+        cap = 40 * wtr.nq
+        feats = torch.empty((cap, nhq.MLP_INPUTS), dtype=torch.float32, device=dev)
+        labels = torch.empty(cap, dtype=torch.uint8, device=dev)
+        tq = torch.empty(cap, dtype=torch.int32, device=dev)
+        ef_tr = max(int(x) for x in a.learned_efs.split(","))
+        ntr = nhq.nhq_search_trace(ix.handle, Qtr, QAtr, a.k, ef_tr, feats, labels, tq,
+                                   stop_min=4, stop_every=2, seed_mode=a.seed_mode)
+        perm = torch.randperm(ntr, generator=torch.Generator().manual_seed(0)).to(dev)
+        F = feats[:ntr][perm].contiguous()
+        Y = labels[:ntr][perm].to(torch.float32).contiguous()
+        init = np.random.default_rng(9).standard_normal(nhq.MLP_PARAMS).astype(np.float32) * 0.1
+        init[-1] = 0.0
+        stop_model = torch.from_numpy(init).to(dev)
+        nhq.nhq_mlp_train(stop_model, F, Y, epochs=8, batch=2048, lr=2e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        del feats, labels, tq, F, Y
+        lsweep = []
+        for lef in [int(x) for x in a.learned_efs.split(",") if int(x) >= a.k]:
+            for tau in [float(x) for x in a.taus.split(",")]:
+                def run_l(lef=lef, tau=tau, diag=False):
+                    nhq.nhq_search(ix.handle, Qv, QA, a.k, lef, ids, dists, chi, h=1,
+                                   expansions=exps if diag else None, seed=12345,
+                                   seed_mode=a.seed_mode, stop_model=stop_model,
+                                   stop_threshold=tau, stop_min=4, stop_every=2, stream=stream)
+                run_l(diag=True)
+                torch.cuda.synchronize()
+                rec, _ = hybrid_recall(ids.cpu().numpy(), w.A, w.QA, gt_h, P, a.k)
+                mexp = float(exps.float().mean().item())
+                ev0, ev1 = (torch.cuda.Event(enable_timing=True),
+                            torch.cuda.Event(enable_timing=True))
+                run_l()
+                ev0.record(stream)
+                run_l()
+                run_l()
+                ev1.record(stream)
+                ev1.synchronize()
+                ms = ev0.elapsed_time(ev1) / 2
+                lsweep.append({"ef": lef, "tau": tau, "recall": rec, "ms": ms,
+                               "mean_expansions": mexp})
+        ok = [x for x in lsweep if x["recall"] >= a.target]
+        if ok:
+            learned = min(ok, key=lambda x: x["ms"])
+        ok2 = [x for x in lsweep if x["recall"] >= a.target2]
+        plain2 = [x for x in sweep if x["recall"] >= a.target2 and x["vec"] == "f32"]
+        learned_info = {"traces": int(ntr), "train_s": t_train, "sweep": lsweep,
+                        "chosen": learned,
+                        "at_target2": {
+                            "target": a.target2,
+                            "learned": min(ok2, key=lambda x: x["ms"]) if ok2 else None,
+                            "plain_f32": min(plain2, key=lambda x: x["ms"]) if plain2 else None}}
+
     if not choices:
         raise SystemExit(f"no setting reached hybrid Recall@{a.k} >= {a.target}: {sweep}")
     best = min(choices, key=lambda c: c[4])
     ef, h, vec, rec, _ = best
+    use_learned = learned is not None and learned["ms"] < best[4]
+    tau = 0.5
+    if use_learned:
+        ef, h, vec, rec, tau = learned["ef"], 1, nhq.VEC_F32, learned["recall"], learned["tau"]
 
+    if use_learned:
+        sel["model"], sel["tau"] = stop_model, tau
     # diagnostics at the chosen setting: NDC and expansions for the algorithmic bytes
     run(ef, h, vec, diag=True)
     torch.cuda.synchronize()
@@ -373,7 +449,8 @@ def main():
     def run_host():
         nhq.nhq_search(ix.handle, Qh, QAh, a.k, ef, ids_h, d_h, c_h, h=h, seed=12345,
                        vec_dtype=vec, rerank=int(vec == nhq.VEC_FP8E4M3),
-                       seed_mode=a.seed_mode, stream=stream)
+                       seed_mode=a.seed_mode, stop_model=sel["model"],
+                       stop_threshold=sel["tau"], stop_min=4, stop_every=2, stream=stream)
 
     for _ in range(max(3, a.warmup)):
         run_host()
@@ -394,6 +471,8 @@ def main():
         "config": {"workload": workload_name(a), "ef": ef, "h": h,
                    "seed_set": ["random (Sec. 3.2)", "attribute entry"][a.seed_mode],
                    "scoring_copy": VEC_NAMES[vec] + (" + f32 re-rank" if vec == 2 else ""),
+                   "learned_stop": ({"threshold": tau, "stop_min": 4, "stop_every": 2}
+                                    if use_learned else None),
                    "recall": rec,
                    "recall_kind": "hybrid Recall@10 vs filter-mode brute force",
                    "l2": "inputs larger than L2 (vectors 512 MB + adjacency 256 MB)",
@@ -402,6 +481,7 @@ def main():
         "plain_f32": ({"ef": plain[0], "h": plain[1], "recall": plain[3],
                        "qps": w.nq / (plain[4] / 1000.0)} if plain else None),
         "sweep": sweep,
+        "learned": learned_info if (not a.no_learned and not a.fixed) else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_kind": peak_kind,

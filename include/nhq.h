@@ -88,6 +88,14 @@ typedef enum nhq_seed_mode {
     NHQ_SEED_GIVEN = 2      /* B = the valid distinct ids of seeds[q][0..n_seeds)            */
 } nhq_seed_mode;
 
+/* Learned early stop (a project addition; the paper's search has no learned
+ * part): a 2-layer perceptron with NHQ_MLP_INPUTS inputs, NHQ_MLP_HIDDEN ReLU
+ * units and one logit.  Parameters are one flat f32 vector:
+ * W1[NHQ_MLP_INPUTS][NHQ_MLP_HIDDEN] (input-major) | b1 | W2 | b2. */
+#define NHQ_MLP_INPUTS 8
+#define NHQ_MLP_HIDDEN 64
+#define NHQ_MLP_PARAMS (NHQ_MLP_INPUTS * NHQ_MLP_HIDDEN + 2 * NHQ_MLP_HIDDEN + 1)
+
 typedef struct nhq_search_params {
     uint64_t seed;           /* random seeds and S1 neighbour subsets derive from splitmix64(seed) */
     int32_t h;               /* two-stage routing: S1 visits ceil(R/h) neighbours; 1 = off     */
@@ -100,6 +108,11 @@ typedef struct nhq_search_params {
     int32_t n_seeds;         /* NHQ_SEED_GIVEN: row width of `seeds`, 1..64                     */
     const uint32_t *seeds;   /* NHQ_SEED_GIVEN: [Q][n_seeds] ids (device or host), 0xFFFFFFFF
                                 entries are skipped                                           */
+    const float *stop_model; /* device, NHQ_MLP_PARAMS f32, or NULL: no learned stop         */
+    float stop_threshold;    /* stop when sigmoid(logit) > this probability                   */
+    int32_t stop_min;        /* first expansion count at which the model is consulted          */
+    int32_t stop_every;      /* consult it every this many expansions (>= 1 when a model is set) */
+    int32_t reserved;
 } nhq_search_params;
 
 typedef struct nhq_index nhq_index;
@@ -250,6 +263,39 @@ nhq_status nhq_brute_force_noalloc(const float *vectors, const uint32_t *packed_
                                    const uint32_t *packed_query_attributes, int64_t Q, int32_t k,
                                    nhq_weights w, uint32_t *ids, float *dists, uint8_t *chi,
                                    void *stream);
+
+/*
+ * Learned early stop, training data.  Runs nhq_search (params->stop_model is
+ * ignored) and, at every expansion count c >= params->stop_min with
+ * (c - stop_min) % stop_every == 0 while the pool holds >= k records, records the
+ * model's NHQ_MLP_INPUTS features (beam statistics: expansions so far, spread of
+ * the top-k, distance of the pool's last record, depth and distance of the next
+ * parent, records inserted by the last expansion, expansions since the top-k last
+ * changed, pool fill) into features[cap][NHQ_MLP_INPUTS], the query row into
+ * query[cap], and labels[cap] = 1 if stopping there would return the same top-k
+ * ids in the same order as the full search, else 0.  *n_traces receives the
+ * number of records produced (records beyond cap are dropped).  Device pointers.
+ */
+nhq_status nhq_search_trace(const nhq_index *index, const float *queries,
+                            const uint8_t *query_attributes, int64_t Q, int32_t k, int32_t ef,
+                            const nhq_search_params *params, float *features, uint8_t *labels,
+                            int32_t *query, int64_t cap, int64_t *n_traces, void *stream);
+
+/* Model logits for features[n][NHQ_MLP_INPUTS] with the fp16-rounded weights the
+ * search reads (f32 accumulation).  Device pointers. */
+nhq_status nhq_mlp_forward(const float *params, const float *features, int64_t n, float *logits,
+                           void *stream);
+
+/* Mean binary cross-entropy with logits over n samples (labels 0/1 as f32) and its
+ * gradient w.r.t. the f32 parameters, written to grad[NHQ_MLP_PARAMS] and *loss.
+ * Device pointers. */
+nhq_status nhq_mlp_grad(const float *params, const float *features, const float *labels,
+                        int64_t n, float *grad, float *loss, void *stream);
+
+/* Trains params in place with Adam (beta1 0.9, beta2 0.999) on batches of `batch`
+ * consecutive samples for `epochs` passes.  Device pointers. */
+nhq_status nhq_mlp_train(float *params, const float *features, const float *labels, int64_t n,
+                         int32_t epochs, int32_t batch, float lr, void *stream);
 
 /*
  * Index persistence: header {magic "NHQIDX01", version, N, d, m, R, weights}

@@ -27,7 +27,8 @@ __all__ = [
     "nhq_pack_attributes", "nhq_knn", "nhq_edge_select", "nhq_reverse_candidates",
     "nhq_index_set_graph", "nhq_index_get_graph", "nhq_index_build", "nhq_build",
     "nhq_brute_force", "nhq_search", "nhq_search_batched", "nhq_save", "nhq_load",
-    "nhq_brute_force_noalloc",
+    "nhq_brute_force_noalloc", "nhq_search_trace", "nhq_mlp_forward", "nhq_mlp_grad",
+    "nhq_mlp_train", "MLP_INPUTS", "MLP_HIDDEN", "MLP_PARAMS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -36,6 +37,8 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libnhq.so")
 W_PROPORTIONAL, W_CONSTANT, W_FILTER = 0, 1, 2
 VEC_F32, VEC_BF16, VEC_FP8E4M3 = 0, 1, 2
 SEED_RANDOM, SEED_ATTRIBUTE, SEED_GIVEN = 0, 1, 2
+MLP_INPUTS, MLP_HIDDEN = 8, 64
+MLP_PARAMS = MLP_INPUTS * MLP_HIDDEN + 2 * MLP_HIDDEN + 1
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_ITER_LIMIT, ERR_IO = range(6)
 NONE_ID = 0xFFFFFFFF
 
@@ -59,7 +62,9 @@ class _SearchParams(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("h", C.c_int32), ("max_iters", C.c_int32),
                 ("warps_per_block", C.c_int32), ("hash_bits", C.c_int32),
                 ("vec_dtype", C.c_int32), ("rerank", C.c_int32), ("seed_mode", C.c_int32),
-                ("n_seeds", C.c_int32), ("seeds", C.c_void_p)]
+                ("n_seeds", C.c_int32), ("seeds", C.c_void_p), ("stop_model", C.c_void_p),
+                ("stop_threshold", C.c_float), ("stop_min", C.c_int32),
+                ("stop_every", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -104,6 +109,11 @@ def load_library():
                                        P, P, P, P]),
             "nhq_brute_force_noalloc": (S, [P, P, i64, i32, i32, P, P, i64, i32, _Weights, P, P,
                                             P, P]),
+            "nhq_search_trace": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P, P, P,
+                                     i64, C.POINTER(C.c_int64), P]),
+            "nhq_mlp_forward": (S, [P, P, i64, P, P]),
+            "nhq_mlp_grad": (S, [P, P, P, i64, P, P, P]),
+            "nhq_mlp_train": (S, [P, P, P, i64, i32, i32, C.c_float, P]),
             "nhq_save": (S, [P, C.c_char_p]),
             "nhq_load": (S, [C.c_char_p, P, C.POINTER(P)]),
         }
@@ -282,26 +292,31 @@ def nhq_brute_force(index, queries, query_attributes, k, ids, dists=None, chi=No
 
 
 def _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
-                   seed_mode=SEED_RANDOM, seeds=None, Q=None):
-    """Search parameters; ``seeds`` ([Q][n] uint32, 0xFFFFFFFF = none) selects SEED_GIVEN."""
+                   seed_mode=SEED_RANDOM, seeds=None, Q=None, stop_model=None,
+                   stop_threshold=0.5, stop_min=0, stop_every=1):
+    """Search parameters; ``seeds`` ([Q][n] uint32, 0xFFFFFFFF = none) selects SEED_GIVEN;
+    ``stop_model`` (device f32 [MLP_PARAMS]) turns on the learned early stop."""
     n_seeds, sp = 0, None
     if seeds is not None:
         seed_mode = SEED_GIVEN
         n_seeds = _shape(seeds)[1]
         sp = _ptr(seeds, np.uint32, (Q, n_seeds), "seeds")
+    mp = _ptr(stop_model, np.float32, (MLP_PARAMS,), "stop_model")
     return _SearchParams(int(seed) & (2**64 - 1), int(h), int(max_iters), int(warps_per_block),
                          int(hash_bits), int(vec_dtype), int(rerank), int(seed_mode),
-                         int(n_seeds), sp)
+                         int(n_seeds), sp, mp, float(stop_threshold), int(stop_min),
+                         int(stop_every), 0)
 
 
 def nhq_search(index, queries, query_attributes, k, ef, ids, dists=None, chi=None, status=None,
                ndc=None, expansions=None, h=1, seed=0, max_iters=0, warps_per_block=0,
                hash_bits=0, vec_dtype=VEC_F32, rerank=0, seed_mode=SEED_RANDOM, seeds=None,
+               stop_model=None, stop_threshold=0.5, stop_min=0, stop_every=1,
                stream=None) -> None:
     Q, d = _shape(queries)
     m = _shape(query_attributes)[1]
     p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
-                       seed_mode, seeds, Q)
+                       seed_mode, seeds, Q, stop_model, stop_threshold, stop_min, stop_every)
     _check(load_library().nhq_search(
         index, _ptr(queries, np.float32, (Q, d), "queries"),
         _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, ef, C.byref(p),
@@ -344,6 +359,50 @@ def nhq_brute_force_noalloc(vectors, packed_attributes, m, queries, packed_query
         _weights(weights), _ptr(ids, np.uint32, (Q, k), "ids"),
         _ptr(dists, np.float32, (Q, k), "dists"), _ptr(chi, np.uint8, (Q, k), "chi"),
         _stream(stream)))
+
+
+def nhq_search_trace(index, queries, query_attributes, k, ef, features, labels, query,
+                     stop_min=0, stop_every=1, h=1, seed=0, seed_mode=SEED_RANDOM,
+                     vec_dtype=VEC_F32, stream=None) -> int:
+    """Training records for the learned stop (device arrays); returns their count."""
+    Q, d = _shape(queries)
+    m = _shape(query_attributes)[1]
+    cap = _shape(labels)[0]
+    p = _search_params(seed, h, 0, 0, 0, vec_dtype, 0, seed_mode, None, Q, None, 0.5, stop_min,
+                       stop_every)
+    n = C.c_int64(0)
+    _check(load_library().nhq_search_trace(
+        index, _ptr(queries, np.float32, (Q, d), "queries"),
+        _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, ef, C.byref(p),
+        _ptr(features, np.float32, (cap, MLP_INPUTS), "features"),
+        _ptr(labels, np.uint8, (cap,), "labels"), _ptr(query, np.int32, (cap,), "query"), cap,
+        C.byref(n), _stream(stream)))
+    return n.value
+
+
+def nhq_mlp_forward(params, features, logits, stream=None) -> None:
+    n = _shape(features)[0]
+    _check(load_library().nhq_mlp_forward(_ptr(params, np.float32, (MLP_PARAMS,), "params"),
+                                          _ptr(features, np.float32, (n, MLP_INPUTS), "features"),
+                                          n, _ptr(logits, np.float32, (n,), "logits"),
+                                          _stream(stream)))
+
+
+def nhq_mlp_grad(params, features, labels, grad, loss, stream=None) -> None:
+    n = _shape(features)[0]
+    _check(load_library().nhq_mlp_grad(_ptr(params, np.float32, (MLP_PARAMS,), "params"),
+                                       _ptr(features, np.float32, (n, MLP_INPUTS), "features"),
+                                       _ptr(labels, np.float32, (n,), "labels"), n,
+                                       _ptr(grad, np.float32, (MLP_PARAMS,), "grad"),
+                                       _ptr(loss, np.float32, (1,), "loss"), _stream(stream)))
+
+
+def nhq_mlp_train(params, features, labels, epochs=3, batch=4096, lr=1e-3, stream=None) -> None:
+    n = _shape(features)[0]
+    _check(load_library().nhq_mlp_train(_ptr(params, np.float32, (MLP_PARAMS,), "params"),
+                                        _ptr(features, np.float32, (n, MLP_INPUTS), "features"),
+                                        _ptr(labels, np.float32, (n,), "labels"), n, epochs,
+                                        batch, float(lr), _stream(stream)))
 
 
 def nhq_save(index, path) -> None:

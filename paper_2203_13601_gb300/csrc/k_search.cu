@@ -397,6 +397,40 @@ __device__ __forceinline__ Adjacency load_adjacency(const SearchArgs &a, uint32_
     return r;
 }
 
+// Hash of the first kk pool ids in order (equal hashes <=> same top-k, up to collisions).
+__device__ __forceinline__ unsigned long long topk_hash(const unsigned long long *pool, int kk,
+                                                        int lane) {
+    unsigned long long h = 0ull;
+    for (int j = lane; j < kk; j += 32)
+        h ^= mix64((unsigned long long)key_id(pool[j]) * kGolden + (unsigned long long)(j + 1));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        h ^= __shfl_xor_sync(FULL, h, o);
+    return h;
+}
+
+// Beam statistics fed to the learned early-stop model (warp-uniform).
+__device__ __forceinline__ void stop_features(float *f, const unsigned long long *pool, int n,
+                                              int k, int ef, int pidx, int iters, int last_surv,
+                                              int since_change, int R) {
+    // fast approximate operations are enough here: training traces and the
+    // decisions both come from this same code
+    const int kk = min(k, n);
+    const float g0 = key_gamma(pool[0]);
+    const float gk = key_gamma(pool[kk - 1]);
+    const float gl = key_gamma(pool[n - 1]);
+    const float gp = key_gamma(pool[pidx]);
+    const float ik = __frcp_rn(gk + 1e-6f);
+    f[0] = __logf(1.f + (float)iters) * 0.25f;                  // expansions so far
+    f[1] = fminf(__fdividef(gk, g0 + 1e-6f) - 1.f, 10.f);        // spread of the top-k
+    f[2] = fminf(gl * ik - 1.f, 10.f);                          // last record vs k-th
+    f[3] = __fdividef((float)pidx, (float)ef);                  // depth of the next parent
+    f[4] = fminf(gp * ik, 10.f);                                // next parent vs k-th
+    f[5] = __fdividef((float)last_surv, (float)R);              // records inserted last time
+    f[6] = __logf(1.f + (float)since_change) * 0.33f;           // expansions since a top-k change
+    f[7] = __fdividef((float)n, (float)ef);                     // pool fill
+}
+
 __device__ __forceinline__ void clear_expanded(unsigned long long *pool, int n, int lane) {
     __syncwarp();
     for (int i = lane; i < n; i += 32)
@@ -449,6 +483,13 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
     const int H = 1 << a.hash_bits;
     const int R = a.R;
     const uint32_t amask = a.w.mask;
+    // the learned stop's fp16 weights, staged once per block after the warps' areas
+    __half *w16 = reinterpret_cast<__half *>(smem + (blockDim.x >> 5) * L.total);
+    if (a.stop_w16 != nullptr) {
+        for (int i = threadIdx.x; i < NHQ_MLP_PARAMS; i += blockDim.x)
+            w16[i] = a.stop_w16[i];
+        __syncthreads();
+    }
 
     for (;;) {
         unsigned long long qq = 0;
@@ -540,6 +581,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
         Adjacency adj{kNone, kNone, 0u, 0u};
         if (pidx >= 0)
             adj = load_adjacency<TWO>(a, key_id(pool[pidx]), lane);
+        int last_surv = 0, since_change = 0;  // beam statistics of the learned stop
         for (;;) {
             if (pidx < 0) {
                 if (stage == 1) {  // S1 exhausted C: S2 with C = C u R
@@ -552,6 +594,27 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
                     continue;
                 }
                 break;
+            }
+            if (a.stop_every > 0 && iters >= a.stop_min &&
+                (iters - a.stop_min) % a.stop_every == 0 && n >= k) {
+                float f[NHQ_MLP_INPUTS];
+                stop_features(f, pool, n, k, ef, pidx, iters, last_surv, since_change, R);
+                if (a.tr_feat != nullptr) {  // training record: features now, label later
+                    const unsigned long long th = topk_hash(pool, min(k, n), lane);
+                    unsigned int slot = 0;
+                    if (lane == 0)
+                        slot = atomicAdd(a.tr_count, 1u);
+                    slot = __shfl_sync(FULL, slot, 0);
+                    if (lane == 0 && (int64_t)slot < a.tr_cap) {
+#pragma unroll
+                        for (int i = 0; i < NHQ_MLP_INPUTS; ++i)
+                            a.tr_feat[(int64_t)slot * NHQ_MLP_INPUTS + i] = f[i];
+                        a.tr_hash[slot] = th;
+                        a.tr_q[slot] = (int32_t)q;
+                    }
+                }
+                if (a.stop_w16 != nullptr && mlp_logit_warp(w16, f, lane) > a.stop_logit)
+                    break;  // the model predicts the top-k will not change any more
             }
             if (iters >= a.max_iters) {
                 status = NHQ_ERR_ITER_LIMIT;
@@ -641,6 +704,9 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
                                     ef, rebuilt);
             }
             const unsigned long long cmin = warp_min_key(k0 < k1 ? k0 : k1);
+            if (a.stop_every > 0)
+                last_surv = __popc(__ballot_sync(FULL, k0 != kInfKey)) +
+                            (TWO ? __popc(__ballot_sync(FULL, k1 != kInfKey)) : 0);
             // next parent and its adjacency, before the merge
             const int uo = first_unexpanded(pool, n, cursor, lane);
             const unsigned long long uo_key = uo >= 0 ? (pool[uo] & ~1ull) : kInfKey;
@@ -656,6 +722,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
             }
             if (next >= 0)
                 adj = load_adjacency<TWO>(a, next_id, lane);
+            since_change = (cmin != kInfKey && cpos < k) ? 0 : since_change + 1;
             if (cmin != kInfKey) {
                 merge_round(pool, n, ef, k0, sorted32, lane);
                 if (TWO)
@@ -674,6 +741,11 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
         }
 
         __syncwarp();
+        if (a.tr_final != nullptr) {
+            const unsigned long long th = topk_hash(pool, min(k, n), lane);
+            if (lane == 0)
+                a.tr_final[q] = th;
+        }
         int first_pad = 0;
         if (!std::is_same<VT, float>::value && a.rerank) {
             // re-score the final pool with the f32 vectors ...
@@ -816,11 +888,11 @@ cudaError_t launch_search(SearchArgs a, void *scratch, int sm_count, size_t smem
         return cudaErrorInvalidValue;
     const WarpLayout L = warp_layout(ef_cap, a.hash_bits, a.xstride);
     int wpb = a.warps_per_block > 0 ? a.warps_per_block : 8;
-    while (wpb > 1 && L.total * wpb > smem_optin)
+    while (wpb > 1 && L.total * wpb + 2048 > smem_optin)
         wpb >>= 1;
-    if (L.total * wpb > smem_optin)
+    if (L.total * wpb + 2048 > smem_optin)
         return cudaErrorInvalidValue;
-    const size_t smem = L.total * wpb;
+    const size_t smem = L.total * wpb + (a.stop_w16 != nullptr ? 2 * 656 : 0);
     if (a.vec_dtype == NHQ_VEC_BF16)
         return launch_dtype<__nv_bfloat16>(a, a.Xh, ef_cap, wpb, smem, sm_count, s);
     if (a.vec_dtype == NHQ_VEC_FP8E4M3)

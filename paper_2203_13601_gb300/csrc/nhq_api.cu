@@ -508,12 +508,20 @@ nhq_status nhq_brute_force(const nhq_index *cix, const float *queries,
     return st.finish(s);
 }
 
+struct TraceOut {
+    float *features = nullptr;
+    uint8_t *labels = nullptr;
+    int32_t *query = nullptr;
+    int64_t cap = 0;
+    int64_t *n_traces = nullptr;
+};
+
 static nhq_status search_common(const nhq_index *cix, const float *queries,
                                 const uint8_t *query_attributes, int64_t Q, const int32_t *k_arr,
                                 const int32_t *ef_arr, int32_t k, int32_t ef, int32_t k_out,
                                 const nhq_search_params *p, uint32_t *ids, float *dists,
                                 uint8_t *chi, int32_t *status, int32_t *ndc, int32_t *expansions,
-                                void *stream) {
+                                void *stream, const TraceOut *trace = nullptr) {
     nhq_index *ix = const_cast<nhq_index *>(cix);
     cudaStream_t s = as_stream(stream);
     nhq_search_params P{};
@@ -536,6 +544,17 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         return fail(NHQ_ERR_ARG, "unknown seed_mode %d", P.seed_mode);
     if (P.seed_mode == NHQ_SEED_GIVEN && (P.seeds == nullptr || P.n_seeds < 1 || P.n_seeds > 64))
         return fail(NHQ_ERR_ARG, "NHQ_SEED_GIVEN needs seeds and n_seeds in 1..64");
+    const bool use_model = P.stop_model != nullptr && trace == nullptr;
+    if (use_model || trace != nullptr) {
+        if (P.stop_min < 0 || P.stop_every < 1)
+            return fail(NHQ_ERR_ARG, "stop_min must be >= 0 and stop_every >= 1");
+    }
+    if (use_model) {
+        if (!is_device_ptr(P.stop_model))
+            return fail(NHQ_ERR_ARG, "stop_model must be device memory");
+        if (!(P.stop_threshold > 0.f && P.stop_threshold < 1.f))
+            return fail(NHQ_ERR_ARG, "stop_threshold must be a probability in (0, 1)");
+    }
     if (P.seed_mode == NHQ_SEED_ATTRIBUTE && ix->attr_sorted == nullptr) {
         CK(cudaMalloc(&ix->attr_sorted, sizeof(uint32_t) * (size_t)ix->N));
         CK(cudaMalloc(&ix->id_sorted, sizeof(uint32_t) * (size_t)ix->N));
@@ -600,7 +619,38 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     a.expansions = (int32_t *)st.dev(ix_);
     a.warps_per_block = P.warps_per_block;
     a.hash_bits = P.hash_bits;
-    CKS(scratch(ix, search_scratch_bytes(Q)));
+    // scratch: work counter and seeds | fp16 model | trace counter, hashes, final hashes
+    const size_t off_w16 = (search_scratch_bytes(Q) + 255) & ~(size_t)255;
+    const size_t off_tr = off_w16 + 2048;
+    const size_t tr_bytes = trace ? 256 + sizeof(unsigned long long) * ((size_t)trace->cap + Q) : 0;
+    CKS(scratch(ix, off_tr + tr_bytes));
+    a.stop_w16 = nullptr;
+    a.stop_every = 0;
+    a.stop_min = P.stop_min;
+    a.tr_feat = nullptr;
+    a.tr_hash = nullptr;
+    a.tr_q = nullptr;
+    a.tr_count = nullptr;
+    a.tr_cap = 0;
+    a.tr_final = nullptr;
+    if (use_model) {
+        __half *w16 = reinterpret_cast<__half *>((char *)ix->scratch + off_w16);
+        CK(launch_mlp_to_half(P.stop_model, w16, s));
+        a.stop_w16 = w16;
+        a.stop_logit = logf(P.stop_threshold / (1.f - P.stop_threshold));
+        a.stop_every = P.stop_every;
+    }
+    if (trace != nullptr) {
+        char *t = (char *)ix->scratch + off_tr;
+        a.tr_count = reinterpret_cast<unsigned int *>(t);
+        a.tr_hash = reinterpret_cast<unsigned long long *>(t + 256);
+        a.tr_final = a.tr_hash + trace->cap;
+        a.tr_feat = trace->features;
+        a.tr_q = trace->query;
+        a.tr_cap = trace->cap;
+        a.stop_every = P.stop_every;
+        CK(cudaMemsetAsync(a.tr_count, 0, sizeof(unsigned int), s));
+    }
     a.seeds = nullptr;
     a.n_seeds = 0;
     if (P.seed_mode == NHQ_SEED_GIVEN) {
@@ -617,6 +667,14 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         return fail(NHQ_ERR_ARG, "search launch: ef/hash_bits/warps_per_block do not fit shared memory");
     if (e != cudaSuccess)
         return fail_cuda(e, "search kernel launch");
+    if (trace != nullptr) {
+        unsigned int cnt = 0;
+        CK(cudaMemcpyAsync(&cnt, a.tr_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const int64_t nt = (int64_t)cnt < trace->cap ? (int64_t)cnt : trace->cap;
+        CK(launch_trace_labels(a.tr_hash, a.tr_q, a.tr_final, nt, trace->labels, s));
+        *trace->n_traces = nt;
+    }
     return st.finish(s);
 }
 
@@ -677,6 +735,68 @@ nhq_status nhq_search_batched(const nhq_index *ix, const float *queries,
     }
     return search_common(ix, queries, query_attributes, Q, k_arr, ef_arr, k_max, ef_max, k_max,
                          params, ids, dists, chi, status, ndc, expansions, stream);
+}
+
+nhq_status nhq_search_trace(const nhq_index *ix, const float *queries,
+                            const uint8_t *query_attributes, int64_t Q, int32_t k, int32_t ef,
+                            const nhq_search_params *params, float *features, uint8_t *labels,
+                            int32_t *query, int64_t cap, int64_t *n_traces, void *stream) {
+    if (ix == nullptr || ix->nbr == nullptr)
+        return fail(NHQ_ERR_ARG, "index with a graph is required");
+    if (Q < 1 || k < 1 || k > kMaxK || ef < k || ef > kMaxEf || cap < 1 || n_traces == nullptr)
+        return fail(NHQ_ERR_ARG, "need Q >= 1, k in 1..256, ef in k..1024, cap >= 1, n_traces");
+    if (!is_device_ptr(queries) || !is_device_ptr(query_attributes) || !is_device_ptr(features) ||
+        !is_device_ptr(labels) || !is_device_ptr(query))
+        return fail(NHQ_ERR_ARG, "nhq_search_trace takes device pointers");
+    if (params == nullptr)
+        return fail(NHQ_ERR_ARG, "params (stop_min, stop_every) are required");
+    uint32_t *ids = nullptr;
+    CK(cudaMallocAsync((void **)&ids, sizeof(uint32_t) * (size_t)Q * k, as_stream(stream)));
+    TraceOut t;
+    t.features = features;
+    t.labels = labels;
+    t.query = query;
+    t.cap = cap;
+    t.n_traces = n_traces;
+    nhq_status st = search_common(ix, queries, query_attributes, Q, nullptr, nullptr, k, ef, k,
+                                  params, ids, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                  stream, &t);
+    cudaFreeAsync(ids, as_stream(stream));
+    return st;
+}
+
+nhq_status nhq_mlp_forward(const float *params, const float *features, int64_t n, float *logits,
+                           void *stream) {
+    if (n < 0 || params == nullptr || (n > 0 && (features == nullptr || logits == nullptr)))
+        return fail(NHQ_ERR_ARG, "params, features and logits are required, n >= 0");
+    if (!is_device_ptr(params) || (n > 0 && (!is_device_ptr(features) || !is_device_ptr(logits))))
+        return fail(NHQ_ERR_ARG, "nhq_mlp_forward takes device pointers");
+    CK(mlp_forward(params, features, n, logits, as_stream(stream)));
+    return NHQ_OK;
+}
+
+nhq_status nhq_mlp_grad(const float *params, const float *features, const float *labels,
+                        int64_t n, float *grad, float *loss, void *stream) {
+    if (n < 1 || !params || !features || !labels || !grad || !loss)
+        return fail(NHQ_ERR_ARG, "params, features, labels, grad and loss are required, n >= 1");
+    if (!is_device_ptr(params) || !is_device_ptr(features) || !is_device_ptr(labels) ||
+        !is_device_ptr(grad) || !is_device_ptr(loss))
+        return fail(NHQ_ERR_ARG, "nhq_mlp_grad takes device pointers");
+    cudaStream_t s = as_stream(stream);
+    CK(cudaMemsetAsync(grad, 0, sizeof(float) * NHQ_MLP_PARAMS, s));
+    CK(cudaMemsetAsync(loss, 0, sizeof(float), s));
+    CK(mlp_grad(params, features, labels, n, n, grad, loss, s));
+    return NHQ_OK;
+}
+
+nhq_status nhq_mlp_train(float *params, const float *features, const float *labels, int64_t n,
+                         int32_t epochs, int32_t batch, float lr, void *stream) {
+    if (n < 1 || epochs < 0 || batch < 1 || !(lr > 0.f) || !params || !features || !labels)
+        return fail(NHQ_ERR_ARG, "need n >= 1, epochs >= 0, batch >= 1, lr > 0 and arrays");
+    if (!is_device_ptr(params) || !is_device_ptr(features) || !is_device_ptr(labels))
+        return fail(NHQ_ERR_ARG, "nhq_mlp_train takes device pointers");
+    CK(mlp_train(params, features, labels, n, epochs, batch, lr, as_stream(stream)));
+    return NHQ_OK;
 }
 
 static const char kMagic[8] = {'N', 'H', 'Q', 'I', 'D', 'X', '0', '1'};

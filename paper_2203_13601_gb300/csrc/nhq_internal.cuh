@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "nhq.h"
@@ -64,6 +65,27 @@ __device__ __forceinline__ uint32_t key_id(unsigned long long k) {
 }
 __device__ __forceinline__ float key_gamma(unsigned long long k) {
     return __uint_as_float((uint32_t)(k >> 32));
+}
+
+// Logit of the learned early-stop model for the warp-uniform features f (every
+// lane passes the same f): lane owns hidden units lane and lane + 32; fp16
+// weights, f32 accumulation, butterfly sum over the warp.
+__device__ __forceinline__ float mlp_logit_warp(const __half *w, const float *f, int lane) {
+    constexpr int I = NHQ_MLP_INPUTS, H = NHQ_MLP_HIDDEN;
+    float acc = 0.f;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        const int j = lane + 32 * hh;
+        float z = __half2float(w[I * H + j]);
+#pragma unroll
+        for (int i = 0; i < I; ++i)
+            z = fmaf(__half2float(w[i * H + j]), f[i], z);
+        acc = fmaf(__half2float(w[I * H + H + j]), fmaxf(z, 0.f), acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    return acc + __half2float(w[I * H + 2 * H]);
 }
 
 }  // namespace nhq
@@ -167,6 +189,17 @@ struct SearchArgs {
     int32_t *expansions;
     const uint32_t *seeds;  // [nq][n_seeds] given seed ids or null (random stream)
     int n_seeds;
+    // learned early stop: fp16 weights (null = off), logit threshold, schedule
+    const __half *stop_w16;
+    float stop_logit;
+    int stop_min, stop_every;  // stop_every == 0: neither model nor traces
+    // traces (null = off): features [cap][8], top-k hash and query row per record
+    float *tr_feat;
+    unsigned long long *tr_hash;
+    int32_t *tr_q;
+    unsigned int *tr_count;
+    int64_t tr_cap;
+    unsigned long long *tr_final;  // [nq] top-k hash at the end of each query
     unsigned long long *counter;  // scratch work counter (zeroed by the launcher)
     int warps_per_block;
     int hash_bits;
@@ -176,6 +209,18 @@ cudaError_t launch_attribute_sort(const uint32_t *attr, int64_t N, uint32_t *att
                                   uint32_t *id_sorted, void *scratch, size_t scratch_bytes,
                                   cudaStream_t s);
 size_t attribute_sort_scratch_bytes(int64_t N);
+// k_mlp.cu
+cudaError_t launch_mlp_to_half(const float *params, __half *w16, cudaStream_t s);
+cudaError_t launch_trace_labels(const unsigned long long *hash, const int32_t *tq,
+                                const unsigned long long *final_hash, int64_t n, uint8_t *lab,
+                                cudaStream_t s);
+cudaError_t mlp_forward(const float *params, const float *X, int64_t n, float *logits,
+                        cudaStream_t s);
+cudaError_t mlp_grad(const float *params, const float *X, const float *y, int64_t n,
+                     int64_t total, float *g, float *loss, cudaStream_t s);
+cudaError_t mlp_train(float *params, const float *X, const float *y, int64_t n, int epochs,
+                      int batch, float lr, cudaStream_t s);
+
 // Seeds of NHQ_SEED_ATTRIBUTE into seeds[nq][32] (rows padded with kNone).
 cudaError_t launch_attribute_seeds(const SearchArgs &a, const uint32_t *attr_sorted,
                                    const uint32_t *id_sorted, uint32_t *seeds, cudaStream_t s);

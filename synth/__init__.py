@@ -137,14 +137,20 @@ def _int_mixture(rng, n, cent, sigma, chunk=1 << 16):
     return X, comp
 
 
-def c2(N=1_000_000, nq=10_000, d=128, cards=(3, 10, 20), n_comp=1_000, seed=1001):
+def c2(N=1_000_000, nq=10_000, d=128, cards=(3, 10, 20), n_comp=1_000, seed=1001,
+       query_stream=0):
     """SIFT1M-shaped: integer-valued components 0..255 stored as f32, Zipf attributes.
 
     With integer components the squared distance is an integer <= d*255^2, which
     for d <= 256 is below 2^24, so it is exact in f32 in any summation order.
+    query_stream > 0 draws the queries from another independent stream (same
+    object set, same mixture): e.g. training queries for the learned stop.
     """
     _check_cards(cards)
     rb, rq, ra, rqa = _rngs(seed)
+    if query_stream:
+        rq, rqa = (np.random.default_rng(x)
+                   for x in np.random.SeedSequence([seed, query_stream]).spawn(2))
     cent = np.clip(np.rint(64.0 + 40.0 * rb.standard_normal((n_comp, d))), 0, 255).astype(np.float32)
     X, _ = _int_mixture(rb, N, cent, 20.0)
     Qv, _ = _int_mixture(rq, nq, cent, 20.0)

@@ -402,3 +402,50 @@ def test_reduced_precision_search_equals_plain_on_exact_data(oracle_mod):
             g = O.gamma(O.delta(w.Qv[q], w.X[i], O.F32), O.chi(w.QA[q], w.A[i]), w.m, prec=O.F32)
             assert d["gamma"][q, j] == g
         assert all(np.diff(d["gamma"][q]) >= 0)
+
+
+# ------------------------------------------------------------------ learned stop model (oracle)
+def test_mlp_zero_weights_closed_form():
+    from oracle import mlp
+
+    p = np.zeros(mlp.N_PARAMS)
+    X = np.random.default_rng(0).standard_normal((50, 8))
+    y = (np.arange(50) % 3 == 0).astype(float)
+    loss, g = mlp.loss_and_grad(p, X, y)
+    assert loss == pytest.approx(np.log(2.0), rel=1e-15)   # sigmoid(0) = 1/2
+    W1, b1, W2, b2 = mlp.unpack(g)
+    assert b2 == pytest.approx(np.mean(0.5 - y), rel=1e-14)
+    assert not W1.any() and not b1.any() and not W2.any()   # h = 0 and W2 = 0
+
+
+def test_mlp_gradient_matches_finite_differences():
+    from oracle import mlp
+
+    r = np.random.default_rng(1)
+    p = r.standard_normal(mlp.N_PARAMS) * 0.3
+    X = r.standard_normal((40, 8))
+    y = (r.random(40) < 0.4).astype(float)
+    _, g = mlp.loss_and_grad(p, X, y)
+    eps = 1e-6
+    for i in r.choice(mlp.N_PARAMS, 60, replace=False):
+        e = np.zeros_like(p)
+        e[i] = eps
+        lp, _ = mlp.loss_and_grad(p + e, X, y)
+        lm, _ = mlp.loss_and_grad(p - e, X, y)
+        assert g[i] == pytest.approx((lp - lm) / (2 * eps), rel=1e-5, abs=1e-9)
+
+
+def test_mlp_forward_hand_case():
+    from oracle import mlp
+
+    W1 = np.zeros((8, 64))
+    W1[0, 0], W1[1, 0], W1[2, 1] = 2.0, -1.0, 1.0
+    b1 = np.zeros(64)
+    b1[1] = -0.5
+    W2 = np.zeros(64)
+    W2[0], W2[1] = 1.5, -2.0
+    p = mlp.pack(W1, b1, W2, 0.25)
+    x = np.array([[1.0, 0.5, 2.0, 0, 0, 0, 0, 0], [-1.0, 0.0, 0.2, 0, 0, 0, 0, 0]])
+    # row 0: h0 = relu(2 - .5) = 1.5, h1 = relu(2 - .5) = 1.5 -> 1.5*1.5 - 2*1.5 + .25 = -0.5
+    # row 1: h0 = relu(-2) = 0, h1 = relu(.2 - .5) = 0 -> 0.25
+    assert np.allclose(mlp.forward(p, x), [-0.5, 0.25], rtol=0, atol=1e-15)
