@@ -265,6 +265,37 @@ nhq_status nhq_brute_force_noalloc(const float *vectors, const uint32_t *packed_
                                    void *stream);
 
 /*
+ * Autotuner (a project addition): times nhq_search on this batch for every launch
+ * shape that leaves the results unchanged -- warps per block in {2, 4, 8} and
+ * visited-filter sizes 2^b for b from the smallest legal size up to two above
+ * it -- with CUDA events (one warm-up and three timed runs each), and writes
+ * the fastest into params->warps_per_block / params->hash_bits (the other
+ * fields are used as given).  *best_ms (may be NULL) receives its time per
+ * call.  Device pointers; the outputs are overwritten by the trial runs.
+ */
+nhq_status nhq_autotune_search(const nhq_index *index, const float *queries,
+                               const uint8_t *query_attributes, int64_t Q, int32_t k, int32_t ef,
+                               nhq_search_params *params, uint32_t *ids, float *best_ms,
+                               void *stream);
+
+/*
+ * Captured search (a project addition): records one nhq_search call (counter
+ * reset, seed pre-pass, search kernel) into an instantiated CUDA graph that
+ * nhq_search_graph_launch replays on any stream with the same pointers; update
+ * the query buffers in place between launches.  Device pointers only; the
+ * lazily built index parts (reduced-precision copies, attribute table, scratch)
+ * are built by the capture call itself before capturing.  Free with
+ * nhq_search_graph_free.
+ */
+typedef struct nhq_search_graph nhq_search_graph;
+nhq_status nhq_search_graph_create(const nhq_index *index, const float *queries,
+                                   const uint8_t *query_attributes, int64_t Q, int32_t k,
+                                   int32_t ef, const nhq_search_params *params, uint32_t *ids,
+                                   float *dists, uint8_t *chi, nhq_search_graph **out);
+nhq_status nhq_search_graph_launch(nhq_search_graph *graph, void *stream);
+void nhq_search_graph_free(nhq_search_graph *graph);
+
+/*
  * Learned early stop, training data.  Runs nhq_search (params->stop_model is
  * ignored) and, at every expansion count c >= params->stop_min with
  * (c - stop_min) % stop_every == 0 while the pool holds >= k records, records the

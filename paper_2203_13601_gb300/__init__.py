@@ -28,7 +28,8 @@ __all__ = [
     "nhq_index_set_graph", "nhq_index_get_graph", "nhq_index_build", "nhq_build",
     "nhq_brute_force", "nhq_search", "nhq_search_batched", "nhq_save", "nhq_load",
     "nhq_brute_force_noalloc", "nhq_search_trace", "nhq_mlp_forward", "nhq_mlp_grad",
-    "nhq_mlp_train", "MLP_INPUTS", "MLP_HIDDEN", "MLP_PARAMS",
+    "nhq_mlp_train", "MLP_INPUTS", "MLP_HIDDEN", "MLP_PARAMS", "nhq_autotune_search",
+    "nhq_search_graph_create", "nhq_search_graph_launch", "nhq_search_graph_free",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -109,6 +110,12 @@ def load_library():
                                        P, P, P, P]),
             "nhq_brute_force_noalloc": (S, [P, P, i64, i32, i32, P, P, i64, i32, _Weights, P, P,
                                             P, P]),
+            "nhq_autotune_search": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P,
+                                        C.POINTER(C.c_float), P]),
+            "nhq_search_graph_create": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P,
+                                            P, P, C.POINTER(P)]),
+            "nhq_search_graph_launch": (S, [P, P]),
+            "nhq_search_graph_free": (None, [P]),
             "nhq_search_trace": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P, P, P,
                                      i64, C.POINTER(C.c_int64), P]),
             "nhq_mlp_forward": (S, [P, P, i64, P, P]),
@@ -359,6 +366,68 @@ def nhq_brute_force_noalloc(vectors, packed_attributes, m, queries, packed_query
         _weights(weights), _ptr(ids, np.uint32, (Q, k), "ids"),
         _ptr(dists, np.float32, (Q, k), "dists"), _ptr(chi, np.uint8, (Q, k), "chi"),
         _stream(stream)))
+
+
+def nhq_autotune_search(index, queries, query_attributes, k, ef, ids, h=1, seed=0,
+                        vec_dtype=VEC_F32, rerank=0, seed_mode=SEED_RANDOM, stream=None):
+    """Fastest result-preserving launch shape for this batch; returns
+    (warps_per_block, hash_bits, ms_per_call)."""
+    Q, d = _shape(queries)
+    m = _shape(query_attributes)[1]
+    p = _search_params(seed, h, 0, 0, 0, vec_dtype, rerank, seed_mode, None, Q)
+    ms = C.c_float(0.0)
+    _check(load_library().nhq_autotune_search(
+        index, _ptr(queries, np.float32, (Q, d), "queries"),
+        _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, ef, C.byref(p),
+        _ptr(ids, np.uint32, (Q, k), "ids"), C.byref(ms), _stream(stream)))
+    return p.warps_per_block, p.hash_bits, ms.value
+
+
+class SearchGraph:
+    """A captured nhq_search call (see nhq_search_graph_create); replays with launch()."""
+
+    def __init__(self, index, queries, query_attributes, k, ef, ids, dists=None, chi=None, **kw):
+        Q, d = _shape(queries)
+        m = _shape(query_attributes)[1]
+        kw.setdefault("seed_mode", SEED_RANDOM)
+        self._p = _search_params(kw.get("seed", 0), kw.get("h", 1), kw.get("max_iters", 0),
+                                 kw.get("warps_per_block", 0), kw.get("hash_bits", 0),
+                                 kw.get("vec_dtype", VEC_F32), kw.get("rerank", 0),
+                                 kw["seed_mode"], None, Q)
+        out = C.c_void_p()
+        _check(load_library().nhq_search_graph_create(
+            index, _ptr(queries, np.float32, (Q, d), "queries"),
+            _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, ef,
+            C.byref(self._p), _ptr(ids, np.uint32, (Q, k), "ids"),
+            _ptr(dists, np.float32, (Q, k), "dists"), _ptr(chi, np.uint8, (Q, k), "chi"),
+            C.byref(out)))
+        self.handle = out.value
+
+    def launch(self, stream=None):
+        _check(load_library().nhq_search_graph_launch(self.handle, _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            load_library().nhq_search_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nhq_search_graph_create(*a, **kw):
+    return SearchGraph(*a, **kw)
+
+
+def nhq_search_graph_launch(graph, stream=None):
+    graph.launch(stream)
+
+
+def nhq_search_graph_free(graph):
+    graph.close()
 
 
 def nhq_search_trace(index, queries, query_attributes, k, ef, features, labels, query,

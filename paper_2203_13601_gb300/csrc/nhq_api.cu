@@ -737,6 +737,136 @@ nhq_status nhq_search_batched(const nhq_index *ix, const float *queries,
                          params, ids, dists, chi, status, ndc, expansions, stream);
 }
 
+nhq_status nhq_autotune_search(const nhq_index *ix, const float *queries,
+                               const uint8_t *query_attributes, int64_t Q, int32_t k, int32_t ef,
+                               nhq_search_params *params, uint32_t *ids, float *best_ms,
+                               void *stream) {
+    if (ix == nullptr || params == nullptr || ids == nullptr || Q < 1)
+        return fail(NHQ_ERR_ARG, "index, params, ids and Q >= 1 are required");
+    if (!is_device_ptr(queries) || !is_device_ptr(query_attributes) || !is_device_ptr(ids))
+        return fail(NHQ_ERR_ARG, "nhq_autotune_search takes device pointers");
+    cudaStream_t s = as_stream(stream);
+    const int ef_cap = (ef + 31) & ~31;
+    int bmin = 10;
+    while ((1 << bmin) < 2 * (ef_cap + ix->R) + 64)
+        ++bmin;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    nhq_search_params best = *params;
+    float best_t = 1e30f;
+    bool any = false;
+    const int wpbs[3] = {2, 4, 8};
+    for (int wi = 0; wi < 3; ++wi) {
+        for (int b = bmin; b <= bmin + 2; ++b) {
+            nhq_search_params P = *params;
+            P.warps_per_block = wpbs[wi];
+            P.hash_bits = b;
+            nhq_status st = nhq_search(ix, queries, query_attributes, Q, k, ef, &P, ids, nullptr,
+                                       nullptr, nullptr, nullptr, nullptr, stream);
+            if (st == NHQ_ERR_ARG)
+                continue;  // this shape does not fit shared memory
+            if (st != NHQ_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return st;
+            }
+            CK(cudaEventRecord(e0, s));
+            for (int r = 0; r < 3; ++r)
+                nhq_search(ix, queries, query_attributes, Q, k, ef, &P, ids, nullptr, nullptr,
+                           nullptr, nullptr, nullptr, stream);
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            ms /= 3.f;
+            if (ms < best_t) {
+                best_t = ms;
+                best = P;
+                any = true;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!any)
+        return fail(NHQ_ERR_ARG, "no launch shape fits shared memory for ef = %d", ef);
+    params->warps_per_block = best.warps_per_block;
+    params->hash_bits = best.hash_bits;
+    if (best_ms)
+        *best_ms = best_t;
+    return NHQ_OK;
+}
+
+}  // extern "C"
+
+struct nhq_search_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+nhq_status nhq_search_graph_create(const nhq_index *ix, const float *queries,
+                                   const uint8_t *query_attributes, int64_t Q, int32_t k,
+                                   int32_t ef, const nhq_search_params *params, uint32_t *ids,
+                                   float *dists, uint8_t *chi, nhq_search_graph **out) {
+    if (out == nullptr)
+        return fail(NHQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!is_device_ptr(queries) || !is_device_ptr(query_attributes) || !is_device_ptr(ids) ||
+        (dists && !is_device_ptr(dists)) || (chi && !is_device_ptr(chi)))
+        return fail(NHQ_ERR_ARG, "nhq_search_graph_create takes device pointers");
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    // one ordinary call first: builds lazy index parts and sizes the scratch
+    nhq_status st = nhq_search(ix, queries, query_attributes, Q, k, ef, params, ids, dists, chi,
+                               nullptr, nullptr, nullptr, cs);
+    cudaError_t e = cudaStreamSynchronize(cs);
+    if (st == NHQ_OK && e != cudaSuccess)
+        st = fail_cuda(e, "cudaStreamSynchronize");
+    nhq_search_graph *g = nullptr;
+    if (st == NHQ_OK) {
+        g = new nhq_search_graph();
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            st = fail_cuda(e, "cudaStreamBeginCapture");
+        } else {
+            st = nhq_search(ix, queries, query_attributes, Q, k, ef, params, ids, dists, chi,
+                            nullptr, nullptr, nullptr, cs);
+            e = cudaStreamEndCapture(cs, &g->graph);
+            if (st == NHQ_OK && e != cudaSuccess)
+                st = fail_cuda(e, "cudaStreamEndCapture");
+            if (st == NHQ_OK && (e = cudaGraphInstantiate(&g->exec, g->graph, 0)) != cudaSuccess)
+                st = fail_cuda(e, "cudaGraphInstantiate");
+        }
+    }
+    cudaStreamDestroy(cs);
+    if (st != NHQ_OK) {
+        nhq_search_graph_free(g);
+        return st;
+    }
+    *out = g;
+    return NHQ_OK;
+}
+
+nhq_status nhq_search_graph_launch(nhq_search_graph *g, void *stream) {
+    if (g == nullptr || g->exec == nullptr)
+        return fail(NHQ_ERR_ARG, "graph is NULL");
+    CK(cudaGraphLaunch(g->exec, as_stream(stream)));
+    return NHQ_OK;
+}
+
+void nhq_search_graph_free(nhq_search_graph *g) {
+    if (g == nullptr)
+        return;
+    if (g->exec)
+        cudaGraphExecDestroy(g->exec);
+    if (g->graph)
+        cudaGraphDestroy(g->graph);
+    delete g;
+}
+
 nhq_status nhq_search_trace(const nhq_index *ix, const float *queries,
                             const uint8_t *query_attributes, int64_t Q, int32_t k, int32_t ef,
                             const nhq_search_params *params, float *features, uint8_t *labels,
