@@ -186,6 +186,23 @@ def reference_arm(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- multi-rank timing
+def max_over_ranks(ms, dist, device=None):
+    """The slowest rank's timed-region length (every rank gets the same value)."""
+    if dist is None:
+        return float(ms)
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank_per_step, steps, world, max_ms):
+    """Whole-job throughput: every rank processed its own batch each step."""
+    return world * units_per_rank_per_step * steps / (max_ms / 1000.0)
+
+
 # ---------------------------------------------------------------- our arm
 def hybrid_recall(ids, A, QA, gt, P, k):
     """Sec. 6.1 recall: returned ids whose attributes equal the query's, against
@@ -429,12 +446,9 @@ def main():
     total_ms = e_start.elapsed_time(e_end)
     clk = clocks.stop()
     step_ms = [s0.elapsed_time(s1) for s0, s1 in evs]
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     ms_per_step = total_ms / a.steps
-    qps = world * w.nq * a.steps / (total_ms / 1000.0)
+    qps = weak_scaling_value(w.nq, a.steps, world, total_ms)
     launch_ms = float(np.mean(step_ms))
     achieved = alg_bytes / (launch_ms / 1000.0) / 1e9
     peak, peak_kind = peaks()
