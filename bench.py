@@ -135,6 +135,27 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def recorded_traffic(ef, h, vec, seed_mode, n, nq, learned):
+    """DRAM bytes per launch of the search kernel from the committed ncu record, if the
+    kernel sources still hash to the recorded value and the setting is the recorded one
+    (otherwise None: counters of another kernel or setting would not apply)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    csrc = os.path.join(ROOT, "paper_2203_13601_gb300", "csrc")
+    src = b"".join(open(os.path.join(csrc, x), "rb").read()
+                   for x in ("k_search.cu", "nhq_internal.cuh"))
+    st = rec["setting"]
+    same = (hashlib.sha256(src).hexdigest() == rec["kernel_sources_sha256"] and
+            st == {"ef": ef, "h": h, "vec": VEC_NAMES[vec], "seed_mode": seed_mode} and
+            n == 1_000_000 and nq == 10_000 and not learned)
+    return float(rec["dram_bytes_per_launch"]) if same else None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -497,7 +518,9 @@ def main():
         "sweep": sweep,
         "learned": learned_info if (not a.no_learned and not a.fixed) else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": recorded_traffic(ef, h, vec, a.seed_mode, a.n, a.nq,
+                                                 use_learned),
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms, "mean_ndc": float(ndc_h.mean()),
