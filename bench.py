@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--seed-mode", type=int, default=1,
                     help="seed set B: 0 random (the paper's), 1 attribute entry")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned early stop")
+    ap.add_argument("--knn-dtype", type=int, default=1,
+                    help="candidate build: 0 exact f32 SIMT, 1 bf16 tensor cores (exact here)")
     ap.add_argument("--learned-efs", default="16,24,32,48,64")
     ap.add_argument("--taus", default="0.7,0.8,0.9,0.95")
     return ap.parse_args()
@@ -282,7 +284,7 @@ def main():
     torch.cuda.synchronize()
 
     t0 = time.perf_counter()
-    ix = nhq.Index.build(X, A, degree=a.R, weights=CONST_W, K=64)
+    ix = nhq.Index.build(X, A, degree=a.R, weights=CONST_W, K=64, knn_dtype=a.knn_dtype)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
 
@@ -511,7 +513,8 @@ def main():
                    "recall": rec,
                    "recall_kind": "hybrid Recall@10 vs filter-mode brute force",
                    "l2": "inputs larger than L2 (vectors 512 MB + adjacency 256 MB)",
-                   "build_s": t_build, "gen_s": t_gen, "ground_truth_s": t_gt,
+                   "build_s": t_build, "build_candidates": ["f32 SIMT", "bf16 tensor cores"][a.knn_dtype],
+                   "gen_s": t_gen, "ground_truth_s": t_gt,
                    "queries_with_no_match": int((P == 0).sum())},
         "plain_f32": ({"ef": plain[0], "h": plain[1], "recall": plain[3],
                        "qps": w.nq / (plain[4] / 1000.0)} if plain else None),

@@ -75,7 +75,7 @@ typedef struct nhq_build_params {
     int32_t K;           /* candidate-set size l of Sec. 4.1 (exact K nearest by Gamma); 0 -> 64 */
     int32_t reverse;     /* 1: second selection pass over N(v) plus reverse sources (default)   */
     int32_t reverse_cap; /* at most this many reverse sources per vertex; 0 -> 64               */
-    int32_t reserved;
+    int32_t knn_dtype;   /* 0: exact f32 candidates (nhq_knn); 1: bf16 tensor cores (nhq_knn_bf16) */
 } nhq_build_params;
 
 /* How the seed set B of Alg. 2 is chosen (the paper draws it at random). */
@@ -155,6 +155,19 @@ nhq_status nhq_pack_attributes(const uint8_t *attributes, int64_t n, int32_t m, 
  */
 nhq_status nhq_knn(const nhq_index *index, int32_t K, uint32_t *cand_ids, float *cand_dist,
                    void *stream);
+
+/*
+ * The same candidate sets with the dot products on the tensor cores: every
+ * object row is rounded to bf16 (nearest even, padded with zeros to a multiple
+ * of 64 dimensions) and delta^2 = |u|^2 + |v|^2 - 2 u.v is formed from the
+ * rounded rows with f32 accumulation; Gamma and the (Gamma, v) order are then
+ * exactly as in nhq_knn.  Rows whose components are integers 0..255 with d <= 128
+ * round exactly and give nhq_knn's result bit for bit; other rows give the
+ * exact candidates of their bf16 roundings.  Errors: K outside 1..64 or K >= N;
+ * NHQ_ERR_CUDA if the tensor-core pipeline stalls (its waits are bounded).
+ */
+nhq_status nhq_knn_bf16(const nhq_index *index, int32_t K, uint32_t *cand_ids, float *cand_dist,
+                        void *stream);
 
 /*
  * Landing-zone edge selection (Sec. 4.1, Def. 6) for every vertex u over the

@@ -24,7 +24,7 @@ __all__ = [
     "W_PROPORTIONAL", "W_CONSTANT", "W_FILTER", "VEC_F32", "VEC_BF16", "VEC_FP8E4M3",
     "SEED_RANDOM", "SEED_ATTRIBUTE", "SEED_GIVEN",
     "nhq_last_error", "nhq_version", "nhq_index_create", "nhq_free", "nhq_index_info",
-    "nhq_pack_attributes", "nhq_knn", "nhq_edge_select", "nhq_reverse_candidates",
+    "nhq_pack_attributes", "nhq_knn", "nhq_knn_bf16", "nhq_edge_select", "nhq_reverse_candidates",
     "nhq_index_set_graph", "nhq_index_get_graph", "nhq_index_build", "nhq_build",
     "nhq_brute_force", "nhq_search", "nhq_search_batched", "nhq_save", "nhq_load",
     "nhq_brute_force_noalloc", "nhq_search_trace", "nhq_mlp_forward", "nhq_mlp_grad",
@@ -56,7 +56,7 @@ class _Weights(C.Structure):
 
 class _BuildParams(C.Structure):
     _fields_ = [("K", C.c_int32), ("reverse", C.c_int32), ("reverse_cap", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("knn_dtype", C.c_int32)]
 
 
 class _SearchParams(C.Structure):
@@ -96,6 +96,7 @@ def load_library():
             "nhq_index_info": (S, [P, P, P, P, P]),
             "nhq_pack_attributes": (S, [P, i64, i32, P, P]),
             "nhq_knn": (S, [P, i32, P, P, P]),
+            "nhq_knn_bf16": (S, [P, i32, P, P, P]),
             "nhq_edge_select": (S, [P, P, i32, i32, P, P]),
             "nhq_reverse_candidates": (S, [P, P, i32, i32, P, P]),
             "nhq_index_set_graph": (S, [P, P, i32, P]),
@@ -235,6 +236,13 @@ def nhq_knn(index, K, cand_ids, cand_dist=None, stream=None) -> None:
                                   _stream(stream)))
 
 
+def nhq_knn_bf16(index, K, cand_ids, cand_dist=None, stream=None) -> None:
+    N = nhq_index_info(index)[0]
+    _check(load_library().nhq_knn_bf16(index, K, _ptr(cand_ids, np.uint32, (N, K), "cand_ids"),
+                                       _ptr(cand_dist, np.float32, (N, K), "cand_dist"),
+                                       _stream(stream)))
+
+
 def nhq_edge_select(index, cand_ids, R, nbr_out, stream=None) -> None:
     N = nhq_index_info(index)[0]
     L = _shape(cand_ids)[1]
@@ -264,20 +272,21 @@ def nhq_index_get_graph(index, nbr, stream=None) -> None:
                                               _stream(stream)))
 
 
-def _build_params(K, reverse, reverse_cap):
-    return _BuildParams(int(K), int(reverse), int(reverse_cap), 0)
+def _build_params(K, reverse, reverse_cap, knn_dtype=0):
+    return _BuildParams(int(K), int(reverse), int(reverse_cap), int(knn_dtype))
 
 
-def nhq_index_build(index, degree, K=64, reverse=1, reverse_cap=64, stream=None) -> None:
-    p = _build_params(K, reverse, reverse_cap)
+def nhq_index_build(index, degree, K=64, reverse=1, reverse_cap=64, knn_dtype=0,
+                    stream=None) -> None:
+    p = _build_params(K, reverse, reverse_cap, knn_dtype)
     _check(load_library().nhq_index_build(index, degree, C.byref(p), _stream(stream)))
 
 
 def nhq_build(vectors, attributes, degree, weights=None, K=64, reverse=1, reverse_cap=64,
-              stream=None) -> int:
+              knn_dtype=0, stream=None) -> int:
     N, d = _shape(vectors)
     m = _shape(attributes)[1]
-    p = _build_params(K, reverse, reverse_cap)
+    p = _build_params(K, reverse, reverse_cap, knn_dtype)
     out = C.c_void_p()
     _check(load_library().nhq_build(_ptr(vectors, np.float32, (N, d), "vectors"), N, d,
                                      _ptr(attributes, np.uint8, (N, m), "attributes"), m, degree,
@@ -496,9 +505,9 @@ class Index:
 
     @classmethod
     def build(cls, vectors, attributes, degree=32, weights=None, K=64, reverse=1,
-              reverse_cap=64, stream=None):
+              reverse_cap=64, knn_dtype=0, stream=None):
         return cls(nhq_build(vectors, attributes, degree, weights, K, reverse, reverse_cap,
-                             stream))
+                             knn_dtype, stream))
 
     @property
     def info(self):

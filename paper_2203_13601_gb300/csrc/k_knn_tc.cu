@@ -1,0 +1,419 @@
+// k_knn_tc.cu -- candidate sets C(u) of Sec. 4.1 (the exact K nearest by Gamma)
+// with the dot products on the 5th-generation tensor cores.
+//
+// delta^2(u, v) = |u|^2 + |v|^2 - 2 u.v with u, v the bf16-rounded object rows
+// (for integer components 0..255 the rounding is exact and every sum stays
+// below 2^24, so delta^2, delta and Gamma equal the f32 path bit for bit).
+//
+// One CTA owns 128 rows and sweeps all column tiles of 128:
+//   warp 0 (one lane)   TMA: 128B-swizzled bf16 boxes of 128 rows x 64 dims of
+//                       both operands into a 3-stage shared-memory ring
+//   warp 1 (one lane)   tcgen05.mma kind::f16, M = 128, N = 128, K = 16, f32
+//                       accumulators in two TMEM buffers of 128 columns
+//   warps 4..7          epilogue: tcgen05.ld of its 32 lanes (= rows), delta^2,
+//                       a delta-only lower bound against the row's current K-th
+//                       record, exact Gamma (Eq. 6) for survivors, and a sorted
+//                       per-row list of K records in shared memory
+// Every mbarrier wait is bounded; a timeout records an error code and the CTA
+// drains its tensor-core work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "nhq_internal.cuh"
+
+namespace nhq {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int STAGES = 3;
+constexpr int KMAX = 64;
+constexpr int LSTRIDE = KMAX + 1;  // u64 entries per row list (padded against bank conflicts)
+constexpr int NTHREADS = 256;
+constexpr uint32_t TILE_BYTES = BM * BK * 2;  // one operand box: 16 KB
+constexpr uint32_t STAGE_BYTES = 2 * TILE_BYTES;
+constexpr uint32_t TMEM_COLS = 2 * BN;
+constexpr long long kWaitLimit = 1ll << 26;
+
+struct TcArgs {
+    const float *norms;  // |x|^2 of the bf16-rounded rows
+    const uint32_t *attr;
+    int64_t N;
+    int kblocks;
+    Fusion w;
+    int K;
+    uint32_t *ids;
+    float *dists;
+    int *err;
+};
+
+// ---- PTX wrappers ----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false (and an error code recorded) if the phase never completes
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int *err, int code) {
+    for (long long i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(a, parity))
+            return true;
+    atomicCAS(err, 0, code);
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (the layout TMA writes for a 64-element bf16 box width)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused with swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+    d |= (uint64_t)1 << 46;                  // descriptor version
+    d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+    return d;
+}
+// instruction descriptor: bf16 x bf16 -> f32, both K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *ring = sm;                                           // STAGES x 32 KB
+    unsigned long long *lists =
+        reinterpret_cast<unsigned long long *>(sm + STAGES * STAGE_BYTES);  // 128 x LSTRIDE
+    float *colnorm = reinterpret_cast<float *>(lists + BM * LSTRIDE);      // [2][BN]
+    uint32_t *colattr = reinterpret_cast<uint32_t *>(colnorm + 2 * BN);   // [2][BN]
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(colattr + 2 * BN);
+    // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], done
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * BM;
+    const int ntiles = (int)((a.N + BN - 1) / BN);
+    const int kb_n = a.kblocks;
+    auto bar = [&](int i) { return smem_u32(bars + i); };
+    const int FULL0 = 0, EMPTY0 = STAGES, TFULL0 = 2 * STAGES, TEMPTY0 = 2 * STAGES + 2,
+              DONE = 2 * STAGES + 4;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(bar(FULL0 + s), 1);
+            mbar_init(bar(EMPTY0 + s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar(TFULL0 + b), 1);
+            mbar_init(bar(TEMPTY0 + b), BM);
+        }
+        mbar_init(bar(DONE), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                smem_u32(tmem_holder)),
+            "r"(TMEM_COLS)
+            : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int t = 0; t < ntiles && ok; ++t) {
+            for (int kb = 0; kb < kb_n && ok; ++kb) {
+                ok = mbar_wait(bar(EMPTY0 + stage), phase ^ 1u, a.err, 1);
+                if (!ok)
+                    break;
+                const uint32_t dstA = smem_u32(ring + stage * STAGE_BYTES);
+                mbar_expect_tx(bar(FULL0 + stage), STAGE_BYTES);
+                tma_load_2d(dstA, &tmap, bar(FULL0 + stage), kb * BK, (int)row0);
+                tma_load_2d(dstA + TILE_BYTES, &tmap, bar(FULL0 + stage), kb * BK, t * BN);
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true, issued = false;
+        for (int t = 0; t < ntiles && ok; ++t) {
+            const int b = t & 1;
+            const uint32_t tph = (uint32_t)(t >> 1) & 1u;
+            ok = mbar_wait(bar(TEMPTY0 + b), tph ^ 1u, a.err, 2);
+            if (!ok)
+                break;
+            tc_fence_after();
+            const uint32_t d_tmem = tmem + (uint32_t)(b * BN);
+            for (int kb = 0; kb < kb_n; ++kb) {
+                ok = mbar_wait(bar(FULL0 + stage), phase, a.err, 3);
+                if (!ok)
+                    break;
+                tc_fence_after();
+                const uint32_t sA = smem_u32(ring + stage * STAGE_BYTES);
+                const uint32_t sB = sA + TILE_BYTES;
+#pragma unroll
+                for (int k4 = 0; k4 < BK / 16; ++k4)
+                    umma_bf16(d_tmem, sw128_desc(sA + 32u * k4), sw128_desc(sB + 32u * k4),
+                              (kb | k4) != 0 ? 1u : 0u);
+                issued = true;
+                umma_commit(bar(EMPTY0 + stage));  // the stage is free once these complete
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+            if (ok)
+                umma_commit(bar(TFULL0 + b));  // accumulators of tile t are complete
+        }
+        if (issued) {  // wait for every issued MMA before TMEM can be released
+            umma_commit(bar(DONE));
+            mbar_wait(bar(DONE), 0, a.err, 4);
+        }
+    } else if (warp >= 4) {
+        // ---------------- epilogue: thread r owns row row0 + r
+        const int r = (warp - 4) * 32 + lane;
+        const int64_t u = row0 + r;
+        const bool row_ok = u < a.N;
+        const float nu = row_ok ? a.norms[u] : 0.f;
+        const uint32_t au = row_ok ? a.attr[u] : 0u;
+        unsigned long long *list = lists + r * LSTRIDE;
+        int cnt = 0;
+        unsigned long long thr = kInfKey;
+        // Gamma >= w * delta for every record (w = 1 for the proportional weights)
+        const float wlow = a.w.mode == NHQ_W_CONSTANT ? a.w.wv : 1.f;
+        float lim2 = __int_as_float(0x7f800000);  // delta^2 bound that can still enter
+        const uint32_t lane_base = (uint32_t)((warp - 4) * 32) << 16;
+        bool ok = true;
+        for (int t = 0; t < ntiles && ok; ++t) {
+            const int b = t & 1;
+            const uint32_t tph = (uint32_t)(t >> 1) & 1u;
+            const int64_t cme = (int64_t)t * BN + r;
+            colnorm[b * BN + r] = cme < a.N ? a.norms[cme] : 0.f;
+            colattr[b * BN + r] = cme < a.N ? a.attr[cme] : 0u;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            ok = mbar_wait(bar(TFULL0 + b), tph, a.err, 5);
+            __syncwarp();  // tcgen05.ld below needs the whole warp converged
+            if (!__all_sync(0xFFFFFFFFu, ok)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + c0), v);
+                if (!row_ok)
+                    continue;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int c = c0 + j;
+                    const int64_t col = (int64_t)t * BN + c;
+                    if (col >= a.N || col == u)
+                        continue;
+                    const float dot = __uint_as_float(v[j]);
+                    const float d2 = fmaxf((nu + colnorm[b * BN + c]) - 2.f * dot, 0.f);
+                    if (d2 > lim2)
+                        continue;  // cannot reach the row's current K-th record
+                    const float g = fusion_gamma(__fsqrt_rn(d2),
+                                                 chi_packed(au, colattr[b * BN + c], a.w.mask),
+                                                 a.w);
+                    const unsigned long long key =
+                        ((unsigned long long)__float_as_uint(g) << 32) | (uint32_t)col;
+                    if (key >= thr)
+                        continue;
+                    int pos = cnt < a.K ? cnt : a.K - 1;
+                    while (pos > 0 && list[pos - 1] > key) {
+                        list[pos] = list[pos - 1];
+                        --pos;
+                    }
+                    list[pos] = key;
+                    if (cnt < a.K)
+                        ++cnt;
+                    if (cnt == a.K) {
+                        thr = list[a.K - 1];
+                        const float gt = __uint_as_float((uint32_t)(thr >> 32));
+                        const float bound = gt / fmaxf(wlow, 1e-30f);
+                        lim2 = wlow > 0.f ? bound * bound * 1.00002f + 1e-30f
+                                          : __int_as_float(0x7f800000);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(bar(TEMPTY0 + b));
+        }
+        if (row_ok) {
+            for (int j = 0; j < a.K; ++j) {
+                const int64_t o = u * a.K + j;
+                if (j < cnt) {
+                    a.ids[o] = (uint32_t)list[j];
+                    if (a.dists)
+                        a.dists[o] = __uint_as_float((uint32_t)(list[j] >> 32));
+                } else {
+                    a.ids[o] = kNone;
+                    if (a.dists)
+                        a.dists[o] = __int_as_float(0x7f800000);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// bf16 rows padded to kpad (multiple of 64) and the squared norms of the rounded rows
+__global__ void bf16_rows_norms_kernel(const float *__restrict__ X, int xstride, int d,
+                                       int64_t N, int kpad, __nv_bfloat16 *__restrict__ Xk,
+                                       float *__restrict__ norms) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= N)
+        return;
+    float acc = 0.f;
+    for (int c = lane; c < kpad; c += 32) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(c < d ? X[r * xstride + c] : 0.f);
+        Xk[r * kpad + c] = h;
+        const float f = __bfloat162float(h);
+        acc = fmaf(f, f, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if (lane == 0)
+        norms[r] = acc;
+}
+
+size_t tc_smem_bytes() {
+    return 1024 + STAGES * STAGE_BYTES + sizeof(unsigned long long) * BM * LSTRIDE +
+           (sizeof(float) + sizeof(uint32_t)) * 2 * BN + sizeof(unsigned long long) * 16 + 64;
+}
+
+}  // namespace
+
+int knn_tc_kmax() { return KMAX; }
+
+cudaError_t launch_knn_tc_prepare(const float *X, int xstride, int d, int64_t N, int kpad,
+                                  __nv_bfloat16 *Xk, float *norms, cudaStream_t s) {
+    const int wpb = 8;
+    bf16_rows_norms_kernel<<<(unsigned)((N + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
+        X, xstride, d, N, kpad, Xk, norms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_knn_tc(const __nv_bfloat16 *Xk, int kpad, const float *norms,
+                          const uint32_t *attr, int64_t N, const Fusion &w, int K, uint32_t *ids,
+                          float *dists, int *err, cudaStream_t s) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (encode == nullptr) {
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion(
+            "cuTensorMapEncodeTiled", reinterpret_cast<void **>(&encode), 12000,
+            cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || encode == nullptr) {
+            encode = nullptr;
+            return e != cudaSuccess ? e : cudaErrorNotSupported;
+        }
+    }
+    CUtensorMap tmap;
+    const cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)kpad * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult cr = encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(Xk),
+                         dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    TcArgs a;
+    a.norms = norms;
+    a.attr = attr;
+    a.N = N;
+    a.kblocks = kpad / BK;
+    a.w = w;
+    a.K = K;
+    a.ids = ids;
+    a.dists = dists;
+    a.err = err;
+    const size_t smem = tc_smem_bytes();
+    cudaError_t e =
+        cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    knn_tc_kernel<<<(unsigned)((N + BM - 1) / BM), NTHREADS, smem, s>>>(tmap, a);
+    return cudaGetLastError();
+}
+
+}  // namespace nhq

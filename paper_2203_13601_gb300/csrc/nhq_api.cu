@@ -260,6 +260,8 @@ void nhq_free(nhq_index *ix) {
     cudaFree(ix->attr);
     cudaFree(ix->nbr);
     cudaFree(ix->nbr_attr);
+    cudaFree(ix->Xk);
+    cudaFree(ix->normk);
     cudaFree(ix->attr_sorted);
     cudaFree(ix->id_sorted);
     cudaFree(ix->scratch);
@@ -324,6 +326,41 @@ nhq_status nhq_knn(const nhq_index *cix, int32_t K, uint32_t *cand_ids, float *c
     CKS(scratch(ix, need + 256));
     CK(launch_topk(a, ix->scratch, ix->scratch_bytes, ix->sm_count, s));
     return st.finish(s);
+}
+
+nhq_status nhq_knn_bf16(const nhq_index *cix, int32_t K, uint32_t *cand_ids, float *cand_dist,
+                        void *stream) {
+    nhq_index *ix = const_cast<nhq_index *>(cix);
+    if (ix == nullptr || cand_ids == nullptr)
+        return fail(NHQ_ERR_ARG, "index and cand_ids are required");
+    if (K < 1 || K > knn_tc_kmax() || K >= ix->N)
+        return fail(NHQ_ERR_ARG, "K must be in 1..min(64, N-1) (got %d)", K);
+    cudaStream_t s = as_stream(stream);
+    if (ix->Xk == nullptr) {
+        ix->kpad = (ix->d + 63) & ~63;
+        CK(cudaMalloc(&ix->Xk, sizeof(__nv_bfloat16) * (size_t)ix->N * ix->kpad));
+        CK(cudaMalloc(&ix->normk, sizeof(float) * (size_t)ix->N));
+        CK(launch_knn_tc_prepare(ix->X, ix->xstride, ix->d, ix->N, ix->kpad, ix->Xk, ix->normk, s));
+    }
+    Stager st;
+    int io = st.add(cand_ids, sizeof(uint32_t) * (size_t)ix->N * K, false);
+    int id = st.add(cand_dist, sizeof(float) * (size_t)ix->N * K, false);
+    CKS(st.commit(&g_stage.p, &g_stage.cap, s));
+    CKS(scratch(ix, 256));
+    int *err = reinterpret_cast<int *>(ix->scratch);
+    CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    cudaError_t e = launch_knn_tc(ix->Xk, ix->kpad, ix->normk, ix->attr, ix->N,
+                                  make_fusion(ix->w, ix->m), K, (uint32_t *)st.dev(io),
+                                  (float *)st.dev(id), err, s);
+    if (e != cudaSuccess)
+        return fail_cuda(e, "tensor-core candidate kernel launch");
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKS(st.finish(s));
+    CK(cudaStreamSynchronize(s));
+    if (herr)
+        return fail(NHQ_ERR_CUDA, "tensor-core candidate pipeline timed out (stage %d)", herr);
+    return NHQ_OK;
 }
 
 nhq_status nhq_edge_select(const nhq_index *cix, const uint32_t *cand_ids, int32_t L, int32_t R,
@@ -422,7 +459,13 @@ nhq_status nhq_index_build(nhq_index *ix, int32_t degree, const nhq_build_params
         cleanup();
         return fail_cuda(e, "cudaMalloc(build buffers)");
     }
-    nhq_status st = nhq_knn(ix, K, cand, nullptr, stream);
+    const int tc = p ? p->knn_dtype : 0;
+    if (tc != 0 && tc != 1)
+        return fail(NHQ_ERR_ARG, "knn_dtype must be 0 (f32) or 1 (bf16 tensor cores)");
+    if (tc == 1 && K > knn_tc_kmax())
+        K = knn_tc_kmax();
+    nhq_status st = tc == 1 ? nhq_knn_bf16(ix, K, cand, nullptr, stream)
+                            : nhq_knn(ix, K, cand, nullptr, stream);
     if (st == NHQ_OK)
         st = nhq_edge_select(ix, cand, K, degree, nbr, stream);
     if (st == NHQ_OK && rev) {

@@ -105,6 +105,9 @@ struct nhq_index {
     uint32_t *attr = nullptr;      // [N] packed attributes
     uint32_t *nbr = nullptr;       // [N][R] adjacency, kNone padded
     uint32_t *nbr_attr = nullptr;  // [N][R] packed attributes of each neighbour
+    __nv_bfloat16 *Xk = nullptr;  // [N][kpad] bf16 rows for the tensor-core candidate build
+    float *normk = nullptr;       // [N] squared norms of those rows
+    int kpad = 0;                 // d rounded up to a multiple of 64
     uint32_t *attr_sorted = nullptr;  // [N] packed attributes, ascending (stable radix sort)
     uint32_t *id_sorted = nullptr;    // [N] object ids in that order
     // scratch arena (grown on demand, owned by the index)
@@ -209,6 +212,14 @@ cudaError_t launch_attribute_sort(const uint32_t *attr, int64_t N, uint32_t *att
                                   uint32_t *id_sorted, void *scratch, size_t scratch_bytes,
                                   cudaStream_t s);
 size_t attribute_sort_scratch_bytes(int64_t N);
+// k_knn_tc.cu
+int knn_tc_kmax();
+cudaError_t launch_knn_tc_prepare(const float *X, int xstride, int d, int64_t N, int kpad,
+                                  __nv_bfloat16 *Xk, float *norms, cudaStream_t s);
+cudaError_t launch_knn_tc(const __nv_bfloat16 *Xk, int kpad, const float *norms,
+                          const uint32_t *attr, int64_t N, const Fusion &w, int K, uint32_t *ids,
+                          float *dists, int *err, cudaStream_t s);
+
 // k_mlp.cu
 cudaError_t launch_mlp_to_half(const float *params, __half *w16, cudaStream_t s);
 cudaError_t launch_trace_labels(const unsigned long long *hash, const int32_t *tq,

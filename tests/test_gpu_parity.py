@@ -456,3 +456,43 @@ def test_search_rerank_on_float_data(nhq):
         # rounded Gammas nearly tie, so require a high overlap with the oracle
         overlap = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(got, ref["ids"])])
         assert overlap > 0.97, (vec, overlap)
+
+
+# ------------------------------------------------------------------ tensor-core candidates
+@pytest.mark.parametrize("weights", [None, CONST])
+@pytest.mark.parametrize("N,d", [(2500, 32), (2500, 128), (300, 64)])
+def test_knn_tensor_cores_exact_on_integer_data(nhq, weights, N, d):
+    w = synth.int_valued(N, 1, d, seed=60 + d)
+    ref, ref_g = O.knn(w.X, w.A, 64, weights=weights, prec=O.F32)
+    with _index(nhq, w, weights) as ix:
+        cand = torch.empty((w.N, 64), dtype=torch.uint32, device="cuda:0")
+        dist = torch.empty((w.N, 64), dtype=torch.float32, device="cuda:0")
+        nhq.nhq_knn_bf16(ix.handle, 64, cand, dist)
+        torch.cuda.synchronize()
+    assert (ids_i64(cand) == ref).all()
+    assert np.array_equal(dist.cpu().numpy().astype(np.float64), ref_g)
+
+
+def test_knn_tensor_cores_on_float_data(nhq):
+    # bf16 rounding of float rows: candidates are exact for the rounded rows, so
+    # they overlap the f32 candidates almost everywhere
+    w = synth.c1(N=3000, nq=1, d=100, seed=61)
+    ref, _ = O.knn(w.X, w.A, 32, prec=O.F32)
+    with _index(nhq, w) as ix:
+        cand = torch.empty((w.N, 32), dtype=torch.uint32, device="cuda:0")
+        nhq.nhq_knn_bf16(ix.handle, 32, cand)
+        torch.cuda.synchronize()
+    got = ids_i64(cand)
+    overlap = np.mean([len(set(a) & set(b)) / 32 for a, b in zip(got, ref)])
+    assert overlap > 0.95
+    assert not (got == np.arange(w.N)[:, None]).any()
+
+
+def test_build_with_tensor_core_candidates_equals_f32_build(nhq):
+    w = synth.int_valued(2200, 1, 32, seed=62)
+    ref, _, _ = O.build_graph(w.X, w.A, R=24, K=48, weights=CONST)
+    with nhq.Index.build(dev(w.X), dev(w.A), degree=24, weights=CONST, K=48, knn_dtype=1) as ix:
+        out = torch.empty((w.N, 24), dtype=torch.uint32, device="cuda:0")
+        nhq.nhq_index_get_graph(ix.handle, out)
+        torch.cuda.synchronize()
+    assert (ids_i64(out) == ref).all()
