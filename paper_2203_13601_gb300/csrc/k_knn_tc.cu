@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         reinterpret_cast<unsigned long long *>(sm + STAGES * STAGE_BYTES);  // 128 x LSTRIDE
     float *colnorm = reinterpret_cast<float *>(lists + BM * LSTRIDE);      // [2][BN]
     uint32_t *colattr = reinterpret_cast<uint32_t *>(colnorm + 2 * BN);   // [2][BN]
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(colattr + 2 * BN);
+    uint2 *stage = reinterpret_cast<uint2 *>(colattr + 2 * BN);                  // [BM][33]
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(stage + BM * 33);
     // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], done
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
 
@@ -246,11 +247,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const float nu = row_ok ? a.norms[u] : 0.f;
         const uint32_t au = row_ok ? a.attr[u] : 0u;
         unsigned long long *list = lists + r * LSTRIDE;
+        uint2 *stg = stage + r * (32 + 1);  // survivors of one 32-column chunk
         int cnt = 0;
         unsigned long long thr = kInfKey;
-        // Gamma >= w * delta for every record (w = 1 for the proportional weights)
-        const float wlow = a.w.mode == NHQ_W_CONSTANT ? a.w.wv : 1.f;
-        float lim2 = __int_as_float(0x7f800000);  // delta^2 bound that can still enter
+        // delta^2 bounds per chi: a record with this chi and a larger delta^2 cannot
+        // reach the row's current K-th record (Gamma grows with delta and with chi)
+        float lim[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+            lim[c] = __int_as_float(0x7f800000);
         const uint32_t lane_base = (uint32_t)((warp - 4) * 32) << 16;
         bool ok = true;
         for (int t = 0; t < ntiles && ok; ++t) {
@@ -272,19 +277,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + c0), v);
                 if (!row_ok)
                     continue;
+                int ns = 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int c = c0 + j;
+                    const float dot = __uint_as_float(v[j]);
+                    const float d2 = fmaxf((nu + colnorm[b * BN + c]) - 2.f * dot, 0.f);
+                    const int ch = chi_packed(au, colattr[b * BN + c], a.w.mask);
+                    const float L = ch == 0 ? lim[0]
+                                            : ch == 1 ? lim[1]
+                                                      : ch == 2 ? lim[2] : ch == 3 ? lim[3] : lim[4];
+                    if (d2 <= L) {
+                        stg[ns] = make_uint2(__float_as_uint(d2), (uint32_t)c | ((uint32_t)ch << 16));
+                        ++ns;
+                    }
+                }
+                for (int i = 0; i < ns; ++i) {
+                    const uint2 e = stg[i];
+                    const int c = (int)(e.y & 0xFFFFu), ch = (int)(e.y >> 16);
                     const int64_t col = (int64_t)t * BN + c;
                     if (col >= a.N || col == u)
                         continue;
-                    const float dot = __uint_as_float(v[j]);
-                    const float d2 = fmaxf((nu + colnorm[b * BN + c]) - 2.f * dot, 0.f);
-                    if (d2 > lim2)
-                        continue;  // cannot reach the row's current K-th record
-                    const float g = fusion_gamma(__fsqrt_rn(d2),
-                                                 chi_packed(au, colattr[b * BN + c], a.w.mask),
-                                                 a.w);
+                    const float g = fusion_gamma(__fsqrt_rn(__uint_as_float(e.x)), ch, a.w);
                     const unsigned long long key =
                         ((unsigned long long)__float_as_uint(g) << 32) | (uint32_t)col;
                     if (key >= thr)
@@ -299,10 +313,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         ++cnt;
                     if (cnt == a.K) {
                         thr = list[a.K - 1];
-                        const float gt = __uint_as_float((uint32_t)(thr >> 32));
-                        const float bound = gt / fmaxf(wlow, 1e-30f);
-                        lim2 = wlow > 0.f ? bound * bound * 1.00002f + 1e-30f
-                                          : __int_as_float(0x7f800000);
+                        // with slack 1e-5: the f32 roundings of Gamma stay far inside it
+                        const float gt = __uint_as_float((uint32_t)(thr >> 32)) * 1.00001f;
+#pragma unroll
+                        for (int cc = 0; cc < 5; ++cc) {
+                            float tt;
+                            if (a.w.mode == NHQ_W_CONSTANT)
+                                tt = a.w.wv > 0.f ? (gt - a.w.wl * (float)cc) / a.w.wv
+                                                  : (gt >= a.w.wl * (float)cc
+                                                         ? __int_as_float(0x7f800000)
+                                                         : -1.f);
+                            else
+                                tt = gt * (float)a.w.m / (float)(a.w.m + cc);
+                            lim[cc] = tt < 0.f ? -1.f : tt * tt;
+                        }
                     }
                 }
             }
@@ -357,7 +381,8 @@ __global__ void bf16_rows_norms_kernel(const float *__restrict__ X, int xstride,
 
 size_t tc_smem_bytes() {
     return 1024 + STAGES * STAGE_BYTES + sizeof(unsigned long long) * BM * LSTRIDE +
-           (sizeof(float) + sizeof(uint32_t)) * 2 * BN + sizeof(unsigned long long) * 16 + 64;
+           (sizeof(float) + sizeof(uint32_t)) * 2 * BN + sizeof(uint2) * BM * 33 +
+           sizeof(unsigned long long) * 16 + 64;
 }
 
 }  // namespace
