@@ -10,10 +10,11 @@
 //                       both operands into a 3-stage shared-memory ring
 //   warp 1 (one lane)   tcgen05.mma kind::f16, M = 128, N = 128, K = 16, f32
 //                       accumulators in two TMEM buffers of 128 columns
-//   warps 4..7          epilogue: tcgen05.ld of its 32 lanes (= rows), delta^2,
-//                       a delta-only lower bound against the row's current K-th
-//                       record, exact Gamma (Eq. 6) for survivors, and a sorted
-//                       per-row list of K records in shared memory
+//   warps 4..7          epilogue: tcgen05.ld of its 32 lanes (= rows), delta^2 and
+//                       chi of every pair against a per-row table of delta^2
+//                       bounds by chi (branch-free), then for the few survivors
+//                       exact Gamma (Eq. 6) and a per-row max-heap of the K best
+//                       records in shared memory (sorted once at the end)
 // Every mbarrier wait is bounded; a timeout records an error code and the CTA
 // drains its tensor-core work, frees its TMEM and returns.
 #include <cuda.h>
@@ -28,7 +29,9 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int STAGES = 3;
 constexpr int KMAX = 64;
-constexpr int LSTRIDE = KMAX + 1;  // u64 entries per row list (padded against bank conflicts)
+// u64 entries per row heap: slot 0 unused, 1..K the heap, K+1 a zero sentinel (so a
+// node's two children are one aligned 16-byte pair); even, so every row is 16-byte aligned
+constexpr int LSTRIDE = KMAX + 2;
 constexpr int NTHREADS = 256;
 constexpr uint32_t TILE_BYTES = BM * BK * 2;  // one operand box: 16 KB
 constexpr uint32_t STAGE_BYTES = 2 * TILE_BYTES;
@@ -134,6 +137,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// max-heap hp[1..n] with hp[n+1] == 0: sift `key` down from node i
+__device__ __forceinline__ void heap_sift(unsigned long long *hp, int n, int i,
+                                          unsigned long long key) {
+    for (;;) {
+        const int c = 2 * i;
+        if (c > n)
+            break;
+        const ulonglong2 ch = *reinterpret_cast<const ulonglong2 *>(hp + c);
+        const bool right = ch.y > ch.x;
+        const unsigned long long big = right ? ch.y : ch.x;
+        if (big <= key)
+            break;
+        hp[i] = big;
+        i = c + (right ? 1 : 0);
+    }
+    hp[i] = key;
+}
+
+// number of differing attribute bytes under the mask (chi of Eq. 3 on packed codes):
+// bit 7 of each byte of y is set iff that byte of x is nonzero
+__device__ __forceinline__ int chi_bytes(uint32_t a, uint32_t b, uint32_t mask) {
+    const uint32_t x = (a ^ b) & mask;
+    const uint32_t y = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
+    return __popc(y & 0x80808080u);
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
     knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
@@ -144,7 +173,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         reinterpret_cast<unsigned long long *>(sm + STAGES * STAGE_BYTES);  // 128 x LSTRIDE
     float *colnorm = reinterpret_cast<float *>(lists + BM * LSTRIDE);      // [2][BN]
     uint32_t *colattr = reinterpret_cast<uint32_t *>(colnorm + 2 * BN);   // [2][BN]
-    uint2 *stage = reinterpret_cast<uint2 *>(colattr + 2 * BN);                  // [BM][33]
+    float *limtab = reinterpret_cast<float *>(colattr + 2 * BN);                 // [5][BM]
+    uint2 *stage = reinterpret_cast<uint2 *>(limtab + 5 * BM);                   // [BM][33]
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(stage + BM * 33);
     // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], done
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
@@ -246,16 +276,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const bool row_ok = u < a.N;
         const float nu = row_ok ? a.norms[u] : 0.f;
         const uint32_t au = row_ok ? a.attr[u] : 0u;
-        unsigned long long *list = lists + r * LSTRIDE;
+        unsigned long long *hp = lists + r * LSTRIDE;
         uint2 *stg = stage + r * (32 + 1);  // survivors of one 32-column chunk
+        const int K = a.K;
         int cnt = 0;
         unsigned long long thr = kInfKey;
         // delta^2 bounds per chi: a record with this chi and a larger delta^2 cannot
         // reach the row's current K-th record (Gamma grows with delta and with chi)
-        float lim[5];
+        // delta^2 bound of chi = c for this row at limtab[c * BM + r]
+        float fac[5];
 #pragma unroll
-        for (int c = 0; c < 5; ++c)
-            lim[c] = __int_as_float(0x7f800000);
+        for (int c = 0; c < 5; ++c) {
+            limtab[c * BM + r] = __int_as_float(0x7f800000);
+            fac[c] = a.w.mode == NHQ_W_CONSTANT
+                         ? a.w.wl * (float)c
+                         : (float)a.w.m / (float)(a.w.m + c);
+        }
+        const float inv_wv = a.w.wv > 0.f ? 1.f / a.w.wv : 0.f;
+        auto update_lim = [&]() {
+            thr = hp[1];
+            // with slack 1e-5: the f32 roundings of Gamma and of these bounds stay far inside it
+            const float gt = __uint_as_float((uint32_t)(thr >> 32)) * 1.00001f;
+#pragma unroll
+            for (int cc = 0; cc < 5; ++cc) {
+                float tt;
+                if (a.w.mode == NHQ_W_CONSTANT)
+                    tt = a.w.wv > 0.f ? (gt - fac[cc]) * inv_wv
+                                      : (gt >= fac[cc] ? __int_as_float(0x7f800000) : -1.f);
+                else
+                    tt = gt * fac[cc];
+                limtab[cc * BM + r] = tt < 0.f ? -1.f : tt * tt;
+            }
+        };
         const uint32_t lane_base = (uint32_t)((warp - 4) * 32) << 16;
         bool ok = true;
         for (int t = 0; t < ntiles && ok; ++t) {
@@ -277,19 +329,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + c0), v);
                 if (!row_ok)
                     continue;
+                // branch-free filter: every column is written to the next stage slot
+                // and kept (ns advanced) only if it passes the bound of its chi
                 int ns = 0;
+                const float4 *cn4 = reinterpret_cast<const float4 *>(colnorm + b * BN + c0);
+                const uint4 *ca4 = reinterpret_cast<const uint4 *>(colattr + b * BN + c0);
+                const float *lt = limtab + r;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int c = c0 + j;
-                    const float dot = __uint_as_float(v[j]);
-                    const float d2 = fmaxf((nu + colnorm[b * BN + c]) - 2.f * dot, 0.f);
-                    const int ch = chi_packed(au, colattr[b * BN + c], a.w.mask);
-                    const float L = ch == 0 ? lim[0]
-                                            : ch == 1 ? lim[1]
-                                                      : ch == 2 ? lim[2] : ch == 3 ? lim[3] : lim[4];
-                    if (d2 <= L) {
-                        stg[ns] = make_uint2(__float_as_uint(d2), (uint32_t)c | ((uint32_t)ch << 16));
-                        ++ns;
+                for (int j4 = 0; j4 < 8; ++j4) {
+                    const float4 n4 = cn4[j4];
+                    const uint4 at4 = ca4[j4];
+                    const float nc[4] = {n4.x, n4.y, n4.z, n4.w};
+                    const uint32_t ac[4] = {at4.x, at4.y, at4.z, at4.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = j4 * 4 + q;
+                        const float d2 = fmaxf((nu + nc[q]) - 2.f * __uint_as_float(v[j]), 0.f);
+                        const int ch = chi_bytes(au, ac[q], a.w.mask);
+                        stg[ns] = make_uint2(__float_as_uint(d2), (uint32_t)(c0 + j) | ((uint32_t)ch << 16));
+                        ns += d2 <= lt[ch * BM] ? 1 : 0;
                     }
                 }
                 for (int i = 0; i < ns; ++i) {
@@ -303,30 +361,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         ((unsigned long long)__float_as_uint(g) << 32) | (uint32_t)col;
                     if (key >= thr)
                         continue;
-                    int pos = cnt < a.K ? cnt : a.K - 1;
-                    while (pos > 0 && list[pos - 1] > key) {
-                        list[pos] = list[pos - 1];
-                        --pos;
-                    }
-                    list[pos] = key;
-                    if (cnt < a.K)
-                        ++cnt;
-                    if (cnt == a.K) {
-                        thr = list[a.K - 1];
-                        // with slack 1e-5: the f32 roundings of Gamma stay far inside it
-                        const float gt = __uint_as_float((uint32_t)(thr >> 32)) * 1.00001f;
-#pragma unroll
-                        for (int cc = 0; cc < 5; ++cc) {
-                            float tt;
-                            if (a.w.mode == NHQ_W_CONSTANT)
-                                tt = a.w.wv > 0.f ? (gt - a.w.wl * (float)cc) / a.w.wv
-                                                  : (gt >= a.w.wl * (float)cc
-                                                         ? __int_as_float(0x7f800000)
-                                                         : -1.f);
-                            else
-                                tt = gt * (float)a.w.m / (float)(a.w.m + cc);
-                            lim[cc] = tt < 0.f ? -1.f : tt * tt;
+                    if (cnt < K) {  // filling: unordered, heapified once full
+                        hp[1 + cnt] = key;
+                        if (++cnt == K) {
+                            hp[K + 1] = 0ull;
+                            for (int h = K / 2; h >= 1; --h)
+                                heap_sift(hp, K, h, hp[h]);
+                            update_lim();
                         }
+                    } else {  // replace the largest of the K records
+                        heap_sift(hp, K, 1, key);
+                        update_lim();
                     }
                 }
             }
@@ -334,17 +379,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_arrive(bar(TEMPTY0 + b));
         }
         if (row_ok) {
-            for (int j = 0; j < a.K; ++j) {
-                const int64_t o = u * a.K + j;
-                if (j < cnt) {
-                    a.ids[o] = (uint32_t)list[j];
-                    if (a.dists)
-                        a.dists[o] = __uint_as_float((uint32_t)(list[j] >> 32));
-                } else {
+            // heap sort: pop the largest into the last open output slot
+            if (cnt < K) {
+                hp[cnt + 1] = 0ull;
+                for (int h = cnt / 2; h >= 1; --h)
+                    heap_sift(hp, cnt, h, hp[h]);
+            }
+            for (int j = K - 1; j >= 0; --j) {
+                const int64_t o = u * K + j;
+                if (j >= cnt) {
                     a.ids[o] = kNone;
                     if (a.dists)
                         a.dists[o] = __int_as_float(0x7f800000);
+                    continue;
                 }
+                const unsigned long long top = hp[1];
+                a.ids[o] = (uint32_t)top;
+                if (a.dists)
+                    a.dists[o] = __uint_as_float((uint32_t)(top >> 32));
+                const unsigned long long last = hp[j + 1];
+                hp[j + 1] = 0ull;  // sentinel of the heap of size j
+                if (j > 0)
+                    heap_sift(hp, j, 1, last);
             }
         }
     }
@@ -381,7 +437,8 @@ __global__ void bf16_rows_norms_kernel(const float *__restrict__ X, int xstride,
 
 size_t tc_smem_bytes() {
     return 1024 + STAGES * STAGE_BYTES + sizeof(unsigned long long) * BM * LSTRIDE +
-           (sizeof(float) + sizeof(uint32_t)) * 2 * BN + sizeof(uint2) * BM * 33 +
+           (sizeof(float) + sizeof(uint32_t)) * 2 * BN + sizeof(float) * 5 * BM +
+           sizeof(uint2) * BM * 33 +
            sizeof(unsigned long long) * 16 + 64;
 }
 
