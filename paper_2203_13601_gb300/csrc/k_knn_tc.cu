@@ -329,9 +329,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + c0), v);
                 if (!row_ok)
                     continue;
-                // branch-free filter: every column is written to the next stage slot
-                // and kept (ns advanced) only if it passes the bound of its chi
-                int ns = 0;
+                // branch-free filter in two phases, all shared-memory loads before any
+                // store: delta^2 and chi of each column against the bound of its chi
+                // (a pass mask), then the passing columns are appended to the stage
+                uint32_t pass = 0;
                 const float4 *cn4 = reinterpret_cast<const float4 *>(colnorm + b * BN + c0);
                 const uint4 *ca4 = reinterpret_cast<const uint4 *>(colattr + b * BN + c0);
                 const float *lt = limtab + r;
@@ -345,17 +346,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     for (int q = 0; q < 4; ++q) {
                         const int j = j4 * 4 + q;
                         const float d2 = fmaxf((nu + nc[q]) - 2.f * __uint_as_float(v[j]), 0.f);
+                        v[j] = __float_as_uint(d2);
                         const int ch = chi_bytes(au, ac[q], a.w.mask);
-                        stg[ns] = make_uint2(__float_as_uint(d2), (uint32_t)(c0 + j) | ((uint32_t)ch << 16));
-                        ns += d2 <= lt[ch * BM] ? 1 : 0;
+                        pass |= (d2 <= lt[ch * BM] ? 1u : 0u) << j;
                     }
+                }
+                int ns = 0;
+                if (pass != 0u) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if ((pass >> j) & 1u)
+                            stg[ns++] = make_uint2(v[j], (uint32_t)(c0 + j));
                 }
                 for (int i = 0; i < ns; ++i) {
                     const uint2 e = stg[i];
-                    const int c = (int)(e.y & 0xFFFFu), ch = (int)(e.y >> 16);
+                    const int c = (int)e.y;
                     const int64_t col = (int64_t)t * BN + c;
                     if (col >= a.N || col == u)
                         continue;
+                    const int ch = chi_bytes(au, colattr[b * BN + c], a.w.mask);
                     const float g = fusion_gamma(__fsqrt_rn(__uint_as_float(e.x)), ch, a.w);
                     const unsigned long long key =
                         ((unsigned long long)__float_as_uint(g) << 32) | (uint32_t)col;
