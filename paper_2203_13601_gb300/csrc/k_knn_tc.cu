@@ -5,7 +5,16 @@
 // (for integer components 0..255 the rounding is exact and every sum stays
 // below 2^24, so delta^2, delta and Gamma equal the f32 path bit for bit).
 //
-// One CTA owns 128 rows and sweeps all column tiles of 128:
+// The objects are taken in the order of their packed attribute words (a stable
+// sort, so the tuple runs are contiguous): a tile of 128 columns then mostly
+// holds one attribute tuple, chi is one number per row and tile, and where the
+// row's bound for that chi is already negative the tile costs no filtering.
+// Records keep the original ids, so the result (ties by id included) does not
+// depend on this order.
+//
+// One CTA owns 128 rows and sweeps all column tiles of 128, starting at its
+// own (diagonal) tile so that each row first meets the objects of its own tuple
+// (concurrent CTAs then read a sliding window of neighbouring tiles from L2):
 //   warp 0 (one lane)   TMA: 128B-swizzled bf16 boxes of 128 rows x 64 dims of
 //                       both operands into a 3-stage shared-memory ring
 //   warp 1 (one lane)   tcgen05.mma kind::f16, M = 128, N = 128, K = 16, f32
@@ -39,8 +48,9 @@ constexpr uint32_t TMEM_COLS = 2 * BN;
 constexpr long long kWaitLimit = 1ll << 26;
 
 struct TcArgs {
-    const float *norms;  // |x|^2 of the bf16-rounded rows
-    const uint32_t *attr;
+    const float *norms;     // |x|^2 of the bf16-rounded rows, sorted order
+    const uint32_t *attr;   // packed attribute words, sorted order
+    const uint32_t *perm;   // sorted position -> original id
     int64_t N;
     int kblocks;
     Fusion w;
@@ -74,11 +84,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait: false (and an error code recorded) if the phase never completes
+// bounded wait: false (and an error code recorded) if the phase never completes,
+// or false early once another thread has recorded an error
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int *err, int code) {
-    for (long long i = 0; i < kWaitLimit; ++i)
+    for (long long i = 0; i < kWaitLimit; ++i) {
         if (mbar_try_wait(a, parity))
             return true;
+        if ((i & 1023) == 1023 && *reinterpret_cast<volatile int *>(err) != 0)
+            return false;
+    }
     atomicCAS(err, 0, code);
     return false;
 }
@@ -173,7 +187,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         reinterpret_cast<unsigned long long *>(sm + STAGES * STAGE_BYTES);  // 128 x LSTRIDE
     float *colnorm = reinterpret_cast<float *>(lists + BM * LSTRIDE);      // [2][BN]
     uint32_t *colattr = reinterpret_cast<uint32_t *>(colnorm + 2 * BN);   // [2][BN]
-    float *limtab = reinterpret_cast<float *>(colattr + 2 * BN);                 // [5][BM]
+    uint32_t *colid = colattr + 2 * BN;                                          // [2][BN]
+    float *limtab = reinterpret_cast<float *>(colid + 2 * BN);                   // [5][BM]
     uint2 *stage = reinterpret_cast<uint2 *>(limtab + 5 * BM);                   // [BM][33]
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(stage + BM * 33);
     // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], done
@@ -182,6 +197,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.x * BM;
     const int ntiles = (int)((a.N + BN - 1) / BN);
+    const int t0 = (int)blockIdx.x;  // the diagonal tile comes first
+    auto tile_at = [&](int i) { return t0 + i < ntiles ? t0 + i : t0 + i - ntiles; };
     const int kb_n = a.kblocks;
     auto bar = [&](int i) { return smem_u32(bars + i); };
     const int FULL0 = 0, EMPTY0 = STAGES, TFULL0 = 2 * STAGES, TEMPTY0 = 2 * STAGES + 2,
@@ -216,7 +233,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
-        for (int t = 0; t < ntiles && ok; ++t) {
+        // after a failed wait the warps keep stepping through the named barrier (so
+        // none waits there for another) but do no more work
+        for (int i = 0; i < ntiles; ++i) {
+            const int t = tile_at(i);
             for (int kb = 0; kb < kb_n && ok; ++kb) {
                 ok = mbar_wait(bar(EMPTY0 + stage), phase ^ 1u, a.err, 1);
                 if (!ok)
@@ -236,9 +256,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true, issued = false;
-        for (int t = 0; t < ntiles && ok; ++t) {
-            const int b = t & 1;
-            const uint32_t tph = (uint32_t)(t >> 1) & 1u;
+        for (int i = 0; i < ntiles && ok; ++i) {
+            const int b = i & 1;
+            const uint32_t tph = (uint32_t)(i >> 1) & 1u;
             ok = mbar_wait(bar(TEMPTY0 + b), tph ^ 1u, a.err, 2);
             if (!ok)
                 break;
@@ -263,14 +283,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             if (ok)
-                umma_commit(bar(TFULL0 + b));  // accumulators of tile t are complete
+                umma_commit(bar(TFULL0 + b));  // accumulators of the i-th tile are complete
         }
         if (issued) {  // wait for every issued MMA before TMEM can be released
             umma_commit(bar(DONE));
             mbar_wait(bar(DONE), 0, a.err, 4);
         }
     } else if (warp >= 4) {
-        // ---------------- epilogue: thread r owns row row0 + r
+        // ---------------- epilogue: thread r owns row row0 + r (sorted position)
         const int r = (warp - 4) * 32 + lane;
         const int64_t u = row0 + r;
         const bool row_ok = u < a.N;
@@ -281,9 +301,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int K = a.K;
         int cnt = 0;
         unsigned long long thr = kInfKey;
-        // delta^2 bounds per chi: a record with this chi and a larger delta^2 cannot
-        // reach the row's current K-th record (Gamma grows with delta and with chi)
-        // delta^2 bound of chi = c for this row at limtab[c * BM + r]
+        // delta^2 bound of chi = c for this row at limtab[c * BM + r]: a record with
+        // this chi and a larger delta^2 cannot reach the row's current K-th record
+        // (Gamma grows with delta and with chi); -1 where no delta can
         float fac[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
@@ -309,46 +329,94 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         };
         const uint32_t lane_base = (uint32_t)((warp - 4) * 32) << 16;
+        const float *lt = limtab + r;
+        // column metadata of the next tile, loaded one tile ahead
+        float pn = 0.f;
+        uint32_t pa = 0u, pi = 0u;
+        {
+            const int64_t cme = (int64_t)tile_at(0) * BN + r;
+            if (cme < a.N) {
+                pn = a.norms[cme];
+                pa = a.attr[cme];
+                pi = a.perm[cme];
+            }
+        }
         bool ok = true;
-        for (int t = 0; t < ntiles && ok; ++t) {
-            const int b = t & 1;
-            const uint32_t tph = (uint32_t)(t >> 1) & 1u;
-            const int64_t cme = (int64_t)t * BN + r;
-            colnorm[b * BN + r] = cme < a.N ? a.norms[cme] : 0.f;
-            colattr[b * BN + r] = cme < a.N ? a.attr[cme] : 0u;
+        for (int i = 0; i < ntiles && ok; ++i) {
+            const int t = tile_at(i);
+            const int b = i & 1;
+            const uint32_t tph = (uint32_t)(i >> 1) & 1u;
+            colnorm[b * BN + r] = pn;
+            colattr[b * BN + r] = pa;
+            colid[b * BN + r] = pi;
             asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (i + 1 < ntiles) {
+                const int64_t cme = (int64_t)tile_at(i + 1) * BN + r;
+                const bool in = cme < a.N;
+                pn = in ? a.norms[cme] : 0.f;
+                pa = in ? a.attr[cme] : 0u;
+                pi = in ? a.perm[cme] : 0u;
+            }
+            // one tuple in the whole tile (sorted order: first == last)
+            const uint32_t ta = colattr[b * BN];
+            const bool uni = (int64_t)(t + 1) * BN <= a.N && ta == colattr[b * BN + BN - 1];
+            const int ch_t = chi_bytes(au, ta, a.w.mask);
+            if (!ok)
+                continue;
             ok = mbar_wait(bar(TFULL0 + b), tph, a.err, 5);
             __syncwarp();  // tcgen05.ld below needs the whole warp converged
             if (!__all_sync(0xFFFFFFFFu, ok)) {
                 ok = false;
-                break;
+                continue;
             }
             tc_fence_after();
             for (int c0 = 0; c0 < BN; c0 += 32) {
+                // the bounds only tighten: a row whose bound for this tile's chi is
+                // negative rejects every column of the tile
+                const bool dead = !row_ok || (uni && lt[ch_t * BM] < 0.f);
+                if (__all_sync(0xFFFFFFFFu, dead))
+                    break;
                 uint32_t v[32];
                 tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + c0), v);
-                if (!row_ok)
+                if (dead)
                     continue;
                 // branch-free filter in two phases, all shared-memory loads before any
-                // store: delta^2 and chi of each column against the bound of its chi
-                // (a pass mask), then the passing columns are appended to the stage
+                // store: a pass mask of the columns within the bound of their chi,
+                // then the passing columns are appended to the stage
                 uint32_t pass = 0;
                 const float4 *cn4 = reinterpret_cast<const float4 *>(colnorm + b * BN + c0);
-                const uint4 *ca4 = reinterpret_cast<const uint4 *>(colattr + b * BN + c0);
-                const float *lt = limtab + r;
+                if (uni) {
+                    const float L = lt[ch_t * BM];
 #pragma unroll
-                for (int j4 = 0; j4 < 8; ++j4) {
-                    const float4 n4 = cn4[j4];
-                    const uint4 at4 = ca4[j4];
-                    const float nc[4] = {n4.x, n4.y, n4.z, n4.w};
-                    const uint32_t ac[4] = {at4.x, at4.y, at4.z, at4.w};
+                    for (int j4 = 0; j4 < 8; ++j4) {
+                        const float4 n4 = cn4[j4];
+                        const float nc[4] = {n4.x, n4.y, n4.z, n4.w};
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = j4 * 4 + q;
-                        const float d2 = fmaxf((nu + nc[q]) - 2.f * __uint_as_float(v[j]), 0.f);
-                        v[j] = __float_as_uint(d2);
-                        const int ch = chi_bytes(au, ac[q], a.w.mask);
-                        pass |= (d2 <= lt[ch * BM] ? 1u : 0u) << j;
+                        for (int q = 0; q < 4; ++q) {
+                            const int j = j4 * 4 + q;
+                            const float d2 =
+                                fmaxf((nu + nc[q]) - 2.f * __uint_as_float(v[j]), 0.f);
+                            v[j] = __float_as_uint(d2);
+                            pass |= (d2 <= L ? 1u : 0u) << j;
+                        }
+                    }
+                } else {
+                    const uint4 *ca4 = reinterpret_cast<const uint4 *>(colattr + b * BN + c0);
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; ++j4) {
+                        const float4 n4 = cn4[j4];
+                        const uint4 at4 = ca4[j4];
+                        const float nc[4] = {n4.x, n4.y, n4.z, n4.w};
+                        const uint32_t ac[4] = {at4.x, at4.y, at4.z, at4.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int j = j4 * 4 + q;
+                            const float d2 =
+                                fmaxf((nu + nc[q]) - 2.f * __uint_as_float(v[j]), 0.f);
+                            v[j] = __float_as_uint(d2);
+                            const int ch = chi_bytes(au, ac[q], a.w.mask);
+                            pass |= (d2 <= lt[ch * BM] ? 1u : 0u) << j;
+                        }
                     }
                 }
                 int ns = 0;
@@ -358,8 +426,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         if ((pass >> j) & 1u)
                             stg[ns++] = make_uint2(v[j], (uint32_t)(c0 + j));
                 }
-                for (int i = 0; i < ns; ++i) {
-                    const uint2 e = stg[i];
+                for (int s2 = 0; s2 < ns; ++s2) {
+                    const uint2 e = stg[s2];
                     const int c = (int)e.y;
                     const int64_t col = (int64_t)t * BN + c;
                     if (col >= a.N || col == u)
@@ -367,7 +435,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const int ch = chi_bytes(au, colattr[b * BN + c], a.w.mask);
                     const float g = fusion_gamma(__fsqrt_rn(__uint_as_float(e.x)), ch, a.w);
                     const unsigned long long key =
-                        ((unsigned long long)__float_as_uint(g) << 32) | (uint32_t)col;
+                        ((unsigned long long)__float_as_uint(g) << 32) | colid[b * BN + c];
                     if (key >= thr)
                         continue;
                     if (cnt < K) {  // filling: unordered, heapified once full
@@ -388,14 +456,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_arrive(bar(TEMPTY0 + b));
         }
         if (row_ok) {
-            // heap sort: pop the largest into the last open output slot
+            // heap sort: pop the largest into the last open output slot of the
+            // object's own (original) row
+            const int64_t orow = (int64_t)a.perm[u] * K;
             if (cnt < K) {
                 hp[cnt + 1] = 0ull;
                 for (int h = cnt / 2; h >= 1; --h)
                     heap_sift(hp, cnt, h, hp[h]);
             }
             for (int j = K - 1; j >= 0; --j) {
-                const int64_t o = u * K + j;
+                const int64_t o = orow + j;
                 if (j >= cnt) {
                     a.ids[o] = kNone;
                     if (a.dists)
@@ -422,17 +492,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-// bf16 rows padded to kpad (multiple of 64) and the squared norms of the rounded rows
+// bf16 rows padded to kpad (multiple of 64) and the squared norms of the rounded rows,
+// row r taken from object perm[r]
 __global__ void bf16_rows_norms_kernel(const float *__restrict__ X, int xstride, int d,
-                                       int64_t N, int kpad, __nv_bfloat16 *__restrict__ Xk,
+                                       int64_t N, int kpad, const uint32_t *__restrict__ perm,
+                                       __nv_bfloat16 *__restrict__ Xk,
                                        float *__restrict__ norms) {
     const int lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= N)
         return;
+    const int64_t src = perm[r];
     float acc = 0.f;
     for (int c = lane; c < kpad; c += 32) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(c < d ? X[r * xstride + c] : 0.f);
+        const __nv_bfloat16 h = __float2bfloat16_rn(c < d ? X[src * xstride + c] : 0.f);
         Xk[r * kpad + c] = h;
         const float f = __bfloat162float(h);
         acc = fmaf(f, f, acc);
@@ -446,7 +519,7 @@ __global__ void bf16_rows_norms_kernel(const float *__restrict__ X, int xstride,
 
 size_t tc_smem_bytes() {
     return 1024 + STAGES * STAGE_BYTES + sizeof(unsigned long long) * BM * LSTRIDE +
-           (sizeof(float) + sizeof(uint32_t)) * 2 * BN + sizeof(float) * 5 * BM +
+           (sizeof(float) + 2 * sizeof(uint32_t)) * 2 * BN + sizeof(float) * 5 * BM +
            sizeof(uint2) * BM * 33 +
            sizeof(unsigned long long) * 16 + 64;
 }
@@ -456,16 +529,17 @@ size_t tc_smem_bytes() {
 int knn_tc_kmax() { return KMAX; }
 
 cudaError_t launch_knn_tc_prepare(const float *X, int xstride, int d, int64_t N, int kpad,
-                                  __nv_bfloat16 *Xk, float *norms, cudaStream_t s) {
+                                  const uint32_t *perm, __nv_bfloat16 *Xk, float *norms,
+                                  cudaStream_t s) {
     const int wpb = 8;
     bf16_rows_norms_kernel<<<(unsigned)((N + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
-        X, xstride, d, N, kpad, Xk, norms);
+        X, xstride, d, N, kpad, perm, Xk, norms);
     return cudaGetLastError();
 }
 
 cudaError_t launch_knn_tc(const __nv_bfloat16 *Xk, int kpad, const float *norms,
-                          const uint32_t *attr, int64_t N, const Fusion &w, int K, uint32_t *ids,
-                          float *dists, int *err, cudaStream_t s) {
+                          const uint32_t *attr, const uint32_t *perm, int64_t N, const Fusion &w,
+                          int K, uint32_t *ids, float *dists, int *err, cudaStream_t s) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (encode == nullptr) {
         cudaDriverEntryPointQueryResult q;
@@ -491,6 +565,7 @@ cudaError_t launch_knn_tc(const __nv_bfloat16 *Xk, int kpad, const float *norms,
     TcArgs a;
     a.norms = norms;
     a.attr = attr;
+    a.perm = perm;
     a.N = N;
     a.kblocks = kpad / BK;
     a.w = w;

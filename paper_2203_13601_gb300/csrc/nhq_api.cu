@@ -328,6 +328,18 @@ nhq_status nhq_knn(const nhq_index *cix, int32_t K, uint32_t *cand_ids, float *c
     return st.finish(s);
 }
 
+// the packed attribute words sorted ascending with their ids (stable), built once
+static nhq_status ensure_attribute_order(nhq_index *ix, cudaStream_t s) {
+    if (ix->attr_sorted != nullptr)
+        return NHQ_OK;
+    CK(cudaMalloc(&ix->attr_sorted, sizeof(uint32_t) * (size_t)ix->N));
+    CK(cudaMalloc(&ix->id_sorted, sizeof(uint32_t) * (size_t)ix->N));
+    CKS(scratch(ix, attribute_sort_scratch_bytes(ix->N)));
+    CK(launch_attribute_sort(ix->attr, ix->N, ix->attr_sorted, ix->id_sorted, ix->scratch,
+                             ix->scratch_bytes, s));
+    return NHQ_OK;
+}
+
 nhq_status nhq_knn_bf16(const nhq_index *cix, int32_t K, uint32_t *cand_ids, float *cand_dist,
                         void *stream) {
     nhq_index *ix = const_cast<nhq_index *>(cix);
@@ -336,11 +348,13 @@ nhq_status nhq_knn_bf16(const nhq_index *cix, int32_t K, uint32_t *cand_ids, flo
     if (K < 1 || K > knn_tc_kmax() || K >= ix->N)
         return fail(NHQ_ERR_ARG, "K must be in 1..min(64, N-1) (got %d)", K);
     cudaStream_t s = as_stream(stream);
-    if (ix->Xk == nullptr) {
+    CKS(ensure_attribute_order(ix, s));
+    if (ix->Xk == nullptr) {  // bf16 rows in attribute order
         ix->kpad = (ix->d + 63) & ~63;
         CK(cudaMalloc(&ix->Xk, sizeof(__nv_bfloat16) * (size_t)ix->N * ix->kpad));
         CK(cudaMalloc(&ix->normk, sizeof(float) * (size_t)ix->N));
-        CK(launch_knn_tc_prepare(ix->X, ix->xstride, ix->d, ix->N, ix->kpad, ix->Xk, ix->normk, s));
+        CK(launch_knn_tc_prepare(ix->X, ix->xstride, ix->d, ix->N, ix->kpad, ix->id_sorted,
+                                 ix->Xk, ix->normk, s));
     }
     Stager st;
     int io = st.add(cand_ids, sizeof(uint32_t) * (size_t)ix->N * K, false);
@@ -349,8 +363,8 @@ nhq_status nhq_knn_bf16(const nhq_index *cix, int32_t K, uint32_t *cand_ids, flo
     CKS(scratch(ix, 256));
     int *err = reinterpret_cast<int *>(ix->scratch);
     CK(cudaMemsetAsync(err, 0, sizeof(int), s));
-    cudaError_t e = launch_knn_tc(ix->Xk, ix->kpad, ix->normk, ix->attr, ix->N,
-                                  make_fusion(ix->w, ix->m), K, (uint32_t *)st.dev(io),
+    cudaError_t e = launch_knn_tc(ix->Xk, ix->kpad, ix->normk, ix->attr_sorted, ix->id_sorted,
+                                  ix->N, make_fusion(ix->w, ix->m), K, (uint32_t *)st.dev(io),
                                   (float *)st.dev(id), err, s);
     if (e != cudaSuccess)
         return fail_cuda(e, "tensor-core candidate kernel launch");
@@ -598,13 +612,8 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         if (!(P.stop_threshold > 0.f && P.stop_threshold < 1.f))
             return fail(NHQ_ERR_ARG, "stop_threshold must be a probability in (0, 1)");
     }
-    if (P.seed_mode == NHQ_SEED_ATTRIBUTE && ix->attr_sorted == nullptr) {
-        CK(cudaMalloc(&ix->attr_sorted, sizeof(uint32_t) * (size_t)ix->N));
-        CK(cudaMalloc(&ix->id_sorted, sizeof(uint32_t) * (size_t)ix->N));
-        CKS(scratch(ix, attribute_sort_scratch_bytes(ix->N)));
-        CK(launch_attribute_sort(ix->attr, ix->N, ix->attr_sorted, ix->id_sorted, ix->scratch,
-                                 ix->scratch_bytes, s));
-    }
+    if (P.seed_mode == NHQ_SEED_ATTRIBUTE)
+        CKS(ensure_attribute_order(ix, s));
     if (P.vec_dtype == NHQ_VEC_BF16 && ix->Xh == nullptr) {
         CK(cudaMalloc(&ix->Xh, sizeof(__nv_bfloat16) * (size_t)ix->N * ix->xstride));
         CK(launch_rows_to_bf16(ix->X, (int64_t)ix->N * ix->xstride, ix->Xh, s));

@@ -214,11 +214,14 @@ cudaError_t launch_attribute_sort(const uint32_t *attr, int64_t N, uint32_t *att
 size_t attribute_sort_scratch_bytes(int64_t N);
 // k_knn_tc.cu
 int knn_tc_kmax();
+// Xk/norms rows in the order perm (sorted position -> original id); the candidate
+// kernel takes attributes in the same order and writes rows and ids in original ids
 cudaError_t launch_knn_tc_prepare(const float *X, int xstride, int d, int64_t N, int kpad,
-                                  __nv_bfloat16 *Xk, float *norms, cudaStream_t s);
+                                  const uint32_t *perm, __nv_bfloat16 *Xk, float *norms,
+                                  cudaStream_t s);
 cudaError_t launch_knn_tc(const __nv_bfloat16 *Xk, int kpad, const float *norms,
-                          const uint32_t *attr, int64_t N, const Fusion &w, int K, uint32_t *ids,
-                          float *dists, int *err, cudaStream_t s);
+                          const uint32_t *attr, const uint32_t *perm, int64_t N, const Fusion &w,
+                          int K, uint32_t *ids, float *dists, int *err, cudaStream_t s);
 
 // k_mlp.cu
 cudaError_t launch_mlp_to_half(const float *params, __half *w16, cudaStream_t s);

@@ -473,6 +473,21 @@ def test_knn_tensor_cores_exact_on_integer_data(nhq, weights, N, d):
     assert np.array_equal(dist.cpu().numpy().astype(np.float64), ref_g)
 
 
+@pytest.mark.parametrize("weights", [None, CONST])
+def test_knn_tensor_cores_exact_with_long_tuple_runs(nhq, weights):
+    # six attribute tuples: most column tiles hold a single tuple (the per-tile chi
+    # path), and rows whose lists are full of matching objects reject whole tiles
+    w = synth.int_valued(3001, 1, 48, cards=(2, 3), n_comp=12, seed=63)
+    ref, ref_g = O.knn(w.X, w.A, 24, weights=weights, prec=O.F32)
+    with _index(nhq, w, weights) as ix:
+        cand = torch.empty((w.N, 24), dtype=torch.uint32, device="cuda:0")
+        dist = torch.empty((w.N, 24), dtype=torch.float32, device="cuda:0")
+        nhq.nhq_knn_bf16(ix.handle, 24, cand, dist)
+        torch.cuda.synchronize()
+    assert (ids_i64(cand) == ref).all()
+    assert np.array_equal(dist.cpu().numpy().astype(np.float64), ref_g)
+
+
 def test_knn_tensor_cores_on_float_data(nhq):
     # bf16 rounding of float rows: candidates are exact for the rounded rows, so
     # they overlap the f32 candidates almost everywhere
