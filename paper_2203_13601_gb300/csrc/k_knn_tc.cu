@@ -15,8 +15,11 @@
 // One CTA owns 128 rows and sweeps all column tiles of 128, starting at its
 // own (diagonal) tile so that each row first meets the objects of its own tuple
 // (concurrent CTAs then read a sliding window of neighbouring tiles from L2):
-//   warp 0 (one lane)   TMA: 128B-swizzled bf16 boxes of 128 rows x 64 dims of
-//                       both operands into a 3-stage shared-memory ring
+//   warp 0              scheduler + TMA: decides for each tile whether any row
+//                       can still take a record from it (skipped tiles are never
+//                       loaded or multiplied), then one lane loads 128B-swizzled
+//                       bf16 boxes of 128 rows x 64 dims; with d <= 128 the row
+//                       operand is loaded once and stays resident
 //   warp 1 (one lane)   tcgen05.mma kind::f16, M = 128, N = 128, K = 16, f32
 //                       accumulators in two TMEM buffers of 128 columns
 //   warps 4..7          epilogue: tcgen05.ld of its 32 lanes (= rows), delta^2 and
@@ -24,8 +27,12 @@
 //                       bounds by chi (branch-free), then for the few survivors
 //                       exact Gamma (Eq. 6) and a per-row max-heap of the K best
 //                       records in shared memory (sorted once at the end)
-// Every mbarrier wait is bounded; a timeout records an error code and the CTA
-// drains its tensor-core work, frees its TMEM and returns.
+// A tile is skipped when every row's bound for the smallest chi the tile can
+// have with it is negative: in the constant and filter weightings a row whose K
+// records all match its tuple rejects every other tuple.  The bounds only
+// tighten, so a decision taken on older bounds is still correct.
+// Every wait is bounded; a timeout records an error code, the other waits see it
+// and return, the CTA drains its tensor-core work, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -36,14 +43,16 @@ namespace nhq {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int STAGES = 3;
 constexpr int KMAX = 64;
 // u64 entries per row heap: slot 0 unused, 1..K the heap, K+1 a zero sentinel (so a
 // node's two children are one aligned 16-byte pair); even, so every row is 16-byte aligned
 constexpr int LSTRIDE = KMAX + 2;
 constexpr int NTHREADS = 256;
-constexpr uint32_t TILE_BYTES = BM * BK * 2;  // one operand box: 16 KB
-constexpr uint32_t STAGE_BYTES = 2 * TILE_BYTES;
+constexpr uint32_t BOX_BYTES = BM * BK * 2;  // one operand box: 16 KB
+// operand ring of 6 boxes: 3 stages of (A, B) boxes, or with d <= 128 the resident
+// A boxes (2) and 4 single-box B stages
+constexpr uint32_t RING_BYTES = 6 * BOX_BYTES;
+constexpr int MAX_STAGES = 4;
 constexpr uint32_t TMEM_COLS = 2 * BN;
 constexpr long long kWaitLimit = 1ll << 26;
 
@@ -177,43 +186,106 @@ __device__ __forceinline__ int chi_bytes(uint32_t a, uint32_t b, uint32_t mask) 
     return __popc(y & 0x80808080u);
 }
 
+// bounded wait for the scheduler's decision on the i-th tile of the sweep
+__device__ __forceinline__ bool wait_decided(const int *decided, int i, int *err, int code) {
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        if (*reinterpret_cast<const volatile int *>(decided) > i) {
+            __threadfence_block();
+            return true;
+        }
+        if ((it & 1023) == 1023 && *reinterpret_cast<volatile int *>(err) != 0)
+            return false;
+        __nanosleep(32);
+    }
+    atomicCAS(err, 0, code);
+    return false;
+}
+// the first sweep index >= i that the scheduler kept (ntiles if none), scanning the
+// published skip bits a word at a time; -1 if a wait failed
+__device__ __forceinline__ int next_kept(const int *decided, const uint32_t *bits, int i,
+                                         int ntiles, int *err, int code) {
+    while (i < ntiles) {
+        if (!wait_decided(decided, i, err, code))
+            return -1;
+        const int dec = *reinterpret_cast<const volatile int *>(decided);
+        while (i < dec) {
+            const int sh = i & 31;
+            const int n = dec - i < 32 - sh ? dec - i : 32 - sh;
+            const uint32_t w = reinterpret_cast<const volatile uint32_t *>(bits)[i >> 5] >> sh;
+            const uint32_t keep = ~w & (n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u));
+            if (keep != 0u)
+                return i + __ffs((int)keep) - 1;
+            i += n;
+        }
+    }
+    return ntiles;
+}
+
+struct TcSmem {  // byte offsets in the dynamic shared memory (after 1024-byte alignment)
+    uint32_t heaps, stage, limtab, meta, bits, bars, misc, total;
+};
+__host__ __device__ inline TcSmem tc_smem_layout(int ntiles) {
+    TcSmem L;
+    L.heaps = RING_BYTES;
+    L.stage = L.heaps + 8u * BM * LSTRIDE;                         // [BM][33] uint2
+    L.limtab = L.stage + 8u * BM * 33;                             // [5][BM] f32
+    L.meta = L.limtab + 4u * 5 * BM;                               // per epilogue warp: norm, attr, id [BN]
+    L.bits = L.meta + 4u * 3 * 4 * BN;                             // skip bit per tile
+    L.bars = L.bits + ((4u * (uint32_t)((ntiles + 31) / 32) + 15u) & ~15u);
+    L.misc = L.bars + 8u * 16;                                     // decided counter, TMEM address
+    L.total = L.misc + 16;
+    return L;
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
     knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    unsigned char *ring = sm;                                           // STAGES x 32 KB
-    unsigned long long *lists =
-        reinterpret_cast<unsigned long long *>(sm + STAGES * STAGE_BYTES);  // 128 x LSTRIDE
-    float *colnorm = reinterpret_cast<float *>(lists + BM * LSTRIDE);      // [2][BN]
-    uint32_t *colattr = reinterpret_cast<uint32_t *>(colnorm + 2 * BN);   // [2][BN]
-    uint32_t *colid = colattr + 2 * BN;                                          // [2][BN]
-    float *limtab = reinterpret_cast<float *>(colid + 2 * BN);                   // [5][BM]
-    uint2 *stage = reinterpret_cast<uint2 *>(limtab + 5 * BM);                   // [BM][33]
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(stage + BM * 33);
-    // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], done
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
+    const int ntiles = (int)((a.N + BN - 1) / BN);
+    const TcSmem L = tc_smem_layout(ntiles);
+    unsigned char *ring = sm;
+    unsigned long long *heaps = reinterpret_cast<unsigned long long *>(sm + L.heaps);
+    uint2 *stage = reinterpret_cast<uint2 *>(sm + L.stage);
+    float *limtab = reinterpret_cast<float *>(sm + L.limtab);
+    unsigned char *meta = sm + L.meta;
+    uint32_t *skipbits = reinterpret_cast<uint32_t *>(sm + L.bits);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(sm + L.bars);
+    int *decided = reinterpret_cast<int *>(sm + L.misc);
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(sm + L.misc + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.x * BM;
-    const int ntiles = (int)((a.N + BN - 1) / BN);
+    const int kb_n = a.kblocks;
+    const bool resA = kb_n <= 2;  // the row operand stays in shared memory
+    const int nst = resA ? 4 : 3;
+    const uint32_t sbytes = resA ? BOX_BYTES : 2 * BOX_BYTES;
+    const uint32_t boff = resA ? 0u : BOX_BYTES;  // B box within a stage
+    unsigned char *aregion = ring + 4 * BOX_BYTES;
     const int t0 = (int)blockIdx.x;  // the diagonal tile comes first
     auto tile_at = [&](int i) { return t0 + i < ntiles ? t0 + i : t0 + i - ntiles; };
-    const int kb_n = a.kblocks;
     auto bar = [&](int i) { return smem_u32(bars + i); };
-    const int FULL0 = 0, EMPTY0 = STAGES, TFULL0 = 2 * STAGES, TEMPTY0 = 2 * STAGES + 2,
-              DONE = 2 * STAGES + 4;
+    const int FULL0 = 0, EMPTY0 = MAX_STAGES, TFULL0 = 2 * MAX_STAGES, TEMPTY0 = TFULL0 + 2,
+              AFULL = TEMPTY0 + 2, DONE = AFULL + 1;
+    // whole tiles are rejected only where a negative bound is possible
+    const bool skip_on = a.w.mode != NHQ_W_PROPORTIONAL;
 
+    for (int i = threadIdx.x; i < (ntiles + 31) / 32; i += NTHREADS)
+        skipbits[i] = 0u;
+    for (int i = threadIdx.x; i < 5 * BM; i += NTHREADS)
+        limtab[i] = __int_as_float(0x7f800000);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(bar(FULL0 + s), 1);
-            mbar_init(bar(EMPTY0 + s), 1);
+        for (int q = 0; q < MAX_STAGES; ++q) {
+            mbar_init(bar(FULL0 + q), 1);
+            mbar_init(bar(EMPTY0 + q), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(bar(TFULL0 + b), 1);
             mbar_init(bar(TEMPTY0 + b), BM);
         }
+        mbar_init(bar(AFULL), 1);
         mbar_init(bar(DONE), 1);
+        *decided = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -228,37 +300,126 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer
+    if (warp == 0) {
+        // ---------------- scheduler (all lanes) + TMA producer (lane 0)
+        uint32_t ra[4];
+        bool rv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t u = row0 + lane + 32 * k;
+            rv[k] = u < a.N;
+            ra[k] = rv[k] ? a.attr[u] : 0u;
+        }
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
-        // after a failed wait the warps keep stepping through the named barrier (so
-        // none waits there for another) but do no more work
-        for (int i = 0; i < ntiles; ++i) {
-            const int t = tile_at(i);
-            for (int kb = 0; kb < kb_n && ok; ++kb) {
-                ok = mbar_wait(bar(EMPTY0 + stage), phase ^ 1u, a.err, 1);
-                if (!ok)
-                    break;
-                const uint32_t dstA = smem_u32(ring + stage * STAGE_BYTES);
-                mbar_expect_tx(bar(FULL0 + stage), STAGE_BYTES);
-                tma_load_2d(dstA, &tmap, bar(FULL0 + stage), kb * BK, (int)row0);
-                tma_load_2d(dstA + TILE_BYTES, &tmap, bar(FULL0 + stage), kb * BK, t * BN);
-                if (++stage == STAGES) {
-                    stage = 0;
-                    phase ^= 1u;
+        if (resA && lane == 0) {
+            mbar_expect_tx(bar(AFULL), (uint32_t)kb_n * BOX_BYTES);
+            for (int kb = 0; kb < kb_n; ++kb)
+                tma_load_2d(smem_u32(aregion + kb * BOX_BYTES), &tmap, bar(AFULL), kb * BK,
+                            (int)row0);
+        }
+        // first and last attribute word of tiles i..i+31 (lane l: tile i + l), loaded
+        // one group of 32 ahead
+        auto codes = [&](int base, uint32_t &f, uint32_t &l) {
+            const int ii = base + lane;
+            f = l = 0u;
+            if (ii < ntiles) {
+                const int64_t c0 = (int64_t)tile_at(ii) * BN;
+                const int64_t c1 = (c0 + BN < a.N ? c0 + BN : a.N) - 1;
+                f = __ldg(a.attr + c0);
+                l = __ldg(a.attr + c1);
+            }
+        };
+        uint32_t cf, cl, nf, nl;
+        codes(0, cf, cl);
+        codes(32, nf, nl);
+        uint32_t wbits = 0u;        // skip bits of the current word, published by lane 0
+        uint32_t dead_tuple = 0u;  // a tuple whose tiles were found dead (stays dead)
+        bool have_dead = false;
+        for (int i = 0; i < ntiles && ok; ++i) {
+            if ((i & 31) == 0 && i > 0) {
+                cf = nf;
+                cl = nl;
+                codes(i + 32, nf, nl);
+            }
+            const uint32_t tf = __shfl_sync(0xFFFFFFFFu, cf, i & 31);
+            const uint32_t tl = __shfl_sync(0xFFFFFFFFu, cl, i & 31);
+            bool need = true;
+            if (skip_on) {
+                if (have_dead && tf == tl && tf == dead_tuple) {
+                    need = false;  // the bounds only tighten
+                } else {
+                    // the smallest chi a column of the tile can have with the row: 0 if
+                    // the row's word lies in the tile's (sorted) range, that of the
+                    // tile's one tuple if it has one, else at least 1
+                    bool live = false;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (!rv[k])
+                            continue;
+                        const int ch = (ra[k] >= tf && ra[k] <= tl)
+                                           ? 0
+                                           : (tf == tl ? chi_bytes(ra[k], tf, a.w.mask) : 1);
+                        const float lim = reinterpret_cast<const volatile float *>(
+                            limtab)[ch * BM + lane + 32 * k];
+                        live = live || !(lim < 0.f);
+                    }
+                    need = __any_sync(0xFFFFFFFFu, live);
+                    if (!need && tf == tl) {
+                        dead_tuple = tf;
+                        have_dead = true;
+                    }
                 }
             }
+            if (!need)
+                wbits |= 1u << (i & 31);
+            // publish before loading (the consumers need the decision first) and at the
+            // end of every word
+            if (lane == 0 && (need || (i & 31) == 31 || i + 1 == ntiles)) {
+                skipbits[i >> 5] = wbits;
+                __threadfence_block();
+                *reinterpret_cast<volatile int *>(decided) = i + 1;
+            }
+            if ((i & 31) == 31)
+                wbits = 0u;
+            if (need && lane == 0) {
+                const int t = tile_at(i);
+                for (int kb = 0; kb < kb_n && ok; ++kb) {
+                    ok = mbar_wait(bar(EMPTY0 + stage), phase ^ 1u, a.err, 1);
+                    if (!ok)
+                        break;
+                    const uint32_t dst = smem_u32(ring + stage * sbytes);
+                    mbar_expect_tx(bar(FULL0 + stage), sbytes);
+                    if (!resA)
+                        tma_load_2d(dst, &tmap, bar(FULL0 + stage), kb * BK, (int)row0);
+                    tma_load_2d(dst + boff, &tmap, bar(FULL0 + stage), kb * BK, t * BN);
+                    if (++stage == nst) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
-        int stage = 0;
+        int stage = 0, p = 0;
         uint32_t phase = 0;
         bool ok = true, issued = false;
-        for (int i = 0; i < ntiles && ok; ++i) {
-            const int b = i & 1;
-            const uint32_t tph = (uint32_t)(i >> 1) & 1u;
+        if (resA)
+            ok = mbar_wait(bar(AFULL), 0, a.err, 6);
+        for (int i = 0; ok; ++i) {
+            i = next_kept(decided, skipbits, i, ntiles, a.err, 7);
+            if (i < 0) {
+                ok = false;
+                break;
+            }
+            if (i >= ntiles)
+                break;
+            const int b = p & 1;
+            const uint32_t tph = (uint32_t)(p >> 1) & 1u;
+            ++p;
             ok = mbar_wait(bar(TEMPTY0 + b), tph ^ 1u, a.err, 2);
             if (!ok)
                 break;
@@ -269,21 +430,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (!ok)
                     break;
                 tc_fence_after();
-                const uint32_t sA = smem_u32(ring + stage * STAGE_BYTES);
-                const uint32_t sB = sA + TILE_BYTES;
+                const uint32_t sS = smem_u32(ring + stage * sbytes);
+                const uint32_t sA = resA ? smem_u32(aregion + kb * BOX_BYTES) : sS;
+                const uint32_t sB = sS + boff;
 #pragma unroll
                 for (int k4 = 0; k4 < BK / 16; ++k4)
                     umma_bf16(d_tmem, sw128_desc(sA + 32u * k4), sw128_desc(sB + 32u * k4),
                               (kb | k4) != 0 ? 1u : 0u);
                 issued = true;
                 umma_commit(bar(EMPTY0 + stage));  // the stage is free once these complete
-                if (++stage == STAGES) {
+                if (++stage == nst) {
                     stage = 0;
                     phase ^= 1u;
                 }
             }
             if (ok)
-                umma_commit(bar(TFULL0 + b));  // accumulators of the i-th tile are complete
+                umma_commit(bar(TFULL0 + b));  // accumulators of this tile are complete
         }
         if (issued) {  // wait for every issued MMA before TMEM can be released
             umma_commit(bar(DONE));
@@ -291,13 +453,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else if (warp >= 4) {
         // ---------------- epilogue: thread r owns row row0 + r (sorted position)
-        const int r = (warp - 4) * 32 + lane;
+        const int ew = warp - 4;
+        const int r = ew * 32 + lane;
         const int64_t u = row0 + r;
         const bool row_ok = u < a.N;
         const float nu = row_ok ? a.norms[u] : 0.f;
         const uint32_t au = row_ok ? a.attr[u] : 0u;
-        unsigned long long *hp = lists + r * LSTRIDE;
+        unsigned long long *hp = heaps + r * LSTRIDE;
         uint2 *stg = stage + r * (32 + 1);  // survivors of one 32-column chunk
+        // this warp's copy of the tile's column metadata
+        float *mnorm = reinterpret_cast<float *>(meta) + ew * 3 * BN;
+        uint32_t *mattr = reinterpret_cast<uint32_t *>(mnorm + BN);
+        uint32_t *mid = mattr + BN;
         const int K = a.K;
         int cnt = 0;
         unsigned long long thr = kInfKey;
@@ -306,12 +473,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // (Gamma grows with delta and with chi); -1 where no delta can
         float fac[5];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            limtab[c * BM + r] = __int_as_float(0x7f800000);
-            fac[c] = a.w.mode == NHQ_W_CONSTANT
-                         ? a.w.wl * (float)c
-                         : (float)a.w.m / (float)(a.w.m + c);
-        }
+        for (int c = 0; c < 5; ++c)
+            fac[c] = a.w.mode == NHQ_W_CONSTANT ? a.w.wl * (float)c
+                                                : (float)a.w.m / (float)(a.w.m + c);
         const float inv_wv = a.w.wv > 0.f ? 1.f / a.w.wv : 0.f;
         auto update_lim = [&]() {
             thr = hp[1];
@@ -328,52 +492,60 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 limtab[cc * BM + r] = tt < 0.f ? -1.f : tt * tt;
             }
         };
-        const uint32_t lane_base = (uint32_t)((warp - 4) * 32) << 16;
+        const uint32_t lane_base = (uint32_t)(ew * 32) << 16;
         const float *lt = limtab + r;
-        // column metadata of the next tile, loaded one tile ahead
-        float pn = 0.f;
-        uint32_t pa = 0u, pi = 0u;
-        {
-            const int64_t cme = (int64_t)tile_at(0) * BN + r;
-            if (cme < a.N) {
-                pn = a.norms[cme];
-                pa = a.attr[cme];
-                pi = a.perm[cme];
-            }
-        }
         bool ok = true;
-        for (int i = 0; i < ntiles && ok; ++i) {
-            const int t = tile_at(i);
-            const int b = i & 1;
-            const uint32_t tph = (uint32_t)(i >> 1) & 1u;
-            colnorm[b * BN + r] = pn;
-            colattr[b * BN + r] = pa;
-            colid[b * BN + r] = pi;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (i + 1 < ntiles) {
-                const int64_t cme = (int64_t)tile_at(i + 1) * BN + r;
-                const bool in = cme < a.N;
-                pn = in ? a.norms[cme] : 0.f;
-                pa = in ? a.attr[cme] : 0u;
-                pi = in ? a.perm[cme] : 0u;
-            }
-            // one tuple in the whole tile (sorted order: first == last)
-            const uint32_t ta = colattr[b * BN];
-            const bool uni = (int64_t)(t + 1) * BN <= a.N && ta == colattr[b * BN + BN - 1];
-            const int ch_t = chi_bytes(au, ta, a.w.mask);
-            if (!ok)
-                continue;
-            ok = mbar_wait(bar(TFULL0 + b), tph, a.err, 5);
-            __syncwarp();  // tcgen05.ld below needs the whole warp converged
+        int p = 0;
+        for (int i = 0;; ++i) {
+            i = next_kept(decided, skipbits, i, ntiles, a.err, 8);
+            ok = i >= 0;
             if (!__all_sync(0xFFFFFFFFu, ok)) {
                 ok = false;
-                continue;
+                break;
+            }
+            i = __shfl_sync(0xFFFFFFFFu, i, 0);  // every lane saw the same published bits
+            if (i >= ntiles)
+                break;
+            const int t = tile_at(i);
+            const int b = p & 1;
+            const uint32_t tph = (uint32_t)(p >> 1) & 1u;
+            ++p;
+            const int64_t cbase = (int64_t)t * BN;
+            // the tile's column metadata: loads issued before the accumulator wait,
+            // stored to this warp's copy after it
+            float rn[4];
+            uint32_t rat[4], rid[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t col = cbase + lane + 32 * k;
+                const bool in = col < a.N;
+                rn[k] = in ? __ldg(a.norms + col) : 0.f;
+                rat[k] = in ? __ldg(a.attr + col) : 0u;
+                rid[k] = in ? __ldg(a.perm + col) : 0u;
+            }
+            ok = mbar_wait(bar(TFULL0 + b), tph, a.err, 5);
+            __syncwarp();  // every lane is done with the previous tile's metadata
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                mnorm[lane + 32 * k] = rn[k];
+                mattr[lane + 32 * k] = rat[k];
+                mid[lane + 32 * k] = rid[k];
+            }
+            __syncwarp();  // metadata visible; tcgen05.ld below needs the warp converged
+            if (!__all_sync(0xFFFFFFFFu, ok)) {
+                ok = false;
+                break;
             }
             tc_fence_after();
+            const int nvalid = a.N - cbase < BN ? (int)(a.N - cbase) : BN;
+            const uint32_t tf = mattr[0], tl = mattr[nvalid - 1];
+            const bool uni = tf == tl;  // one tuple in the whole tile (sorted order)
+            const int ch_t = chi_bytes(au, tf, a.w.mask);
+            const int ch_min = (au >= tf && au <= tl) ? 0 : (uni ? ch_t : 1);
             for (int c0 = 0; c0 < BN; c0 += 32) {
-                // the bounds only tighten: a row whose bound for this tile's chi is
-                // negative rejects every column of the tile
-                const bool dead = !row_ok || (uni && lt[ch_t * BM] < 0.f);
+                // the bounds only tighten: a row whose bound for the smallest chi of
+                // this tile is negative rejects every column of it
+                const bool dead = !row_ok || lt[ch_min * BM] < 0.f;
                 if (__all_sync(0xFFFFFFFFu, dead))
                     break;
                 uint32_t v[32];
@@ -384,9 +556,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 // store: a pass mask of the columns within the bound of their chi,
                 // then the passing columns are appended to the stage
                 uint32_t pass = 0;
-                const float4 *cn4 = reinterpret_cast<const float4 *>(colnorm + b * BN + c0);
+                const float4 *cn4 = reinterpret_cast<const float4 *>(mnorm + c0);
                 if (uni) {
-                    const float L = lt[ch_t * BM];
+                    const float Lb = lt[ch_t * BM];
 #pragma unroll
                     for (int j4 = 0; j4 < 8; ++j4) {
                         const float4 n4 = cn4[j4];
@@ -397,11 +569,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             const float d2 =
                                 fmaxf((nu + nc[q]) - 2.f * __uint_as_float(v[j]), 0.f);
                             v[j] = __float_as_uint(d2);
-                            pass |= (d2 <= L ? 1u : 0u) << j;
+                            pass |= (d2 <= Lb ? 1u : 0u) << j;
                         }
                     }
                 } else {
-                    const uint4 *ca4 = reinterpret_cast<const uint4 *>(colattr + b * BN + c0);
+                    const uint4 *ca4 = reinterpret_cast<const uint4 *>(mattr + c0);
 #pragma unroll
                     for (int j4 = 0; j4 < 8; ++j4) {
                         const float4 n4 = cn4[j4];
@@ -429,13 +601,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int s2 = 0; s2 < ns; ++s2) {
                     const uint2 e = stg[s2];
                     const int c = (int)e.y;
-                    const int64_t col = (int64_t)t * BN + c;
+                    const int64_t col = cbase + c;
                     if (col >= a.N || col == u)
                         continue;
-                    const int ch = chi_bytes(au, colattr[b * BN + c], a.w.mask);
+                    const int ch = chi_bytes(au, mattr[c], a.w.mask);
                     const float g = fusion_gamma(__fsqrt_rn(__uint_as_float(e.x)), ch, a.w);
                     const unsigned long long key =
-                        ((unsigned long long)__float_as_uint(g) << 32) | colid[b * BN + c];
+                        ((unsigned long long)__float_as_uint(g) << 32) | mid[c];
                     if (key >= thr)
                         continue;
                     if (cnt < K) {  // filling: unordered, heapified once full
@@ -517,12 +689,7 @@ __global__ void bf16_rows_norms_kernel(const float *__restrict__ X, int xstride,
         norms[r] = acc;
 }
 
-size_t tc_smem_bytes() {
-    return 1024 + STAGES * STAGE_BYTES + sizeof(unsigned long long) * BM * LSTRIDE +
-           (sizeof(float) + 2 * sizeof(uint32_t)) * 2 * BN + sizeof(float) * 5 * BM +
-           sizeof(uint2) * BM * 33 +
-           sizeof(unsigned long long) * 16 + 64;
-}
+size_t tc_smem_bytes(int ntiles) { return 1024 + tc_smem_layout(ntiles).total; }
 
 }  // namespace
 
@@ -573,12 +740,21 @@ cudaError_t launch_knn_tc(const __nv_bfloat16 *Xk, int kpad, const float *norms,
     a.ids = ids;
     a.dists = dists;
     a.err = err;
-    const size_t smem = tc_smem_bytes();
-    cudaError_t e =
+    const int ntiles = (int)((N + BN - 1) / BN);
+    const size_t smem = tc_smem_bytes(ntiles);
+    int dev = 0, smax = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess)
+        return e;
+    if (smem > (size_t)smax)  // one skip bit per tile: N up to about 2.3e7
+        return cudaErrorInvalidValue;
+    e =
         cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    knn_tc_kernel<<<(unsigned)((N + BM - 1) / BM), NTHREADS, smem, s>>>(tmap, a);
+    knn_tc_kernel<<<(unsigned)ntiles, NTHREADS, smem, s>>>(tmap, a);
     return cudaGetLastError();
 }
 

@@ -460,7 +460,7 @@ def test_search_rerank_on_float_data(nhq):
 
 # ------------------------------------------------------------------ tensor-core candidates
 @pytest.mark.parametrize("weights", [None, CONST])
-@pytest.mark.parametrize("N,d", [(2500, 32), (2500, 128), (300, 64)])
+@pytest.mark.parametrize("N,d", [(2500, 32), (2500, 128), (300, 64), (1500, 200)])
 def test_knn_tensor_cores_exact_on_integer_data(nhq, weights, N, d):
     w = synth.int_valued(N, 1, d, seed=60 + d)
     ref, ref_g = O.knn(w.X, w.A, 64, weights=weights, prec=O.F32)
