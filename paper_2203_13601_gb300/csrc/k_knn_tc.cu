@@ -332,19 +332,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         };
         uint32_t cf, cl, nf, nl;
+        int gcur = 0;  // group of 32 tiles whose codes are in cf, cl
         codes(0, cf, cl);
         codes(32, nf, nl);
-        uint32_t wbits = 0u;        // skip bits of the current word, published by lane 0
+        uint32_t wbits = 0u;       // skip bits of the current word, published by lane 0
         uint32_t dead_tuple = 0u;  // a tuple whose tiles were found dead (stays dead)
         bool have_dead = false;
-        for (int i = 0; i < ntiles && ok; ++i) {
-            if ((i & 31) == 0 && i > 0) {
+        int i = 0;
+        while (i < ntiles && ok) {
+            if ((i >> 5) != gcur) {
                 cf = nf;
                 cl = nl;
-                codes(i + 32, nf, nl);
+                ++gcur;
+                codes((gcur + 1) * 32, nf, nl);
             }
-            const uint32_t tf = __shfl_sync(0xFFFFFFFFu, cf, i & 31);
-            const uint32_t tl = __shfl_sync(0xFFFFFFFFu, cl, i & 31);
+            const int j = i & 31;
+            const uint32_t tf = __shfl_sync(0xFFFFFFFFu, cf, j);
+            const uint32_t tl = __shfl_sync(0xFFFFFFFFu, cl, j);
             bool need = true;
             if (skip_on) {
                 if (have_dead && tf == tl && tf == dead_tuple) {
@@ -372,17 +376,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
             }
-            if (!need)
-                wbits |= 1u << (i & 31);
+            int step = 1;
+            if (!need) {
+                // the following tiles of this group with the same first and last word
+                // are rejected by the same bounds
+                const uint32_t same =
+                    __ballot_sync(0xFFFFFFFFu, gcur * 32 + lane < ntiles && cf == tf && cl == tl) >>
+                    j;
+                step = (~same == 0u) ? 32 - j : __ffs((int)~same) - 1;
+                wbits |= (step == 32 ? 0xFFFFFFFFu : ((1u << step) - 1u)) << j;
+            }
+            const int inext = i + step;
             // publish before loading (the consumers need the decision first) and at the
             // end of every word
-            if (lane == 0 && (need || (i & 31) == 31 || i + 1 == ntiles)) {
+            const bool word_end = (inext & 31) == 0 || inext >= ntiles;
+            if (lane == 0 && (need || word_end)) {
                 skipbits[i >> 5] = wbits;
                 __threadfence_block();
-                *reinterpret_cast<volatile int *>(decided) = i + 1;
+                *reinterpret_cast<volatile int *>(decided) = need ? i + 1 : inext;
             }
-            if ((i & 31) == 31)
-                wbits = 0u;
             if (need && lane == 0) {
                 const int t = tile_at(i);
                 for (int kb = 0; kb < kb_n && ok; ++kb) {
@@ -400,7 +412,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
             }
+            if (word_end)
+                wbits = 0u;
             ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+            i = inext;
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
