@@ -2,12 +2,16 @@
 // and the reverse-candidate lists of the optional second selection pass.
 //
 // Edge selection: one CTA (4 warps) per vertex u.  The candidate rows (and u's)
-// are staged in shared memory when they fit, so every later distance reads
-// on-chip memory.  Gamma(p, u) of all candidates is computed by 16 teams of 8
-// lanes, the records (Gamma, p) are bitonic-sorted, and the selection walks
-// them in order: candidate p joins N(u) iff for every accepted j
-//     Gamma(p, u) < Gamma(p, j)   and   Gamma(p, u) > Gamma(u, j),
-// the 16 teams testing 16 accepted neighbours per pass (a CTA-wide vote).
+// are copied into shared memory with cp.async when they fit, so every later
+// distance reads on-chip memory.  Gamma(p, u) of all candidates is computed by 16
+// teams of 8 lanes and the records (Gamma(p, u), p) are bitonic-sorted.  Def. 6
+// admits p iff for every neighbour j accepted before it
+//     Gamma(p, u) < Gamma(p, j)   and   Gamma(p, u) > Gamma(u, j).
+// The walk applies it the other way round: when j is accepted, the teams test every
+// later candidate that is still alive against j and reject those that fail, so the
+// next alive candidate in order is accepted without further tests.  That takes one
+// parallel round of distances per accepted neighbour instead of one test sequence
+// per candidate, and gives the same neighbours as testing candidate by candidate.
 #include <cub/cub.cuh>
 
 #include "nhq_internal.cuh"
@@ -53,137 +57,145 @@ __device__ __forceinline__ float team_dist2(const float *__restrict__ a,
     return acc;
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
 __global__ void __launch_bounds__(ES_THREADS) edge_select_kernel(EdgeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(smem);  // [kMaxCand]
-    uint32_t *cid = reinterpret_cast<uint32_t *>(keys + kMaxCand);           // [kMaxCand]
-    uint32_t *acc_id = cid + kMaxCand;                                       // [kMaxDegree]
-    int *acc_slot = reinterpret_cast<int *>(acc_id + kMaxDegree);            // [kMaxDegree]
-    float *acc_g = reinterpret_cast<float *>(acc_slot + kMaxDegree);         // [kMaxDegree]
-    int *misc = reinterpret_cast<int *>(acc_g + kMaxDegree);                 // [4]
-    float *rows = reinterpret_cast<float *>(misc + 4);                       // [(L+1)][rstride]
+    uint32_t *cid = reinterpret_cast<uint32_t *>(keys + kMaxCand);           // [kMaxCand] by slot
+    int *order = reinterpret_cast<int *>(cid + kMaxCand);                     // [kMaxCand] slot of rank
+    float *gpu = reinterpret_cast<float *>(order + kMaxCand);                 // [kMaxCand] by slot
+    uint32_t *acc_id = reinterpret_cast<uint32_t *>(gpu + kMaxCand);          // [kMaxDegree]
+    int *misc = reinterpret_cast<int *>(acc_id + kMaxDegree);                 // [4]
+    unsigned char *rej = reinterpret_cast<unsigned char *>(misc + 4);         // [kMaxCand] by rank
+    float *rows = reinterpret_cast<float *>(rej + kMaxCand);                  // [(L+1)][rstride]
 
-    const int tid = threadIdx.x, team = tid / TEAM, tl = tid % TEAM;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int team = tid / TEAM, tl = tid % TEAM;
     const int xs4 = a.xstride / 4;
     const int64_t u = blockIdx.x;
     const uint32_t au = a.attr[u];
 
-    // 1. candidate ids (invalid, self and out-of-range dropped; repeats later)
-    if (tid == 0)
-        misc[0] = 0;
-    __syncthreads();
-    for (int s = tid; s < a.L; s += ES_THREADS) {
-        uint32_t p = a.cand[u * a.L + s];
-        bool ok = p != kNone && (int64_t)p < a.N && (int64_t)p != u;
-        if (ok) {
-            int slot = atomicAdd(&misc[0], 1);
-            cid[slot] = p;
-        }
+    // 1. candidate ids (invalid, self and out-of-range dropped) in list order
+    {
+        const uint32_t p = tid < a.L ? a.cand[u * a.L + tid] : kNone;
+        const bool ok = p != kNone && (int64_t)p < a.N && (int64_t)p != u;
+        const unsigned bal = __ballot_sync(FULL, ok);
+        if (lane == 0)
+            misc[warp] = __popc(bal);
+        __syncthreads();
+        int pos = __popc(bal & ((1u << lane) - 1u));
+        for (int w = 0; w < warp; ++w)
+            pos += misc[w];
+        if (ok)
+            cid[pos] = p;
     }
+    int n = 0;
+    for (int w = 0; w < ES_THREADS / 32; ++w)
+        n += misc[w];
     __syncthreads();
-    const int n = misc[0];  // staging slots are in arrival order; results do not depend on it
 
-    const float *urow = a.X + u * a.xstride;
+    // 2. rows of the candidates (slots 0..n-1) and of u (slot n) into shared memory
     if (a.staged) {
-        float *dst = rows + (size_t)a.L * a.rstride;
-        for (int c = tid; c < xs4; c += ES_THREADS)
-            reinterpret_cast<float4 *>(dst)[c] = reinterpret_cast<const float4 *>(urow)[c];
-        urow = dst;
-        for (int idx = tid; idx < n * xs4; idx += ES_THREADS) {
-            int i = idx / xs4, c = idx % xs4;
-            reinterpret_cast<float4 *>(rows + (size_t)i * a.rstride)[c] =
-                reinterpret_cast<const float4 *>(a.X + (int64_t)cid[i] * a.xstride)[c];
+        const uint32_t rbase = (uint32_t)__cvta_generic_to_shared(rows);
+        for (int idx = tid; idx < (n + 1) * xs4; idx += ES_THREADS) {
+            const int r = idx / xs4, c = idx % xs4;
+            const int64_t src = r < n ? (int64_t)cid[r] : u;
+            cp_async16(rbase + (uint32_t)(r * a.rstride + 4 * c) * 4u,
+                       a.X + src * a.xstride + 4 * c);
         }
+        asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
     }
     auto row_of_slot = [&](int i) -> const float * {
-        return a.staged ? rows + (size_t)i * a.rstride : a.X + (int64_t)cid[i] * a.xstride;
+        if (a.staged)
+            return rows + (size_t)i * a.rstride;
+        return a.X + (i < n ? (int64_t)cid[i] : u) * a.xstride;
     };
 
-    // 2. Gamma(p, u) for every candidate; key = (Gamma, p) with the staging slot kept aside
+    // 3. Gamma(p, u) of every candidate; records (Gamma, p) with the slot kept in order[]
     for (int base = 0; base < n; base += TEAMS) {
-        int i = base + team;
-        int ii = i < n ? i : 0;
-        float dd = team_dist2(row_of_slot(ii), urow, xs4, tl);
+        const int i = base + team;
+        const float dd = team_dist2(row_of_slot(i < n ? i : 0), row_of_slot(n), xs4, tl);
         if (i < n && tl == 0) {
-            uint32_t p = cid[i];
-            float g = fusion_gamma(__fsqrt_rn(dd), chi_packed(a.attr[p], au, a.w.mask), a.w);
-            // high 32 bits Gamma, then id (32 bits) -> order by (Gamma, id); the slot is
-            // recovered after sorting by searching cid (ids are unique after dedup below)
+            const uint32_t p = cid[i];
+            const float g = fusion_gamma(__fsqrt_rn(dd), chi_packed(a.attr[p], au, a.w.mask), a.w);
+            gpu[i] = g;
             keys[i] = ((unsigned long long)__float_as_uint(g) << 32) | p;
+            order[i] = i;
         }
     }
-    __syncthreads();
-    for (int i = n + tid; i < kMaxCand; i += ES_THREADS)
+    int P = 2;
+    while (P < n)
+        P <<= 1;
+    for (int i = n + tid; i < P; i += ES_THREADS) {
         keys[i] = ~0ull;
+        order[i] = 0;
+    }
     __syncthreads();
 
-    // 3. bitonic sort of kMaxCand keys ascending
-    for (int size = 2; size <= kMaxCand; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = tid; i < kMaxCand / 2; i += ES_THREADS) {
-                int lo = 2 * stride * (i / stride) + (i % stride);
-                int hi = lo + stride;
-                bool up = ((lo & size) == 0);
-                unsigned long long x = keys[lo], y = keys[hi];
-                if ((x > y) == up) {
-                    keys[lo] = y;
-                    keys[hi] = x;
+    // 4. bitonic sort of the P records (warp 0), slots carried along
+    if (warp == 0) {
+        for (int size = 2; size <= P; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = lane; i < P / 2; i += 32) {
+                    const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const unsigned long long x = keys[lo], y = keys[hi];
+                    if ((x > y) == up) {
+                        keys[lo] = y;
+                        keys[hi] = x;
+                        const int o = order[lo];
+                        order[lo] = order[hi];
+                        order[hi] = o;
+                    }
                 }
+                __syncwarp();
             }
-            __syncthreads();
-        }
     }
+    __syncthreads();
+    for (int t = tid; t < n; t += ES_THREADS)  // a repeated candidate is considered once
+        rej[t] = t > 0 && keys[t] == keys[t - 1] ? 1 : 0;
+    __syncthreads();
 
-    // 4. sequential landing-zone selection
-    int deg = 0;
+    // 5. landing-zone walk (Def. 6)
+    int deg = 0, t = 0;
     const int R = a.R;
-    for (int t = 0; t < n && deg < R; ++t) {
-        unsigned long long kt = keys[t];
-        if (t > 0 && kt == keys[t - 1])
-            continue;  // repeated candidate
-        uint32_t p = (uint32_t)kt;
-        float gpu_ = __uint_as_float((uint32_t)(kt >> 32));
-        // staging slot of p
+    for (;;) {
+        while (t < n && rej[t])
+            ++t;
+        if (t >= n)
+            break;
+        const int sj = order[t];
+        const float gju = gpu[sj];
         if (tid == 0)
-            misc[1] = -1;
-        __syncthreads();
-        for (int i = tid; i < n; i += ES_THREADS)
-            if (cid[i] == p)
-                atomicMax(&misc[1], i);
-        __syncthreads();
-        int ps = misc[1];
-        bool ok = true;
-        if (deg > 0) {
-            const float *prow = row_of_slot(ps);
-            uint32_t ap = a.attr[p];
-            int fail = 0;
-            for (int base = 0; base < deg && !fail; base += TEAMS) {
-                int j = base + team;
-                int jj = j < deg ? j : 0;
-                float dd = team_dist2(prow, row_of_slot(acc_slot[jj]), xs4, tl);
-                bool bad = false;
-                if (j < deg) {
-                    float gpj = fusion_gamma(__fsqrt_rn(dd),
-                                             chi_packed(ap, a.attr[acc_id[j]], a.w.mask), a.w);
-                    bad = !(gpu_ < gpj && gpu_ > acc_g[j]);
-                }
-                fail = __syncthreads_or(bad ? 1 : 0);
+            acc_id[deg] = cid[sj];
+        if (++deg >= R)
+            break;
+        const float *jrow = row_of_slot(sj);
+        const uint32_t aj = a.attr[cid[sj]];
+        // every later live candidate is tested against j; whole warps run every round
+        for (int base = t + 1; base < n; base += TEAMS) {
+            const int q = base + team;
+            const bool live = q < n && !rej[q];
+            const int sq = order[live ? q : t];
+            const float dd = team_dist2(row_of_slot(sq), jrow, xs4, tl);
+            if (live && tl == 0) {
+                const float g =
+                    fusion_gamma(__fsqrt_rn(dd), chi_packed(a.attr[cid[sq]], aj, a.w.mask), a.w);
+                const float gq = gpu[sq];
+                if (!(gq < g && gq > gju))
+                    rej[q] = 1;
             }
-            ok = !fail;
         }
-        if (ok) {
-            if (tid == 0) {
-                acc_id[deg] = p;
-                acc_slot[deg] = ps;
-                acc_g[deg] = gpu_;
-            }
-            ++deg;
-            __syncthreads();
-        }
+        __syncthreads();
+        ++t;
     }
-    for (int s = tid; s < R; s += ES_THREADS)
-        a.out[u * R + s] = s < deg ? acc_id[s] : kNone;
+    __syncthreads();
+    for (int s2 = tid; s2 < R; s2 += ES_THREADS)
+        a.out[u * R + s2] = s2 < deg ? acc_id[s2] : kNone;
 }
 
 // ---------------------------------------------------------------- reverse pass
@@ -308,8 +320,9 @@ cudaError_t launch_edge_select(const nhq_index *ix, const uint32_t *cand, int L,
     a.R = R;
     a.out = out;
     a.rstride = ix->xstride + 4;
-    size_t fixed = sizeof(unsigned long long) * kMaxCand + sizeof(uint32_t) * kMaxCand +
-                   (sizeof(uint32_t) + sizeof(int) + sizeof(float)) * kMaxDegree + 4 * sizeof(int);
+    size_t fixed = sizeof(unsigned long long) * kMaxCand +
+                   (sizeof(uint32_t) + sizeof(int) + sizeof(float)) * kMaxCand +
+                   sizeof(uint32_t) * kMaxDegree + 4 * sizeof(int) + kMaxCand;
     fixed = (fixed + 15) & ~(size_t)15;
     size_t staged = sizeof(float) * (size_t)(L + 1) * a.rstride;
     a.staged = fixed + staged <= 100 * 1024 ? 1 : 0;
