@@ -21,8 +21,6 @@ namespace nhq {
 namespace {
 
 constexpr int ES_THREADS = 128;
-constexpr int TEAM = 8;
-constexpr int TEAMS = ES_THREADS / TEAM;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct EdgeArgs {
@@ -38,23 +36,44 @@ struct EdgeArgs {
     int rstride; // floats per staged row
 };
 
-// squared distance between two rows, one team of 8 lanes; result in every team lane
-__device__ __forceinline__ float team_dist2(const float *__restrict__ a,
-                                            const float *__restrict__ b, int xs4, int tl) {
+// squared distance between two rows, one team of T lanes (T = 4 or 8); result in
+// every lane of the team
+template <int T>
+__device__ __forceinline__ float team_dist2_t(const float *__restrict__ a,
+                                              const float *__restrict__ b, int xs4, int tl) {
     float acc = 0.f;
-    for (int c = tl; c < xs4; c += TEAM) {
-        float4 x = reinterpret_cast<const float4 *>(a)[c];
-        float4 y = reinterpret_cast<const float4 *>(b)[c];
+    for (int c = tl; c < xs4; c += T) {
+        const float4 x = reinterpret_cast<const float4 *>(a)[c];
+        const float4 y = reinterpret_cast<const float4 *>(b)[c];
         float t;
         t = x.x - y.x; acc = fmaf(t, t, acc);
         t = x.y - y.y; acc = fmaf(t, t, acc);
         t = x.z - y.z; acc = fmaf(t, t, acc);
         t = x.w - y.w; acc = fmaf(t, t, acc);
     }
-    acc += __shfl_xor_sync(FULL, acc, 1);
-    acc += __shfl_xor_sync(FULL, acc, 2);
-    acc += __shfl_xor_sync(FULL, acc, 4);
+#pragma unroll
+    for (int o = 1; o < T; o <<= 1)
+        acc += __shfl_xor_sync(FULL, acc, o);
     return acc;
+}
+
+// stable block-wide compaction (128 threads): the values of the flagged threads, in
+// thread order, into out[]; returns their count (every thread)
+__device__ __forceinline__ int block_compact(bool flag, int value, int *out, int *cnt, int lane,
+                                             int warp) {
+    const unsigned bal = __ballot_sync(FULL, flag);
+    if (lane == 0)
+        cnt[warp] = __popc(bal);
+    __syncthreads();
+    int pos = __popc(bal & ((1u << lane) - 1u)), total = 0;
+    for (int w = 0; w < 4; ++w) {
+        pos += w < warp ? cnt[w] : 0;
+        total += cnt[w];
+    }
+    if (flag)
+        out[pos] = value;
+    __syncthreads();
+    return total;
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
@@ -66,14 +85,18 @@ __global__ void __launch_bounds__(ES_THREADS) edge_select_kernel(EdgeArgs a) {
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(smem);  // [kMaxCand]
     uint32_t *cid = reinterpret_cast<uint32_t *>(keys + kMaxCand);           // [kMaxCand] by slot
     int *order = reinterpret_cast<int *>(cid + kMaxCand);                     // [kMaxCand] slot of rank
-    float *gpu = reinterpret_cast<float *>(order + kMaxCand);                 // [kMaxCand] by slot
+    int *listA = order + kMaxCand;                                            // [kMaxCand] live ranks
+    int *listB = listA + kMaxCand;                                            // [kMaxCand]
+    int *keep = listB + kMaxCand;                                             // [kMaxCand]
+    float *gpu = reinterpret_cast<float *>(keep + kMaxCand);                  // [kMaxCand] by slot
     uint32_t *acc_id = reinterpret_cast<uint32_t *>(gpu + kMaxCand);          // [kMaxDegree]
-    int *misc = reinterpret_cast<int *>(acc_id + kMaxDegree);                 // [4]
-    unsigned char *rej = reinterpret_cast<unsigned char *>(misc + 4);         // [kMaxCand] by rank
-    float *rows = reinterpret_cast<float *>(rej + kMaxCand);                  // [(L+1)][rstride]
+    uint32_t *sattr = acc_id + kMaxDegree;                                    // [kMaxCand] by slot
+    int *misc = reinterpret_cast<int *>(sattr + kMaxCand);                    // [4]
+    float *rows = reinterpret_cast<float *>(misc + 4);                        // [(L+1)][rstride]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int team = tid / TEAM, tl = tid % TEAM;
+    constexpr int T4 = 4, TEAMS4 = ES_THREADS / T4;  // teams of 4 lanes
+    const int team = tid / T4, tl = tid % T4;
     const int xs4 = a.xstride / 4;
     const int64_t u = blockIdx.x;
     const uint32_t au = a.attr[u];
@@ -89,8 +112,10 @@ __global__ void __launch_bounds__(ES_THREADS) edge_select_kernel(EdgeArgs a) {
         int pos = __popc(bal & ((1u << lane) - 1u));
         for (int w = 0; w < warp; ++w)
             pos += misc[w];
-        if (ok)
+        if (ok) {
             cid[pos] = p;
+            sattr[pos] = a.attr[p];
+        }
     }
     int n = 0;
     for (int w = 0; w < ES_THREADS / 32; ++w)
@@ -115,83 +140,71 @@ __global__ void __launch_bounds__(ES_THREADS) edge_select_kernel(EdgeArgs a) {
         return a.X + (i < n ? (int64_t)cid[i] : u) * a.xstride;
     };
 
-    // 3. Gamma(p, u) of every candidate; records (Gamma, p) with the slot kept in order[]
-    for (int base = 0; base < n; base += TEAMS) {
+    // 3. Gamma(p, u) of every candidate and its record (Gamma, p)
+    for (int base = 0; base < n; base += TEAMS4) {
         const int i = base + team;
-        const float dd = team_dist2(row_of_slot(i < n ? i : 0), row_of_slot(n), xs4, tl);
+        const float dd = team_dist2_t<T4>(row_of_slot(i < n ? i : 0), row_of_slot(n), xs4, tl);
         if (i < n && tl == 0) {
-            const uint32_t p = cid[i];
-            const float g = fusion_gamma(__fsqrt_rn(dd), chi_packed(a.attr[p], au, a.w.mask), a.w);
+            const float g = fusion_gamma(__fsqrt_rn(dd), chi_packed(sattr[i], au, a.w.mask), a.w);
             gpu[i] = g;
-            keys[i] = ((unsigned long long)__float_as_uint(g) << 32) | p;
-            order[i] = i;
+            keys[i] = ((unsigned long long)__float_as_uint(g) << 32) | cid[i];
         }
     }
-    int P = 2;
-    while (P < n)
-        P <<= 1;
-    for (int i = n + tid; i < P; i += ES_THREADS) {
-        keys[i] = ~0ull;
-        order[i] = 0;
-    }
     __syncthreads();
 
-    // 4. bitonic sort of the P records (warp 0), slots carried along
-    if (warp == 0) {
-        for (int size = 2; size <= P; size <<= 1)
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = lane; i < P / 2; i += 32) {
-                    const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
-                    const bool up = (lo & size) == 0;
-                    const unsigned long long x = keys[lo], y = keys[hi];
-                    if ((x > y) == up) {
-                        keys[lo] = y;
-                        keys[hi] = x;
-                        const int o = order[lo];
-                        order[lo] = order[hi];
-                        order[hi] = o;
-                    }
-                }
-                __syncwarp();
-            }
+    // 4. rank of every record by counting (equal records, i.e. a repeated candidate,
+    //    by slot; only the first of them is considered)
+    bool first = false;
+    if (tid < n) {
+        const unsigned long long ki = keys[tid];
+        int rk = 0;
+        bool dup = false;
+        for (int j = 0; j < n; ++j) {
+            const unsigned long long kj = keys[j];
+            const bool same_before = kj == ki && j < tid;
+            rk += (kj < ki || same_before) ? 1 : 0;
+            dup = dup || same_before;
+        }
+        order[rk] = tid;
+        keep[rk] = dup ? 0 : 1;
     }
     __syncthreads();
-    for (int t = tid; t < n; t += ES_THREADS)  // a repeated candidate is considered once
-        rej[t] = t > 0 && keys[t] == keys[t - 1] ? 1 : 0;
-    __syncthreads();
+    first = tid < n && keep[tid] != 0;
+    int na = block_compact(first, tid, listA, misc, lane, warp);  // live ranks, ascending
 
-    // 5. landing-zone walk (Def. 6)
-    int deg = 0, t = 0;
+    // 5. landing-zone walk (Def. 6): the first live record is accepted, the others are
+    //    tested against it and the survivors stay live, in order
+    int deg = 0;
     const int R = a.R;
-    for (;;) {
-        while (t < n && rej[t])
-            ++t;
-        if (t >= n)
-            break;
-        const int sj = order[t];
+    int *A = listA, *B = listB;
+    while (na > 0) {
+        const int sj = order[A[0]];
         const float gju = gpu[sj];
         if (tid == 0)
             acc_id[deg] = cid[sj];
         if (++deg >= R)
             break;
         const float *jrow = row_of_slot(sj);
-        const uint32_t aj = a.attr[cid[sj]];
-        // every later live candidate is tested against j; whole warps run every round
-        for (int base = t + 1; base < n; base += TEAMS) {
-            const int q = base + team;
-            const bool live = q < n && !rej[q];
-            const int sq = order[live ? q : t];
-            const float dd = team_dist2(row_of_slot(sq), jrow, xs4, tl);
+        const uint32_t aj = sattr[sj];
+        for (int base = 1; base < na; base += TEAMS4) {  // whole warps run every round
+            const int k = base + team;
+            const bool live = k < na;
+            const int sq = order[A[live ? k : 0]];
+            const float dd = team_dist2_t<T4>(row_of_slot(sq), jrow, xs4, tl);
             if (live && tl == 0) {
                 const float g =
-                    fusion_gamma(__fsqrt_rn(dd), chi_packed(a.attr[cid[sq]], aj, a.w.mask), a.w);
+                    fusion_gamma(__fsqrt_rn(dd), chi_packed(sattr[sq], aj, a.w.mask), a.w);
                 const float gq = gpu[sq];
-                if (!(gq < g && gq > gju))
-                    rej[q] = 1;
+                keep[k] = (gq < g && gq > gju) ? 1 : 0;
             }
         }
         __syncthreads();
-        ++t;
+        const int k = tid + 1;
+        const bool kept = k < na && keep[k] != 0;
+        na = block_compact(kept, kept ? A[k] : 0, B, misc, lane, warp);
+        int *tmp = A;
+        A = B;
+        B = tmp;
     }
     __syncthreads();
     for (int s2 = tid; s2 < R; s2 += ES_THREADS)
@@ -321,8 +334,8 @@ cudaError_t launch_edge_select(const nhq_index *ix, const uint32_t *cand, int L,
     a.out = out;
     a.rstride = ix->xstride + 4;
     size_t fixed = sizeof(unsigned long long) * kMaxCand +
-                   (sizeof(uint32_t) + sizeof(int) + sizeof(float)) * kMaxCand +
-                   sizeof(uint32_t) * kMaxDegree + 4 * sizeof(int) + kMaxCand;
+                   (sizeof(uint32_t) + 4 * sizeof(int) + sizeof(float)) * kMaxCand +
+                   sizeof(uint32_t) * (kMaxDegree + kMaxCand) + 4 * sizeof(int);
     fixed = (fixed + 15) & ~(size_t)15;
     size_t staged = sizeof(float) * (size_t)(L + 1) * a.rstride;
     a.staged = fixed + staged <= 100 * 1024 ? 1 : 0;
