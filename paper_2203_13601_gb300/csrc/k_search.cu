@@ -201,6 +201,17 @@ __device__ __forceinline__ void accum_chunk<__nv_fp8_e4m3>(float &acc, const QCh
         sq4(acc, q.v[i], f[2 * i].x, f[2 * i].y, f[2 * i + 1].x, f[2 * i + 1].y);
 }
 
+// Ask L2 for a candidate's whole row as soon as the candidate is known to be
+// evaluated: the passes of eval_dist2 below load 8 rows at a time, so without this
+// every pass after the first would wait for HBM again.
+template <typename VT>
+__device__ __forceinline__ void prefetch_row(const VT *X, int xstride, uint32_t v) {
+    const char *r = reinterpret_cast<const char *>(X + (int64_t)v * xstride);
+    const int bytes = xstride * (int)sizeof(VT);
+    for (int o = 0; o < bytes; o += 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(r + o));
+}
+
 // Squared distances of cnt candidates cid[0..cnt) into d2s[0..cnt).  Teams of 8
 // lanes, two rows per team per pass (8 rows in flight per warp).  CPL > 0: each
 // lane covers at most CPL chunks of a row (EXACT: exactly CPL, no bounds test);
@@ -528,6 +539,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
                 take = hash_insert(hash, a.hash_bits, v);  // false if an earlier round had it
             const unsigned kb = __ballot_sync(FULL, take);
             if (take) {
+                prefetch_row(Xs, a.xstride, v);
                 const int p = __popc(kb & lanemask_lt(lane));
                 cid[p] = v;
                 cchi[p] = chi_packed(a.attr[v], qa, amask);
@@ -557,6 +569,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
             const unsigned kb = __ballot_sync(FULL, keep);
             if (keep) {
                 hash_insert(hash, a.hash_bits, v);
+                prefetch_row(Xs, a.xstride, v);
                 const int p = __popc(kb & lanemask_lt(lane));
                 cid[p] = v;
                 cchi[p] = chi_packed(a.attr[v], qa, amask);
@@ -679,6 +692,10 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
                 if (TWO && nw1 && make_key(__fmul_rn(a.w.wl, (float)c1), v1) > worst)
                     nw1 = false;
             }
+            if (nw0)
+                prefetch_row(Xs, a.xstride, v0);
+            if (TWO && nw1)
+                prefetch_row(Xs, a.xstride, v1);
             const unsigned e0 = __ballot_sync(FULL, nw0);
             const unsigned e1 = TWO ? __ballot_sync(FULL, nw1) : 0u;
             if (nw0) {
