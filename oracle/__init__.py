@@ -82,9 +82,9 @@ def _L():
             lib.or_knn.argtypes = [P, P, i64, i32, i32, i32, i32, f64, f64, i32, P, i64, P, P]
             lib.or_edge_select.restype = None
             lib.or_edge_select.argtypes = [P, P, i64, i32, i32, P, i32, i32, i32, f64, f64, i32,
-                                           P, P]
+                                           P, i64, P, P]
             lib.or_reverse_candidates.restype = None
-            lib.or_reverse_candidates.argtypes = [P, i64, i32, i32, P]
+            lib.or_reverse_candidates.argtypes = [P, i64, i32, i32, P, i64, P]
             lib.or_graph_quality.restype = f64
             lib.or_graph_quality.argtypes = [P, i64, i32, P, i32]
             lib.or_search.restype = None
@@ -195,24 +195,37 @@ def knn(X, A, K, weights=None, prec=F64, rows=None):
     return ids, g
 
 
-def edge_select(X, A, cand, R, weights=None, prec=F64):
-    """Landing-zone edge selection over candidate lists cand [N,K] -> nbr [N,R] (-1 pad), deg [N]."""
+def edge_select(X, A, cand, R, weights=None, prec=F64, rows=None):
+    """Landing-zone edge selection over candidate lists cand [N,K] -> nbr [N,R] (-1 pad), deg [N].
+    With ``rows`` (vertex ids), cand holds one row per listed vertex and so do the outputs."""
     X, A, cand = _f32(X), _u8(A), _i64(cand)
-    N, K = cand.shape
-    nbr = np.empty((N, R), np.int64)
-    deg = np.empty(N, np.int32)
+    nr, K = cand.shape
+    if rows is None:
+        rp = None
+    else:
+        rows = _i64(rows)
+        assert rows.shape[0] == nr
+        rp = _p(rows)
+    nbr = np.empty((nr, R), np.int64)
+    deg = np.empty(nr, np.int32)
     mode, wv, wl = _mode(weights)
-    _L().or_edge_select(_p(X), _p(A), N, X.shape[1], A.shape[1], _p(cand), K, R, mode, wv, wl,
-                        prec, _p(nbr), _p(deg))
+    _L().or_edge_select(_p(X), _p(A), X.shape[0], X.shape[1], A.shape[1], _p(cand), K, R, mode,
+                        wv, wl, prec, rp, nr, _p(nbr), _p(deg))
     return nbr, deg
 
 
-def reverse_candidates(nbr, cap=64):
-    """Rows N(v) + up to ``cap`` smallest reverse sources {u : v in N(u)} -> [N, R+cap]."""
+def reverse_candidates(nbr, cap=64, rows=None):
+    """Rows N(v) + up to ``cap`` smallest reverse sources {u : v in N(u)} -> [N, R+cap]
+    (or one row per vertex listed in ``rows``)."""
     nbr = _i64(nbr)
     N, R = nbr.shape
-    out = np.empty((N, R + cap), np.int64)
-    _L().or_reverse_candidates(_p(nbr), N, R, cap, _p(out))
+    if rows is None:
+        rp, nr = None, N
+    else:
+        rows = _i64(rows)
+        rp, nr = _p(rows), rows.shape[0]
+    out = np.empty((nr, R + cap), np.int64)
+    _L().or_reverse_candidates(_p(nbr), N, R, cap, rp, nr, _p(out))
     return out
 
 

@@ -300,18 +300,21 @@ void or_knn(const float *X, const uint8_t *A, int64_t N, int d, int m, int K,
 /*         Gamma(p, u) > Gamma(u, j)   (outside the ball)              */
 /*       until |N(u)| = R.  Unused slots get -1.                       */
 /* Gamma plays the role of delta for the composite index (Sec. 5.1).  */
+/* rows == NULL: every vertex u = 0..N-1 with cand row u (nrows = N); */
+/* otherwise vertex rows[r] with cand row r, output row r.            */
 /* ------------------------------------------------------------------ */
 void or_edge_select(const float *X, const uint8_t *A, int64_t N, int d, int m,
                     const int64_t *cand, int K, int R, int mode, double wv, double wl, int prec,
-                    int64_t *out_nbr, int32_t *out_deg)
+                    const int64_t *rows, int64_t nrows, int64_t *out_nbr, int32_t *out_deg)
 {
     rec_t *c = (rec_t *)malloc(sizeof(rec_t) * (size_t)(K > 0 ? K : 1));
-    for (int64_t u = 0; u < N; ++u) {
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t u = rows ? rows[r] : r;
         const float *xu = X + u * (int64_t)d;
         const uint8_t *au = A + u * (int64_t)m;
         int n = 0;
         for (int j = 0; j < K; ++j) {
-            int64_t p = cand[u * (int64_t)K + j];
+            int64_t p = cand[r * (int64_t)K + j];
             if (p < 0 || p >= N || p == u)
                 continue;
             int dup = 0;
@@ -326,7 +329,7 @@ void or_edge_select(const float *X, const uint8_t *A, int64_t N, int d, int m,
             ++n;
         }
         qsort(c, (size_t)n, sizeof(rec_t), rec_cmp);
-        int64_t *nb = out_nbr + u * (int64_t)R;
+        int64_t *nb = out_nbr + r * (int64_t)R;
         double *nbg = (double *)malloc(sizeof(double) * (size_t)(R > 0 ? R : 1));
         int deg = 0;
         for (int t = 0; t < n && deg < R; ++t) {
@@ -348,7 +351,7 @@ void or_edge_select(const float *X, const uint8_t *A, int64_t N, int d, int m,
         }
         for (int s = deg; s < R; ++s)
             nb[s] = -1;
-        out_deg[u] = deg;
+        out_deg[r] = deg;
         free(nbg);
     }
     free(c);
@@ -359,12 +362,15 @@ void or_edge_select(const float *X, const uint8_t *A, int64_t N, int d, int m,
  *   out[v] = N(v) (its selected neighbours, in slot order), followed by the
  *            sources u with v in N(u) that are not already in N(v), taking the
  *            `cap` smallest such ids in ascending order; -1 pads the row.
- * Row width is R + cap.  The second pass runs or_edge_select on these rows. */
-void or_reverse_candidates(const int64_t *nbr, int64_t N, int R, int cap, int64_t *out)
+ * Row width is R + cap.  The second pass runs or_edge_select on these rows.
+ * rows == NULL: every v = 0..N-1 (nrows = N); otherwise vertex rows[r] -> out row r. */
+void or_reverse_candidates(const int64_t *nbr, int64_t N, int R, int cap,
+                           const int64_t *rows, int64_t nrows, int64_t *out)
 {
     int W = R + cap;
-    for (int64_t v = 0; v < N; ++v) {
-        int64_t *row = out + v * (int64_t)W;
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t v = rows ? rows[r] : r;
+        int64_t *row = out + r * (int64_t)W;
         int n = 0;
         for (int s = 0; s < R; ++s)
             if (nbr[v * (int64_t)R + s] >= 0)
