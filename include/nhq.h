@@ -223,6 +223,27 @@ nhq_status nhq_brute_force(const nhq_index *index, const float *queries,
                            void *stream);
 
 /*
+ * Merge of per-shard top-k lists: the paper's parallel form (Sec. 6.1, the object set
+ * split into P shards with one graph each, every shard searched for every query, the
+ * results combined).  Shard p holds the objects with global ids offsets[p] + local
+ * id; its list for query q is row q of the p-th [Q][k_in] block, sorted by
+ * (Gamma, local id) as nhq_search and nhq_brute_force return it.  Output row q is
+ * the k_out smallest records of all P rows by (Gamma, global id), ids made global;
+ * shorter results are padded with 0xFFFFFFFF / +inf / chi 255.
+ *   ids[P][Q][k_in] u32 (0xFFFFFFFF = none), dists[P][Q][k_in] f32,
+ *   chi[P][Q][k_in] u8 (may be NULL; then out_chi must be NULL), offsets[P] u32.
+ *   out_ids[Q][k_out] u32, out_dists[Q][k_out] f32, out_chi[Q][k_out] u8 (or NULL).
+ * Pointers may be device or host memory (host arrays are staged; the call then
+ * synchronises).  Errors: P outside 1..4096, k_in or k_out outside 1..1024, Q < 0,
+ * a global id that does not fit in 32 bits is not detected (the caller's offsets
+ * must keep offsets[p] + local id below 0xFFFFFFFF).
+ */
+nhq_status nhq_merge_topk(int32_t P, int64_t Q, int32_t k_in, int32_t k_out,
+                          const uint32_t *ids, const float *dists, const uint8_t *chi,
+                          const uint32_t *offsets, uint32_t *out_ids, float *out_dists,
+                          uint8_t *out_chi, void *stream);
+
+/*
  * search(queries, query_attributes, k, ef): joint pruning (Alg. 2) on the
  * composite index, ef-bounded, with the two-stage routing of Sec. 4.2 / 5.2
  * when params->h > 1.  Per query: a pool of ef records sorted by (Gamma, id);

@@ -30,6 +30,7 @@ __all__ = [
     "nhq_brute_force_noalloc", "nhq_search_trace", "nhq_mlp_forward", "nhq_mlp_grad",
     "nhq_mlp_train", "MLP_INPUTS", "MLP_HIDDEN", "MLP_PARAMS", "nhq_autotune_search",
     "nhq_search_graph_create", "nhq_search_graph_launch", "nhq_search_graph_free",
+    "nhq_merge_topk",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -105,6 +106,7 @@ def load_library():
             "nhq_build": (S, [P, i64, i32, P, i32, i32, _Weights, C.POINTER(_BuildParams), P,
                               C.POINTER(P)]),
             "nhq_brute_force": (S, [P, P, P, i64, i32, C.POINTER(_Weights), P, P, P, P]),
+            "nhq_merge_topk": (S, [i32, i64, i32, i32, P, P, P, P, P, P, P, P]),
             "nhq_search": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P, P, P, P, P,
                                P, P]),
             "nhq_search_batched": (S, [P, P, P, i64, P, P, i32, C.POINTER(_SearchParams), P, P, P,
@@ -293,6 +295,19 @@ def nhq_build(vectors, attributes, degree, weights=None, K=64, reverse=1, revers
                                      _weights(weights), C.byref(p), _stream(stream),
                                      C.byref(out)))
     return out.value
+
+
+def nhq_merge_topk(ids, dists, offsets, k_out, out_ids, out_dists, chi=None, out_chi=None,
+                   stream=None) -> None:
+    """Merge per-shard top-k lists ids/dists [P, Q, k_in] (shard-local ids, global id =
+    offsets[p] + local) into out_ids/out_dists [Q, k_out] by (Gamma, global id)."""
+    P, Q, k_in = _shape(ids)
+    _check(load_library().nhq_merge_topk(
+        P, Q, k_in, k_out, _ptr(ids, np.uint32, (P, Q, k_in), "ids"),
+        _ptr(dists, np.float32, (P, Q, k_in), "dists"), _ptr(chi, np.uint8, (P, Q, k_in), "chi"),
+        _ptr(offsets, np.uint32, (P,), "offsets"), _ptr(out_ids, np.uint32, (Q, k_out), "out_ids"),
+        _ptr(out_dists, np.float32, (Q, k_out), "out_dists"),
+        _ptr(out_chi, np.uint8, (Q, k_out), "out_chi"), _stream(stream)))
 
 
 def nhq_brute_force(index, queries, query_attributes, k, ids, dists=None, chi=None,

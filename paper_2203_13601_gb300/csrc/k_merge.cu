@@ -1,0 +1,137 @@
+// k_merge.cu -- merge of per-shard top-k lists (the paper's parallel form: the
+// object set split into shards with one graph each, every shard searched for
+// every query, the lists combined by (Gamma, id)).
+//
+// One warp per query.  Every shard's list is already sorted by (Gamma, local id),
+// and adding the shard's offset keeps that order, so the merge only compares the
+// heads: lane l owns the heads of shards l, l + 32, ...; each round the warp takes
+// the smallest head key (Gamma bits << 32 | global id) and its owner advances.
+#include "nhq_internal.cuh"
+
+namespace nhq {
+
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+struct MergeArgs {
+    int P, k_in, k_out;
+    int64_t Q;
+    const uint32_t *ids;
+    const float *dists;
+    const uint8_t *chi;
+    const uint32_t *offsets;
+    uint32_t *out_ids;
+    float *out_dists;
+    uint8_t *out_chi;
+};
+
+__device__ __forceinline__ unsigned long long head_key(const MergeArgs &a, int p, int64_t q,
+                                                       int h) {
+    if (h >= a.k_in)
+        return ~0ull;
+    const int64_t o = ((int64_t)p * a.Q + q) * a.k_in + h;
+    const uint32_t id = a.ids[o];
+    if (id == kNone)
+        return ~0ull;  // the rest of the row is padding
+    return ((unsigned long long)__float_as_uint(a.dists[o]) << 32) | (uint32_t)(a.offsets[p] + id);
+}
+
+__global__ void merge_topk_kernel(MergeArgs a, int heads_per_lane) {
+    extern __shared__ int head_pos[];  // [warps per block][32 * heads_per_lane]
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (q >= a.Q)
+        return;
+    int *pos = head_pos + wib * 32 * heads_per_lane;
+    // best head of this lane's shards, kept with its shard index
+    unsigned long long best = ~0ull;
+    int best_p = -1;
+    for (int i = 0; i < heads_per_lane; ++i) {
+        const int p = lane + 32 * i;
+        pos[lane * heads_per_lane + i] = 0;
+        if (p < a.P) {
+            const unsigned long long kk = head_key(a, p, q, 0);
+            if (kk < best) {
+                best = kk;
+                best_p = p;
+            }
+        }
+    }
+    for (int r = 0; r < a.k_out; ++r) {
+        unsigned long long m = best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(FULL, m, o);
+            m = other < m ? other : m;
+        }
+        const int64_t out = q * a.k_out + r;
+        if (m == ~0ull) {  // every shard is exhausted
+            if (lane == 0) {
+                a.out_ids[out] = kNone;
+                a.out_dists[out] = __int_as_float(0x7f800000);
+                if (a.out_chi)
+                    a.out_chi[out] = 255;
+            }
+            continue;
+        }
+        // keys are unique (global ids differ), so exactly one lane owns the minimum
+        if (best == m) {
+            const int p = best_p;
+            const int slot = lane * heads_per_lane + p / 32;
+            const int h = pos[slot];
+            const int64_t o = ((int64_t)p * a.Q + q) * a.k_in + h;
+            a.out_ids[out] = (uint32_t)m;
+            a.out_dists[out] = __uint_as_float((uint32_t)(m >> 32));
+            if (a.out_chi)
+                a.out_chi[out] = a.chi[o];
+            pos[slot] = h + 1;
+            best = ~0ull;
+            best_p = -1;
+            for (int i = 0; i < heads_per_lane; ++i) {
+                const int pp = lane + 32 * i;
+                if (pp < a.P) {
+                    const unsigned long long kk = head_key(a, pp, q, pos[lane * heads_per_lane + i]);
+                    if (kk < best) {
+                        best = kk;
+                        best_p = pp;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_merge_topk(int P, int64_t Q, int k_in, int k_out, const uint32_t *ids,
+                              const float *dists, const uint8_t *chi, const uint32_t *offsets,
+                              uint32_t *out_ids, float *out_dists, uint8_t *out_chi,
+                              cudaStream_t s) {
+    if (Q <= 0)
+        return cudaSuccess;
+    MergeArgs a;
+    a.P = P;
+    a.k_in = k_in;
+    a.k_out = k_out;
+    a.Q = Q;
+    a.ids = ids;
+    a.dists = dists;
+    a.chi = chi;
+    a.offsets = offsets;
+    a.out_ids = out_ids;
+    a.out_dists = out_dists;
+    a.out_chi = out_chi;
+    const int hpl = (P + 31) / 32;
+    const int wpb = 4;
+    const size_t smem = sizeof(int) * 32 * hpl * wpb;
+    cudaError_t e = cudaFuncSetAttribute(merge_topk_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    merge_topk_kernel<<<(unsigned)((Q + wpb - 1) / wpb), 32 * wpb, smem, s>>>(a, hpl);
+    return cudaGetLastError();
+}
+
+}  // namespace nhq

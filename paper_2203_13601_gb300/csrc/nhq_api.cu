@@ -565,6 +565,41 @@ nhq_status nhq_brute_force(const nhq_index *cix, const float *queries,
     return st.finish(s);
 }
 
+nhq_status nhq_merge_topk(int32_t P, int64_t Q, int32_t k_in, int32_t k_out,
+                          const uint32_t *ids, const float *dists, const uint8_t *chi,
+                          const uint32_t *offsets, uint32_t *out_ids, float *out_dists,
+                          uint8_t *out_chi, void *stream) {
+    if (P < 1 || P > 4096)
+        return fail(NHQ_ERR_ARG, "P must be in 1..4096 (got %d)", P);
+    if (k_in < 1 || k_in > 1024 || k_out < 1 || k_out > 1024)
+        return fail(NHQ_ERR_ARG, "k_in and k_out must be in 1..1024");
+    if (Q < 0)
+        return fail(NHQ_ERR_ARG, "Q must be >= 0");
+    if (Q == 0)
+        return NHQ_OK;
+    if (ids == nullptr || dists == nullptr || offsets == nullptr || out_ids == nullptr ||
+        out_dists == nullptr)
+        return fail(NHQ_ERR_ARG, "ids, dists, offsets, out_ids and out_dists are required");
+    if (out_chi != nullptr && chi == nullptr)
+        return fail(NHQ_ERR_ARG, "out_chi needs the shards' chi");
+    cudaStream_t s = as_stream(stream);
+    const size_t in_n = (size_t)P * (size_t)Q * (size_t)k_in, out_n = (size_t)Q * (size_t)k_out;
+    Stager st;
+    int ii = st.add(ids, sizeof(uint32_t) * in_n, true);
+    int idd = st.add(dists, sizeof(float) * in_n, true);
+    int ic = st.add(out_chi ? chi : nullptr, in_n, true);
+    int io = st.add(offsets, sizeof(uint32_t) * (size_t)P, true);
+    int oi = st.add(out_ids, sizeof(uint32_t) * out_n, false);
+    int od = st.add(out_dists, sizeof(float) * out_n, false);
+    int oc = st.add(out_chi, out_n, false);
+    CKS(st.commit(&g_stage.p, &g_stage.cap, s));
+    CK(launch_merge_topk(P, Q, k_in, k_out, (const uint32_t *)st.dev(ii),
+                         (const float *)st.dev(idd), (const uint8_t *)st.dev(ic),
+                         (const uint32_t *)st.dev(io), (uint32_t *)st.dev(oi),
+                         (float *)st.dev(od), (uint8_t *)st.dev(oc), s));
+    return st.finish(s);
+}
+
 struct TraceOut {
     float *features = nullptr;
     uint8_t *labels = nullptr;

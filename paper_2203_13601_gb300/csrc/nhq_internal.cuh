@@ -238,6 +238,10 @@ cudaError_t mlp_train(float *params, const float *X, const float *y, int64_t n, 
 // Seeds of NHQ_SEED_ATTRIBUTE into seeds[nq][32] (rows padded with kNone).
 cudaError_t launch_attribute_seeds(const SearchArgs &a, const uint32_t *attr_sorted,
                                    const uint32_t *id_sorted, uint32_t *seeds, cudaStream_t s);
+cudaError_t launch_merge_topk(int P, int64_t Q, int k_in, int k_out, const uint32_t *ids,
+                              const float *dists, const uint8_t *chi, const uint32_t *offsets,
+                              uint32_t *out_ids, float *out_dists, uint8_t *out_chi,
+                              cudaStream_t s);
 cudaError_t launch_search(SearchArgs a, void *scratch, int sm_count, size_t smem_optin,
                           cudaStream_t s);
 

@@ -83,6 +83,14 @@ def test_argument_errors_before_cuda(lib):
     assert lib.nhq_index_build(None, 32, None, None) == nhq.ERR_ARG
     assert lib.nhq_save(None, b"/tmp/x") == nhq.ERR_ARG
     lib.nhq_free(None)  # no-op
+    # shard merge: counts checked before any CUDA work
+    assert lib.nhq_merge_topk(0, 1, 1, 1, None, None, None, None, None, None, None,
+                              None) == nhq.ERR_ARG
+    assert "P must be" in nhq.nhq_last_error()
+    assert lib.nhq_merge_topk(2, 1, 0, 1, None, None, None, None, None, None, None,
+                              None) == nhq.ERR_ARG
+    assert lib.nhq_merge_topk(2, 1, 4, 4, None, None, None, None, None, None, None,
+                              None) == nhq.ERR_ARG
 
 
 def test_load_rejects_missing_and_corrupt_files(lib, tmp_path):
