@@ -530,7 +530,7 @@ def main():
                      "mean_expansions": float(exp_h.mean())},
         "e2e": {"value": w.nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "recall": e2e_rec},
-        "gpu_launches": a.steps * (2 if a.seed_mode == 1 else 1),
+        "gpu_launches": a.steps * (3 if a.seed_mode == 1 else 1),
         "clocks": clk,
     }
     if rank == 0 and not a.no_cpu_baseline:

@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
         qq = __shfl_sync(FULL, qq, 0);
         if (qq >= (unsigned long long)a.nq)
             break;
-        const int64_t q = (int64_t)qq;
+        const int64_t q = a.order ? (int64_t)a.order[qq] : (int64_t)qq;
         const int k = a.k_arr ? a.k_arr[q] : a.k;
         const int ef = a.ef_arr ? a.ef_arr[q] : a.ef;
 
@@ -888,7 +888,10 @@ cudaError_t launch_dtype(const SearchArgs &a, const VT *X, int ef_cap, int wpb, 
 
 }  // namespace
 
-size_t search_scratch_bytes(int64_t nq) { return 256 + sizeof(uint32_t) * 32 * (size_t)nq; }
+// work counter | seeds [nq][32] u32 | order [nq] u32 | buckets [nq] u8
+size_t search_scratch_bytes(int64_t nq) {
+    return 256 + sizeof(uint32_t) * 33 * (size_t)nq + (size_t)nq + 256;
+}
 
 cudaError_t launch_search(SearchArgs a, void *scratch, int sm_count, size_t smem_optin,
                           cudaStream_t s) {

@@ -7,6 +7,13 @@
 // S = min(ef, 32, |P|) of them evenly spaced: P[floor(j * |P| / S)], j < S.
 // A query whose tuple does not occur falls back to the random stream of
 // NHQ_SEED_RANDOM (first min(ef, 32) distinct ids of <= 64 splitmix64 draws).
+//
+// The same pass sorts the queries into cost buckets, 31 - bit length of (|P| + 1):
+// under constant weights a query whose tuple is frequent expands more records (its
+// pool fills with matching objects and keeps improving), so the search takes the
+// queries with the largest |P| first and the batch does not end on a few long ones
+// started last.  The order decides only which warp takes a query when; every
+// query's result is the same.
 #include <cub/cub.cuh>
 
 #include "nhq_internal.cuh"
@@ -35,7 +42,8 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *a, int64_t n,
 
 __global__ void attribute_seeds_kernel(SearchArgs a, const uint32_t *__restrict__ attr_sorted,
                                        const uint32_t *__restrict__ id_sorted,
-                                       uint32_t *__restrict__ seeds) {
+                                       uint32_t *__restrict__ seeds,
+                                       uint8_t *__restrict__ bucket) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= a.nq)
         return;
@@ -47,6 +55,10 @@ __global__ void attribute_seeds_kernel(SearchArgs a, const uint32_t *__restrict_
     const int64_t lo = lower_bound_u32(attr_sorted, a.N, qa);
     const int64_t hi = qa == 0xFFFFFFFFu ? a.N : lower_bound_u32(attr_sorted, a.N, qa + 1u);
     const int64_t c = hi - lo;
+    if (bucket != nullptr) {
+        const int bits = 64 - __clzll((unsigned long long)c + 1ull);  // 1..
+        bucket[q] = (uint8_t)(bits >= 32 ? 0 : 32 - bits);
+    }
     uint32_t *row = seeds + q * 32;
     int j = 0;
     if (c > 0) {
@@ -66,6 +78,28 @@ __global__ void attribute_seeds_kernel(SearchArgs a, const uint32_t *__restrict_
     }
     for (; j < 32; ++j)
         row[j] = kNone;
+}
+
+// counting sort of the query indices by bucket, one block
+__global__ void query_order_kernel(const uint8_t *__restrict__ bucket, int64_t nq,
+                                   uint32_t *__restrict__ order) {
+    __shared__ unsigned int hist[32], base[32];
+    if (threadIdx.x < 32)
+        hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t q = threadIdx.x; q < nq; q += blockDim.x)
+        atomicAdd(&hist[bucket[q] & 31], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int sum = 0;
+        for (int b = 0; b < 32; ++b) {
+            base[b] = sum;
+            sum += hist[b];
+        }
+    }
+    __syncthreads();
+    for (int64_t q = threadIdx.x; q < nq; q += blockDim.x)
+        order[atomicAdd(&base[bucket[q] & 31], 1u)] = (uint32_t)q;
 }
 
 }  // namespace
@@ -101,11 +135,21 @@ cudaError_t launch_attribute_sort(const uint32_t *attr, int64_t N, uint32_t *att
 }
 
 cudaError_t launch_attribute_seeds(const SearchArgs &a, const uint32_t *attr_sorted,
-                                   const uint32_t *id_sorted, uint32_t *seeds, cudaStream_t s) {
+                                   const uint32_t *id_sorted, uint32_t *seeds, uint8_t *bucket,
+                                   cudaStream_t s) {
     if (a.nq <= 0)
         return cudaSuccess;
     attribute_seeds_kernel<<<(unsigned)((a.nq + 127) / 128), 128, 0, s>>>(a, attr_sorted,
-                                                                            id_sorted, seeds);
+                                                                            id_sorted, seeds,
+                                                                            bucket);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_query_order(const uint8_t *bucket, int64_t nq, uint32_t *order,
+                               cudaStream_t s) {
+    if (nq <= 0)
+        return cudaSuccess;
+    query_order_kernel<<<1, 1024, 0, s>>>(bucket, nq, order);
     return cudaGetLastError();
 }
 

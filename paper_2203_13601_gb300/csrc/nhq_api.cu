@@ -740,14 +740,19 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     }
     a.seeds = nullptr;
     a.n_seeds = 0;
+    a.order = nullptr;
     if (P.seed_mode == NHQ_SEED_GIVEN) {
         a.seeds = (const uint32_t *)st.dev(isd);
         a.n_seeds = P.n_seeds;
     } else if (P.seed_mode == NHQ_SEED_ATTRIBUTE) {
         uint32_t *sd = reinterpret_cast<uint32_t *>((char *)ix->scratch + 256);
-        CK(launch_attribute_seeds(a, ix->attr_sorted, ix->id_sorted, sd, s));
+        uint32_t *order = sd + (size_t)32 * Q;
+        uint8_t *bucket = reinterpret_cast<uint8_t *>(order + Q);
+        CK(launch_attribute_seeds(a, ix->attr_sorted, ix->id_sorted, sd, bucket, s));
+        CK(launch_query_order(bucket, Q, order, s));
         a.seeds = sd;
         a.n_seeds = 32;
+        a.order = order;
     }
     cudaError_t e = launch_search(a, ix->scratch, ix->sm_count, ix->smem_optin, s);
     if (e == cudaErrorInvalidValue)

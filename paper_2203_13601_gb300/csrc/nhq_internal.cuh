@@ -192,6 +192,7 @@ struct SearchArgs {
     int32_t *expansions;
     const uint32_t *seeds;  // [nq][n_seeds] given seed ids or null (random stream)
     int n_seeds;
+    const uint32_t *order;  // [nq] processing order of the queries, or null (index order)
     // learned early stop: fp16 weights (null = off), logit threshold, schedule
     const __half *stop_w16;
     float stop_logit;
@@ -237,7 +238,11 @@ cudaError_t mlp_train(float *params, const float *X, const float *y, int64_t n, 
 
 // Seeds of NHQ_SEED_ATTRIBUTE into seeds[nq][32] (rows padded with kNone).
 cudaError_t launch_attribute_seeds(const SearchArgs &a, const uint32_t *attr_sorted,
-                                   const uint32_t *id_sorted, uint32_t *seeds, cudaStream_t s);
+                                   const uint32_t *id_sorted, uint32_t *seeds, uint8_t *bucket,
+                                   cudaStream_t s);
+// order[0..nq) = the queries by ascending bucket (each bucket in any order)
+cudaError_t launch_query_order(const uint8_t *bucket, int64_t nq, uint32_t *order,
+                               cudaStream_t s);
 cudaError_t launch_merge_topk(int P, int64_t Q, int k_in, int k_out, const uint32_t *ids,
                               const float *dists, const uint8_t *chi, const uint32_t *offsets,
                               uint32_t *out_ids, float *out_dists, uint8_t *out_chi,
