@@ -834,8 +834,12 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
     }
 }
 
+// the smallest visited filter the rebuild rule allows (a rebuilt filter holds at most
+// ef ids and takes R more per expansion before it is half full again): at large ef the
+// filter is most of a warp's shared memory, and resident warps matter more than the
+// rarer rebuilds a larger filter would save
 int auto_hash_bits(int ef_cap, int R) {
-    int need = 4 * (ef_cap + R);
+    int need = 2 * (ef_cap + R) + 64;
     int bits = 10;  // 1024 slots: small enough for 32 resident warps per SM at small ef
     while ((1 << bits) < need)
         ++bits;
