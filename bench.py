@@ -65,10 +65,12 @@ def parse():
                     help="candidate build: 0 exact f32 SIMT, 1 bf16 tensor cores (exact here)")
     ap.add_argument("--learned-efs", default="16,24,32,48,64")
     ap.add_argument("--taus", default="0.7,0.8,0.9,0.95")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "strategies"],
                     help="c2: the headline workload (default); c4: the heterogeneous batch "
                          "(1M x 96, 100k queries with mixed k and ef) through "
-                         "nhq_search_batched, one JSON line of its own")
+                         "nhq_search_batched; strategies: NHQ against post-filtering on a "
+                         "plain L2 graph and exact pre-filtering, on the c2 workload; each "
+                         "prints one JSON line of its own")
     return ap.parse_args()
 
 
@@ -355,6 +357,170 @@ def c4_arm(a, rank, world, local):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- strategies
+def strategies_arm(a):
+    """The paper's comparison (Sec. 6.2) inside this framework, on one GPU and the c2
+    workload: NHQ (composite index, constant weights, attribute-entry seeds) against
+    B(1) post-filtering (a proximity graph on vector distance only, searched for k'
+    records with random seeds, then the matching ones kept) and B(2) pre-filtering
+    (exact top-k among the matching objects, the filter-mode brute force)."""
+    import torch
+
+    import paper_2203_13601_gb300 as nhq
+    from paper_2203_13601_gb300 import build as B
+
+    B.build()
+    nhq.load_library()
+    dev = torch.device("cuda", 0)
+    w = make_workload(a)
+    X, A = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.A).to(dev)
+    Qv, QA = torch.from_numpy(w.Qv).to(dev), torch.from_numpy(w.QA).to(dev)
+    k = a.k
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    t0 = time.perf_counter()
+    ix = nhq.Index.build(X, A, degree=a.R, weights=CONST_W, K=64, knn_dtype=1)
+    torch.cuda.synchronize()
+    t_nhq = time.perf_counter() - t0
+    gt = torch.empty((w.nq, k), dtype=torch.uint32, device=dev)
+    ms_pre = timed(lambda: nhq.nhq_brute_force(ix.handle, Qv, QA, k, gt, weights="filter"), 3)
+    gt_h = gt.cpu().numpy()
+    mult = np.array([1, 256, 65536])[: w.m]
+    codes, qcodes = (w.A.astype(np.int64) * mult).sum(1), (w.QA.astype(np.int64) * mult).sum(1)
+    uniq, cnt = np.unique(codes, return_counts=True)
+    pos = np.minimum(np.searchsorted(uniq, qcodes), len(uniq) - 1)
+    P = np.where(uniq[pos] == qcodes, cnt[pos], 0)
+
+    ids, dd, ch = (torch.empty((w.nq, k), dtype=torch.uint32, device=dev),
+                   torch.empty((w.nq, k), dtype=torch.float32, device=dev),
+                   torch.empty((w.nq, k), dtype=torch.uint8, device=dev))
+    nhq_rows = []
+    for ef in (16, 24, 32, 48):
+        run = lambda ef=ef: nhq.nhq_search(ix.handle, Qv, QA, k, ef, ids, dd, ch, seed=12345,
+                                           seed_mode=nhq.SEED_ATTRIBUTE)
+        ms = timed(run)
+        rec, _ = hybrid_recall(ids.cpu().numpy(), w.A, w.QA, gt_h, P, k)
+        nhq_rows.append({"ef": ef, "recall": rec, "ms": ms, "qps": w.nq / ms * 1e3})
+    ix.close()
+
+    t0 = time.perf_counter()
+    ixl = nhq.Index.build(X, A, degree=a.R, weights=(1.0, 0.0), K=64, knn_dtype=1)
+    torch.cuda.synchronize()
+    t_l2 = time.perf_counter() - t0
+    # entry points of the L2 search: the 32 nearest of a 4,096-object sample (the objects
+    # are in random order, so the first rows are a uniform sample); random seeds rarely
+    # reach the query's cluster on a graph of exact nearest neighbours
+    S = 4096
+    ixs = nhq.Index.create(X[:S].contiguous(), A[:S].contiguous(), (1.0, 0.0))
+    seeds = torch.empty((w.nq, 32), dtype=torch.uint32, device=dev)
+    post_rows = []
+    fi = torch.empty((w.nq, k), dtype=torch.uint32, device=dev)
+    fd = torch.empty((w.nq, k), dtype=torch.float32, device=dev)
+    for kp in (10, 32, 64, 128, 256):
+        exact = torch.empty((w.nq, kp), dtype=torch.uint32, device=dev)
+        nhq.nhq_brute_force(ixl.handle, Qv, QA, kp, exact)
+        ex_h = exact.cpu().numpy()
+        for ef in sorted({max(kp, 32), 2 * kp, 4 * kp}):
+            if ef > 1024:
+                continue
+            i2, d2, c2 = (torch.empty((w.nq, kp), dtype=torch.uint32, device=dev),
+                          torch.empty((w.nq, kp), dtype=torch.float32, device=dev),
+                          torch.empty((w.nq, kp), dtype=torch.uint8, device=dev))
+
+            def run(kp=kp, ef=ef, i2=i2, d2=d2, c2=c2):
+                nhq.nhq_brute_force(ixs.handle, Qv, QA, 32, seeds)
+                nhq.nhq_search(ixl.handle, Qv, QA, kp, ef, i2, d2, c2, seed=12345,
+                               seed_mode=nhq.SEED_GIVEN, seeds=seeds)
+                nhq.nhq_postfilter(i2, d2, c2, k, fi, fd)
+
+            ms = timed(run)
+            rec, _ = hybrid_recall(fi.cpu().numpy(), w.A, w.QA, gt_h, P, k)
+            got = i2.cpu().numpy()
+            l2rec = float(np.mean([len(set(x) & set(y)) / kp for x, y in zip(got, ex_h)]))
+            post_rows.append({"k_prime": kp, "ef": ef, "recall": rec, "l2_recall": l2rec,
+                              "ms": ms, "qps": w.nq / ms * 1e3})
+    ixs.close()
+    ixl.close()
+
+    # pre-filtering on an attribute partition: the objects grouped by tuple (built before
+    # the timed region, like an index), then for each tuple that queries ask for one exact
+    # brute force over its objects only
+    order = np.argsort(codes, kind="stable")
+    starts = np.searchsorted(codes[order], uniq)
+    parts = []
+    for t in np.unique(qcodes):
+        j = int(np.searchsorted(uniq, t))
+        if j >= len(uniq) or uniq[j] != t:
+            continue  # no object carries this tuple: the query has no answer
+        members = order[starts[j]:starts[j] + cnt[j]]
+        qi = np.nonzero(qcodes == t)[0]
+        mt = torch.from_numpy(members).to(dev)
+        sub = nhq.Index.create(X[mt].contiguous(), A[mt].contiguous(), (1.0, 0.0))
+        out = torch.empty((len(qi), k), dtype=torch.uint32, device=dev)
+        parts.append((sub, Qv[torch.from_numpy(qi).to(dev)].contiguous(),
+                      QA[torch.from_numpy(qi).to(dev)].contiguous(), out, members, qi))
+    torch.cuda.synchronize()
+
+    def run_parts():
+        for sub, qv, qa, out, _, _ in parts:
+            nhq.nhq_brute_force(sub.handle, qv, qa, k, out)
+
+    ms_part = timed(run_parts, 3)
+    peak, _ = peaks()
+    pre_bytes = float(P.sum()) * (4 * w.d + 4)
+    pre_ms_bound = pre_bytes / (peak * 1e9) * 1e3
+    part_ids = np.full((w.nq, k), 0xFFFFFFFF, np.uint32)
+    for sub, _, _, out, members, qi in parts:
+        loc = out.cpu().numpy().astype(np.int64)
+        glob = np.where(loc == 0xFFFFFFFF, 0xFFFFFFFF, members[np.minimum(loc, len(members) - 1)])
+        part_ids[qi] = glob.astype(np.uint32)
+        sub.close()
+    rec_part, _ = hybrid_recall(part_ids, w.A, w.QA, gt_h, P, k)
+
+    def best(rows):
+        ok = [r for r in rows if r["recall"] >= a.target]
+        return min(ok, key=lambda r: r["ms"]) if ok else max(rows, key=lambda r: r["recall"])
+
+    line = {
+        "metric": f"QPS at hybrid Recall@{k} >= {a.target}: NHQ vs post- and pre-filtering",
+        "unit": "queries/s", "n_gpus": 1, "data": "synthetic", "config": {
+            "workload": workload_name(a),
+            "nhq": "composite index (w_v=1, w_l=10000), attribute-entry seeds",
+            "post_filter": "plain L2 graph (w_l=0, same build), seeds = the 32 nearest of a "
+                           "4,096-object sample (brute force, timed), search k' records, keep "
+                           "the matching ones (nhq_postfilter)",
+            "pre_filter": "exact top-k among the matching objects: objects partitioned by "
+                          "attribute tuple before timing, one brute force per queried tuple "
+                          "over its objects only",
+            "pre_filter_scan_all": "filter-mode brute force over all N objects",
+            "build_s": {"nhq": t_nhq, "l2_graph": t_l2}},
+        "nhq": {"best": best(nhq_rows), "sweep": nhq_rows},
+        "post_filter": {"best": best(post_rows), "sweep": post_rows},
+        "pre_filter": {"recall": rec_part, "ms": ms_part, "qps": w.nq / ms_part * 1e3,
+                       "launches": len(parts)},
+        "pre_filter_scan_all": {"recall": 1.0, "ms": ms_pre, "qps": w.nq / ms_pre * 1e3},
+        # no pre-filter can do better than reading every matching object's row once per
+        # query at the measured HBM bandwidth
+        "pre_filter_roofline": {"bytes": pre_bytes, "ms": pre_ms_bound,
+                                "qps": w.nq / pre_ms_bound * 1e3, "peak_gbs": peak},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- our arm
 def hybrid_recall(ids, A, QA, gt, P, k):
     """Sec. 6.1 recall: returned ids whose attributes equal the query's, against
@@ -385,6 +551,10 @@ def main():
         return
     if a.workload == "c4":
         c4_arm(a, rank, world, local)
+        return
+    if a.workload == "strategies":
+        if rank == 0:
+            strategies_arm(a)
         return
 
     import torch

@@ -244,6 +244,19 @@ nhq_status nhq_merge_topk(int32_t P, int64_t Q, int32_t k_in, int32_t k_out,
                           uint8_t *out_chi, void *stream);
 
 /*
+ * Post-filter of a result list (the "search, then filter" strategy the paper compares
+ * NHQ against, Sec. 2 and Sec. 6.2): row q of out is the first k_out records of row
+ * q of the input whose chi is 0 (attributes equal to the query's), in input order;
+ * shorter results are padded with 0xFFFFFFFF / +inf.
+ *   ids[Q][k_in] u32 (0xFFFFFFFF = none), dists[Q][k_in] f32, chi[Q][k_in] u8,
+ *   out_ids[Q][k_out] u32, out_dists[Q][k_out] f32.
+ * Pointers may be device or host memory.  Errors: k_in or k_out outside 1..1024, Q < 0.
+ */
+nhq_status nhq_postfilter(int64_t Q, int32_t k_in, int32_t k_out, const uint32_t *ids,
+                          const float *dists, const uint8_t *chi, uint32_t *out_ids,
+                          float *out_dists, void *stream);
+
+/*
  * search(queries, query_attributes, k, ef): joint pruning (Alg. 2) on the
  * composite index, ef-bounded, with the two-stage routing of Sec. 4.2 / 5.2
  * when params->h > 1.  Per query: a pool of ef records sorted by (Gamma, id);

@@ -30,7 +30,7 @@ __all__ = [
     "nhq_brute_force_noalloc", "nhq_search_trace", "nhq_mlp_forward", "nhq_mlp_grad",
     "nhq_mlp_train", "MLP_INPUTS", "MLP_HIDDEN", "MLP_PARAMS", "nhq_autotune_search",
     "nhq_search_graph_create", "nhq_search_graph_launch", "nhq_search_graph_free",
-    "nhq_merge_topk",
+    "nhq_merge_topk", "nhq_postfilter",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -107,6 +107,7 @@ def load_library():
                               C.POINTER(P)]),
             "nhq_brute_force": (S, [P, P, P, i64, i32, C.POINTER(_Weights), P, P, P, P]),
             "nhq_merge_topk": (S, [i32, i64, i32, i32, P, P, P, P, P, P, P, P]),
+            "nhq_postfilter": (S, [i64, i32, i32, P, P, P, P, P, P]),
             "nhq_search": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P, P, P, P, P,
                                P, P]),
             "nhq_search_batched": (S, [P, P, P, i64, P, P, i32, C.POINTER(_SearchParams), P, P, P,
@@ -295,6 +296,17 @@ def nhq_build(vectors, attributes, degree, weights=None, K=64, reverse=1, revers
                                      _weights(weights), C.byref(p), _stream(stream),
                                      C.byref(out)))
     return out.value
+
+
+def nhq_postfilter(ids, dists, chi, k_out, out_ids, out_dists, stream=None) -> None:
+    """Keep the records with chi = 0 of each row of ids/dists/chi [Q, k_in], in order,
+    into out_ids/out_dists [Q, k_out] (the post-filter strategy)."""
+    Q, k_in = _shape(ids)
+    _check(load_library().nhq_postfilter(
+        Q, k_in, k_out, _ptr(ids, np.uint32, (Q, k_in), "ids"),
+        _ptr(dists, np.float32, (Q, k_in), "dists"), _ptr(chi, np.uint8, (Q, k_in), "chi"),
+        _ptr(out_ids, np.uint32, (Q, k_out), "out_ids"),
+        _ptr(out_dists, np.float32, (Q, k_out), "out_dists"), _stream(stream)))
 
 
 def nhq_merge_topk(ids, dists, offsets, k_out, out_ids, out_dists, chi=None, out_chi=None,

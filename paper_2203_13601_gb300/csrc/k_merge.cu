@@ -1,6 +1,9 @@
-// k_merge.cu -- merge of per-shard top-k lists (the paper's parallel form: the
-// object set split into shards with one graph each, every shard searched for
-// every query, the lists combined by (Gamma, id)).
+// k_merge.cu -- operations on finished result lists:
+//   * merge of per-shard top-k lists (the paper's parallel form: the object set
+//     split into shards with one graph each, every shard searched for every
+//     query, the lists combined by (Gamma, id));
+//   * post-filter (the "search, then filter by attributes" strategy the paper
+//     compares against): the records with chi = 0, in order.
 //
 // One warp per query.  Every shard's list is already sorted by (Gamma, local id),
 // and adding the shard's offset keeps that order, so the merge only compares the
@@ -103,7 +106,45 @@ __global__ void merge_topk_kernel(MergeArgs a, int heads_per_lane) {
     }
 }
 
+// one warp per query: stable compaction of the records with chi = 0
+__global__ void postfilter_kernel(int64_t Q, int k_in, int k_out, const uint32_t *__restrict__ ids,
+                                  const float *__restrict__ dists, const uint8_t *__restrict__ chi,
+                                  uint32_t *__restrict__ out_ids, float *__restrict__ out_dists) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= Q)
+        return;
+    int got = 0;
+    for (int base = 0; base < k_in && got < k_out; base += 32) {
+        const int j = base + lane;
+        const int64_t o = q * k_in + j;
+        const bool keep = j < k_in && ids[o] != kNone && chi[o] == 0;
+        const unsigned bal = __ballot_sync(FULL, keep);
+        const int p = got + __popc(bal & ((1u << lane) - 1u));
+        if (keep && p < k_out) {
+            out_ids[q * k_out + p] = ids[o];
+            out_dists[q * k_out + p] = dists[o];
+        }
+        got += __popc(bal);
+    }
+    for (int p = got + lane; p < k_out; p += 32) {
+        out_ids[q * k_out + p] = kNone;
+        out_dists[q * k_out + p] = __int_as_float(0x7f800000);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_postfilter(int64_t Q, int k_in, int k_out, const uint32_t *ids,
+                              const float *dists, const uint8_t *chi, uint32_t *out_ids,
+                              float *out_dists, cudaStream_t s) {
+    if (Q <= 0)
+        return cudaSuccess;
+    const int wpb = 8;
+    postfilter_kernel<<<(unsigned)((Q + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
+        Q, k_in, k_out, ids, dists, chi, out_ids, out_dists);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_merge_topk(int P, int64_t Q, int k_in, int k_out, const uint32_t *ids,
                               const float *dists, const uint8_t *chi, const uint32_t *offsets,

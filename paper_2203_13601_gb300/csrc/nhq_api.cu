@@ -565,6 +565,33 @@ nhq_status nhq_brute_force(const nhq_index *cix, const float *queries,
     return st.finish(s);
 }
 
+nhq_status nhq_postfilter(int64_t Q, int32_t k_in, int32_t k_out, const uint32_t *ids,
+                          const float *dists, const uint8_t *chi, uint32_t *out_ids,
+                          float *out_dists, void *stream) {
+    if (k_in < 1 || k_in > 1024 || k_out < 1 || k_out > 1024)
+        return fail(NHQ_ERR_ARG, "k_in and k_out must be in 1..1024");
+    if (Q < 0)
+        return fail(NHQ_ERR_ARG, "Q must be >= 0");
+    if (Q == 0)
+        return NHQ_OK;
+    if (ids == nullptr || dists == nullptr || chi == nullptr || out_ids == nullptr ||
+        out_dists == nullptr)
+        return fail(NHQ_ERR_ARG, "ids, dists, chi, out_ids and out_dists are required");
+    cudaStream_t s = as_stream(stream);
+    const size_t in_n = (size_t)Q * k_in, out_n = (size_t)Q * k_out;
+    Stager st;
+    int ii = st.add(ids, sizeof(uint32_t) * in_n, true);
+    int idd = st.add(dists, sizeof(float) * in_n, true);
+    int ic = st.add(chi, in_n, true);
+    int oi = st.add(out_ids, sizeof(uint32_t) * out_n, false);
+    int od = st.add(out_dists, sizeof(float) * out_n, false);
+    CKS(st.commit(&g_stage.p, &g_stage.cap, s));
+    CK(launch_postfilter(Q, k_in, k_out, (const uint32_t *)st.dev(ii), (const float *)st.dev(idd),
+                         (const uint8_t *)st.dev(ic), (uint32_t *)st.dev(oi),
+                         (float *)st.dev(od), s));
+    return st.finish(s);
+}
+
 nhq_status nhq_merge_topk(int32_t P, int64_t Q, int32_t k_in, int32_t k_out,
                           const uint32_t *ids, const float *dists, const uint8_t *chi,
                           const uint32_t *offsets, uint32_t *out_ids, float *out_dists,

@@ -243,6 +243,9 @@ cudaError_t launch_attribute_seeds(const SearchArgs &a, const uint32_t *attr_sor
 // order[0..nq) = the queries by ascending bucket (each bucket in any order)
 cudaError_t launch_query_order(const uint8_t *bucket, int64_t nq, uint32_t *order,
                                cudaStream_t s);
+cudaError_t launch_postfilter(int64_t Q, int k_in, int k_out, const uint32_t *ids,
+                              const float *dists, const uint8_t *chi, uint32_t *out_ids,
+                              float *out_dists, cudaStream_t s);
 cudaError_t launch_merge_topk(int P, int64_t Q, int k_in, int k_out, const uint32_t *ids,
                               const float *dists, const uint8_t *chi, const uint32_t *offsets,
                               uint32_t *out_ids, float *out_dists, uint8_t *out_chi,

@@ -91,6 +91,8 @@ def test_argument_errors_before_cuda(lib):
                               None) == nhq.ERR_ARG
     assert lib.nhq_merge_topk(2, 1, 4, 4, None, None, None, None, None, None, None,
                               None) == nhq.ERR_ARG
+    assert lib.nhq_postfilter(1, 0, 1, None, None, None, None, None, None) == nhq.ERR_ARG
+    assert lib.nhq_postfilter(1, 4, 2, None, None, None, None, None, None) == nhq.ERR_ARG
 
 
 def test_load_rejects_missing_and_corrupt_files(lib, tmp_path):
