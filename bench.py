@@ -65,10 +65,11 @@ def parse():
                     help="candidate build: 0 exact f32 SIMT, 1 bf16 tensor cores (exact here)")
     ap.add_argument("--learned-efs", default="16,24,32,48,64")
     ap.add_argument("--taus", default="0.7,0.8,0.9,0.95")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "strategies"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "strategies"],
                     help="c2: the headline workload (default); c4: the heterogeneous batch "
                          "(1M x 96, 100k queries with mixed k and ef) through "
-                         "nhq_search_batched; strategies: NHQ against post-filtering on a "
+                         "nhq_search_batched; c5: the 10M x 96 set (f16-valued), 50k queries; "
+                         "strategies: NHQ against post-filtering on a "
                          "plain L2 graph and exact pre-filtering, on the c2 workload; each "
                          "prints one JSON line of its own")
     return ap.parse_args()
@@ -357,6 +358,105 @@ def c4_arm(a, rank, world, local):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- the largest set
+def c5_arm(a):
+    """The c5-shaped set: N = 10M, d = 96 (values exactly representable in f16, stored
+    as f32), 4,096 centroids, m = 3 Zipf attributes (10/50/200), 50,000 queries, k = 10:
+    build time, then QPS at hybrid Recall@10 >= target over an ef sweep."""
+    import torch
+
+    import paper_2203_13601_gb300 as nhq
+    import synth
+    from paper_2203_13601_gb300 import build as B
+
+    B.build()
+    nhq.load_library()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    w = synth.c5()
+    t_gen = time.perf_counter() - t0
+    X, A = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.A).to(dev)
+    Qv, QA = torch.from_numpy(w.Qv).to(dev), torch.from_numpy(w.QA).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = nhq.Index.build(X, A, degree=a.R, weights=CONST_W, K=64, knn_dtype=1)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    k = a.k
+    gt = torch.empty((w.nq, k), dtype=torch.uint32, device=dev)
+    nhq.nhq_brute_force(ix.handle, Qv, QA, k, gt, weights="filter")
+    gt_h = gt.cpu().numpy()
+    mult = np.array([1, 256, 65536])[: w.m]
+    codes, qcodes = (w.A.astype(np.int64) * mult).sum(1), (w.QA.astype(np.int64) * mult).sum(1)
+    uniq, cnt = np.unique(codes, return_counts=True)
+    pos = np.minimum(np.searchsorted(uniq, qcodes), len(uniq) - 1)
+    P = np.where(uniq[pos] == qcodes, cnt[pos], 0)
+    ids, dd, ch = (torch.empty((w.nq, k), dtype=torch.uint32, device=dev),
+                   torch.empty((w.nq, k), dtype=torch.float32, device=dev),
+                   torch.empty((w.nq, k), dtype=torch.uint8, device=dev))
+    ndc = torch.empty(w.nq, dtype=torch.int32, device=dev)
+    exps = torch.empty(w.nq, dtype=torch.int32, device=dev)
+
+    def run(ef, diag=False):
+        nhq.nhq_search(ix.handle, Qv, QA, k, ef, ids, dd, ch, ndc=ndc if diag else None,
+                       expansions=exps if diag else None, seed=12345,
+                       seed_mode=nhq.SEED_ATTRIBUTE)
+
+    sweep = []
+    for ef in (16, 24, 32, 48, 64, 96):
+        for _ in range(2):
+            run(ef)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run(ef)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rec, nomatch = hybrid_recall(ids.cpu().numpy(), w.A, w.QA, gt_h, P, k)
+        sweep.append({"ef": ef, "recall": rec, "ms": e0.elapsed_time(e1)})
+        if rec >= a.target:
+            break
+    ef = sweep[-1]["ef"]
+    run(ef, diag=True)
+    torch.cuda.synchronize()
+    ndc_h, exp_h = ndc.cpu().numpy().astype(np.float64), exps.cpu().numpy().astype(np.float64)
+    alg_bytes = float((ndc_h * (4 * w.d + 4) + exp_h * a.R * 4 + w.d * 4 + k * 9).sum())
+    for _ in range(max(3, a.warmup)):
+        run(ef)
+    steps = min(a.steps, 200)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        run(ef)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (total_ms / steps / 1000.0) / 1e9
+    print(json.dumps({
+        "metric": f"QPS at hybrid Recall@{k} >= {a.target} on the 10M set",
+        "value": w.nq * steps / (total_ms / 1000.0), "unit": "queries/s", "n_gpus": 1,
+        "steps": steps, "warmup": a.warmup, "ms_per_step": total_ms / steps,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "c5-shaped: N=10,000,000 d=96 (f16-representable values "
+                               "stored as f32), 4,096 centroids, m=3 attrs 10/50/200 Zipf, "
+                               "50,000 queries, k=10, R=32, weights w_v=1 w_l=10000",
+                   "ef": ef, "recall": sweep[-1]["recall"], "sweep": sweep,
+                   "build_s": t_build, "gen_s": t_gen,
+                   "queries_with_no_match": int((P == 0).sum())},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "mean_ndc": float(ndc_h.mean()), "mean_expansions": float(exp_h.mean())},
+        "clocks": clk}), flush=True)
+    ix.close()
+
+
 # ---------------------------------------------------------------- strategies
 def strategies_arm(a):
     """The paper's comparison (Sec. 6.2) inside this framework, on one GPU and the c2
@@ -555,6 +655,10 @@ def main():
     if a.workload == "strategies":
         if rank == 0:
             strategies_arm(a)
+        return
+    if a.workload == "c5":
+        if rank == 0:
+            c5_arm(a)
         return
 
     import torch
