@@ -30,7 +30,7 @@ __all__ = [
     "nhq_brute_force_noalloc", "nhq_search_trace", "nhq_mlp_forward", "nhq_mlp_grad",
     "nhq_mlp_train", "MLP_INPUTS", "MLP_HIDDEN", "MLP_PARAMS", "nhq_autotune_search",
     "nhq_search_graph_create", "nhq_search_graph_launch", "nhq_search_graph_free",
-    "nhq_merge_topk", "nhq_postfilter",
+    "nhq_merge_topk", "nhq_postfilter", "nhq_knn_nndescent",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -98,6 +98,7 @@ def load_library():
             "nhq_pack_attributes": (S, [P, i64, i32, P, P]),
             "nhq_knn": (S, [P, i32, P, P, P]),
             "nhq_knn_bf16": (S, [P, i32, P, P, P]),
+            "nhq_knn_nndescent": (S, [P, i32, i32, C.c_uint64, P, P, P, P]),
             "nhq_edge_select": (S, [P, P, i32, i32, P, P]),
             "nhq_reverse_candidates": (S, [P, P, i32, i32, P, P]),
             "nhq_index_set_graph": (S, [P, P, i32, P]),
@@ -244,6 +245,19 @@ def nhq_knn_bf16(index, K, cand_ids, cand_dist=None, stream=None) -> None:
     _check(load_library().nhq_knn_bf16(index, K, _ptr(cand_ids, np.uint32, (N, K), "cand_ids"),
                                        _ptr(cand_dist, np.float32, (N, K), "cand_dist"),
                                        _stream(stream)))
+
+
+def nhq_knn_nndescent(index, K, cand_ids, cand_dist=None, max_iters=12, seed=0x2203,
+                      stream=None) -> int:
+    """Candidate sets by NN-descent into cand_ids [N, K] (and cand_dist); returns the
+    number of iterations run."""
+    N = nhq_index_info(index)[0]
+    it = C.c_int32(0)
+    _check(load_library().nhq_knn_nndescent(
+        index, K, max_iters, C.c_uint64(int(seed) & (2**64 - 1)),
+        _ptr(cand_ids, np.uint32, (N, K), "cand_ids"),
+        _ptr(cand_dist, np.float32, (N, K), "cand_dist"), C.byref(it), _stream(stream)))
+    return it.value
 
 
 def nhq_edge_select(index, cand_ids, R, nbr_out, stream=None) -> None:

@@ -377,6 +377,36 @@ nhq_status nhq_knn_bf16(const nhq_index *cix, int32_t K, uint32_t *cand_ids, flo
     return NHQ_OK;
 }
 
+nhq_status nhq_knn_nndescent(const nhq_index *ix, int32_t K, int32_t max_iters, uint64_t seed,
+                             uint32_t *cand_ids, float *cand_dist, int32_t *iterations,
+                             void *stream) {
+    if (ix == nullptr || cand_ids == nullptr)
+        return fail(NHQ_ERR_ARG, "index and cand_ids are required");
+    if (K < 1 || K > nnd_kmax() || K >= ix->N)
+        return fail(NHQ_ERR_ARG, "K must be in 1..min(64, N-1) (got %d)", K);
+    if (max_iters < 1 || max_iters > 100)
+        return fail(NHQ_ERR_ARG, "max_iters must be in 1..100 (got %d)", max_iters);
+    cudaStream_t s = as_stream(stream);
+    Stager st;
+    int io = st.add(cand_ids, sizeof(uint32_t) * (size_t)ix->N * K, false);
+    int id = st.add(cand_dist, sizeof(float) * (size_t)ix->N * K, false);
+    CKS(st.commit(&g_stage.p, &g_stage.cap, s));
+    void *work = nullptr;
+    CK(cudaMalloc(&work, nnd_scratch_bytes(ix->N, K)));
+    int done = 0;
+    cudaError_t e = launch_nndescent(ix->X, ix->xstride, ix->N, ix->attr, make_fusion(ix->w, ix->m),
+                                     K, max_iters, 1e-3, seed, work, (uint32_t *)st.dev(io),
+                                     (float *)st.dev(id), &done, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    cudaFree(work);
+    if (e != cudaSuccess)
+        return fail_cuda(e, "NN-descent");
+    if (iterations)
+        *iterations = done;
+    return st.finish(s);
+}
+
 nhq_status nhq_edge_select(const nhq_index *cix, const uint32_t *cand_ids, int32_t L, int32_t R,
                            uint32_t *nbr_out, void *stream) {
     const nhq_index *ix = cix;
@@ -474,12 +504,17 @@ nhq_status nhq_index_build(nhq_index *ix, int32_t degree, const nhq_build_params
         return fail_cuda(e, "cudaMalloc(build buffers)");
     }
     const int tc = p ? p->knn_dtype : 0;
-    if (tc != 0 && tc != 1)
-        return fail(NHQ_ERR_ARG, "knn_dtype must be 0 (f32) or 1 (bf16 tensor cores)");
+    if (tc < 0 || tc > 2)
+        return fail(NHQ_ERR_ARG,
+                    "knn_dtype must be 0 (f32), 1 (bf16 tensor cores) or 2 (NN-descent)");
     if (tc == 1 && K > knn_tc_kmax())
         K = knn_tc_kmax();
-    nhq_status st = tc == 1 ? nhq_knn_bf16(ix, K, cand, nullptr, stream)
-                            : nhq_knn(ix, K, cand, nullptr, stream);
+    if (tc == 2 && K > nnd_kmax())
+        K = nnd_kmax();
+    nhq_status st = tc == 1   ? nhq_knn_bf16(ix, K, cand, nullptr, stream)
+                    : tc == 2 ? nhq_knn_nndescent(ix, K, 12, 0x2203ull, cand, nullptr, nullptr,
+                                                  stream)
+                              : nhq_knn(ix, K, cand, nullptr, stream);
     if (st == NHQ_OK)
         st = nhq_edge_select(ix, cand, K, degree, nbr, stream);
     if (st == NHQ_OK && rev) {

@@ -243,6 +243,12 @@ cudaError_t launch_attribute_seeds(const SearchArgs &a, const uint32_t *attr_sor
 // order[0..nq) = the queries by ascending bucket (each bucket in any order)
 cudaError_t launch_query_order(const uint8_t *bucket, int64_t nq, uint32_t *order,
                                cudaStream_t s);
+int nnd_kmax();
+size_t nnd_scratch_bytes(int64_t N, int K);
+cudaError_t launch_nndescent(const float *X, int xstride, int64_t N, const uint32_t *attr,
+                             const Fusion &w, int K, int max_iters, double delta, uint64_t seed,
+                             void *scratch, uint32_t *ids, float *dists, int *iters_done,
+                             cudaStream_t s);
 cudaError_t launch_postfilter(int64_t Q, int k_in, int k_out, const uint32_t *ids,
                               const float *dists, const uint8_t *chi, uint32_t *out_ids,
                               float *out_dists, cudaStream_t s);
