@@ -33,6 +33,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 W_PROPORTIONAL = 0  # w_v = 1, w_l = delta / m  (Sec. 3.2, curve iv)
 W_CONSTANT = 1      # w_v, w_l given             (Eq. 6, curve v)
+W_HARMONIC = 3      # 2 delta h / (delta + h), h = chi (curve i) or 1 / c chi (curve ii)
 F64 = 0
 F32 = 1
 ITER_LIMIT = 4
@@ -116,9 +117,14 @@ def _p(a):
 
 
 def _mode(weights):
-    """weights: None / "proportional" -> Sec. 3.2 recommended form; (w_v, w_l) -> constant."""
+    """weights: None / "proportional" -> Sec. 3.2 recommended form; (w_v, w_l) -> constant;
+    "harmonic" -> curve i of Sec. 6.5; ("harmonic", c) -> curve ii with constant c."""
     if weights is None or weights == "proportional":
         return W_PROPORTIONAL, 1.0, 0.0
+    if weights == "harmonic":
+        return W_HARMONIC, 1.0, 0.0
+    if weights[0] == "harmonic":
+        return W_HARMONIC, 1.0, float(weights[1])
     wv, wl = weights
     return W_CONSTANT, float(wv), float(wl)
 

@@ -11,6 +11,10 @@
  *   Eq. 4-5      attribute distance chi (mismatch count)     or_chi
  *   Eq. 6        fusion distance Gamma = w_v*delta + w_l*chi or_gamma64 / or_gamma32
  *   Sec. 3.2     recommended weights w_v = 1, w_l = delta/m  (mode OR_W_PROPORTIONAL)
+ *   Sec. 6.5     curves i/ii: w_v = chi/(delta+chi), w_l = delta/(delta+chi), i.e.
+ *                the harmonic mean 2 delta chi / (delta + chi), with chi replaced by
+ *                1 (chi = 0) or c * chi (chi > 0) for curve ii   (mode OR_W_HARMONIC,
+ *                c = wl; wl = 0 is curve i)
  *   Def. 2, 4    exact top-k by Gamma (brute force)          or_fused_topk
  *   Sec. 6.1     hybrid ground truth (exact attribute match,
  *                k nearest by delta)                         or_filtered_topk
@@ -40,6 +44,7 @@
 
 #define OR_W_PROPORTIONAL 0
 #define OR_W_CONSTANT 1
+#define OR_W_HARMONIC 3
 #define OR_F64 0
 #define OR_F32 1
 
@@ -138,6 +143,13 @@ float or_round_e4m3(float x)
 /* Eq. 6 in double.  Proportional mode: w_v = 1, w_l = delta / m (Sec. 3.2). */
 double or_gamma64(double delta, int chi, int m, int mode, double wv, double wl)
 {
+    if (mode == OR_W_HARMONIC) {
+        /* the attribute term of the harmonic mean: chi itself (curve i), or the adjusted
+         * value 1 for chi = 0 and c * chi otherwise (curve ii, c = wl) */
+        double h = wl > 0.0 ? (chi == 0 ? 1.0 : wl * (double)chi) : (double)chi;
+        double den = delta + h;
+        return den == 0.0 ? 0.0 : 2.0 * delta * h / den;
+    }
     if (mode == OR_W_PROPORTIONAL) {
         double w_l = delta / (double)m;
         return 1.0 * delta + w_l * (double)chi;
@@ -148,6 +160,13 @@ double or_gamma64(double delta, int chi, int m, int mode, double wv, double wl)
 /* Eq. 6 in float, each operation rounded once */
 float or_gamma32(float delta, int chi, int m, int mode, float wv, float wl)
 {
+    if (mode == OR_W_HARMONIC) {
+        float h = wl > 0.f ? (chi == 0 ? 1.f : wl * (float)chi) : (float)chi;
+        float two_d = 2.f * delta;
+        float num = two_d * h;
+        float den = delta + h;
+        return den == 0.f ? 0.f : num / den;
+    }
     if (mode == OR_W_PROPORTIONAL) {
         float w_l = delta / (float)m;
         float t = w_l * (float)chi;

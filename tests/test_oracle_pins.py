@@ -449,3 +449,55 @@ def test_mlp_forward_hand_case():
     # row 0: h0 = relu(2 - .5) = 1.5, h1 = relu(2 - .5) = 1.5 -> 1.5*1.5 - 2*1.5 + .25 = -0.5
     # row 1: h0 = relu(-2) = 0, h1 = relu(.2 - .5) = 0 -> 0.25
     assert np.allclose(mlp.forward(p, x), [-0.5, 0.25], rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------------------ curves i and ii (Sec. 6.5)
+def test_harmonic_curve_i_is_the_harmonic_mean_and_vanishes_at_chi_zero(oracle_mod):
+    O = oracle_mod
+    # Gamma = 2 delta chi / (delta + chi); the paper's stated defect: chi = 0 gives 0
+    assert O.gamma(3.0, 1, 3, "harmonic") == pytest.approx(1.5, rel=0, abs=1e-15)
+    assert O.gamma(1.0, 3, 3, "harmonic") == pytest.approx(1.5, rel=0, abs=1e-15)  # symmetric
+    for d in (0.0, 0.5, 7.0, 1e6):
+        assert O.gamma(d, 0, 3, "harmonic") == 0.0
+        assert O.gamma(d, 0, 3, "harmonic", O.F32) == 0.0
+
+
+def test_harmonic_curve_ii_adjusts_chi(oracle_mod):
+    O = oracle_mod
+    # chi -> 1 for chi = 0 and c * chi otherwise (c = 100)
+    for d in (0.25, 3.0, 40.0):
+        assert O.gamma(d, 0, 3, ("harmonic", 100.0)) == pytest.approx(2 * d / (d + 1), rel=1e-15)
+        assert O.gamma(d, 2, 3, ("harmonic", 100.0)) == pytest.approx(400 * d / (d + 200),
+                                                                        rel=1e-15)
+
+
+@pytest.mark.parametrize("c", [0.0, 100.0])
+def test_harmonic_bounds_monotonicity_and_f32(oracle_mod, c):
+    O = oracle_mod
+    w = ("harmonic", c) if c else "harmonic"
+    rng = np.random.default_rng(5)
+    for d in rng.random(200) * 50:
+        prev = -1.0
+        for chi in range(4):
+            h = chi if c == 0 else (1.0 if chi == 0 else c * chi)
+            g = O.gamma(d, chi, 3, w)
+            # a harmonic mean lies between the smaller value and twice it
+            assert min(d, h) - 1e-12 <= g <= 2 * min(d, h) + 1e-12
+            assert g >= prev  # non-decreasing in chi
+            prev = g
+            g32 = O.gamma(float(np.float32(d)), chi, 3, w, O.F32)
+            assert g32 == pytest.approx(O.gamma(float(np.float32(d)), chi, 3, w), rel=1e-6,
+                                        abs=1e-30)
+        assert O.gamma(d, 1, 3, w) <= O.gamma(d + 1.0, 1, 3, w)  # non-decreasing in delta
+
+
+def test_curve_i_brute_force_returns_the_smallest_matching_ids(oracle_mod):
+    O = oracle_mod
+    # every exact attribute match has Gamma 0, so the top-k are the k smallest matching
+    # ids (ties by id) whenever there are at least k matches
+    w = synth.int_valued(600, 8, 8, cards=(2, 3), seed=12)
+    ids, g, chi = O.fused_topk(w.X, w.A, w.Qv, w.QA, 5, weights="harmonic", prec=O.F32)
+    for q in range(w.nq):
+        match = np.nonzero((w.A == w.QA[q]).all(axis=1))[0]
+        assert len(match) >= 5
+        assert (ids[q] == match[:5]).all() and (g[q] == 0).all() and (chi[q] == 0).all()
