@@ -54,6 +54,9 @@ typedef enum nhq_status {
 typedef enum nhq_weight_mode {
     NHQ_W_PROPORTIONAL = 0, /* w_v = 1, w_l = delta / m: the recommended setting of Sec. 3.2 */
     NHQ_W_CONSTANT = 1,     /* w_v, w_l as given (Sec. 6.5, curve v)                         */
+    NHQ_W_HARMONIC = 3,     /* curves i/ii of Sec. 6.5: Gamma = 2 delta h / (delta + h), h = chi
+                               (w_l = 0, curve i) or h = 1 for chi = 0 and w_l * chi otherwise
+                               (w_l = c >= 1, curve ii); w_v is unused                      */
     NHQ_W_FILTER = 2        /* brute force only: Gamma = delta if chi = 0, else excluded; the
                                hybrid ground truth of Sec. 6.1                               */
 } nhq_weight_mode;

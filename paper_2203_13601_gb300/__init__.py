@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "NHQError", "Index", "load_library", "library_path",
-    "W_PROPORTIONAL", "W_CONSTANT", "W_FILTER", "VEC_F32", "VEC_BF16", "VEC_FP8E4M3",
+    "W_PROPORTIONAL", "W_CONSTANT", "W_FILTER", "W_HARMONIC", "VEC_F32", "VEC_BF16", "VEC_FP8E4M3",
     "SEED_RANDOM", "SEED_ATTRIBUTE", "SEED_GIVEN",
     "nhq_last_error", "nhq_version", "nhq_index_create", "nhq_free", "nhq_index_info",
     "nhq_pack_attributes", "nhq_knn", "nhq_knn_bf16", "nhq_edge_select", "nhq_reverse_candidates",
@@ -36,7 +36,7 @@ __all__ = [
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libnhq.so")
 
-W_PROPORTIONAL, W_CONSTANT, W_FILTER = 0, 1, 2
+W_PROPORTIONAL, W_CONSTANT, W_FILTER, W_HARMONIC = 0, 1, 2, 3
 VEC_F32, VEC_BF16, VEC_FP8E4M3 = 0, 1, 2
 SEED_RANDOM, SEED_ATTRIBUTE, SEED_GIVEN = 0, 1, 2
 MLP_INPUTS, MLP_HIDDEN = 8, 64
@@ -187,6 +187,10 @@ def _weights(weights):
         return _Weights(W_PROPORTIONAL, 1.0, 0.0)
     if weights == "filter":
         return _Weights(W_FILTER, 1.0, 0.0)
+    if weights == "harmonic":  # curve i of Sec. 6.5
+        return _Weights(W_HARMONIC, 1.0, 0.0)
+    if weights[0] == "harmonic":  # curve ii with constant c
+        return _Weights(W_HARMONIC, 1.0, float(weights[1]))
     wv, wl = weights
     return _Weights(W_CONSTANT, float(wv), float(wl))
 

@@ -384,7 +384,8 @@ extern "C" nhq_status nhq_brute_force_noalloc(const float *vectors,
                                          "1..4, Q >= 0, k in 1..256");
     if (d % 4 != 0)
         return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: d must be a multiple of 4");
-    if (w.mode != NHQ_W_PROPORTIONAL && w.mode != NHQ_W_CONSTANT && w.mode != NHQ_W_FILTER)
+    if (w.mode != NHQ_W_PROPORTIONAL && w.mode != NHQ_W_CONSTANT && w.mode != NHQ_W_HARMONIC &&
+        w.mode != NHQ_W_FILTER)
         return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: unknown weight mode");
     if (w.mode == NHQ_W_CONSTANT &&
         (!std::isfinite(w.w_v) || !std::isfinite(w.w_l) || w.w_v < 0.f || w.w_l < 0.f))

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int FULL0 = 0, EMPTY0 = MAX_STAGES, TFULL0 = 2 * MAX_STAGES, TEMPTY0 = TFULL0 + 2,
               AFULL = TEMPTY0 + 2, DONE = AFULL + 1;
     // whole tiles are rejected only where a negative bound is possible
-    const bool skip_on = a.w.mode != NHQ_W_PROPORTIONAL;
+    const bool skip_on = a.w.mode == NHQ_W_CONSTANT;
 
     for (int i = threadIdx.x; i < (ntiles + 31) / 32; i += NTHREADS)
         skipbits[i] = 0u;
@@ -489,8 +489,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         float fac[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c)
-            fac[c] = a.w.mode == NHQ_W_CONSTANT ? a.w.wl * (float)c
-                                                : (float)a.w.m / (float)(a.w.m + c);
+            fac[c] = a.w.mode == NHQ_W_CONSTANT   ? a.w.wl * (float)c
+                     : a.w.mode == NHQ_W_HARMONIC // the attribute term h of the harmonic mean
+                         ? (a.w.wl > 0.f ? (c == 0 ? 1.f : a.w.wl * (float)c) : (float)c)
+                         : (float)a.w.m / (float)(a.w.m + c);
         const float inv_wv = a.w.wv > 0.f ? 1.f / a.w.wv : 0.f;
         auto update_lim = [&]() {
             thr = hp[1];
@@ -499,11 +501,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int cc = 0; cc < 5; ++cc) {
                 float tt;
-                if (a.w.mode == NHQ_W_CONSTANT)
+                if (a.w.mode == NHQ_W_CONSTANT) {
                     tt = a.w.wv > 0.f ? (gt - fac[cc]) * inv_wv
                                       : (gt >= fac[cc] ? __int_as_float(0x7f800000) : -1.f);
-                else
+                } else if (a.w.mode == NHQ_W_HARMONIC) {
+                    // Gamma = 2 delta h / (delta + h) < 2 h for every delta: no bound while
+                    // gt >= 2 h; below that, delta <= gt h / (2 h - gt)
+                    const float h = fac[cc];
+                    tt = (h == 0.f || gt >= 2.f * h) ? __int_as_float(0x7f800000)
+                                                     : gt * h / (2.f * h - gt);
+                } else {
                     tt = gt * fac[cc];
+                }
                 limtab[cc * BM + r] = tt < 0.f ? -1.f : tt * tt;
             }
         };

@@ -127,9 +127,12 @@ struct Stager {
 };
 
 nhq_status check_weights(const nhq_weights &w, bool allow_filter) {
-    if (w.mode != NHQ_W_PROPORTIONAL && w.mode != NHQ_W_CONSTANT &&
+    if (w.mode != NHQ_W_PROPORTIONAL && w.mode != NHQ_W_CONSTANT && w.mode != NHQ_W_HARMONIC &&
         !(allow_filter && w.mode == NHQ_W_FILTER))
         return fail(NHQ_ERR_ARG, "unknown weight mode %d", w.mode);
+    // curve ii's adjusted chi (1, c, 2c, ...) must grow with chi: c = 0 (curve i) or c >= 1
+    if (w.mode == NHQ_W_HARMONIC && !(std::isfinite(w.w_l) && (w.w_l == 0.f || w.w_l >= 1.f)))
+        return fail(NHQ_ERR_ARG, "harmonic weights need w_l = 0 (curve i) or w_l >= 1 (curve ii)");
     if (w.mode == NHQ_W_CONSTANT &&
         (!std::isfinite(w.w_v) || !std::isfinite(w.w_l) || w.w_v < 0.f || w.w_l < 0.f))
         return fail(NHQ_ERR_ARG, "constant weights must be finite and >= 0");

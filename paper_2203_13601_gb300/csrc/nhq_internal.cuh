@@ -52,6 +52,11 @@ __device__ __forceinline__ float fusion_gamma(float delta, int chi, const Fusion
     }
     if (w.mode == NHQ_W_CONSTANT)
         return __fadd_rn(__fmul_rn(w.wv, delta), __fmul_rn(w.wl, (float)chi));
+    if (w.mode == NHQ_W_HARMONIC) {  // Sec. 6.5 curves i (w.wl = 0) and ii (w.wl = c)
+        const float h = w.wl > 0.f ? (chi == 0 ? 1.f : __fmul_rn(w.wl, (float)chi)) : (float)chi;
+        const float den = __fadd_rn(delta, h);
+        return den == 0.f ? 0.f : __fdiv_rn(__fmul_rn(__fmul_rn(2.f, delta), h), den);
+    }
     return chi == 0 ? delta : __int_as_float(0x7f800000);  // NHQ_W_FILTER
 }
 

@@ -71,6 +71,10 @@ def test_argument_errors_before_cuda(lib):
     # N = 0
     st = lib.nhq_index_create(x.ctypes.data, 0, 3, a.ctypes.data, 2, w, None, C.byref(out))
     assert st == nhq.ERR_ARG
+    # curve ii needs c >= 1 (its adjusted chi must grow with chi)
+    st = lib.nhq_index_create(x.ctypes.data, 4, 3, a.ctypes.data, 2, nhq._Weights(3, 1.0, 0.5),
+                              None, C.byref(out))
+    assert st == nhq.ERR_ARG and "harmonic" in nhq.nhq_last_error()
     # negative constant weight
     st = lib.nhq_index_create(x.ctypes.data, 4, 3, a.ctypes.data, 2, nhq._Weights(1, -1.0, 1.0),
                               None, C.byref(out))
