@@ -65,12 +65,14 @@ def parse():
                     help="candidate build: 0 exact f32 SIMT, 1 bf16 tensor cores (exact here)")
     ap.add_argument("--learned-efs", default="16,24,32,48,64")
     ap.add_argument("--taus", default="0.7,0.8,0.9,0.95")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5", "strategies"],
+    ap.add_argument("--workload", default="c2",
+                    choices=["c2", "c4", "c5", "strategies", "curves"],
                     help="c2: the headline workload (default); c4: the heterogeneous batch "
                          "(1M x 96, 100k queries with mixed k and ef) through "
                          "nhq_search_batched; c5: the 10M x 96 set (f16-valued), 50k queries; "
                          "strategies: NHQ against post-filtering on a "
-                         "plain L2 graph and exact pre-filtering, on the c2 workload; each "
+                         "plain L2 graph and exact pre-filtering, on the c2 workload; curves: "
+                         "the weightings i-v of Sec. 6.5 on the c2 workload; each "
                          "prints one JSON line of its own")
     return ap.parse_args()
 
@@ -457,6 +459,74 @@ def c5_arm(a):
     ix.close()
 
 
+# ---------------------------------------------------------------- weightings
+def curves_arm(a):
+    """The weightings of Sec. 6.5 on the c2 workload, each with its own composite index
+    (exact candidates on the tensor cores) and attribute-entry seeds: i harmonic mean of
+    delta and chi, ii the same with chi -> 1 / 100 chi, iii delta / delta_max + chi / m
+    (delta_max = the bounding-box diagonal of the set, a bound known in advance), iv
+    delta + delta chi / m (the library default), v delta + 10,000 chi.  For each: the
+    cheapest ef reaching hybrid Recall@10 >= target, else the best recall of the sweep."""
+    import torch
+
+    import paper_2203_13601_gb300 as nhq
+    from paper_2203_13601_gb300 import build as B
+
+    B.build()
+    nhq.load_library()
+    dev = torch.device("cuda", 0)
+    w = make_workload(a)
+    X, A = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.A).to(dev)
+    Qv, QA = torch.from_numpy(w.Qv).to(dev), torch.from_numpy(w.QA).to(dev)
+    k = a.k
+    dmax = float(np.linalg.norm(w.X.max(axis=0).astype(np.float64) - w.X.min(axis=0)))
+    curves = [("i", "harmonic"), ("ii", ("harmonic", 100.0)),
+              ("iii", (1.0 / dmax, 1.0 / w.m)), ("iv", None), ("v", CONST_W)]
+    mult = np.array([1, 256, 65536])[: w.m]
+    codes, qcodes = (w.A.astype(np.int64) * mult).sum(1), (w.QA.astype(np.int64) * mult).sum(1)
+    uniq, cnt = np.unique(codes, return_counts=True)
+    pos = np.minimum(np.searchsorted(uniq, qcodes), len(uniq) - 1)
+    P = np.where(uniq[pos] == qcodes, cnt[pos], 0)
+    gt = torch.empty((w.nq, k), dtype=torch.uint32, device=dev)
+    ids, dd, ch = (torch.empty((w.nq, k), dtype=torch.uint32, device=dev),
+                   torch.empty((w.nq, k), dtype=torch.float32, device=dev),
+                   torch.empty((w.nq, k), dtype=torch.uint8, device=dev))
+    rows = []
+    for name, wts in curves:
+        t0 = time.perf_counter()
+        ix = nhq.Index.build(X, A, degree=a.R, weights=wts, K=64, knn_dtype=1)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        if name == "i":
+            nhq.nhq_brute_force(ix.handle, Qv, QA, k, gt, weights="filter")
+            gt_h = gt.cpu().numpy()
+        sweep = []
+        for ef in (16, 24, 32, 48, 64, 96, 128, 200):
+            run = lambda ef=ef: nhq.nhq_search(ix.handle, Qv, QA, k, ef, ids, dd, ch,
+                                               seed=12345, seed_mode=nhq.SEED_ATTRIBUTE)
+            for _ in range(2):
+                run()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            rec, _ = hybrid_recall(ids.cpu().numpy(), w.A, w.QA, gt_h, P, k)
+            ms = e0.elapsed_time(e1)
+            sweep.append({"ef": ef, "recall": rec, "ms": ms, "qps": w.nq / ms * 1e3})
+            if rec >= a.target:
+                break
+        ix.close()
+        best = sweep[-1] if sweep[-1]["recall"] >= a.target else max(sweep,
+                                                                        key=lambda r: r["recall"])
+        rows.append({"curve": name, "weights": str(wts), "build_s": t_build, "best": best,
+                     "reached_target": best["recall"] >= a.target, "sweep": sweep})
+    print(json.dumps({"metric": f"hybrid Recall@{k} and QPS per weighting (Sec. 6.5)",
+                      "config": {"workload": workload_name(a), "delta_max": dmax,
+                                 "target": a.target},
+                      "curves": rows}), flush=True)
+
+
 # ---------------------------------------------------------------- strategies
 def strategies_arm(a):
     """The paper's comparison (Sec. 6.2) inside this framework, on one GPU and the c2
@@ -659,6 +729,10 @@ def main():
     if a.workload == "c5":
         if rank == 0:
             c5_arm(a)
+        return
+    if a.workload == "curves":
+        if rank == 0:
+            curves_arm(a)
         return
 
     import torch
