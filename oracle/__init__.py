@@ -246,6 +246,63 @@ def build_graph(X, A, R=32, K=64, weights=None, prec=F32, reverse=True, rev_cap=
     return nbr, deg, cand
 
 
+def nsw_waves(N, wave_max):
+    """Insertion waves [s, e) of the incremental build: vertex 0 alone, then waves of
+    1, 2, 4, ... vertices, at most wave_max each."""
+    waves, s = [], 1
+    while s < N:
+        e = min(N, s + min(s, wave_max))
+        waves.append((s, e))
+        s = e
+    return waves
+
+
+def nsw_seeds(v, s, seed, n=32):
+    """Entry points of vertex v's insertion search in the graph of [0, s): min(n, s)
+    consecutive ids (h + j) mod s from h = splitmix64(seed ^ mix64(v))[0] mod s, so every
+    earlier vertex is a seed while s <= n; -1 pads the row."""
+    h = splitmix64_stream(seed ^ mix64(v), 1)[0] % s
+    row = [(h + j) % s for j in range(min(n, s))]
+    return row + [-1] * (n - len(row))
+
+
+def build_nsw(X, A, R=32, L=64, weights=None, seed=0, wave_max=4096, rev_cap=64, prec=F32,
+              trace=False):
+    """Incremental build (NPG_nsw of Sec. 4.3, batched into insertion waves): the vertices
+    of a wave [s, e) each search the graph of [0, s) (Alg. 2 with the nsw_seeds entry
+    points, k = ef = L) for their candidates and keep a landing-zone selection of them
+    (Def. 6); then every earlier vertex u that one of them selected re-selects its
+    neighbours from N(u) plus those new sources (ascending ids, at most rev_cap).  Every
+    wave sees the graph as it was when the wave began.  With trace=True also returns the
+    candidate lists of every wave."""
+    X, A = _f32(X), _u8(A)
+    N = X.shape[0]
+    nbr = np.full((N, R), -1, np.int64)
+    steps = []
+    for s, e in nsw_waves(N, wave_max):
+        W = np.arange(s, e)
+        seeds = np.array([nsw_seeds(int(v), s, seed) for v in W], np.int64)
+        r = search(X, A, nbr, X[W], A[W], L, L, seeds=seeds, weights=weights, prec=prec)
+        cand = r["ids"]
+        new_rows, _ = edge_select(X, A, cand, R, weights=weights, prec=prec, rows=W)
+        if trace:
+            steps.append((W, cand))
+        sources = {}
+        for i, v in enumerate(W):
+            for u in new_rows[i]:
+                if u >= 0:
+                    sources.setdefault(int(u), []).append(int(v))
+        nbr[W] = new_rows
+        if sources:
+            U = np.array(sorted(sources), np.int64)
+            cu = np.full((len(U), R + rev_cap), -1, np.int64)
+            for i, u in enumerate(U):
+                row = [int(x) for x in nbr[u] if x >= 0] + sorted(sources[int(u)])[:rev_cap]
+                cu[i, :len(row)] = row
+            nbr[U], _ = edge_select(X, A, cu, R, weights=weights, prec=prec, rows=U)
+    return (nbr, steps) if trace else nbr
+
+
 def graph_quality(nbr, knn_ids) -> float:
     nbr, knn_ids = _i64(nbr), _i64(knn_ids)
     return float(_L().or_graph_quality(_p(nbr), nbr.shape[0], nbr.shape[1], _p(knn_ids),

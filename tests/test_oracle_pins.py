@@ -501,3 +501,41 @@ def test_curve_i_brute_force_returns_the_smallest_matching_ids(oracle_mod):
         match = np.nonzero((w.A == w.QA[q]).all(axis=1))[0]
         assert len(match) >= 5
         assert (ids[q] == match[:5]).all() and (g[q] == 0).all() and (chi[q] == 0).all()
+
+
+# ------------------------------------------------------------------ incremental build (NPG_nsw)
+def test_nsw_waves_cover_every_vertex_once(oracle_mod):
+    O = oracle_mod
+    for N, cap in ((1, 8), (2, 8), (100, 8), (1000, 64)):
+        waves = O.nsw_waves(N, cap)
+        covered = [v for s, e in waves for v in range(s, e)]
+        assert covered == list(range(1, N))
+        assert all(e - s <= min(s, cap) for s, e in waves)
+
+
+def test_nsw_insertion_search_is_exhaustive_on_a_small_prefix(oracle_mod):
+    # with waves of one vertex and every earlier vertex a seed (s <= 32), each insertion
+    # evaluates all of [0, v): its candidates are the exact fused top-L of the prefix
+    O = oracle_mod
+    w = synth.int_valued(33, 1, 8, cards=(2, 3), seed=21)
+    for weights in (None, (1.0, 10000.0)):
+        _, steps = O.build_nsw(w.X, w.A, R=4, L=40, weights=weights, wave_max=1, trace=True)
+        assert len(steps) == 32
+        for W, cand in steps:
+            v = int(W[0])
+            ref, _, _ = O.fused_topk(w.X[:v], w.A[:v], w.X[v:v + 1], w.A[v:v + 1], min(40, v),
+                                     weights=weights, prec=O.F32)
+            assert (cand[0, :v] == ref[0]).all() and (cand[0, v:] == -1).all()
+
+
+def test_nsw_graph_is_well_formed(oracle_mod):
+    O = oracle_mod
+    w = synth.int_valued(400, 1, 8, cards=(2, 3), seed=22)
+    nbr = O.build_nsw(w.X, w.A, R=8, L=24, wave_max=16)
+    assert nbr.shape == (400, 8)
+    for u in range(400):
+        row = nbr[u][nbr[u] >= 0]
+        # vertex 0 gains its edges from later insertions; every other vertex keeps at least
+        # the nearest vertex its search found
+        assert len(row) >= 1
+        assert u not in row and len(set(row.tolist())) == len(row) and (row < 400).all()
