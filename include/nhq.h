@@ -229,6 +229,21 @@ nhq_status nhq_index_get_graph(const nhq_index *index, uint32_t *nbr, void *stre
 nhq_status nhq_index_build(nhq_index *index, int32_t degree, const nhq_build_params *params,
                            void *stream);
 
+/*
+ * Incremental build (NPG_nsw of Sec. 4.3), batched into insertion waves: vertex 0 alone,
+ * then waves [s, e) of 1, 2, 4, ... vertices (at most wave_max).  Every vertex of a wave
+ * searches the graph of [0, s) (Alg. 2 with k = ef = L from min(32, s) entry points: the
+ * consecutive ids (h + j) mod s, h = splitmix64(seed ^ mix64(v))[0] mod s) and keeps a
+ * landing-zone selection of the result (Def. 6, degree R); then every earlier vertex u it
+ * selected re-selects from N(u) plus its new sources (ascending ids, at most rev_cap).
+ * Every wave sees the graph as it was when the wave began, so the result is
+ * deterministic.  Replaces the index's graph.
+ * Errors: degree outside 1..64, L outside degree..128, degree + rev_cap > 128,
+ * wave_max outside 1..65536.
+ */
+nhq_status nhq_index_build_nsw(nhq_index *index, int32_t degree, int32_t L, int32_t wave_max,
+                               int32_t rev_cap, uint64_t seed, void *stream);
+
 /* build(vectors, attributes, degree, weights): nhq_index_create + nhq_index_build. */
 nhq_status nhq_build(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
                      int32_t m, int32_t degree, nhq_weights w, const nhq_build_params *params,

@@ -30,7 +30,7 @@ __all__ = [
     "nhq_brute_force_noalloc", "nhq_search_trace", "nhq_mlp_forward", "nhq_mlp_grad",
     "nhq_mlp_train", "MLP_INPUTS", "MLP_HIDDEN", "MLP_PARAMS", "nhq_autotune_search",
     "nhq_search_graph_create", "nhq_search_graph_launch", "nhq_search_graph_free",
-    "nhq_merge_topk", "nhq_postfilter", "nhq_knn_nndescent",
+    "nhq_merge_topk", "nhq_postfilter", "nhq_knn_nndescent", "nhq_index_build_nsw",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -99,6 +99,7 @@ def load_library():
             "nhq_knn": (S, [P, i32, P, P, P]),
             "nhq_knn_bf16": (S, [P, i32, P, P, P]),
             "nhq_knn_nndescent": (S, [P, i32, i32, C.c_uint64, P, P, P, P]),
+            "nhq_index_build_nsw": (S, [P, i32, i32, i32, i32, C.c_uint64, P]),
             "nhq_edge_select": (S, [P, P, i32, i32, P, P]),
             "nhq_reverse_candidates": (S, [P, P, i32, i32, P, P]),
             "nhq_index_set_graph": (S, [P, P, i32, P]),
@@ -262,6 +263,14 @@ def nhq_knn_nndescent(index, K, cand_ids, cand_dist=None, max_iters=12, seed=0x2
         _ptr(cand_ids, np.uint32, (N, K), "cand_ids"),
         _ptr(cand_dist, np.float32, (N, K), "cand_dist"), C.byref(it), _stream(stream)))
     return it.value
+
+
+def nhq_index_build_nsw(index, degree, L=64, wave_max=4096, rev_cap=64, seed=0,
+                        stream=None) -> None:
+    """Incremental build (insertion waves) of the index's graph; see include/nhq.h."""
+    _check(load_library().nhq_index_build_nsw(index, degree, L, wave_max, rev_cap,
+                                              C.c_uint64(int(seed) & (2**64 - 1)),
+                                              _stream(stream)))
 
 
 def nhq_edge_select(index, cand_ids, R, nbr_out, stream=None) -> None:

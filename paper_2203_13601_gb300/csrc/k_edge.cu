@@ -34,6 +34,8 @@ struct EdgeArgs {
     uint32_t *out;
     int staged;  // candidate rows live in shared memory
     int rstride; // floats per staged row
+    const uint32_t *rows;  // vertex of block b: rows[b], or row0 + b when rows is null;
+    int64_t row0;          // cand and out are indexed by b
 };
 
 // squared distance between two rows, one team of T lanes (T = 4 or 8); result in
@@ -98,12 +100,13 @@ __global__ void __launch_bounds__(ES_THREADS) edge_select_kernel(EdgeArgs a) {
     constexpr int T4 = 4, TEAMS4 = ES_THREADS / T4;  // teams of 4 lanes
     const int team = tid / T4, tl = tid % T4;
     const int xs4 = a.xstride / 4;
-    const int64_t u = blockIdx.x;
+    const int64_t b = blockIdx.x;
+    const int64_t u = a.rows ? (int64_t)a.rows[b] : a.row0 + b;
     const uint32_t au = a.attr[u];
 
     // 1. candidate ids (invalid, self and out-of-range dropped) in list order
     {
-        const uint32_t p = tid < a.L ? a.cand[u * a.L + tid] : kNone;
+        const uint32_t p = tid < a.L ? a.cand[b * a.L + tid] : kNone;
         const bool ok = p != kNone && (int64_t)p < a.N && (int64_t)p != u;
         const unsigned bal = __ballot_sync(FULL, ok);
         if (lane == 0)
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(ES_THREADS) edge_select_kernel(EdgeArgs a) {
     }
     __syncthreads();
     for (int s2 = tid; s2 < R; s2 += ES_THREADS)
-        a.out[u * R + s2] = s2 < deg ? acc_id[s2] : kNone;
+        a.out[b * R + s2] = s2 < deg ? acc_id[s2] : kNone;
 }
 
 // ---------------------------------------------------------------- reverse pass
@@ -319,8 +322,9 @@ inline int grid_for(int64_t n) {
 
 }  // namespace
 
-cudaError_t launch_edge_select(const nhq_index *ix, const uint32_t *cand, int L, int R,
-                               uint32_t *out, cudaStream_t s) {
+cudaError_t launch_edge_select_rows(const nhq_index *ix, const uint32_t *cand, int L, int R,
+                                    const uint32_t *rows, int64_t row0, int64_t count,
+                                    uint32_t *out, cudaStream_t s) {
     EdgeArgs a;
     a.X = ix->X;
     a.xstride = ix->xstride;
@@ -333,6 +337,8 @@ cudaError_t launch_edge_select(const nhq_index *ix, const uint32_t *cand, int L,
     a.R = R;
     a.out = out;
     a.rstride = ix->xstride + 4;
+    a.rows = rows;
+    a.row0 = row0;
     size_t fixed = sizeof(unsigned long long) * kMaxCand +
                    (sizeof(uint32_t) + 4 * sizeof(int) + sizeof(float)) * kMaxCand +
                    sizeof(uint32_t) * (kMaxDegree + kMaxCand) + 4 * sizeof(int);
@@ -344,9 +350,14 @@ cudaError_t launch_edge_select(const nhq_index *ix, const uint32_t *cand, int L,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    if (ix->N > 0)
-        edge_select_kernel<<<(unsigned)ix->N, ES_THREADS, smem, s>>>(a);
+    if (count > 0)
+        edge_select_kernel<<<(unsigned)count, ES_THREADS, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_edge_select(const nhq_index *ix, const uint32_t *cand, int L, int R,
+                               uint32_t *out, cudaStream_t s) {
+    return launch_edge_select_rows(ix, cand, L, R, nullptr, 0, ix->N, out, s);
 }
 
 size_t reverse_scratch_bytes(int64_t N, int R) {

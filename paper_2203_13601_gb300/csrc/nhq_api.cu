@@ -535,6 +535,115 @@ nhq_status nhq_index_build(nhq_index *ix, int32_t degree, const nhq_build_params
     return st;
 }
 
+nhq_status nhq_index_build_nsw(nhq_index *ix, int32_t degree, int32_t L, int32_t wave_max,
+                               int32_t rev_cap, uint64_t seed, void *stream) {
+    if (ix == nullptr)
+        return fail(NHQ_ERR_ARG, "index is NULL");
+    if (degree < 1 || degree > kMaxDegree)
+        return fail(NHQ_ERR_ARG, "degree must be in 1..64 (got %d)", degree);
+    if (L < degree || L > kMaxCand)
+        return fail(NHQ_ERR_ARG, "L must be in degree..128 (got %d)", L);
+    if (rev_cap < 0 || degree + rev_cap > kMaxCand)
+        return fail(NHQ_ERR_ARG, "degree + rev_cap must be at most 128");
+    if (wave_max < 1 || wave_max > 65536)
+        return fail(NHQ_ERR_ARG, "wave_max must be in 1..65536 (got %d)", wave_max);
+    cudaStream_t s = as_stream(stream);
+    const int64_t N = ix->N, R = degree;
+    const int64_t Bmax = std::min<int64_t>(wave_max, std::max<int64_t>(N - 1, 1));
+    const int W = R + rev_cap;
+    const int ns = nsw_seed_count();
+    // the empty graph, then the wave buffers
+    uint32_t *empty = nullptr;
+    CK(cudaMalloc(&empty, sizeof(uint32_t) * (size_t)N * R));
+    CK(cudaMemsetAsync(empty, 0xFF, sizeof(uint32_t) * (size_t)N * R, s));
+    nhq_status st = install_graph(ix, empty, (int)R, s);
+    cudaFree(empty);
+    if (st != NHQ_OK)
+        return st;
+    const int64_t np = Bmax * R;
+    const size_t sort_bytes = nsw_sort_scratch_bytes(np);
+    std::vector<void *> bufs;
+    auto get = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes < 256 ? 256 : bytes) != cudaSuccess)
+            return nullptr;
+        bufs.push_back(p);
+        return p;
+    };
+    auto release = [&]() {
+        cudaStreamSynchronize(s);
+        for (void *p : bufs)
+            cudaFree(p);
+    };
+    float *q = (float *)get(sizeof(float) * Bmax * ix->d);
+    uint8_t *qa = (uint8_t *)get((size_t)Bmax * ix->m);
+    uint32_t *seeds = (uint32_t *)get(sizeof(uint32_t) * Bmax * ns);
+    uint32_t *cand = (uint32_t *)get(sizeof(uint32_t) * Bmax * L);
+    uint32_t *rows = (uint32_t *)get(sizeof(uint32_t) * Bmax * R);
+    unsigned long long *keys = (unsigned long long *)get(8 * np);
+    unsigned long long *sorted = (unsigned long long *)get(8 * np);
+    void *tmp = get(sort_bytes);
+    uint32_t *seg = (uint32_t *)get(sizeof(uint32_t) * np);
+    int *nseg_dev = (int *)get(sizeof(int));
+    uint32_t *U = (uint32_t *)get(sizeof(uint32_t) * np);
+    uint32_t *candU = (uint32_t *)get(sizeof(uint32_t) * np * W);
+    uint32_t *upd = (uint32_t *)get(sizeof(uint32_t) * np * R);
+    for (void *p : bufs)
+        if (p == nullptr) {
+            release();
+            return fail(NHQ_ERR_OOM, "cudaMalloc(incremental build buffers)");
+        }
+    if (bufs.size() != 13) {
+        release();
+        return fail(NHQ_ERR_OOM, "cudaMalloc(incremental build buffers)");
+    }
+    nhq_search_params P{};
+    P.h = 1;
+    P.seed_mode = NHQ_SEED_GIVEN;
+    P.n_seeds = ns;
+    P.seeds = seeds;
+    cudaError_t e = cudaSuccess;
+    for (int64_t s0 = 1; s0 < N && st == NHQ_OK && e == cudaSuccess;) {
+        const int64_t B = std::min<int64_t>(std::min<int64_t>(s0, wave_max), N - s0);
+        if ((e = launch_nsw_seeds(s0, B, seed, seeds, s)) != cudaSuccess ||
+            (e = launch_nsw_queries(ix, s0, B, q, qa, s)) != cudaSuccess)
+            break;
+        st = nhq_search(ix, q, qa, B, L, L, &P, cand, nullptr, nullptr, nullptr, nullptr, nullptr,
+                        stream);
+        if (st != NHQ_OK)
+            break;
+        if ((e = launch_edge_select_rows(ix, cand, L, (int)R, nullptr, s0, B, rows, s)) !=
+                cudaSuccess ||
+            (e = launch_nsw_pairs(rows, (int)R, s0, B, keys, sorted, tmp, sort_bytes, seg,
+                                  nseg_dev, s)) != cudaSuccess)
+            break;
+        int nseg = 0;
+        if ((e = cudaMemcpyAsync(&nseg, nseg_dev, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            break;
+        if (nseg > 0 &&
+            ((e = launch_nsw_reverse(sorted, B * R, seg, nseg, ix->nbr, (int)R, rev_cap, U,
+                                     candU, s)) != cudaSuccess ||
+             (e = launch_edge_select_rows(ix, candU, W, (int)R, U, 0, nseg, upd, s)) !=
+                 cudaSuccess))
+            break;
+        // both selections read the graph as the wave began; now write the rows
+        if ((e = launch_nsw_install(rows, nullptr, s0, B, (int)R, ix->attr, ix->nbr,
+                                    ix->nbr_attr, s)) != cudaSuccess ||
+            (e = launch_nsw_install(upd, U, 0, nseg, (int)R, ix->attr, ix->nbr, ix->nbr_attr,
+                                    s)) != cudaSuccess)
+            break;
+        s0 += B;
+    }
+    release();
+    if (st != NHQ_OK)
+        return st;
+    if (e != cudaSuccess)
+        return fail_cuda(e, "incremental build");
+    return NHQ_OK;
+}
+
 nhq_status nhq_build(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
                      int32_t m, int32_t degree, nhq_weights w, const nhq_build_params *params,
                      void *stream, nhq_index **out) {

@@ -157,6 +157,26 @@ cudaError_t launch_topk(const TopkArgs &a, void *scratch, size_t scratch_bytes, 
                         cudaStream_t s);
 
 // k_edge.cu
+// landing-zone selection for the vertices rows[b] (or row0 + b), candidate row b -> out row b
+cudaError_t launch_edge_select_rows(const nhq_index *ix, const uint32_t *cand, int L, int R,
+                                    const uint32_t *rows, int64_t row0, int64_t count,
+                                    uint32_t *out, cudaStream_t s);
+// incremental build: the per-wave kernels of k_nsw.cu
+int nsw_seed_count();
+cudaError_t launch_nsw_seeds(int64_t s, int64_t B, uint64_t seed, uint32_t *seeds, cudaStream_t st);
+cudaError_t launch_nsw_queries(const nhq_index *ix, int64_t s, int64_t B, float *q, uint8_t *qa,
+                               cudaStream_t st);
+size_t nsw_sort_scratch_bytes(int64_t n);
+cudaError_t launch_nsw_pairs(const uint32_t *rows, int R, int64_t s, int64_t B,
+                             unsigned long long *keys, unsigned long long *sorted, void *tmp,
+                             size_t tmp_bytes, uint32_t *seg_start, int *nseg_dev,
+                             cudaStream_t st);
+cudaError_t launch_nsw_reverse(const unsigned long long *sorted, int64_t n,
+                               const uint32_t *seg_start, int nseg, const uint32_t *nbr, int R,
+                               int cap, uint32_t *U, uint32_t *cand, cudaStream_t st);
+cudaError_t launch_nsw_install(const uint32_t *src, const uint32_t *list, int64_t row0,
+                               int64_t count, int R, const uint32_t *attr, uint32_t *nbr,
+                               uint32_t *nbr_attr, cudaStream_t st);
 cudaError_t launch_edge_select(const nhq_index *ix, const uint32_t *cand, int L, int R,
                                uint32_t *out, cudaStream_t s);
 size_t reverse_scratch_bytes(int64_t N, int R);
