@@ -66,13 +66,14 @@ def parse():
     ap.add_argument("--learned-efs", default="16,24,32,48,64")
     ap.add_argument("--taus", default="0.7,0.8,0.9,0.95")
     ap.add_argument("--workload", default="c2",
-                    choices=["c2", "c4", "c5", "strategies", "curves"],
+                    choices=["c2", "c4", "c5", "strategies", "curves", "builds"],
                     help="c2: the headline workload (default); c4: the heterogeneous batch "
                          "(1M x 96, 100k queries with mixed k and ef) through "
                          "nhq_search_batched; c5: the 10M x 96 set (f16-valued), 50k queries; "
                          "strategies: NHQ against post-filtering on a "
                          "plain L2 graph and exact pre-filtering, on the c2 workload; curves: "
-                         "the weightings i-v of Sec. 6.5 on the c2 workload; each "
+                         "the weightings i-v of Sec. 6.5 on the c2 workload; builds: exact "
+                         "candidates, NN-descent and the incremental build compared; each "
                          "prints one JSON line of its own")
     return ap.parse_args()
 
@@ -527,6 +528,79 @@ def curves_arm(a):
                       "curves": rows}), flush=True)
 
 
+# ---------------------------------------------------------------- build methods
+def builds_arm(a):
+    """The ways to build the composite index on the c2 workload (constant weights,
+    R = 32): NPG_kgraph on exact candidate sets (tensor cores), NPG_kgraph on NN-descent
+    candidate sets (Sec. 4.3), and the incremental NPG_nsw build in insertion waves; for
+    each the build time and the cheapest ef reaching hybrid Recall@10 >= target."""
+    import torch
+
+    import paper_2203_13601_gb300 as nhq
+    from paper_2203_13601_gb300 import build as B
+
+    B.build()
+    nhq.load_library()
+    dev = torch.device("cuda", 0)
+    w = make_workload(a)
+    X, A = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.A).to(dev)
+    Qv, QA = torch.from_numpy(w.Qv).to(dev), torch.from_numpy(w.QA).to(dev)
+    k = a.k
+    mult = np.array([1, 256, 65536])[: w.m]
+    codes, qcodes = (w.A.astype(np.int64) * mult).sum(1), (w.QA.astype(np.int64) * mult).sum(1)
+    uniq, cnt = np.unique(codes, return_counts=True)
+    pos = np.minimum(np.searchsorted(uniq, qcodes), len(uniq) - 1)
+    P = np.where(uniq[pos] == qcodes, cnt[pos], 0)
+    ids, dd, ch = (torch.empty((w.nq, k), dtype=torch.uint32, device=dev),
+                   torch.empty((w.nq, k), dtype=torch.float32, device=dev),
+                   torch.empty((w.nq, k), dtype=torch.uint8, device=dev))
+    gt = torch.empty((w.nq, k), dtype=torch.uint32, device=dev)
+    rows, gt_h = [], None
+
+    def make(method):
+        if method == "kgraph_exact":
+            return nhq.Index.build(X, A, degree=a.R, weights=CONST_W, K=64, knn_dtype=1)
+        if method == "kgraph_nndescent":
+            return nhq.Index.build(X, A, degree=a.R, weights=CONST_W, K=64, knn_dtype=2)
+        ix = nhq.Index.create(X, A, CONST_W)
+        nhq.nhq_index_build_nsw(ix.handle, a.R, L=64, wave_max=4096, rev_cap=64, seed=7,
+                                entry=1 if method == "nsw_attribute_entry" else 0)
+        return ix
+
+    for method in ("kgraph_exact", "kgraph_nndescent", "nsw_id_entry", "nsw_attribute_entry"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = make(method)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        if gt_h is None:
+            nhq.nhq_brute_force(ix.handle, Qv, QA, k, gt, weights="filter")
+            gt_h = gt.cpu().numpy()
+        sweep = []
+        for ef in (16, 24, 32, 48, 64, 96, 128, 200):
+            run = lambda ef=ef: nhq.nhq_search(ix.handle, Qv, QA, k, ef, ids, dd, ch,
+                                               seed=12345, seed_mode=nhq.SEED_ATTRIBUTE)
+            for _ in range(2):
+                run()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            rec, _ = hybrid_recall(ids.cpu().numpy(), w.A, w.QA, gt_h, P, k)
+            ms = e0.elapsed_time(e1)
+            sweep.append({"ef": ef, "recall": rec, "ms": ms, "qps": w.nq / ms * 1e3})
+            if rec >= a.target:
+                break
+        ix.close()
+        best = sweep[-1] if sweep[-1]["recall"] >= a.target else max(sweep,
+                                                                        key=lambda r: r["recall"])
+        rows.append({"method": method, "build_s": t_build, "best": best, "sweep": sweep})
+    print(json.dumps({"metric": f"build time and QPS at hybrid Recall@{k} >= {a.target} per "
+                                "build method", "config": {"workload": workload_name(a)},
+                      "builds": rows}), flush=True)
+
+
 # ---------------------------------------------------------------- strategies
 def strategies_arm(a):
     """The paper's comparison (Sec. 6.2) inside this framework, on one GPU and the c2
@@ -733,6 +807,10 @@ def main():
     if a.workload == "curves":
         if rank == 0:
             curves_arm(a)
+        return
+    if a.workload == "builds":
+        if rank == 0:
+            builds_arm(a)
         return
 
     import torch

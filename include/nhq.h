@@ -236,13 +236,16 @@ nhq_status nhq_index_build(nhq_index *index, int32_t degree, const nhq_build_par
  * consecutive ids (h + j) mod s, h = splitmix64(seed ^ mix64(v))[0] mod s) and keeps a
  * landing-zone selection of the result (Def. 6, degree R); then every earlier vertex u it
  * selected re-selects from N(u) plus its new sources (ascending ids, at most rev_cap).
- * Every wave sees the graph as it was when the wave began, so the result is
- * deterministic.  Replaces the index's graph.
+ * entry = 1 takes the entry points by attributes instead: the earlier vertices whose
+ * attributes all equal v's, ascending, at most 32 evenly spaced (P[floor(j c / S)]), the
+ * id rule when there is none (under constant weights the graph separates by tuple, and
+ * the id rule rarely reaches v's own).  Every wave sees the graph as it was when the wave
+ * began, so the result is deterministic.  Replaces the index's graph.
  * Errors: degree outside 1..64, L outside degree..128, degree + rev_cap > 128,
- * wave_max outside 1..65536.
+ * wave_max outside 1..65536, entry not 0 or 1.
  */
 nhq_status nhq_index_build_nsw(nhq_index *index, int32_t degree, int32_t L, int32_t wave_max,
-                               int32_t rev_cap, uint64_t seed, void *stream);
+                               int32_t rev_cap, int32_t entry, uint64_t seed, void *stream);
 
 /* build(vectors, attributes, degree, weights): nhq_index_create + nhq_index_build. */
 nhq_status nhq_build(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,

@@ -266,22 +266,39 @@ def nsw_seeds(v, s, seed, n=32):
     return row + [-1] * (n - len(row))
 
 
+def nsw_attribute_seeds(v, s, A, seed, n=32):
+    """Attribute entry for vertex v's insertion search: P = the earlier vertices u < s whose
+    attributes all equal v's, ascending; c = |P| > 0: min(n, c) of them evenly spaced,
+    P[floor(j c / S)]; c = 0: the consecutive-id rule of nsw_seeds.  -1 pads the row."""
+    P = np.nonzero((A[:s] == A[v]).all(axis=1))[0]
+    c = len(P)
+    if c == 0:
+        return nsw_seeds(v, s, seed, n)
+    S = min(n, c)
+    row = [int(P[(j * c) // S]) for j in range(S)]
+    return row + [-1] * (n - S)
+
+
 def build_nsw(X, A, R=32, L=64, weights=None, seed=0, wave_max=4096, rev_cap=64, prec=F32,
-              trace=False):
+              trace=False, entry=0):
     """Incremental build (NPG_nsw of Sec. 4.3, batched into insertion waves): the vertices
     of a wave [s, e) each search the graph of [0, s) (Alg. 2 with the nsw_seeds entry
     points, k = ef = L) for their candidates and keep a landing-zone selection of them
     (Def. 6); then every earlier vertex u that one of them selected re-selects its
     neighbours from N(u) plus those new sources (ascending ids, at most rev_cap).  Every
     wave sees the graph as it was when the wave began.  With trace=True also returns the
-    candidate lists of every wave."""
+    candidate lists of every wave.  entry = 1 takes the entry points by attributes
+    (nsw_attribute_seeds) instead of by id (nsw_seeds)."""
     X, A = _f32(X), _u8(A)
     N = X.shape[0]
     nbr = np.full((N, R), -1, np.int64)
     steps = []
     for s, e in nsw_waves(N, wave_max):
         W = np.arange(s, e)
-        seeds = np.array([nsw_seeds(int(v), s, seed) for v in W], np.int64)
+        if entry == 1:
+            seeds = np.array([nsw_attribute_seeds(int(v), s, A, seed) for v in W], np.int64)
+        else:
+            seeds = np.array([nsw_seeds(int(v), s, seed) for v in W], np.int64)
         r = search(X, A, nbr, X[W], A[W], L, L, seeds=seeds, weights=weights, prec=prec)
         cand = r["ids"]
         new_rows, _ = edge_select(X, A, cand, R, weights=weights, prec=prec, rows=W)

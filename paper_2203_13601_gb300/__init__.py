@@ -99,7 +99,7 @@ def load_library():
             "nhq_knn": (S, [P, i32, P, P, P]),
             "nhq_knn_bf16": (S, [P, i32, P, P, P]),
             "nhq_knn_nndescent": (S, [P, i32, i32, C.c_uint64, P, P, P, P]),
-            "nhq_index_build_nsw": (S, [P, i32, i32, i32, i32, C.c_uint64, P]),
+            "nhq_index_build_nsw": (S, [P, i32, i32, i32, i32, i32, C.c_uint64, P]),
             "nhq_edge_select": (S, [P, P, i32, i32, P, P]),
             "nhq_reverse_candidates": (S, [P, P, i32, i32, P, P]),
             "nhq_index_set_graph": (S, [P, P, i32, P]),
@@ -265,10 +265,11 @@ def nhq_knn_nndescent(index, K, cand_ids, cand_dist=None, max_iters=12, seed=0x2
     return it.value
 
 
-def nhq_index_build_nsw(index, degree, L=64, wave_max=4096, rev_cap=64, seed=0,
+def nhq_index_build_nsw(index, degree, L=64, wave_max=4096, rev_cap=64, seed=0, entry=0,
                         stream=None) -> None:
-    """Incremental build (insertion waves) of the index's graph; see include/nhq.h."""
-    _check(load_library().nhq_index_build_nsw(index, degree, L, wave_max, rev_cap,
+    """Incremental build (insertion waves) of the index's graph; entry 0 = entry points by
+    id, 1 = by attributes; see include/nhq.h."""
+    _check(load_library().nhq_index_build_nsw(index, degree, L, wave_max, rev_cap, entry,
                                               C.c_uint64(int(seed) & (2**64 - 1)),
                                               _stream(stream)))
 

@@ -2,7 +2,10 @@
 // insertion waves; the search and the landing-zone selection are the kernels of
 // k_search.cu and k_edge.cu):
 //   seeds    entry points of each new vertex v in the graph of [0, s): min(32, s)
-//            consecutive ids (h + j) mod s from h = splitmix64(seed ^ mix64(v))[0] mod s
+//            consecutive ids (h + j) mod s from h = splitmix64(seed ^ mix64(v))[0] mod s;
+//            or (attribute entry) the earlier vertices whose attributes equal v's, at most
+//            32 evenly spaced, from the index's sorted attribute table (ids ascending
+//            within a tuple, so the earlier ones are a prefix of the tuple's run)
 //   queries  the wave's rows as a contiguous query batch, attributes unpacked
 //   pairs    every selected edge v -> u of the wave as the key u << 32 | v; after a
 //            radix sort the keys of one u are contiguous and ascending in v
@@ -30,6 +33,43 @@ __global__ void nsw_seeds_kernel(int64_t s, int64_t B, uint64_t seed, uint32_t *
     const uint64_t v = (uint64_t)(s + b);
     const uint64_t h = splitmix_at(seed ^ mix64(v), 0) % (uint64_t)s;
     seeds[i] = (int64_t)j < s ? (uint32_t)((h + (uint64_t)j) % (uint64_t)s) : kNone;
+}
+
+__device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *a, int64_t n, uint32_t x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__global__ void nsw_attr_seeds_kernel(int64_t s, int64_t B, uint64_t seed,
+                                      const uint32_t *__restrict__ attr,
+                                      const uint32_t *__restrict__ attr_sorted,
+                                      const uint32_t *__restrict__ id_sorted, int64_t N,
+                                      uint32_t *__restrict__ seeds) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= B)
+        return;
+    const int64_t v = s + b;
+    const uint32_t av = attr[v];
+    const int64_t lo = lower_bound_u32(attr_sorted, N, av);
+    const int64_t hi = av == 0xFFFFFFFFu ? N : lower_bound_u32(attr_sorted, N, av + 1u);
+    const int64_t c = lower_bound_u32(id_sorted + lo, hi - lo, (uint32_t)s);  // ids < s
+    uint32_t *row = seeds + b * NSW_SEEDS;
+    if (c > 0) {
+        const int64_t S = c < NSW_SEEDS ? c : NSW_SEEDS;
+        for (int j = 0; j < NSW_SEEDS; ++j)
+            row[j] = j < S ? id_sorted[lo + ((int64_t)j * c) / S] : kNone;
+    } else {
+        const uint64_t h = splitmix_at(seed ^ mix64((uint64_t)v), 0) % (uint64_t)s;
+        for (int j = 0; j < NSW_SEEDS; ++j)
+            row[j] = (int64_t)j < s ? (uint32_t)((h + (uint64_t)j) % (uint64_t)s) : kNone;
+    }
 }
 
 __global__ void nsw_queries_kernel(const float *__restrict__ X, int xstride, int d,
@@ -112,6 +152,13 @@ int nsw_seed_count() { return NSW_SEEDS; }
 cudaError_t launch_nsw_seeds(int64_t s, int64_t B, uint64_t seed, uint32_t *seeds,
                              cudaStream_t st) {
     nsw_seeds_kernel<<<blocks_for(B * NSW_SEEDS), 256, 0, st>>>(s, B, seed, seeds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nsw_attr_seeds(const nhq_index *ix, int64_t s, int64_t B, uint64_t seed,
+                                  uint32_t *seeds, cudaStream_t st) {
+    nsw_attr_seeds_kernel<<<blocks_for(B), 256, 0, st>>>(s, B, seed, ix->attr, ix->attr_sorted,
+                                                          ix->id_sorted, ix->N, seeds);
     return cudaGetLastError();
 }
 

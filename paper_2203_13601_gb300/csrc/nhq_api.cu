@@ -536,7 +536,7 @@ nhq_status nhq_index_build(nhq_index *ix, int32_t degree, const nhq_build_params
 }
 
 nhq_status nhq_index_build_nsw(nhq_index *ix, int32_t degree, int32_t L, int32_t wave_max,
-                               int32_t rev_cap, uint64_t seed, void *stream) {
+                               int32_t rev_cap, int32_t entry, uint64_t seed, void *stream) {
     if (ix == nullptr)
         return fail(NHQ_ERR_ARG, "index is NULL");
     if (degree < 1 || degree > kMaxDegree)
@@ -547,7 +547,11 @@ nhq_status nhq_index_build_nsw(nhq_index *ix, int32_t degree, int32_t L, int32_t
         return fail(NHQ_ERR_ARG, "degree + rev_cap must be at most 128");
     if (wave_max < 1 || wave_max > 65536)
         return fail(NHQ_ERR_ARG, "wave_max must be in 1..65536 (got %d)", wave_max);
+    if (entry != 0 && entry != 1)
+        return fail(NHQ_ERR_ARG, "entry must be 0 (by id) or 1 (by attributes)");
     cudaStream_t s = as_stream(stream);
+    if (entry == 1)
+        CKS(ensure_attribute_order(ix, s));
     const int64_t N = ix->N, R = degree;
     const int64_t Bmax = std::min<int64_t>(wave_max, std::max<int64_t>(N - 1, 1));
     const int W = R + rev_cap;
@@ -605,7 +609,8 @@ nhq_status nhq_index_build_nsw(nhq_index *ix, int32_t degree, int32_t L, int32_t
     cudaError_t e = cudaSuccess;
     for (int64_t s0 = 1; s0 < N && st == NHQ_OK && e == cudaSuccess;) {
         const int64_t B = std::min<int64_t>(std::min<int64_t>(s0, wave_max), N - s0);
-        if ((e = launch_nsw_seeds(s0, B, seed, seeds, s)) != cudaSuccess ||
+        if ((e = entry == 1 ? launch_nsw_attr_seeds(ix, s0, B, seed, seeds, s)
+                            : launch_nsw_seeds(s0, B, seed, seeds, s)) != cudaSuccess ||
             (e = launch_nsw_queries(ix, s0, B, q, qa, s)) != cudaSuccess)
             break;
         st = nhq_search(ix, q, qa, B, L, L, &P, cand, nullptr, nullptr, nullptr, nullptr, nullptr,

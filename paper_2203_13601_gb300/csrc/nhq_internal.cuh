@@ -166,6 +166,8 @@ int nsw_seed_count();
 cudaError_t launch_nsw_seeds(int64_t s, int64_t B, uint64_t seed, uint32_t *seeds, cudaStream_t st);
 cudaError_t launch_nsw_queries(const nhq_index *ix, int64_t s, int64_t B, float *q, uint8_t *qa,
                                cudaStream_t st);
+cudaError_t launch_nsw_attr_seeds(const nhq_index *ix, int64_t s, int64_t B, uint64_t seed,
+                                  uint32_t *seeds, cudaStream_t st);
 size_t nsw_sort_scratch_bytes(int64_t n);
 cudaError_t launch_nsw_pairs(const uint32_t *rows, int R, int64_t s, int64_t B,
                              unsigned long long *keys, unsigned long long *sorted, void *tmp,

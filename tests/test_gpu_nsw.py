@@ -29,14 +29,16 @@ def nhq():
     return m
 
 
+@pytest.mark.parametrize("entry", [0, 1])
 @pytest.mark.parametrize("weights", [None, CONST])
-def test_incremental_build_matches_oracle(nhq, weights):
+def test_incremental_build_matches_oracle(nhq, weights, entry):
     w = synth.int_valued(3001, 80, 32, cards=(3, 5, 7), n_comp=20, seed=97)
     R, L, wave_max, cap = 16, 48, 128, 32
     ref = O.build_nsw(w.X, w.A, R=R, L=L, weights=weights, seed=5, wave_max=wave_max,
-                      rev_cap=cap)
+                      rev_cap=cap, entry=entry)
     with nhq.Index.create(dev(w.X), dev(w.A), weights) as ix:
-        nhq.nhq_index_build_nsw(ix.handle, R, L=L, wave_max=wave_max, rev_cap=cap, seed=5)
+        nhq.nhq_index_build_nsw(ix.handle, R, L=L, wave_max=wave_max, rev_cap=cap, seed=5,
+                                entry=entry)
         g = torch.empty((w.N, R), dtype=torch.uint32, device="cuda:0")
         nhq.nhq_index_get_graph(ix.handle, g)
         ids, gg, chi = empty_out(w.nq, 10)

@@ -539,3 +539,15 @@ def test_nsw_graph_is_well_formed(oracle_mod):
         # the nearest vertex its search found
         assert len(row) >= 1
         assert u not in row and len(set(row.tolist())) == len(row) and (row < 400).all()
+
+
+def test_nsw_attribute_entry_picks_earlier_matches(oracle_mod):
+    O = oracle_mod
+    A = np.array([[0, 1], [1, 1], [0, 1], [0, 0], [0, 1], [1, 1]], np.uint8)
+    # vertex 4 (0, 1) among [0, 4): matches 0 and 2
+    assert O.nsw_attribute_seeds(4, 4, A, 0)[:3] == [0, 2, -1]
+    # vertex 3 (0, 0) has no earlier match: the id rule
+    assert O.nsw_attribute_seeds(3, 3, A, 9) == O.nsw_seeds(3, 3, 9)
+    # evenly spaced when there are more matches than seeds
+    big = np.zeros((100, 1), np.uint8)
+    assert O.nsw_attribute_seeds(99, 96, big, 0, n=4) == [0, 24, 48, 72]
