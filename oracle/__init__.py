@@ -326,7 +326,7 @@ def graph_quality(nbr, knn_ids) -> float:
                                        knn_ids.shape[1]))
 
 
-SEED_RANDOM, SEED_ATTRIBUTE, SEED_GIVEN = 0, 1, 2
+SEED_RANDOM, SEED_ATTRIBUTE, SEED_GIVEN, SEED_ATTRIBUTE_NEAR = 0, 1, 2, 3
 
 
 ROUND_NONE, ROUND_BF16, ROUND_E4M3 = 0, 1, 2

@@ -86,6 +86,18 @@ double or_delta64(const float *x, const float *y, int d)
 }
 
 /* Eq. 1 in float, summed in index order */
+/* delta^2 in float, summed in index order (no square root) */
+float or_dist2_32(const float *x, const float *y, int d)
+{
+    float s = 0.0f;
+    for (int i = 0; i < d; ++i) {
+        float t = x[i] - y[i];
+        float t2 = t * t;
+        s = s + t2;
+    }
+    return s;
+}
+
 float or_delta32(const float *x, const float *y, int d)
 {
     float s = 0.0f;
@@ -494,7 +506,11 @@ static int pool_insert(pool_t *pool, int *n, int ef, double g, int64_t id)
  *   seed_mode 1  attribute entry: P = the objects whose attributes all equal the
  *                query's, in ascending id; with c = |P| >= 1 and S = min(ef, 32, c),
  *                B = { P[floor(j * c / S)] : j < S }; with c = 0, as mode 0
- *   seed_mode 2  given: the valid distinct ids of seeds_in[q][0..n_seeds), in order */
+ *   seed_mode 2  given: the valid distinct ids of seeds_in[q][0..n_seeds), in order
+ *   seed_mode 3  nearest attribute entry: P as in mode 1; the M = min(256, c) members
+ *                P[floor(j * c / M)], and of them the S = min(ef, 32, M) nearest to the
+ *                query by (delta^2 of the f32 rows, summed in index order, id);
+ *                with c = 0, as mode 0 */
 void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                const int64_t *nbr, int R, const float *Qv, const uint8_t *QA, int64_t nq,
                int k, int ef, int h, uint64_t seed, int64_t max_iters,
@@ -534,7 +550,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
         /* seed set B */
         int want = ef < 32 ? ef : 32;
         int64_t c = 0;
-        if (seed_mode == 1)
+        if (seed_mode == 1 || seed_mode == 3)
             for (int64_t v = 0; v < N; ++v)
                 c += or_chi(qa, A + v * (int64_t)m, m) == 0 ? 1 : 0;
         if (seed_mode == 2) {
@@ -548,6 +564,32 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                                       mode, wv, wl, prec, NULL);
                 pool_insert(pool, &n, ef, g, v);
             }
+        } else if (seed_mode == 3 && c > 0) {
+            const int M = c < 256 ? (int)c : 256;
+            rec_t *cm = (rec_t *)malloc(sizeof(rec_t) * (size_t)M);
+            int64_t rank = 0;
+            int j = 0;
+            for (int64_t v = 0; v < N && j < M; ++v) {
+                if (or_chi(qa, A + v * (int64_t)m, m) != 0)
+                    continue;
+                if (rank == ((int64_t)j * c) / M) {
+                    cm[j].g = (double)or_dist2_32(qv, X + v * (int64_t)d, d);
+                    cm[j].id = v;
+                    ++j;
+                }
+                ++rank;
+            }
+            qsort(cm, (size_t)M, sizeof(rec_t), rec_cmp);
+            const int S = want < M ? want : M;
+            for (int t = 0; t < S; ++t) {
+                const int64_t v = cm[t].id;
+                evaluated[v] = 1;
+                ++ndc;
+                double g = pair_gamma(qv, qa, Xs + v * (int64_t)d, A + v * (int64_t)m, d, m,
+                                      mode, wv, wl, prec, NULL);
+                pool_insert(pool, &n, ef, g, v);
+            }
+            free(cm);
         } else if (seed_mode == 1 && c > 0) {
             int S = (int64_t)want < c ? want : (int)c;
             int64_t rank = 0;  /* position of v within P */

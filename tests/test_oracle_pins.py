@@ -551,3 +551,21 @@ def test_nsw_attribute_entry_picks_earlier_matches(oracle_mod):
     # evenly spaced when there are more matches than seeds
     big = np.zeros((100, 1), np.uint8)
     assert O.nsw_attribute_seeds(99, 96, big, 0, n=4) == [0, 24, 48, 72]
+
+
+def test_nearest_attribute_entry_seeds_are_the_nearest_matches(oracle_mod):
+    # with |P| <= 256 every match is sampled, so the seed pool holds the min(ef, 32)
+    # nearest matches; with no expansion the top-k is the exact filtered top-k
+    O = oracle_mod
+    w = synth.int_valued(3000, 40, 16, cards=(3, 5, 4), seed=23)
+    CONST = (1.0, 10000.0)
+    nbr = np.full((w.N, 4), -1, np.int64)
+    r = O.search(w.X, w.A, nbr, w.Qv, w.QA, 10, 32, weights=CONST, max_iters=0,
+                 seed_mode=O.SEED_ATTRIBUTE_NEAR)
+    ref, _, P = O.filtered_topk(w.X, w.A, w.Qv, w.QA, 10, prec=O.F32)
+    checked = 0
+    for q in range(w.nq):
+        if 10 <= P[q] <= 256:
+            assert (r["ids"][q] == ref[q]).all(), q
+            checked += 1
+    assert checked >= 20
