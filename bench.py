@@ -65,6 +65,8 @@ def parse():
                     help="candidate build: 0 exact f32 SIMT, 1 bf16 tensor cores (exact here)")
     ap.add_argument("--learned-efs", default="16,24,32,48,64")
     ap.add_argument("--taus", default="0.7,0.8,0.9,0.95")
+    ap.add_argument("--c4-build", default="kgraph", choices=["kgraph", "nsw"],
+                    help="c4 workload: graph built from exact candidates or incrementally")
     ap.add_argument("--workload", default="c2",
                     choices=["c2", "c4", "c5", "strategies", "curves", "builds"],
                     help="c2: the headline workload (default); c4: the heterogeneous batch "
@@ -268,7 +270,11 @@ def c4_arm(a, rank, world, local):
     Qv, QA = torch.from_numpy(w.Qv).to(dev), torch.from_numpy(w.QA).to(dev)
     kd, efd = torch.from_numpy(k_arr).to(dev), torch.from_numpy(ef_arr).to(dev)
     t0 = time.perf_counter()
-    ix = nhq.Index.build(X, A, degree=a.R, weights=CONST_W, K=64, knn_dtype=1)
+    if a.c4_build == "nsw":
+        ix = nhq.Index.create(X, A, CONST_W)
+        nhq.nhq_index_build_nsw(ix.handle, a.R, L=64, wave_max=4096, rev_cap=64, seed=7, entry=1)
+    else:
+        ix = nhq.Index.build(X, A, degree=a.R, weights=CONST_W, K=64, knn_dtype=1)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
     gt = torch.empty((w.nq, kmax), dtype=torch.uint32, device=dev)
@@ -279,33 +285,49 @@ def c4_arm(a, rank, world, local):
     ndc = torch.empty(w.nq, dtype=torch.int32, device=dev)
     exps = torch.empty(w.nq, dtype=torch.int32, device=dev)
 
-    def run(diag=False):
+    def run(diag=False, mode=nhq.SEED_ATTRIBUTE_NEAR):
         nhq.nhq_search_batched(ix.handle, Qv, QA, kd, efd, kmax, ids, dists, None, st,
                                ndc=ndc if diag else None, expansions=exps if diag else None,
-                               seed=12345, seed_mode=nhq.SEED_ATTRIBUTE)
+                               seed=12345, seed_mode=mode)
 
-    run(diag=True)
-    torch.cuda.synchronize()
-    ids_h, gt_h = ids.cpu().numpy().astype(np.int64), gt.cpu().numpy().astype(np.int64)
-    ndc_h, exp_h = ndc.cpu().numpy().astype(np.float64), exps.cpu().numpy().astype(np.float64)
+    gt_h = gt.cpu().numpy().astype(np.int64)
     # hybrid recall with each query's own k (Sec. 6.1)
     mult = np.array([1, 256, 65536])[: w.m]
     codes, qcodes = (w.A.astype(np.int64) * mult).sum(1), (w.QA.astype(np.int64) * mult).sum(1)
     uniq, cnt = np.unique(codes, return_counts=True)
     pos = np.minimum(np.searchsorted(uniq, qcodes), len(uniq) - 1)
     P = np.where(uniq[pos] == qcodes, cnt[pos], 0)
-    rec = []
-    for q in range(w.nq):
-        kq = int(k_arr[q])
-        if P[q] == 0:
-            continue
-        got = ids_h[q, :kq]
-        got = got[got != 0xFFFFFFFF]
-        got = got[(w.A[got] == w.QA[q]).all(axis=1)]
-        g = gt_h[q, :kq]
-        g = g[g != 0xFFFFFFFF]
-        rec.append(len(set(got.tolist()) & set(g.tolist())) / min(kq, int(P[q])))
-    recall = float(np.mean(rec))
+    sel = P / w.N
+
+    def quality(mode):
+        run(diag=True, mode=mode)
+        torch.cuda.synchronize()
+        ids_h = ids.cpu().numpy().astype(np.int64)
+        nd, ex = ndc.cpu().numpy().astype(np.float64), exps.cpu().numpy().astype(np.float64)
+        recq = np.full(w.nq, np.nan)
+        for q in range(w.nq):
+            kq = int(k_arr[q])
+            if P[q] == 0:
+                continue
+            got = ids_h[q, :kq]
+            got = got[got != 0xFFFFFFFF]
+            got = got[(w.A[got] == w.QA[q]).all(axis=1)]
+            g = gt_h[q, :kq]
+            g = g[g != 0xFFFFFFFF]
+            recq[q] = len(set(got.tolist()) & set(g.tolist())) / min(kq, int(P[q]))
+        # per selectivity band (|P| / N of the query's tuple)
+        bands = []
+        for lo, hi in ((1e-4, 1e-3), (1e-3, 1e-2), (1e-2, 1e-1), (1e-1, 1.0)):
+            m_ = (sel >= lo) & (sel < hi) & ~np.isnan(recq)
+            if m_.any():
+                bands.append({"selectivity": [lo, hi], "queries": int(m_.sum()),
+                              "recall": float(np.nanmean(recq[m_])),
+                              "mean_expansions": float(ex[m_].mean()),
+                              "mean_ndc": float(nd[m_].mean())})
+        return float(np.nanmean(recq)), bands, nd, ex
+
+    recall_even, bands_even, _, _ = quality(nhq.SEED_ATTRIBUTE)
+    recall, bands, ndc_h, exp_h = quality(nhq.SEED_ATTRIBUTE_NEAR)
     bytes_q = ndc_h * (4 * w.d + 4) + exp_h * a.R * 4 + w.d * 4 + k_arr * 9
     alg_bytes = float(bytes_q.sum())
     for _ in range(max(3, a.warmup)):
@@ -344,8 +366,13 @@ def c4_arm(a, rank, world, local):
                                "5/20/100 correlated with the cluster, 100,000 queries with "
                                "log-uniform selectivity in [1e-4, 1/3], k in {1,10,100}, ef in "
                                "[max(16,k), 512], R=32, weights w_v=1 w_l=10000",
-                   "launch": "nhq_search_batched, attribute-entry seeds",
+                   "launch": "nhq_search_batched, nearest attribute-entry seeds",
                    "recall": recall, "recall_kind": "hybrid Recall@k (each query's own k)",
+                   "by_selectivity": bands,
+                   "graph": ("NPG_nsw, attribute entry, insertion waves" if a.c4_build == "nsw"
+                             else "NPG_kgraph, exact candidates K=64"),
+                   "evenly_spaced_seeds": {"recall": recall_even,
+                                           "by_selectivity": bands_even},
                    "mean_ef": float(ef_arr.mean()), "build_s": t_build,
                    "l2": "inputs larger than L2 (vectors 384 MB + adjacency 256 MB)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -1088,7 +1115,7 @@ def main():
                      "mean_expansions": float(exp_h.mean())},
         "e2e": {"value": w.nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "recall": e2e_rec},
-        "gpu_launches": a.steps * (3 if a.seed_mode == 1 else 1),
+        "gpu_launches": a.steps * (3 if a.seed_mode in (1, 3) else 1),
         "clocks": clk,
     }
     if rank == 0 and not a.no_cpu_baseline:

@@ -89,7 +89,12 @@ typedef enum nhq_seed_mode {
     NHQ_SEED_ATTRIBUTE = 1, /* P = objects whose attributes all equal the query's, ascending id;
                                c = |P| >= 1: S = min(ef, 32, c), B = {P[floor(j*c/S)] : j < S};
                                c = 0: as NHQ_SEED_RANDOM                                     */
-    NHQ_SEED_GIVEN = 2      /* B = the valid distinct ids of seeds[q][0..n_seeds)            */
+    NHQ_SEED_GIVEN = 2,     /* B = the valid distinct ids of seeds[q][0..n_seeds)            */
+    NHQ_SEED_ATTRIBUTE_NEAR = 3 /* P as above; of its M = min(256, c) members P[floor(j*c/M)]
+                               the min(ef, 32) nearest to the query by (delta^2 of the f32
+                               rows summed in index order, id); c = 0 as NHQ_SEED_RANDOM.
+                               For tuples spread over many clusters, where evenly spaced
+                               members rarely include the query's own                       */
 } nhq_seed_mode;
 
 /* Learned early stop (a project addition; the paper's search has no learned

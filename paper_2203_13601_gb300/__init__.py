@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "NHQError", "Index", "load_library", "library_path",
     "W_PROPORTIONAL", "W_CONSTANT", "W_FILTER", "W_HARMONIC", "VEC_F32", "VEC_BF16", "VEC_FP8E4M3",
-    "SEED_RANDOM", "SEED_ATTRIBUTE", "SEED_GIVEN",
+    "SEED_RANDOM", "SEED_ATTRIBUTE", "SEED_GIVEN", "SEED_ATTRIBUTE_NEAR",
     "nhq_last_error", "nhq_version", "nhq_index_create", "nhq_free", "nhq_index_info",
     "nhq_pack_attributes", "nhq_knn", "nhq_knn_bf16", "nhq_edge_select", "nhq_reverse_candidates",
     "nhq_index_set_graph", "nhq_index_get_graph", "nhq_index_build", "nhq_build",
@@ -38,7 +38,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libnhq.so")
 
 W_PROPORTIONAL, W_CONSTANT, W_FILTER, W_HARMONIC = 0, 1, 2, 3
 VEC_F32, VEC_BF16, VEC_FP8E4M3 = 0, 1, 2
-SEED_RANDOM, SEED_ATTRIBUTE, SEED_GIVEN = 0, 1, 2
+SEED_RANDOM, SEED_ATTRIBUTE, SEED_GIVEN, SEED_ATTRIBUTE_NEAR = 0, 1, 2, 3
 MLP_INPUTS, MLP_HIDDEN = 8, 64
 MLP_PARAMS = MLP_INPUTS * MLP_HIDDEN + 2 * MLP_HIDDEN + 1
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_ITER_LIMIT, ERR_IO = range(6)

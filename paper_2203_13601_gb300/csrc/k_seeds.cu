@@ -80,6 +80,116 @@ __global__ void attribute_seeds_kernel(SearchArgs a, const uint32_t *__restrict_
         row[j] = kNone;
 }
 
+// NHQ_SEED_ATTRIBUTE_NEAR: one warp per query; lane l takes the sampled members
+// l, l + 32, ... (at most 256 in all), computes delta^2 to the query in f32 in index order
+// (separately rounded, as the canonical form), and the warp takes the smallest
+// (delta^2, id) keys one at a time
+__global__ void attribute_near_seeds_kernel(SearchArgs a, const uint32_t *__restrict__ attr_sorted,
+                                            const uint32_t *__restrict__ id_sorted,
+                                            uint32_t *__restrict__ seeds,
+                                            uint8_t *__restrict__ bucket) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= a.nq)
+        return;
+    uint32_t qa = 0;
+    for (int j = 0; j < a.w.m; ++j)
+        qa |= (uint32_t)a.qattr[q * a.w.m + j] << (8 * j);
+    const int ef = a.ef_arr ? a.ef_arr[q] : a.ef;
+    const int want = ef < 32 ? ef : 32;
+    const int64_t lo = lower_bound_u32(attr_sorted, a.N, qa);
+    const int64_t hi = qa == 0xFFFFFFFFu ? a.N : lower_bound_u32(attr_sorted, a.N, qa + 1u);
+    const int64_t c = hi - lo;
+    uint32_t *row = seeds + q * 32;
+    if (lane == 0 && bucket != nullptr) {
+        const int bits = 64 - __clzll((unsigned long long)c + 1ull);
+        bucket[q] = (uint8_t)(bits >= 32 ? 0 : 32 - bits);
+    }
+    if (c == 0) {  // the random stream of NHQ_SEED_RANDOM
+        if (lane == 0) {
+            int j = 0;
+            const uint64_t s0 = a.seed ^ mix64((uint64_t)q);
+            for (int t = 0; t < 64 && j < want; ++t) {
+                const uint32_t v = (uint32_t)(splitmix_at(s0, (uint64_t)t) % (unsigned long long)a.N);
+                bool dup = false;
+                for (int i = 0; i < j; ++i)
+                    dup = dup || row[i] == v;
+                if (!dup)
+                    row[j++] = v;
+            }
+            for (; j < 32; ++j)
+                row[j] = kNone;
+        }
+        return;
+    }
+    const int M = c < 256 ? (int)c : 256;
+    const float *qv = a.Q + q * a.qstride;
+    // rows start on 32-byte boundaries (xstride is a multiple of 8); the query row on a
+    // 16-byte one when qstride is a multiple of 4 and the batch is 16-byte aligned
+    const bool vec4 = (a.d & 3) == 0 && (a.qstride & 3) == 0 &&
+                      ((reinterpret_cast<uintptr_t>(a.Q) & 15) == 0);
+    unsigned long long key[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int j = lane + 32 * t;
+        key[t] = ~0ull;
+        if (j < M) {
+            const uint32_t v = id_sorted[lo + ((int64_t)j * c) / M];
+            const float *xv = a.X + (int64_t)v * a.xstride;
+            float s = 0.f;
+            if (vec4) {
+                const float4 *x4 = reinterpret_cast<const float4 *>(xv);
+                const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+                for (int i = 0; i < (a.d >> 2); ++i) {
+                    const float4 xa = __ldg(x4 + i), qa4 = q4[i];
+                    float dd = __fsub_rn(qa4.x, xa.x);
+                    s = __fadd_rn(s, __fmul_rn(dd, dd));
+                    dd = __fsub_rn(qa4.y, xa.y);
+                    s = __fadd_rn(s, __fmul_rn(dd, dd));
+                    dd = __fsub_rn(qa4.z, xa.z);
+                    s = __fadd_rn(s, __fmul_rn(dd, dd));
+                    dd = __fsub_rn(qa4.w, xa.w);
+                    s = __fadd_rn(s, __fmul_rn(dd, dd));
+                }
+            } else {
+                for (int i = 0; i < a.d; ++i) {
+                    const float dd = __fsub_rn(qv[i], xv[i]);
+                    s = __fadd_rn(s, __fmul_rn(dd, dd));
+                }
+            }
+            key[t] = ((unsigned long long)__float_as_uint(s) << 32) | v;
+        }
+    }
+    const int S = want < M ? want : M;
+    for (int r = 0; r < 32; ++r) {
+        unsigned long long best = ~0ull;
+        int bt = -1;
+        if (r < S) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                if (key[t] < best) {
+                    best = key[t];
+                    bt = t;
+                }
+        }
+        unsigned long long m = best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, m, o);
+            m = other < m ? other : m;
+        }
+        if (r < S && bt >= 0 && best == m) {  // keys are unique: one owner
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                if (t == bt)
+                    key[t] = ~0ull;
+            row[r] = (uint32_t)m;
+        }
+        if (r >= S && lane == 0)
+            row[r] = kNone;
+    }
+}
+
 // counting sort of the query indices by bucket, one block
 __global__ void query_order_kernel(const uint8_t *__restrict__ bucket, int64_t nq,
                                    uint32_t *__restrict__ order) {
@@ -142,6 +252,17 @@ cudaError_t launch_attribute_seeds(const SearchArgs &a, const uint32_t *attr_sor
     attribute_seeds_kernel<<<(unsigned)((a.nq + 127) / 128), 128, 0, s>>>(a, attr_sorted,
                                                                             id_sorted, seeds,
                                                                             bucket);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_attribute_near_seeds(const SearchArgs &a, const uint32_t *attr_sorted,
+                                        const uint32_t *id_sorted, uint32_t *seeds,
+                                        uint8_t *bucket, cudaStream_t s) {
+    if (a.nq <= 0)
+        return cudaSuccess;
+    attribute_near_seeds_kernel<<<(unsigned)((a.nq + 7) / 8), 256, 0, s>>>(a, attr_sorted,
+                                                                           id_sorted, seeds,
+                                                                           bucket);
     return cudaGetLastError();
 }
 

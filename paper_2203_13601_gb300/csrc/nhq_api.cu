@@ -811,7 +811,7 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         return fail(NHQ_ERR_ARG, "hash_bits must be in 0..16");
     if (P.warps_per_block < 0 || P.warps_per_block > 8)
         return fail(NHQ_ERR_ARG, "warps_per_block must be in 0..8");
-    if (P.seed_mode < NHQ_SEED_RANDOM || P.seed_mode > NHQ_SEED_GIVEN)
+    if (P.seed_mode < NHQ_SEED_RANDOM || P.seed_mode > NHQ_SEED_ATTRIBUTE_NEAR)
         return fail(NHQ_ERR_ARG, "unknown seed_mode %d", P.seed_mode);
     if (P.seed_mode == NHQ_SEED_GIVEN && (P.seeds == nullptr || P.n_seeds < 1 || P.n_seeds > 64))
         return fail(NHQ_ERR_ARG, "NHQ_SEED_GIVEN needs seeds and n_seeds in 1..64");
@@ -826,7 +826,7 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         if (!(P.stop_threshold > 0.f && P.stop_threshold < 1.f))
             return fail(NHQ_ERR_ARG, "stop_threshold must be a probability in (0, 1)");
     }
-    if (P.seed_mode == NHQ_SEED_ATTRIBUTE)
+    if (P.seed_mode == NHQ_SEED_ATTRIBUTE || P.seed_mode == NHQ_SEED_ATTRIBUTE_NEAR)
         CKS(ensure_attribute_order(ix, s));
     if (P.vec_dtype == NHQ_VEC_BF16 && ix->Xh == nullptr) {
         CK(cudaMalloc(&ix->Xh, sizeof(__nv_bfloat16) * (size_t)ix->N * ix->xstride));
@@ -923,11 +923,14 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     if (P.seed_mode == NHQ_SEED_GIVEN) {
         a.seeds = (const uint32_t *)st.dev(isd);
         a.n_seeds = P.n_seeds;
-    } else if (P.seed_mode == NHQ_SEED_ATTRIBUTE) {
+    } else if (P.seed_mode == NHQ_SEED_ATTRIBUTE || P.seed_mode == NHQ_SEED_ATTRIBUTE_NEAR) {
         uint32_t *sd = reinterpret_cast<uint32_t *>((char *)ix->scratch + 256);
         uint32_t *order = sd + (size_t)32 * Q;
         uint8_t *bucket = reinterpret_cast<uint8_t *>(order + Q);
-        CK(launch_attribute_seeds(a, ix->attr_sorted, ix->id_sorted, sd, bucket, s));
+        if (P.seed_mode == NHQ_SEED_ATTRIBUTE)
+            CK(launch_attribute_seeds(a, ix->attr_sorted, ix->id_sorted, sd, bucket, s));
+        else
+            CK(launch_attribute_near_seeds(a, ix->attr_sorted, ix->id_sorted, sd, bucket, s));
         CK(launch_query_order(bucket, Q, order, s));
         a.seeds = sd;
         a.n_seeds = 32;

@@ -267,6 +267,10 @@ cudaError_t mlp_train(float *params, const float *X, const float *y, int64_t n, 
 cudaError_t launch_attribute_seeds(const SearchArgs &a, const uint32_t *attr_sorted,
                                    const uint32_t *id_sorted, uint32_t *seeds, uint8_t *bucket,
                                    cudaStream_t s);
+// Seeds of NHQ_SEED_ATTRIBUTE_NEAR (one warp per query), with the same cost buckets.
+cudaError_t launch_attribute_near_seeds(const SearchArgs &a, const uint32_t *attr_sorted,
+                                        const uint32_t *id_sorted, uint32_t *seeds,
+                                        uint8_t *bucket, cudaStream_t s);
 // order[0..nq) = the queries by ascending bucket (each bucket in any order)
 cudaError_t launch_query_order(const uint8_t *bucket, int64_t nq, uint32_t *order,
                                cudaStream_t s);

@@ -189,9 +189,12 @@ def c4(N=1_000_000, nq=100_000, d=96, cards=(5, 20, 100), n_comp=1_000, seed=100
        sel_lo=1e-4, sel_hi=1.0 / 3.0):
     """Attributes correlated with the cluster; query selectivity log-uniform.
 
-    Each centroid has its own random relabelling of a Zipf preference per
-    attribute.  Query tuples are picked among the tuples that occur in the base
-    set so that |P|/N is close to a log-uniform target in [sel_lo, sel_hi].
+    Each attribute value is drawn from a Zipf preference (s = 3): with probability
+    1/4 the object's centroid relabels it (each centroid has its own random
+    relabelling, the correlation), otherwise one global labelling applies (so
+    frequent tuples exist across clusters, up to a selectivity near 1/3).  Query tuples are picked among the
+    tuples that occur in the base set so that |P|/N is close to a log-uniform
+    target in [sel_lo, sel_hi].
     """
     _check_cards(cards)
     rb, rq, ra, rqa = _rngs(seed)
@@ -201,8 +204,9 @@ def c4(N=1_000_000, nq=100_000, d=96, cards=(5, 20, 100), n_comp=1_000, seed=100
     A = np.empty((N, len(cards)), dtype=np.uint8)
     for i, c in enumerate(cards):
         perms = np.argsort(ra.random((n_comp, c)), axis=1).astype(np.uint8)
-        draw = ra.choice(c, size=N, p=_zipf_probs(c))
-        A[:, i] = perms[comp, draw]
+        draw = ra.choice(c, size=N, p=_zipf_probs(c, 3.0))
+        local = ra.random(N) < 0.25
+        A[:, i] = np.where(local, perms[comp, draw], draw).astype(np.uint8)
     # tuple frequencies
     mult = np.cumprod((1,) + tuple(cards[:-1]))
     code = (A.astype(np.int64) * mult).sum(axis=1)

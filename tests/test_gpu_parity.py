@@ -389,6 +389,29 @@ def test_search_attribute_entry_seeds_exact(nhq, graph_case, wname, ef):
     assert np.array_equal(g.cpu().numpy().astype(np.float64), ref["gamma"])
 
 
+@pytest.mark.parametrize("cards,ef,d", [((3, 5, 7), 10, 40), ((3, 5, 7), 64, 40),
+                                        ((2,), 10, 40), ((2,), 64, 40), ((2,), 64, 30)])
+def test_search_nearest_attribute_entry_seeds_exact(nhq, cards, ef, d):
+    # (3, 5, 7): every run is shorter than 256, so all members are ranked; (2,): runs of
+    # about 2000, so 256 evenly spaced members are sampled and ranked; d = 30 takes the
+    # scalar row loop, d = 40 the 4-wide one
+    w = synth.int_valued(3000, 64, d, cards=cards, n_comp=12, seed=43)
+    nbr, _, _ = O.build_graph(w.X, w.A, R=16, K=32, weights=CONST)
+    QA = w.QA.copy()
+    QA[::9, 0] = 200  # tuples that no object has: the random stream is used for them
+    ref = O.search(w.X, w.A, nbr, w.Qv, QA, 10, ef, seed=23, weights=CONST,
+                   seed_mode=O.SEED_ATTRIBUTE_NEAR)
+    with _index(nhq, w, CONST) as ix:
+        nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
+        ids, g, chi = empty_out(w.nq, 10)
+        nhq.nhq_search(ix.handle, dev(w.Qv), dev(QA), 10, ef, ids, g, chi, seed=23,
+                       seed_mode=nhq.SEED_ATTRIBUTE_NEAR)
+        torch.cuda.synchronize()
+    assert (ids_i64(ids) == ref["ids"]).all()
+    assert (chi.cpu().numpy().astype(np.int32) == ref["chi"]).all()
+    assert np.array_equal(g.cpu().numpy().astype(np.float64), ref["gamma"])
+
+
 def test_search_given_seeds_exact(nhq, graph_case):
     w, graphs = graph_case
     wts, nbr = graphs["const"]
