@@ -65,7 +65,7 @@ def parse():
                     help="candidate build: 0 exact f32 SIMT, 1 bf16 tensor cores (exact here)")
     ap.add_argument("--learned-efs", default="16,24,32,48,64")
     ap.add_argument("--taus", default="0.7,0.8,0.9,0.95")
-    ap.add_argument("--c4-build", default="kgraph", choices=["kgraph", "nsw"],
+    ap.add_argument("--c4-build", default="nsw", choices=["kgraph", "nsw"],
                     help="c4 workload: graph built from exact candidates or incrementally")
     ap.add_argument("--workload", default="c2",
                     choices=["c2", "c4", "c5", "strategies", "curves", "builds"],
