@@ -68,14 +68,15 @@ def parse():
     ap.add_argument("--c4-build", default="nsw", choices=["kgraph", "nsw"],
                     help="c4 workload: graph built from exact candidates or incrementally")
     ap.add_argument("--workload", default="c2",
-                    choices=["c2", "c4", "c5", "strategies", "curves", "builds"],
+                    choices=["c2", "c4", "c5", "strategies", "curves", "builds", "attrdim"],
                     help="c2: the headline workload (default); c4: the heterogeneous batch "
                          "(1M x 96, 100k queries with mixed k and ef) through "
                          "nhq_search_batched; c5: the 10M x 96 set (f16-valued), 50k queries; "
                          "strategies: NHQ against post-filtering on a "
                          "plain L2 graph and exact pre-filtering, on the c2 workload; curves: "
                          "the weightings i-v of Sec. 6.5 on the c2 workload; builds: exact "
-                         "candidates, NN-descent and the incremental build compared; each "
+                         "candidates, NN-descent and the incremental build compared; "
+                         "attrdim: m = 3, 6 and 9 attributes on c2-shaped vectors; each "
                          "prints one JSON line of its own")
     return ap.parse_args()
 
@@ -555,6 +556,97 @@ def curves_arm(a):
                       "curves": rows}), flush=True)
 
 
+# ---------------------------------------------------------------- attribute dimension
+ATTR_CARDS = (3, 10, 20, 4, 5, 8, 2, 3, 6)
+
+
+def match_counts(A, QA):
+    """|P| for every query: the number of objects whose attribute rows equal its row."""
+    rows = np.ascontiguousarray(np.concatenate([A, QA]))
+    key = rows.view(np.dtype((np.void, rows.shape[1]))).ravel()
+    _, inv = np.unique(key, return_inverse=True)
+    inv = inv.ravel()
+    cnt = np.bincount(inv[: len(A)], minlength=int(inv.max()) + 1)
+    return cnt[inv[len(A):]]
+
+
+def attrdim_arm(a):
+    """The attribute dimension of Sec. 6.4 on c2-shaped vectors: m = 3, 6 and 9 Zipf
+    attributes (cards 3/10/20, then 4/5/8, then 2/3/6; the first m columns are the same
+    draws for every m), one composite index each (exact candidates on the tensor cores,
+    constant weights).  For each, with attribute-entry and with random seeds: the cheapest
+    ef reaching hybrid Recall@10 >= target, else the best recall; and the build time and
+    |P| statistics."""
+    import torch
+
+    import paper_2203_13601_gb300 as nhq
+    import synth
+    from paper_2203_13601_gb300 import build as B
+
+    B.build()
+    nhq.load_library()
+    dev = torch.device("cuda", 0)
+    k = a.k
+    rows = []
+    for m in (3, 6, 9):
+        w = synth.c2(N=a.n, nq=a.nq, d=a.d, cards=ATTR_CARDS[:m],
+                     n_comp=1000 if a.n >= 100_000 else max(10, a.n // 100))
+        P = match_counts(w.A, w.QA)
+        X, A = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.A).to(dev)
+        Qv, QA = torch.from_numpy(w.Qv).to(dev), torch.from_numpy(w.QA).to(dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = nhq.Index.build(X, A, degree=a.R, weights=CONST_W, K=64, knn_dtype=1)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        gt = torch.empty((w.nq, k), dtype=torch.uint32, device=dev)
+        nhq.nhq_brute_force(ix.handle, Qv, QA, k, gt, weights="filter")
+        gt_h = gt.cpu().numpy()
+        ids, dd, ch = (torch.empty((w.nq, k), dtype=torch.uint32, device=dev),
+                       torch.empty((w.nq, k), dtype=torch.float32, device=dev),
+                       torch.empty((w.nq, k), dtype=torch.uint8, device=dev))
+        by_seeds = {}
+        for sname, smode in (("attribute_entry", nhq.SEED_ATTRIBUTE),
+                             ("random", nhq.SEED_RANDOM)):
+            sweep = []
+            for ef in (16, 24, 32, 48, 64, 96, 128, 200, 320, 500):
+                run = lambda ef=ef: nhq.nhq_search(ix.handle, Qv, QA, k, ef, ids, dd, ch,
+                                                   seed=12345, seed_mode=smode)
+                for _ in range(3):
+                    run()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(5):
+                    run()
+                e1.record()
+                torch.cuda.synchronize()
+                rec, excl = hybrid_recall(ids.cpu().numpy(), w.A, w.QA, gt_h, P, k)
+                ms = e0.elapsed_time(e1) / 5
+                sweep.append({"ef": ef, "recall": rec, "ms": ms, "qps": w.nq / ms * 1e3})
+                if rec >= a.target:
+                    break
+            best = sweep[-1] if sweep[-1]["recall"] >= a.target else max(
+                sweep, key=lambda r: r["recall"])
+            by_seeds[sname] = {"best": best, "reached_target": best["recall"] >= a.target,
+                               "sweep": sweep}
+        ix.close()
+        del X, A
+        pos = P[P > 0]
+        rows.append({"m": m, "cards": list(ATTR_CARDS[:m]),
+                     "distinct_tuples": int(len(np.unique(
+                         np.ascontiguousarray(w.A).view(np.dtype((np.void, m)))))),
+                     "queries_with_no_match": int((P == 0).sum()),
+                     "median_P": float(np.median(pos)) if pos.size else 0.0,
+                     "build_s": t_build, "seeds": by_seeds})
+    print(json.dumps({"metric": f"hybrid Recall@{k} and QPS per attribute dimension m (Sec. 6.4)",
+                      "config": {"workload": f"c2-shaped vectors N={a.n:,} d={a.d}, "
+                                             f"{a.nq:,} queries, R={a.R}, weights w_v=1 "
+                                             "w_l=10000, Zipf s=1 attributes",
+                                 "target": a.target},
+                      "dims": rows}), flush=True)
+
+
 # ---------------------------------------------------------------- build methods
 def builds_arm(a):
     """The ways to build the composite index on the c2 workload (constant weights,
@@ -838,6 +930,10 @@ def main():
     if a.workload == "builds":
         if rank == 0:
             builds_arm(a)
+        return
+    if a.workload == "attrdim":
+        if rank == 0:
+            attrdim_arm(a)
         return
 
     import torch

@@ -25,7 +25,7 @@
  *   calling thread.  Invalid sizes or values return NHQ_ERR_ARG before any
  *   work is enqueued; a failing CUDA call returns NHQ_ERR_CUDA; a failed
  *   device allocation returns NHQ_ERR_OOM.
- * - Notation (paper): N objects, d vector dimension, m attributes (1..4, each an
+ * - Notation (paper): N objects, d vector dimension, m attributes (1..32, each an
  *   ordinal code 0..255, Sec. 3.2 "ordinal encoding"), R graph out-degree
  *   (the paper's k in Sec. 4), k results, ef search-pool size.
  * - Result order: ascending by (Gamma, id).  `dists` hold Gamma (Eq. 6), not
@@ -135,9 +135,13 @@ int32_t nhq_version(void);
 /*
  * Object set S of Def. 1: copies vectors[N][d] (f32, row-major) into index-owned
  * HBM (rows padded to a multiple of 16 elements) and packs attributes[N][m] (u8
- * ordinal codes, Sec. 3.2) into one u32 per object.  `w` fixes the fusion
- * distance (Eq. 6) used by build and search.  The graph is empty until
- * nhq_index_build / nhq_index_set_graph.  Errors: N < 1, d < 1, m outside 1..4,
+ * ordinal codes, Sec. 3.2) into one u32 per object: m <= 4 codes take a byte each
+ * (as nhq_pack_attributes); more codes take, in order, fields of the fewest bits
+ * that hold 0..c_j + 1, c_j the largest code of attribute j among the objects, so
+ * that a query code above c_j (which no object has) still counts as a mismatch.
+ * chi is exact either way.  `w` fixes the fusion distance (Eq. 6) used by build
+ * and search.  The graph is empty until nhq_index_build / nhq_index_set_graph.
+ * Errors: N < 1, d < 1, m outside 1..32, fields needing more than 32 bits in all,
  * a non-finite vector component, or w_v/w_l negative or non-finite -> NHQ_ERR_ARG.
  */
 nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
@@ -423,8 +427,10 @@ nhq_status nhq_mlp_train(float *params, const float *features, const float *labe
                          int32_t epochs, int32_t batch, float lr, void *stream);
 
 /*
- * Index persistence: header {magic "NHQIDX01", version, N, d, m, R, weights}
+ * Index persistence: header {magic "NHQIDX01", version, N, d, m, R, weights}, in
+ * version 2 followed by the attribute layout (32 field shifts, 32 field widths, u8),
  * then vectors (f32, unpadded rows), packed attributes (u32) and the graph (u32).
+ * nhq_save writes version 2; nhq_load reads versions 1 (a byte per attribute) and 2.
  * Errors: unreadable/unwritable file or bad header -> NHQ_ERR_IO.
  */
 nhq_status nhq_save(const nhq_index *index, const char *path);

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(NT) topk_tile_kernel(TopkArgs a, int64_t per_s
                 float g = __int_as_float(0x7f800000);
                 if (q < a.nq && o < n_end && !(a.exclude_self && o == q)) {
                     float delta = __fsqrt_rn(acc[i][j]);
-                    g = fusion_gamma(delta, chi_packed(qa, a.attr[o], a.w.mask), a.w);
+                    g = fusion_gamma(delta, chi_packed(qa, a.attr[o], a.w.hi, a.w.lo), a.w);
                 }
                 G[r * TN + c] = g;
             }
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(NT) topk_tile_kernel(TopkArgs a, int64_t per_s
                 if (a.chi)
                     a.chi[q * k + e] =
                         id == kNone ? (uint8_t)255
-                                    : (uint8_t)chi_packed(a.qattr[q], a.attr[id], a.w.mask);
+                                    : (uint8_t)chi_packed(a.qattr[q], a.attr[id], a.w.hi, a.w.lo);
             } else {
                 int64_t o = (q * S + split) * (int64_t)k + e;
                 part_id[o] = id;
@@ -230,7 +230,7 @@ __global__ void topk_merge_kernel(TopkArgs a, int S, const uint32_t *__restrict_
             if (a.chi)
                 a.chi[q * k + e] = id == kNone
                                        ? (uint8_t)255
-                                       : (uint8_t)chi_packed(a.qattr[q], a.attr[id], a.w.mask);
+                                       : (uint8_t)chi_packed(a.qattr[q], a.attr[id], a.w.hi, a.w.lo);
         }
         if (cur == best && best != ~0ull) {
             ++head;

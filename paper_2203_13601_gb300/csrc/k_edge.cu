@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(ES_THREADS) edge_select_kernel(EdgeArgs a) {
         const int i = base + team;
         const float dd = team_dist2_t<T4>(row_of_slot(i < n ? i : 0), row_of_slot(n), xs4, tl);
         if (i < n && tl == 0) {
-            const float g = fusion_gamma(__fsqrt_rn(dd), chi_packed(sattr[i], au, a.w.mask), a.w);
+            const float g = fusion_gamma(__fsqrt_rn(dd), chi_packed(sattr[i], au, a.w.hi, a.w.lo), a.w);
             gpu[i] = g;
             keys[i] = ((unsigned long long)__float_as_uint(g) << 32) | cid[i];
         }
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(ES_THREADS) edge_select_kernel(EdgeArgs a) {
             const float dd = team_dist2_t<T4>(row_of_slot(sq), jrow, xs4, tl);
             if (live && tl == 0) {
                 const float g =
-                    fusion_gamma(__fsqrt_rn(dd), chi_packed(sattr[sq], aj, a.w.mask), a.w);
+                    fusion_gamma(__fsqrt_rn(dd), chi_packed(sattr[sq], aj, a.w.hi, a.w.lo), a.w);
                 const float gq = gpu[sq];
                 keep[k] = (gq < g && gq > gju) ? 1 : 0;
             }
@@ -331,7 +331,7 @@ cudaError_t launch_edge_select_rows(const nhq_index *ix, const uint32_t *cand, i
     a.d = ix->d;
     a.N = ix->N;
     a.attr = ix->attr;
-    a.w = make_fusion(ix->w, ix->m);
+    a.w = make_fusion(ix->w, ix->layout);
     a.cand = cand;
     a.L = L;
     a.R = R;

@@ -178,13 +178,9 @@ __device__ __forceinline__ void heap_sift(unsigned long long *hp, int n, int i,
     hp[i] = key;
 }
 
-// number of differing attribute bytes under the mask (chi of Eq. 3 on packed codes):
-// bit 7 of each byte of y is set iff that byte of x is nonzero
-__device__ __forceinline__ int chi_bytes(uint32_t a, uint32_t b, uint32_t mask) {
-    const uint32_t x = (a ^ b) & mask;
-    const uint32_t y = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
-    return __popc(y & 0x80808080u);
-}
+// row of the bound table for a chi: the table holds chi = 0..4; Gamma grows with chi,
+// so the bound of chi = 4 also holds (more loosely) for every larger chi
+__device__ __forceinline__ int chi_level(int chi) { return chi < 4 ? chi : 4; }
 
 // bounded wait for the scheduler's decision on the i-th tile of the sweep
 __device__ __forceinline__ bool wait_decided(const int *decided, int i, int *err, int code) {
@@ -364,7 +360,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             continue;
                         const int ch = (ra[k] >= tf && ra[k] <= tl)
                                            ? 0
-                                           : (tf == tl ? chi_bytes(ra[k], tf, a.w.mask) : 1);
+                                           : (tf == tl ? chi_level(chi_packed(ra[k], tf, a.w.hi,
+                                                                              a.w.lo))
+                                                       : 1);
                         const float lim = reinterpret_cast<const volatile float *>(
                             limtab)[ch * BM + lane + 32 * k];
                         live = live || !(lim < 0.f);
@@ -564,7 +562,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int nvalid = a.N - cbase < BN ? (int)(a.N - cbase) : BN;
             const uint32_t tf = mattr[0], tl = mattr[nvalid - 1];
             const bool uni = tf == tl;  // one tuple in the whole tile (sorted order)
-            const int ch_t = chi_bytes(au, tf, a.w.mask);
+            const int ch_t = chi_level(chi_packed(au, tf, a.w.hi, a.w.lo));
             const int ch_min = (au >= tf && au <= tl) ? 0 : (uni ? ch_t : 1);
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 // the bounds only tighten: a row whose bound for the smallest chi of
@@ -610,7 +608,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             const float d2 =
                                 fmaxf((nu + nc[q]) - 2.f * __uint_as_float(v[j]), 0.f);
                             v[j] = __float_as_uint(d2);
-                            const int ch = chi_bytes(au, ac[q], a.w.mask);
+                            const int ch = chi_level(chi_packed(au, ac[q], a.w.hi, a.w.lo));
                             pass |= (d2 <= lt[ch * BM] ? 1u : 0u) << j;
                         }
                     }
@@ -628,7 +626,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const int64_t col = cbase + c;
                     if (col >= a.N || col == u)
                         continue;
-                    const int ch = chi_bytes(au, mattr[c], a.w.mask);
+                    const int ch = chi_packed(au, mattr[c], a.w.hi, a.w.lo);
                     const float g = fusion_gamma(__fsqrt_rn(__uint_as_float(e.x)), ch, a.w);
                     const unsigned long long key =
                         ((unsigned long long)__float_as_uint(g) << 32) | mid[c];

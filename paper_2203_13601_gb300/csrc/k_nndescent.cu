@@ -122,7 +122,7 @@ __global__ void nnd_init_kernel(NndArgs a) {
                                       a.N);
         const float d2 = team4_dist2(xu, a.X + (int64_t)v * a.xstride, xs4, tl);
         if (j < K && tl == 0) {
-            k[j] = rec_key(fusion_gamma(__fsqrt_rn(d2), chi_packed(au, a.attr[v], a.w.mask),
+            k[j] = rec_key(fusion_gamma(__fsqrt_rn(d2), chi_packed(au, a.attr[v], a.w.hi, a.w.lo),
                                         a.w),
                            v);
             f[j] = 1;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(JOIN_THREADS) nnd_join_kernel(NndArgs a) {
         const int j = i + 1 + (int)rem;
         const float acc = team4_dist2(rows + i * rs, rows + j * rs, xs4, tl);
         if (live && tl == 0) {
-            const float g = fusion_gamma(__fsqrt_rn(acc), chi_packed(cat[i], cat[j], a.w.mask),
+            const float g = fusion_gamma(__fsqrt_rn(acc), chi_packed(cat[i], cat[j], a.w.hi, a.w.lo),
                                          a.w);
             push_update(a, cid[i], rec_key(g, cid[j]));
             push_update(a, cid[j], rec_key(g, cid[i]));

@@ -73,16 +73,17 @@ __global__ void nsw_attr_seeds_kernel(int64_t s, int64_t B, uint64_t seed,
 }
 
 __global__ void nsw_queries_kernel(const float *__restrict__ X, int xstride, int d,
-                                   const uint32_t *__restrict__ attr, int m, int64_t s, int64_t B,
-                                   float *__restrict__ q, uint8_t *__restrict__ qa) {
+                                   const uint32_t *__restrict__ attr, AttrLayout L, int64_t s,
+                                   int64_t B, float *__restrict__ q, uint8_t *__restrict__ qa) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < B * d) {
         const int64_t b = i / d;
         q[i] = X[(s + b) * xstride + (i % d)];
     }
-    if (i < B * m) {
-        const int64_t b = i / m;
-        qa[i] = (uint8_t)(attr[s + b] >> (8 * (int)(i % m)));
+    if (i < B * L.m) {
+        const int64_t b = i / L.m;
+        const int j = (int)(i % L.m);
+        qa[i] = (uint8_t)((attr[s + b] >> L.shift[j]) & ((1u << L.width[j]) - 1u));
     }
 }
 
@@ -165,8 +166,8 @@ cudaError_t launch_nsw_attr_seeds(const nhq_index *ix, int64_t s, int64_t B, uin
 cudaError_t launch_nsw_queries(const nhq_index *ix, int64_t s, int64_t B, float *q, uint8_t *qa,
                                cudaStream_t st) {
     const int64_t n = B * (ix->d > ix->m ? ix->d : ix->m);
-    nsw_queries_kernel<<<blocks_for(n), 256, 0, st>>>(ix->X, ix->xstride, ix->d, ix->attr, ix->m,
-                                                      s, B, q, qa);
+    nsw_queries_kernel<<<blocks_for(n), 256, 0, st>>>(ix->X, ix->xstride, ix->d, ix->attr,
+                                                      ix->layout, s, B, q, qa);
     return cudaGetLastError();
 }
 

@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
     float *qv = reinterpret_cast<float *>(base + L.qv);
     const int H = 1 << a.hash_bits;
     const int R = a.R;
-    const uint32_t amask = a.w.mask;
+    const uint32_t ahi = a.w.hi, alo = a.w.lo;
     // the learned stop's fp16 weights, staged once per block after the warps' areas
     __half *w16 = reinterpret_cast<__half *>(smem + (blockDim.x >> 5) * L.total);
     if (a.stop_w16 != nullptr) {
@@ -515,9 +515,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
 
         for (int i = lane; i < a.xstride; i += 32)
             qv[i] = i < a.d ? a.Q[q * a.qstride + i] : 0.f;
-        uint32_t qa = 0;
-        for (int j = 0; j < a.w.m; ++j)
-            qa |= (uint32_t)a.qattr[q * a.w.m + j] << (8 * j);
+        const uint32_t qa = pack_query_word(a.qattr + q * a.w.m, a.w);
         for (int i = lane; i < H / 4; i += 32)
             reinterpret_cast<uint4 *>(hash)[i] = make_uint4(kNone, kNone, kNone, kNone);
         __syncwarp();
@@ -542,7 +540,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
                 prefetch_row(Xs, a.xstride, v);
                 const int p = __popc(kb & lanemask_lt(lane));
                 cid[p] = v;
-                cchi[p] = chi_packed(a.attr[v], qa, amask);
+                cchi[p] = chi_packed(a.attr[v], qa, ahi, alo);
             }
             __syncwarp();
             const int cnt = __popc(kb);
@@ -572,7 +570,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
                 prefetch_row(Xs, a.xstride, v);
                 const int p = __popc(kb & lanemask_lt(lane));
                 cid[p] = v;
-                cchi[p] = chi_packed(a.attr[v], qa, amask);
+                cchi[p] = chi_packed(a.attr[v], qa, ahi, alo);
             }
             __syncwarp();
             const int cnt = __popc(kb);
@@ -682,8 +680,8 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
             bool nw1 = TWO && ok1 && hash_insert(hash, a.hash_bits, v1);
             // newly inserted ids fill the filter, pruned or not (they count as evaluated)
             hcount += __popc(__ballot_sync(FULL, nw0)) + (TWO ? __popc(__ballot_sync(FULL, nw1)) : 0);
-            const int c0 = chi_packed(at0, qa, amask);
-            const int c1 = TWO ? chi_packed(at1, qa, amask) : 0;
+            const int c0 = chi_packed(at0, qa, ahi, alo);
+            const int c1 = TWO ? chi_packed(at1, qa, ahi, alo) : 0;
             if (a.w.mode == NHQ_W_CONSTANT && n == ef) {
                 // Gamma >= w_l * chi in f32 (w_v * delta >= 0 and rounding is monotone)
                 const unsigned long long worst = pool[ef - 1] & ~1ull;
@@ -771,7 +769,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
                 for (int j = lane; j < cb; j += 32) {
                     const uint32_t id = key_id(pool[b0 + j]);
                     cid[j] = id;
-                    cchi[j] = chi_packed(a.attr[id], qa, amask);
+                    cchi[j] = chi_packed(a.attr[id], qa, ahi, alo);
                 }
                 __syncwarp();
                 eval_dist2<float, 0, false>(a.X, a.xstride, qv, cid, d2s, cb, lane);
@@ -802,7 +800,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
                     if (a.dists)
                         a.dists[o] = key_gamma(m);
                     if (a.chi)
-                        a.chi[o] = (uint8_t)chi_packed(a.attr[id], qa, amask);
+                        a.chi[o] = (uint8_t)chi_packed(a.attr[id], qa, ahi, alo);
                 }
                 __syncwarp();
             }
@@ -820,7 +818,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
             if (a.dists)
                 a.dists[o] = g;
             if (a.chi)
-                a.chi[o] = id == kNone ? (uint8_t)255 : (uint8_t)chi_packed(a.attr[id], qa, amask);
+                a.chi[o] = id == kNone ? (uint8_t)255 : (uint8_t)chi_packed(a.attr[id], qa, ahi, alo);
         }
         if (lane == 0) {
             if (a.status)

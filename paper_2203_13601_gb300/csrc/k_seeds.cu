@@ -47,9 +47,7 @@ __global__ void attribute_seeds_kernel(SearchArgs a, const uint32_t *__restrict_
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= a.nq)
         return;
-    uint32_t qa = 0;
-    for (int j = 0; j < a.w.m; ++j)
-        qa |= (uint32_t)a.qattr[q * a.w.m + j] << (8 * j);
+    const uint32_t qa = pack_query_word(a.qattr + q * a.w.m, a.w);
     const int ef = a.ef_arr ? a.ef_arr[q] : a.ef;
     const int want = ef < 32 ? ef : 32;
     const int64_t lo = lower_bound_u32(attr_sorted, a.N, qa);
@@ -92,9 +90,7 @@ __global__ void attribute_near_seeds_kernel(SearchArgs a, const uint32_t *__rest
     const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (q >= a.nq)
         return;
-    uint32_t qa = 0;
-    for (int j = 0; j < a.w.m; ++j)
-        qa |= (uint32_t)a.qattr[q * a.w.m + j] << (8 * j);
+    const uint32_t qa = pack_query_word(a.qattr + q * a.w.m, a.w);
     const int ef = a.ef_arr ? a.ef_arr[q] : a.ef;
     const int want = ef < 32 ? ef : 32;
     const int64_t lo = lower_bound_u32(attr_sorted, a.N, qa);

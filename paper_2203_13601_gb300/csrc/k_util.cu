@@ -7,15 +7,34 @@ namespace nhq {
 
 namespace {
 
-__global__ void pack_attr_kernel(const uint8_t *__restrict__ a, int64_t n, int m,
+// code j of row i at bits shift[j]; codes above maxc[j] (queries only) as maxc[j] + 1
+__global__ void pack_attr_kernel(const uint8_t *__restrict__ a, int64_t n, AttrLayout L,
                                  uint32_t *__restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t w = 0;
-        for (int j = 0; j < m; ++j)
-            w |= (uint32_t)a[i * m + j] << (8 * j);
+        for (int j = 0; j < L.m; ++j) {
+            const uint32_t v = a[i * L.m + j];
+            w |= (v <= L.maxc[j] ? v : (uint32_t)L.maxc[j] + 1u) << L.shift[j];
+        }
         out[i] = w;
     }
+}
+
+// out[j] = the largest code of attribute j over the n rows (out zeroed by the caller)
+__global__ void attr_max_kernel(const uint8_t *__restrict__ a, int64_t n, int m,
+                                unsigned int *__restrict__ out) {
+    __shared__ unsigned int smax[kMaxAttr];
+    if (threadIdx.x < kMaxAttr)
+        smax[threadIdx.x] = 0u;
+    __syncthreads();
+    const int64_t total = n * m;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        atomicMax(&smax[(int)(i % m)], (unsigned int)a[i]);
+    __syncthreads();
+    if (threadIdx.x < m)
+        atomicMax(&out[threadIdx.x], smax[threadIdx.x]);
 }
 
 // dst[r][0..xstride) = src[r][0..d) followed by zeros; flags non-finite input.
@@ -73,11 +92,20 @@ inline int grid_for(int64_t n) {
 
 }  // namespace
 
-cudaError_t launch_pack_attributes(const uint8_t *a, int64_t n, int m, uint32_t *out,
-                                   cudaStream_t s) {
+cudaError_t launch_pack_attributes(const uint8_t *a, int64_t n, const AttrLayout &L,
+                                   uint32_t *out, cudaStream_t s) {
     if (n <= 0)
         return cudaSuccess;
-    pack_attr_kernel<<<grid_for(n), 256, 0, s>>>(a, n, m, out);
+    pack_attr_kernel<<<grid_for(n), 256, 0, s>>>(a, n, L, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_attr_max(const uint8_t *a, int64_t n, int m, unsigned int *out,
+                            cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned int) * kMaxAttr, s);
+    if (e != cudaSuccess || n <= 0)
+        return e;
+    attr_max_kernel<<<grid_for(n * m), 256, 0, s>>>(a, n, m, out);
     return cudaGetLastError();
 }
 
@@ -103,14 +131,64 @@ cudaError_t launch_gather_nbr_attr(const uint32_t *nbr, const uint32_t *attr, in
     return cudaGetLastError();
 }
 
-Fusion make_fusion(const nhq_weights &w, int m) {
+static void finish_masks(AttrLayout *L) {
+    L->hi = L->lo = 0u;
+    for (int j = 0; j < L->m; ++j) {
+        const uint32_t top = 1u << (L->shift[j] + L->width[j] - 1);
+        const uint32_t field = (L->width[j] >= 32 ? 0xFFFFFFFFu : ((1u << L->width[j]) - 1u))
+                               << L->shift[j];
+        L->hi |= top;
+        L->lo |= field & ~top;
+    }
+}
+
+AttrLayout byte_layout(int m) {
+    AttrLayout L;
+    L.m = m;
+    for (int j = 0; j < m && j < 4; ++j) {
+        L.shift[j] = (uint8_t)(8 * j);
+        L.width[j] = 8;
+        L.maxc[j] = 255;
+    }
+    finish_masks(&L);
+    return L;
+}
+
+bool compact_layout(int m, const uint8_t *maxc, AttrLayout *out) {
+    AttrLayout L;
+    L.m = m;
+    int bits = 0;
+    for (int j = 0; j < m; ++j) {
+        int w = 1;  // bits for 0..maxc + 1
+        while ((1 << w) <= (int)maxc[j] + 1)
+            ++w;
+        if (bits + w > 32)
+            return false;
+        L.shift[j] = (uint8_t)bits;
+        L.width[j] = (uint8_t)w;
+        L.maxc[j] = maxc[j];
+        bits += w;
+    }
+    finish_masks(&L);
+    *out = L;
+    return true;
+}
+
+Fusion make_fusion(const nhq_weights &w, const AttrLayout &L) {
     Fusion f;
     f.mode = w.mode;
     f.wv = w.w_v;
     f.wl = w.w_l;
-    f.m = m;
-    f.mask = m >= 4 ? 0xFFFFFFFFu : ((1u << (8 * m)) - 1u);
+    f.m = L.m;
+    f.hi = L.hi;
+    f.lo = L.lo;
+    for (int j = 0; j < kMaxAttr; ++j) {
+        f.shift[j] = L.shift[j];
+        f.maxc[j] = L.maxc[j];
+    }
     return f;
 }
+
+Fusion make_fusion(const nhq_weights &w, int m) { return make_fusion(w, byte_layout(m)); }
 
 }  // namespace nhq

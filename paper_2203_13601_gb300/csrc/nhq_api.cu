@@ -198,8 +198,8 @@ nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const ui
         return fail(NHQ_ERR_ARG, "N must be in 1..2^31-2 (got %lld)", (long long)N);
     if (d < 1 || d > 16384)
         return fail(NHQ_ERR_ARG, "d must be in 1..16384 (got %d)", d);
-    if (m < 1 || m > 4)
-        return fail(NHQ_ERR_ARG, "m must be in 1..4 (got %d)", m);
+    if (m < 1 || m > kMaxAttr)
+        return fail(NHQ_ERR_ARG, "m must be in 1..%d (got %d)", kMaxAttr, m);
     if (vectors == nullptr || attributes == nullptr)
         return fail(NHQ_ERR_ARG, "vectors and attributes are required");
     CKS(check_weights(w, false));
@@ -240,7 +240,27 @@ nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const ui
     if ((e = launch_copy_rows((const float *)st.dev(iv), N, d, ix->xstride, ix->X, bad, s)) !=
         cudaSuccess)
         return bail(fail_cuda(e, "copy_rows"));
-    if ((e = launch_pack_attributes((const uint8_t *)st.dev(ia), N, m, ix->attr, s)) != cudaSuccess)
+    if (m <= 4) {
+        ix->layout = byte_layout(m);
+    } else {  // fields as narrow as the largest codes allow
+        unsigned int *amax = reinterpret_cast<unsigned int *>((char *)ix->scratch + 128);
+        unsigned int hmax[kMaxAttr];
+        if ((e = launch_attr_max((const uint8_t *)st.dev(ia), N, m, amax, s)) != cudaSuccess)
+            return bail(fail_cuda(e, "attr_max"));
+        if ((e = cudaMemcpyAsync(hmax, amax, sizeof(hmax), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return bail(fail_cuda(e, "attr_max copy"));
+        uint8_t mc[kMaxAttr];
+        for (int j = 0; j < m; ++j)
+            mc[j] = (uint8_t)hmax[j];
+        if (!compact_layout(m, mc, &ix->layout))
+            return bail(fail(NHQ_ERR_ARG, "the codes of the %d attributes need more than 32 bits "
+                                          "packed (each takes the bits of its largest code + 1)",
+                             m));
+    }
+    if ((e = launch_pack_attributes((const uint8_t *)st.dev(ia), N, ix->layout, ix->attr, s)) !=
+        cudaSuccess)
         return bail(fail_cuda(e, "pack_attributes"));
     int hbad = 0;
     if ((e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
@@ -293,7 +313,7 @@ nhq_status nhq_pack_attributes(const uint8_t *attributes, int64_t n, int32_t m, 
         return NHQ_OK;
     if (!is_device_ptr(attributes) || !is_device_ptr(packed))
         return fail(NHQ_ERR_ARG, "nhq_pack_attributes takes device pointers");
-    CK(launch_pack_attributes(attributes, n, m, packed, as_stream(stream)));
+    CK(launch_pack_attributes(attributes, n, byte_layout(m), packed, as_stream(stream)));
     return NHQ_OK;
 }
 
@@ -321,7 +341,7 @@ nhq_status nhq_knn(const nhq_index *cix, int32_t K, uint32_t *cand_ids, float *c
     a.nq = ix->N;
     a.k = K;
     a.exclude_self = 1;
-    a.w = make_fusion(ix->w, ix->m);
+    a.w = make_fusion(ix->w, ix->layout);
     a.ids = (uint32_t *)st.dev(io);
     a.dists = (float *)st.dev(id);
     a.chi = nullptr;
@@ -367,7 +387,7 @@ nhq_status nhq_knn_bf16(const nhq_index *cix, int32_t K, uint32_t *cand_ids, flo
     int *err = reinterpret_cast<int *>(ix->scratch);
     CK(cudaMemsetAsync(err, 0, sizeof(int), s));
     cudaError_t e = launch_knn_tc(ix->Xk, ix->kpad, ix->normk, ix->attr_sorted, ix->id_sorted,
-                                  ix->N, make_fusion(ix->w, ix->m), K, (uint32_t *)st.dev(io),
+                                  ix->N, make_fusion(ix->w, ix->layout), K, (uint32_t *)st.dev(io),
                                   (float *)st.dev(id), err, s);
     if (e != cudaSuccess)
         return fail_cuda(e, "tensor-core candidate kernel launch");
@@ -397,7 +417,7 @@ nhq_status nhq_knn_nndescent(const nhq_index *ix, int32_t K, int32_t max_iters, 
     void *work = nullptr;
     CK(cudaMalloc(&work, nnd_scratch_bytes(ix->N, K)));
     int done = 0;
-    cudaError_t e = launch_nndescent(ix->X, ix->xstride, ix->N, ix->attr, make_fusion(ix->w, ix->m),
+    cudaError_t e = launch_nndescent(ix->X, ix->xstride, ix->N, ix->attr, make_fusion(ix->w, ix->layout),
                                      K, max_iters, 1e-3, seed, work, (uint32_t *)st.dev(io),
                                      (float *)st.dev(id), &done, s);
     if (e == cudaSuccess)
@@ -702,7 +722,7 @@ nhq_status nhq_brute_force(const nhq_index *cix, const float *queries,
     a.nq = Q;
     a.k = k;
     a.exclude_self = 0;
-    a.w = make_fusion(ww, ix->m);
+    a.w = make_fusion(ww, ix->layout);
     a.ids = (uint32_t *)st.dev(io);
     a.dists = (float *)st.dev(id);
     a.chi = (uint8_t *)st.dev(ic);
@@ -710,7 +730,7 @@ nhq_status nhq_brute_force(const nhq_index *cix, const float *queries,
     size_t need = qa_bytes + topk_scratch_bytes(a, ix->sm_count);
     CKS(scratch(ix, need));
     uint32_t *qa = reinterpret_cast<uint32_t *>(ix->scratch);
-    CK(launch_pack_attributes((const uint8_t *)st.dev(ia), Q, ix->m, qa, s));
+    CK(launch_pack_attributes((const uint8_t *)st.dev(ia), Q, ix->layout, qa, s));
     a.qattr = qa;
     CK(launch_topk(a, (char *)ix->scratch + qa_bytes, ix->scratch_bytes - qa_bytes, ix->sm_count,
                    s));
@@ -862,7 +882,7 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     a.nbr = ix->nbr;
     a.nbr_attr = ix->nbr_attr;
     a.R = ix->R;
-    a.w = make_fusion(ix->w, ix->m);
+    a.w = make_fusion(ix->w, ix->layout);
     a.Q = (const float *)st.dev(iq);
     a.qstride = ix->d;
     a.qattr = (const uint8_t *)st.dev(ia);
@@ -1214,10 +1234,14 @@ nhq_status nhq_save(const nhq_index *ix, const char *path) {
     const size_t N = (size_t)ix->N;
     std::vector<float> row((size_t)ix->xstride * 4096);
     std::vector<uint32_t> attr(N), nbr(N * (size_t)ix->R);
-    int32_t hdr[8] = {1, (int32_t)(ix->N & 0x7FFFFFFF), ix->d, ix->m, ix->R, ix->w.mode, 0, 0};
+    // version 2: version 1 followed by the attribute layout (shift[32], width[32])
+    int32_t hdr[8] = {2, (int32_t)(ix->N & 0x7FFFFFFF), ix->d, ix->m, ix->R, ix->w.mode, 0, 0};
     float wts[2] = {ix->w.w_v, ix->w.w_l};
+    uint8_t lay[2 * kMaxAttr];
+    memcpy(lay, ix->layout.shift, kMaxAttr);
+    memcpy(lay + kMaxAttr, ix->layout.width, kMaxAttr);
     bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
-              fwrite(wts, sizeof(wts), 1, f) == 1;
+              fwrite(wts, sizeof(wts), 1, f) == 1 && fwrite(lay, sizeof(lay), 1, f) == 1;
     cudaError_t e = cudaSuccess;
     for (size_t r0 = 0; ok && r0 < N; r0 += 4096) {
         size_t nr = N - r0 < 4096 ? N - r0 : 4096;
@@ -1253,12 +1277,25 @@ nhq_status nhq_load(const char *path, void *stream, nhq_index **out) {
     char magic[8];
     int32_t hdr[8];
     float wts[2];
-    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kMagic, 8) != 0 ||
-        fread(hdr, sizeof(hdr), 1, f) != 1 || fread(wts, sizeof(wts), 1, f) != 1 || hdr[0] != 1 ||
-        hdr[1] < 1 || hdr[2] < 1 || hdr[3] < 1 || hdr[3] > 4 || hdr[4] < 0 ||
-        hdr[4] > kMaxDegree) {
+    uint8_t lay[2 * kMaxAttr];
+    bool hdr_ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 8) == 0 &&
+                  fread(hdr, sizeof(hdr), 1, f) == 1 && fread(wts, sizeof(wts), 1, f) == 1 &&
+                  (hdr[0] == 1 || hdr[0] == 2) && hdr[1] >= 1 && hdr[2] >= 1 && hdr[3] >= 1 &&
+                  hdr[3] <= (hdr[0] == 1 ? 4 : kMaxAttr) && hdr[4] >= 0 && hdr[4] <= kMaxDegree;
+    if (hdr_ok && hdr[0] == 2)
+        hdr_ok = fread(lay, sizeof(lay), 1, f) == 1;
+    if (hdr_ok && hdr[0] == 1) {  // a byte per attribute
+        for (int j = 0; j < kMaxAttr; ++j) {
+            lay[j] = (uint8_t)(8 * j);
+            lay[kMaxAttr + j] = 8;
+        }
+    }
+    for (int j = 0; hdr_ok && j < hdr[3]; ++j)
+        hdr_ok = lay[kMaxAttr + j] >= 1 && lay[kMaxAttr + j] <= 8 + 1 &&
+                 lay[j] + lay[kMaxAttr + j] <= 32;
+    if (!hdr_ok) {
         fclose(f);
-        return fail(NHQ_ERR_IO, "%s is not an index file of version 1", path);
+        return fail(NHQ_ERR_IO, "%s is not an index file of version 1 or 2", path);
     }
     const size_t N = (size_t)hdr[1], d = (size_t)hdr[2], m = (size_t)hdr[3], R = (size_t)hdr[4];
     std::vector<float> X(N * d);
@@ -1272,7 +1309,7 @@ nhq_status nhq_load(const char *path, void *stream, nhq_index **out) {
     std::vector<uint8_t> a8(N * m);
     for (size_t i = 0; i < N; ++i)
         for (size_t j = 0; j < m; ++j)
-            a8[i * m + j] = (uint8_t)(attr[i] >> (8 * j));
+            a8[i * m + j] = (uint8_t)((attr[i] >> lay[j]) & ((1u << lay[kMaxAttr + j]) - 1u));
     nhq_weights w{hdr[5], wts[0], wts[1]};
     nhq_index *ix = nullptr;
     CKS(nhq_index_create(X.data(), (int64_t)N, (int32_t)d, a8.data(), (int32_t)m, w, stream, &ix));

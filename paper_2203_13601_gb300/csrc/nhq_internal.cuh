@@ -20,12 +20,29 @@ constexpr int kMaxK = 256;
 constexpr int kMaxEf = 1024;
 constexpr int kMaxCand = 128;
 
-// Fusion-distance weights (Eq. 6) as the kernels see them.
+constexpr int kMaxAttr = 32;
+
+// How the m attribute codes of an object share one u32 word: code j occupies bits
+// [shift[j], shift[j] + width[j]).  Up to 4 attributes take a byte each (shift 8j, any
+// code 0..255); more take the fewest bits that hold 0..maxc[j] + 1, where maxc[j] is the
+// largest code of attribute j among the objects.  A query code above maxc[j] equals no
+// object's code and is stored as maxc[j] + 1, so chi on words equals chi on codes.
+struct AttrLayout {
+    int m = 0;
+    uint8_t shift[kMaxAttr] = {};
+    uint8_t width[kMaxAttr] = {};
+    uint8_t maxc[kMaxAttr] = {};
+    uint32_t hi = 0;  // the top bit of every field
+    uint32_t lo = 0;  // the other bits of every field
+};
+
+// Fusion-distance weights (Eq. 6) and the attribute layout, as the kernels see them.
 struct Fusion {
     int mode;  // nhq_weight_mode
     float wv, wl;
     int m;
-    uint32_t mask;  // low 8*m bits set
+    uint32_t hi, lo;  // AttrLayout::hi / lo
+    uint8_t shift[kMaxAttr], maxc[kMaxAttr];
 };
 
 // ---- splitmix64 (Vigna): the finaliser and the j-th output of a stream ----
@@ -38,9 +55,29 @@ __host__ __device__ __forceinline__ uint64_t splitmix_at(uint64_t s0, uint64_t j
     return mix64(s0 + (j + 1) * kGolden);
 }
 
-// chi (Eq. 4-5) on packed attribute words: number of differing bytes among the m used.
-__device__ __forceinline__ int chi_packed(uint32_t a, uint32_t b, uint32_t mask) {
-    return __popc(__vcmpne4((a ^ b) & mask, 0u)) >> 3;
+// chi (Eq. 4-5) on packed attribute words: the number of fields in which a and b differ.
+// In x = a ^ b, adding the low bits of a field to the field's low-bit mask carries into
+// the field's top bit iff a low bit is set, and never past it; so the top bit of
+// ((x & lo) + lo) | x is set exactly for the nonzero fields.
+__host__ __device__ __forceinline__ int chi_packed(uint32_t a, uint32_t b, uint32_t hi,
+                                                   uint32_t lo) {
+    const uint32_t x = a ^ b;
+#ifdef __CUDA_ARCH__
+    return __popc((((x & lo) + lo) | x) & hi);
+#else
+    return __builtin_popcount((((x & lo) + lo) | x) & hi);
+#endif
+}
+
+// A query's packed word under the layout in w (codes above maxc[j] become maxc[j] + 1).
+__device__ __forceinline__ uint32_t pack_query_word(const uint8_t *qa, const Fusion &w) {
+    uint32_t word = 0;
+    for (int j = 0; j < w.m; ++j) {
+        const uint32_t v = qa[j];
+        const uint32_t c = v <= w.maxc[j] ? v : (uint32_t)w.maxc[j] + 1u;
+        word |= c << w.shift[j];
+    }
+    return word;
 }
 
 // Gamma (Eq. 6) from delta and chi, each operation rounded once (round-to-nearest),
@@ -107,6 +144,7 @@ struct nhq_index {
     float *X = nullptr;            // [N][xstride] f32
     __nv_bfloat16 *Xh = nullptr;   // [N][xstride] bf16 copy (built on first BF16 search)
     __nv_fp8_e4m3 *X8 = nullptr;   // [N][xstride] fp8 e4m3 copy (built on first FP8 search)
+    nhq::AttrLayout layout;        // how attr packs the m codes
     uint32_t *attr = nullptr;      // [N] packed attributes
     uint32_t *nbr = nullptr;       // [N][R] adjacency, kNone padded
     uint32_t *nbr_attr = nullptr;  // [N][R] packed attributes of each neighbour
@@ -122,11 +160,21 @@ struct nhq_index {
 
 namespace nhq {
 
-nhq::Fusion make_fusion(const nhq_weights &w, int m);
+// a byte per attribute (m <= 4), the layout of nhq_pack_attributes
+AttrLayout byte_layout(int m);
+// the layout of m attributes whose largest codes are maxc[0..m); false if the fields
+// need more than 32 bits
+bool compact_layout(int m, const uint8_t *maxc, AttrLayout *out);
+nhq::Fusion make_fusion(const nhq_weights &w, const AttrLayout &L);
+nhq::Fusion make_fusion(const nhq_weights &w, int m);  // byte layout
 nhq_status report_error(nhq_status s, const char *message);  // nhq_api.cu
 
 // k_util.cu
-cudaError_t launch_pack_attributes(const uint8_t *a, int64_t n, int m, uint32_t *out, cudaStream_t s);
+cudaError_t launch_pack_attributes(const uint8_t *a, int64_t n, const AttrLayout &L,
+                                   uint32_t *out, cudaStream_t s);
+// out[0..kMaxAttr) = the largest code of each of the m attributes over n rows
+cudaError_t launch_attr_max(const uint8_t *a, int64_t n, int m, unsigned int *out,
+                            cudaStream_t s);
 cudaError_t launch_copy_rows(const float *src, int64_t N, int d, int xstride, float *dst,
                              int *nonfinite_flag, cudaStream_t s);
 cudaError_t launch_rows_to_bf16(const float *src, int64_t n_elems, __nv_bfloat16 *dst, cudaStream_t s);

@@ -109,8 +109,8 @@ def zipf_attributes(rng, n, cards, s=1.0):
 
 
 def _check_cards(cards):
-    if not 1 <= len(cards) <= 4 or any(c < 1 or c > 256 for c in cards):
-        raise ValueError("1..4 attributes with cardinality 1..256 are supported")
+    if not 1 <= len(cards) <= 32 or any(c < 1 or c > 256 for c in cards):
+        raise ValueError("1..32 attributes with cardinality 1..256 are supported")
 
 
 def c1(N=10_000, nq=1_000, d=128, cards=(3, 5, 10), n_comp=100, seed=1000):

@@ -63,11 +63,13 @@ def test_argument_errors_before_cuda(lib):
     out = C.c_void_p()
     w = nhq._Weights(0, 1.0, 0.0)
     x = np.zeros((4, 3), np.float32)
-    a = np.zeros((4, 5), np.uint8)
-    # m = 5 attributes is outside 1..4
-    st = lib.nhq_index_create(x.ctypes.data, 4, 3, a.ctypes.data, 5, w, None, C.byref(out))
+    a = np.zeros((4, 33), np.uint8)
+    # m = 33 attributes is outside 1..32
+    st = lib.nhq_index_create(x.ctypes.data, 4, 3, a.ctypes.data, 33, w, None, C.byref(out))
     assert st == nhq.ERR_ARG and out.value is None
     assert "m must be" in nhq.nhq_last_error()
+    st = lib.nhq_index_create(x.ctypes.data, 4, 3, a.ctypes.data, 0, w, None, C.byref(out))
+    assert st == nhq.ERR_ARG and out.value is None
     # N = 0
     st = lib.nhq_index_create(x.ctypes.data, 0, 3, a.ctypes.data, 2, w, None, C.byref(out))
     assert st == nhq.ERR_ARG
