@@ -70,15 +70,18 @@ def _L():
             lib.or_delta32.argtypes = [P, P, i32]
             lib.or_chi.restype = i32
             lib.or_chi.argtypes = [P, P, i32]
+            lib.or_chi_query.restype = i32
+            lib.or_chi_query.argtypes = [P, P, i32, i32]
             lib.or_gamma64.restype = f64
             lib.or_gamma64.argtypes = [f64, i32, i32, i32, f64, f64]
             lib.or_gamma32.restype = C.c_float
             lib.or_gamma32.argtypes = [C.c_float, i32, i32, i32, C.c_float, C.c_float]
             lib.or_fused_topk.restype = None
             lib.or_fused_topk.argtypes = [P, P, i64, i32, i32, P, P, i64, i32, i32, f64, f64, i32,
-                                          P, P, P]
+                                          P, P, P, i32]
             lib.or_filtered_topk.restype = None
-            lib.or_filtered_topk.argtypes = [P, P, i64, i32, i32, P, P, i64, i32, i32, P, P, P]
+            lib.or_filtered_topk.argtypes = [P, P, i64, i32, i32, P, P, i64, i32, i32, P, P, P,
+                                             i32]
             lib.or_knn.restype = None
             lib.or_knn.argtypes = [P, P, i64, i32, i32, i32, i32, f64, f64, i32, P, i64, P, P]
             lib.or_edge_select.restype = None
@@ -91,7 +94,7 @@ def _L():
             lib.or_search.restype = None
             lib.or_search.argtypes = [P, P, i64, i32, i32, P, i32, P, P, i64, i32, i32, i32, u64,
                                       i64, i32, f64, f64, i32, i32, P, i32, i32, i32, P, P, P, P,
-                                      P, P]
+                                      P, P, i32]
             lib.or_round_bf16.restype = C.c_float
             lib.or_round_bf16.argtypes = [C.c_float]
             lib.or_round_e4m3.restype = C.c_float
@@ -150,6 +153,17 @@ def chi(a, b) -> int:
     return int(_L().or_chi(_p(a), _p(b), a.shape[0]))
 
 
+def chi_query(qa, a, wildcard=None) -> int:
+    """chi of a query against an object; with ``wildcard`` (a code 0..255), query
+    positions holding that code are unconstrained and never count."""
+    qa, a = _u8(qa), _u8(a)
+    return int(_L().or_chi_query(_p(qa), _p(a), qa.shape[0], _wild(wildcard)))
+
+
+def _wild(wildcard):
+    return -1 if wildcard is None else int(wildcard)
+
+
 def gamma(delta_value, chi_value, m, weights=None, prec=F64) -> float:
     mode, wv, wl = _mode(weights)
     if prec == F32:
@@ -158,8 +172,9 @@ def gamma(delta_value, chi_value, m, weights=None, prec=F64) -> float:
 
 
 # ---------------------------------------------------------------- batches
-def fused_topk(X, A, Qv, QA, k, weights=None, prec=F64):
-    """Exact top-k by (Gamma, id): returns ids [nq,k] int64, gamma [nq,k] f64, chi [nq,k]."""
+def fused_topk(X, A, Qv, QA, k, weights=None, prec=F64, wildcard=None):
+    """Exact top-k by (Gamma, id): returns ids [nq,k] int64, gamma [nq,k] f64, chi [nq,k].
+    ``wildcard``: query code that leaves its position unconstrained (None: none)."""
     X, A, Qv, QA = _f32(X), _u8(A), _f32(Qv), _u8(QA)
     nq = Qv.shape[0]
     ids = np.empty((nq, k), np.int64)
@@ -167,11 +182,11 @@ def fused_topk(X, A, Qv, QA, k, weights=None, prec=F64):
     ch = np.empty((nq, k), np.int32)
     mode, wv, wl = _mode(weights)
     _L().or_fused_topk(_p(X), _p(A), X.shape[0], X.shape[1], A.shape[1], _p(Qv), _p(QA), nq, k,
-                       mode, wv, wl, prec, _p(ids), _p(g), _p(ch))
+                       mode, wv, wl, prec, _p(ids), _p(g), _p(ch), _wild(wildcard))
     return ids, g, ch
 
 
-def filtered_topk(X, A, Qv, QA, k, prec=F64):
+def filtered_topk(X, A, Qv, QA, k, prec=F64, wildcard=None):
     """Hybrid ground truth G: k nearest by delta among exact attribute matches.
     Returns ids [nq,k] (-1 padded), delta [nq,k], |P| [nq]."""
     X, A, Qv, QA = _f32(X), _u8(A), _f32(Qv), _u8(QA)
@@ -180,7 +195,7 @@ def filtered_topk(X, A, Qv, QA, k, prec=F64):
     dl = np.empty((nq, k), np.float64)
     P = np.empty(nq, np.int64)
     _L().or_filtered_topk(_p(X), _p(A), X.shape[0], X.shape[1], A.shape[1], _p(Qv), _p(QA), nq,
-                          k, prec, _p(ids), _p(dl), _p(P))
+                          k, prec, _p(ids), _p(dl), _p(P), _wild(wildcard))
     return ids, dl, P
 
 
@@ -341,11 +356,14 @@ def round_e4m3(x) -> float:
 
 
 def search(X, A, nbr, Qv, QA, k, ef, h=1, seed=0, max_iters=1 << 30, weights=None, prec=F32,
-           seed_mode=SEED_RANDOM, seeds=None, vec_round=ROUND_NONE, rerank=False):
+           seed_mode=SEED_RANDOM, seeds=None, vec_round=ROUND_NONE, rerank=False,
+           wildcard=None):
     """Serial Alg. 2 (+ two-stage routing when h > 1).  ``seed_mode`` picks the
     seed set B (random stream / attribute entry / the rows of ``seeds``, -1 =
     none).  ``vec_round`` scores candidates with X rounded to bf16 / fp8 e4m3;
     ``rerank`` re-scores the final pool with X itself before returning the first k.
+    ``wildcard``: query code that leaves its position unconstrained; a query holding it
+    has no tuple run, so the attribute seed modes give it the random stream.
     Returns a dict with ids/gamma/chi [nq,k], ndc/expansions/status [nq]."""
     X, A, nbr, Qv, QA = _f32(X), _u8(A), _i64(nbr), _f32(Qv), _u8(QA)
     if seeds is not None:
@@ -365,7 +383,7 @@ def search(X, A, nbr, Qv, QA, k, ef, h=1, seed=0, max_iters=1 << 30, weights=Non
     _L().or_search(_p(X), _p(A), X.shape[0], X.shape[1], A.shape[1], _p(nbr), nbr.shape[1],
                    _p(Qv), _p(QA), nq, k, ef, h, C.c_uint64(seed & (2**64 - 1)), max_iters,
                    mode, wv, wl, prec, seed_mode, sp, ns, int(vec_round), int(bool(rerank)),
-                   _p(ids), _p(g), _p(ch), _p(ndc), _p(ex), _p(st))
+                   _p(ids), _p(g), _p(ch), _p(ndc), _p(ex), _p(st), _wild(wildcard))
     return dict(ids=ids, gamma=g, chi=ch, ndc=ndc, expansions=ex, status=st)
 
 

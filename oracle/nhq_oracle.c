@@ -118,6 +118,27 @@ int or_chi(const uint8_t *a, const uint8_t *b, int m)
     return c;
 }
 
+/* chi of a query (codes qa) against an object (codes a) when a query code equal to
+ * `wild` places no constraint on its position (a partial constraint, which the paper
+ * does not define): such positions never count.  wild < 0: every position counts,
+ * as or_chi. */
+int or_chi_query(const uint8_t *qa, const uint8_t *a, int m, int wild)
+{
+    int c = 0;
+    for (int i = 0; i < m; ++i)
+        c += (qa[i] != a[i] && (int)qa[i] != wild) ? 1 : 0;
+    return c;
+}
+
+/* whether the query leaves some position open */
+static int or_query_open(const uint8_t *qa, int m, int wild)
+{
+    for (int i = 0; i < m; ++i)
+        if ((int)qa[i] == wild)
+            return 1;
+    return 0;
+}
+
 /* Reduced-precision copies used for scoring (a project addition, not in the
  * paper): each object component rounded to nearest, ties to even.
  *   bf16      : 8 significant bits (the upper half of the f32 encoding)
@@ -190,10 +211,12 @@ float or_gamma32(float delta, int chi, int m, int mode, float wv, float wl)
 }
 
 /* Gamma between row x (attrs ax) and row y (attrs ay) in the chosen precision */
+/* (wild: the query wildcard code when x is a query, else -1) */
 static double pair_gamma(const float *x, const uint8_t *ax, const float *y, const uint8_t *ay,
-                         int d, int m, int mode, double wv, double wl, int prec, int *chi_out)
+                         int d, int m, int mode, double wv, double wl, int prec, int *chi_out,
+                         int wild)
 {
-    int chi = or_chi(ax, ay, m);
+    int chi = or_chi_query(ax, ay, m, wild);
     if (chi_out)
         *chi_out = chi;
     if (prec == OR_F32)
@@ -232,7 +255,7 @@ static int rec_less(double ga, int64_t ia, double gb, int64_t ib)
 void or_fused_topk(const float *X, const uint8_t *A, int64_t N, int d, int m,
                    const float *Qv, const uint8_t *QA, int64_t nq, int k,
                    int mode, double wv, double wl, int prec,
-                   int64_t *out_ids, double *out_g, int32_t *out_chi)
+                   int64_t *out_ids, double *out_g, int32_t *out_chi, int wild)
 {
     rec_t *all = (rec_t *)malloc(sizeof(rec_t) * (size_t)(N > 0 ? N : 1));
     for (int64_t q = 0; q < nq; ++q) {
@@ -241,7 +264,7 @@ void or_fused_topk(const float *X, const uint8_t *A, int64_t N, int d, int m,
         for (int64_t v = 0; v < N; ++v) {
             int chi;
             all[v].g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m,
-                                  mode, wv, wl, prec, &chi);
+                                  mode, wv, wl, prec, &chi, wild);
             all[v].id = v;
             all[v].chi = chi;
         }
@@ -266,7 +289,7 @@ void or_fused_topk(const float *X, const uint8_t *A, int64_t N, int d, int m,
  * whose attributes all equal the query's (chi = 0); out_P[q] = |P|. */
 void or_filtered_topk(const float *X, const uint8_t *A, int64_t N, int d, int m,
                       const float *Qv, const uint8_t *QA, int64_t nq, int k, int prec,
-                      int64_t *out_ids, double *out_delta, int64_t *out_P)
+                      int64_t *out_ids, double *out_delta, int64_t *out_P, int wild)
 {
     rec_t *all = (rec_t *)malloc(sizeof(rec_t) * (size_t)(N > 0 ? N : 1));
     for (int64_t q = 0; q < nq; ++q) {
@@ -274,7 +297,7 @@ void or_filtered_topk(const float *X, const uint8_t *A, int64_t N, int d, int m,
         const uint8_t *qa = QA + q * (int64_t)m;
         int64_t n = 0;
         for (int64_t v = 0; v < N; ++v) {
-            if (or_chi(qa, A + v * (int64_t)m, m) != 0)
+            if (or_chi_query(qa, A + v * (int64_t)m, m, wild) != 0)
                 continue;
             const float *x = X + v * (int64_t)d;
             all[n].g = prec == OR_F32 ? (double)or_delta32(qv, x, d) : or_delta64(qv, x, d);
@@ -307,7 +330,7 @@ void or_knn(const float *X, const uint8_t *A, int64_t N, int d, int m, int K,
             if (v == u)
                 continue;
             all[n].g = pair_gamma(X + u * (int64_t)d, A + u * (int64_t)m, X + v * (int64_t)d,
-                                  A + v * (int64_t)m, d, m, mode, wv, wl, prec, NULL);
+                                  A + v * (int64_t)m, d, m, mode, wv, wl, prec, NULL, -1);
             all[n].id = v;
             ++n;
         }
@@ -355,7 +378,7 @@ void or_edge_select(const float *X, const uint8_t *A, int64_t N, int d, int m,
             if (dup)
                 continue;
             c[n].g = pair_gamma(X + p * (int64_t)d, A + p * (int64_t)m, xu, au, d, m, mode, wv,
-                                wl, prec, NULL);
+                                wl, prec, NULL, -1);
             c[n].id = p;
             ++n;
         }
@@ -370,7 +393,7 @@ void or_edge_select(const float *X, const uint8_t *A, int64_t N, int d, int m,
                 int64_t j = nb[s];
                 double gpj = pair_gamma(X + p * (int64_t)d, A + p * (int64_t)m,
                                         X + j * (int64_t)d, A + j * (int64_t)m, d, m, mode,
-                                        wv, wl, prec, NULL);
+                                        wv, wl, prec, NULL, -1);
                 if (!(c[t].g < gpj && c[t].g > nbg[s]))
                     ok = 0;
             }
@@ -517,7 +540,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                int mode, double wv, double wl, int prec, int seed_mode,
                const int64_t *seeds_in, int n_seeds, int vec_round, int rerank,
                int64_t *out_ids, double *out_g, int32_t *out_chi,
-               int64_t *out_ndc, int64_t *out_exp, int32_t *out_status)
+               int64_t *out_ndc, int64_t *out_exp, int32_t *out_status, int wild)
 {
     /* vec_round: 0 scores with X itself, 1 with X rounded to bf16, 2 to fp8 e4m3.
      * rerank: the final pool is re-scored with X in the chosen precision prec and
@@ -550,7 +573,8 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
         /* seed set B */
         int want = ef < 32 ? ef : 32;
         int64_t c = 0;
-        if (seed_mode == 1 || seed_mode == 3)
+        /* a query that leaves a position open has no tuple run: it takes mode 0 */
+        if ((seed_mode == 1 || seed_mode == 3) && !or_query_open(qa, m, wild))
             for (int64_t v = 0; v < N; ++v)
                 c += or_chi(qa, A + v * (int64_t)m, m) == 0 ? 1 : 0;
         if (seed_mode == 2) {
@@ -561,7 +585,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                 evaluated[v] = 1;
                 ++ndc;
                 double g = pair_gamma(qv, qa, Xs + v * (int64_t)d, A + v * (int64_t)m, d, m,
-                                      mode, wv, wl, prec, NULL);
+                                      mode, wv, wl, prec, NULL, wild);
                 pool_insert(pool, &n, ef, g, v);
             }
         } else if (seed_mode == 3 && c > 0) {
@@ -586,7 +610,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                 evaluated[v] = 1;
                 ++ndc;
                 double g = pair_gamma(qv, qa, Xs + v * (int64_t)d, A + v * (int64_t)m, d, m,
-                                      mode, wv, wl, prec, NULL);
+                                      mode, wv, wl, prec, NULL, wild);
                 pool_insert(pool, &n, ef, g, v);
             }
             free(cm);
@@ -601,7 +625,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                     evaluated[v] = 1;
                     ++ndc;
                     double g = pair_gamma(qv, qa, Xs + v * (int64_t)d, A + v * (int64_t)m, d, m,
-                                          mode, wv, wl, prec, NULL);
+                                          mode, wv, wl, prec, NULL, wild);
                     pool_insert(pool, &n, ef, g, v);
                     ++j;
                 }
@@ -617,7 +641,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                 ++ndc;
                 ++got;
                 double g = pair_gamma(qv, qa, Xs + v * (int64_t)d, A + v * (int64_t)m, d, m,
-                                      mode, wv, wl, prec, NULL);
+                                      mode, wv, wl, prec, NULL, wild);
                 pool_insert(pool, &n, ef, g, v);
             }
         }
@@ -679,7 +703,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                 evaluated[v] = 1;
                 ++ndc;
                 double g = pair_gamma(qv, qa, Xs + v * (int64_t)d, A + v * (int64_t)m, d, m,
-                                      mode, wv, wl, prec, NULL);
+                                      mode, wv, wl, prec, NULL, wild);
                 pool_insert(pool, &n, ef, g, v);
             }
             if (stage == 1) {
@@ -700,7 +724,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
             for (int t = 0; t < n; ++t) {
                 int64_t v = pool[t].id;
                 rr[t].g = pair_gamma(qv, qa, X + v * (int64_t)d, A + v * (int64_t)m, d, m, mode,
-                                     wv, wl, prec, NULL);
+                                     wv, wl, prec, NULL, wild);
                 rr[t].id = v;
             }
             qsort(rr, (size_t)n, sizeof(rec_t), rec_cmp);
@@ -716,7 +740,7 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                 int64_t v = pool[j].id;
                 out_ids[o] = v;
                 out_g[o] = pool[j].g;
-                out_chi[o] = or_chi(qa, A + v * (int64_t)m, m);
+                out_chi[o] = or_chi_query(qa, A + v * (int64_t)m, m, wild);
             } else {
                 out_ids[o] = -1;
                 out_g[o] = INFINITY;

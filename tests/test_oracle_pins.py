@@ -569,3 +569,69 @@ def test_nearest_attribute_entry_seeds_are_the_nearest_matches(oracle_mod):
             assert (r["ids"][q] == ref[q]).all(), q
             checked += 1
     assert checked >= 20
+
+
+# ------------------------------------------------------------------ partial constraints
+def test_chi_query_wildcard_hand_cases(oracle_mod):
+    O = oracle_mod
+    q = np.array([1, 255, 3, 255], np.uint8)
+    assert O.chi_query(q, np.array([1, 7, 3, 0], np.uint8), 255) == 0   # open positions
+    assert O.chi_query(q, np.array([2, 255, 4, 255], np.uint8), 255) == 2
+    assert O.chi_query(q, np.array([1, 7, 4, 0], np.uint8), 255) == 1
+    # without a wildcard 255 is an ordinary code
+    assert O.chi_query(q, np.array([1, 7, 3, 0], np.uint8)) == 2
+    assert O.chi_query(q, np.array([1, 255, 3, 255], np.uint8)) == 0
+    # a different wildcard code
+    assert O.chi_query(np.array([9, 4], np.uint8), np.array([5, 4], np.uint8), 9) == 0
+
+
+def test_fully_open_query_is_plain_l2(oracle_mod):
+    # every position open: chi = 0 for every object, so Gamma = w_v * delta and the
+    # exact fused top-k is the L2 top-k by (delta, id), computed here with numpy
+    O = oracle_mod
+    w = synth.int_valued(500, 20, 12, cards=(3, 4, 5), seed=57)
+    QA = np.full_like(w.QA, 255)
+    d2 = ((w.Qv[:, None, :].astype(np.int64) - w.X[None, :, :].astype(np.int64)) ** 2).sum(-1)
+    want = np.array([np.lexsort((np.arange(w.N), d2[q]))[:10] for q in range(w.nq)])
+    for wts in (None, (1.0, 10000.0)):
+        ids, g, ch = O.fused_topk(w.X, w.A, w.Qv, QA, 10, weights=wts, prec=O.F32,
+                                  wildcard=255)
+        assert (ids == want).all()
+        assert (ch == 0).all()
+        assert np.array_equal(g, np.sqrt(np.take_along_axis(d2, want, 1).astype(np.float32)))
+
+
+def test_partially_open_filter_matches_constrained_columns(oracle_mod):
+    # the hybrid ground truth under a partial constraint: the objects equal on the
+    # constrained columns only, by (delta, id), computed here with numpy
+    O = oracle_mod
+    w = synth.int_valued(800, 30, 8, cards=(3, 4, 5), seed=58)
+    QA = w.QA.copy()
+    QA[::2, 1] = 255
+    QA[::3, 0] = 255
+    ids, dl, P = O.filtered_topk(w.X, w.A, w.Qv, QA, 10, prec=O.F32, wildcard=255)
+    d2 = ((w.Qv[:, None, :].astype(np.int64) - w.X[None, :, :].astype(np.int64)) ** 2).sum(-1)
+    for q in range(w.nq):
+        cols = QA[q] != 255
+        ok = np.flatnonzero((w.A[:, cols] == QA[q, cols]).all(axis=1))
+        assert P[q] == ok.size
+        order = ok[np.lexsort((ok, d2[q, ok]))][:10]
+        assert (ids[q, :order.size] == order).all() and (ids[q, order.size:] == -1).all()
+
+
+def test_search_with_open_positions(oracle_mod):
+    O = oracle_mod
+    w = synth.c1(N=30, nq=12, d=8, cards=(2, 3), seed=13)
+    QA = w.QA.copy()
+    QA[::2, 0] = 255
+    G = _complete_graph(30)
+    ref, rg, _ = O.fused_topk(w.X, w.A, w.Qv, QA, 5, prec=O.F32, wildcard=255)
+    for ef in (5, 30):
+        r = O.search(w.X, w.A, G, w.Qv, QA, 5, ef, seed=3, wildcard=255)
+        assert (r["ids"] == ref).all() and np.array_equal(r["gamma"], rg)
+    # an open query has no tuple run: the attribute seed rule gives it the random stream
+    nbr = np.full((30, 2), -1, np.int64)
+    a = O.search(w.X, w.A, nbr, w.Qv, QA, 5, 8, seed=3, wildcard=255, max_iters=0,
+                 seed_mode=O.SEED_ATTRIBUTE)
+    b = O.search(w.X, w.A, nbr, w.Qv, QA, 5, 8, seed=3, wildcard=255, max_iters=0)
+    assert (a["ids"][::2] == b["ids"][::2]).all()
