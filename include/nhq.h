@@ -121,7 +121,11 @@ typedef struct nhq_search_params {
     float stop_threshold;    /* stop when sigmoid(logit) > this probability                   */
     int32_t stop_min;        /* first expansion count at which the model is consulted          */
     int32_t stop_every;      /* consult it every this many expansions (>= 1 when a model is set) */
-    int32_t reserved;
+    int32_t wildcard;        /* 1: a query code 255 places no constraint on its attribute (a
+                                partial constraint; the paper's hybrid query constrains every
+                                attribute): it never counts toward chi, and a query holding it
+                                has no tuple run, so the attribute seed modes give it the
+                                random stream of NHQ_SEED_RANDOM.  0: 255 is an ordinary code */
 } nhq_search_params;
 
 typedef struct nhq_index nhq_index;
@@ -268,6 +272,11 @@ nhq_status nhq_build(const float *vectors, int64_t N, int32_t d, const uint8_t *
  * Sec. 6.1).  ids[Q][k] u32, dists[Q][k] f32, chi[Q][k] u8 (may be NULL).
  * Errors: k outside 1..256.
  */
+/* nhq_brute_force with the wildcard rule of nhq_search_params::wildcard (0 or 1). */
+nhq_status nhq_brute_force_wildcard(const nhq_index *index, const float *queries,
+                                    const uint8_t *query_attributes, int64_t Q, int32_t k,
+                                    const nhq_weights *w, int32_t wildcard, uint32_t *ids,
+                                    float *dists, uint8_t *chi, void *stream);
 nhq_status nhq_brute_force(const nhq_index *index, const float *queries,
                            const uint8_t *query_attributes, int64_t Q, int32_t k,
                            const nhq_weights *w, uint32_t *ids, float *dists, uint8_t *chi,

@@ -26,7 +26,7 @@ __all__ = [
     "nhq_last_error", "nhq_version", "nhq_index_create", "nhq_free", "nhq_index_info",
     "nhq_pack_attributes", "nhq_knn", "nhq_knn_bf16", "nhq_edge_select", "nhq_reverse_candidates",
     "nhq_index_set_graph", "nhq_index_get_graph", "nhq_index_build", "nhq_build",
-    "nhq_brute_force", "nhq_search", "nhq_search_batched", "nhq_save", "nhq_load",
+    "nhq_brute_force", "nhq_brute_force_wildcard", "nhq_search", "nhq_search_batched", "nhq_save", "nhq_load",
     "nhq_brute_force_noalloc", "nhq_search_trace", "nhq_mlp_forward", "nhq_mlp_grad",
     "nhq_mlp_train", "MLP_INPUTS", "MLP_HIDDEN", "MLP_PARAMS", "nhq_autotune_search",
     "nhq_search_graph_create", "nhq_search_graph_launch", "nhq_search_graph_free",
@@ -66,7 +66,7 @@ class _SearchParams(C.Structure):
                 ("vec_dtype", C.c_int32), ("rerank", C.c_int32), ("seed_mode", C.c_int32),
                 ("n_seeds", C.c_int32), ("seeds", C.c_void_p), ("stop_model", C.c_void_p),
                 ("stop_threshold", C.c_float), ("stop_min", C.c_int32),
-                ("stop_every", C.c_int32), ("reserved", C.c_int32)]
+                ("stop_every", C.c_int32), ("wildcard", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -108,6 +108,8 @@ def load_library():
             "nhq_build": (S, [P, i64, i32, P, i32, i32, _Weights, C.POINTER(_BuildParams), P,
                               C.POINTER(P)]),
             "nhq_brute_force": (S, [P, P, P, i64, i32, C.POINTER(_Weights), P, P, P, P]),
+            "nhq_brute_force_wildcard": (S, [P, P, P, i64, i32, C.POINTER(_Weights), i32, P, P,
+                                             P, P]),
             "nhq_merge_topk": (S, [i32, i64, i32, i32, P, P, P, P, P, P, P, P]),
             "nhq_postfilter": (S, [i64, i32, i32, P, P, P, P, P, P]),
             "nhq_search": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P, P, P, P, P,
@@ -351,20 +353,27 @@ def nhq_merge_topk(ids, dists, offsets, k_out, out_ids, out_dists, chi=None, out
 
 
 def nhq_brute_force(index, queries, query_attributes, k, ids, dists=None, chi=None,
-                    weights="index", stream=None) -> None:
+                    weights="index", stream=None, wildcard=0) -> None:
+    """``wildcard=1``: a query code 255 leaves its attribute unconstrained."""
     Q, d = _shape(queries)
     m = _shape(query_attributes)[1]
     w = None if weights == "index" else C.byref(_weights(weights))
-    _check(load_library().nhq_brute_force(
+    _check(load_library().nhq_brute_force_wildcard(
         index, _ptr(queries, np.float32, (Q, d), "queries"),
-        _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, w,
+        _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, w, int(wildcard),
         _ptr(ids, np.uint32, (Q, k), "ids"), _ptr(dists, np.float32, (Q, k), "dists"),
         _ptr(chi, np.uint8, (Q, k), "chi"), _stream(stream)))
 
 
+def nhq_brute_force_wildcard(index, queries, query_attributes, k, wildcard, ids, dists=None,
+                             chi=None, weights="index", stream=None) -> None:
+    nhq_brute_force(index, queries, query_attributes, k, ids, dists, chi, weights, stream,
+                    wildcard)
+
+
 def _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
                    seed_mode=SEED_RANDOM, seeds=None, Q=None, stop_model=None,
-                   stop_threshold=0.5, stop_min=0, stop_every=1):
+                   stop_threshold=0.5, stop_min=0, stop_every=1, wildcard=0):
     """Search parameters; ``seeds`` ([Q][n] uint32, 0xFFFFFFFF = none) selects SEED_GIVEN;
     ``stop_model`` (device f32 [MLP_PARAMS]) turns on the learned early stop."""
     n_seeds, sp = 0, None
@@ -376,18 +385,19 @@ def _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, re
     return _SearchParams(int(seed) & (2**64 - 1), int(h), int(max_iters), int(warps_per_block),
                          int(hash_bits), int(vec_dtype), int(rerank), int(seed_mode),
                          int(n_seeds), sp, mp, float(stop_threshold), int(stop_min),
-                         int(stop_every), 0)
+                         int(stop_every), int(wildcard))
 
 
 def nhq_search(index, queries, query_attributes, k, ef, ids, dists=None, chi=None, status=None,
                ndc=None, expansions=None, h=1, seed=0, max_iters=0, warps_per_block=0,
                hash_bits=0, vec_dtype=VEC_F32, rerank=0, seed_mode=SEED_RANDOM, seeds=None,
                stop_model=None, stop_threshold=0.5, stop_min=0, stop_every=1,
-               stream=None) -> None:
+               stream=None, wildcard=0) -> None:
     Q, d = _shape(queries)
     m = _shape(query_attributes)[1]
     p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
-                       seed_mode, seeds, Q, stop_model, stop_threshold, stop_min, stop_every)
+                       seed_mode, seeds, Q, stop_model, stop_threshold, stop_min, stop_every,
+                       wildcard)
     _check(load_library().nhq_search(
         index, _ptr(queries, np.float32, (Q, d), "queries"),
         _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, ef, C.byref(p),
@@ -400,11 +410,11 @@ def nhq_search(index, queries, query_attributes, k, ef, ids, dists=None, chi=Non
 def nhq_search_batched(index, queries, query_attributes, k_arr, ef_arr, k_max, ids, dists=None,
                        chi=None, status=None, ndc=None, expansions=None, h=1, seed=0,
                        max_iters=0, warps_per_block=0, hash_bits=0, vec_dtype=VEC_F32, rerank=0,
-                       seed_mode=SEED_RANDOM, seeds=None, stream=None) -> None:
+                       seed_mode=SEED_RANDOM, seeds=None, stream=None, wildcard=0) -> None:
     Q, d = _shape(queries)
     m = _shape(query_attributes)[1]
     p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
-                       seed_mode, seeds, Q)
+                       seed_mode, seeds, Q, wildcard=wildcard)
     _check(load_library().nhq_search_batched(
         index, _ptr(queries, np.float32, (Q, d), "queries"),
         _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q,
@@ -457,7 +467,7 @@ class SearchGraph:
         self._p = _search_params(kw.get("seed", 0), kw.get("h", 1), kw.get("max_iters", 0),
                                  kw.get("warps_per_block", 0), kw.get("hash_bits", 0),
                                  kw.get("vec_dtype", VEC_F32), kw.get("rerank", 0),
-                                 kw["seed_mode"], None, Q)
+                                 kw["seed_mode"], None, Q, wildcard=kw.get("wildcard", 0))
         out = C.c_void_p()
         _check(load_library().nhq_search_graph_create(
             index, _ptr(queries, np.float32, (Q, d), "queries"),

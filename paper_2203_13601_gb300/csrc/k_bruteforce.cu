@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(NT) topk_tile_kernel(TopkArgs a, int64_t per_s
             int r = ty + 16 * i;
             int64_t q = q0 + r;
             uint32_t qa = q < a.nq ? a.qattr[q] : 0u;
+            const uint32_t qh = a.qhi && q < a.nq ? a.qhi[q] : a.w.hi;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 int c = tx + 16 * j;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(NT) topk_tile_kernel(TopkArgs a, int64_t per_s
                 float g = __int_as_float(0x7f800000);
                 if (q < a.nq && o < n_end && !(a.exclude_self && o == q)) {
                     float delta = __fsqrt_rn(acc[i][j]);
-                    g = fusion_gamma(delta, chi_packed(qa, a.attr[o], a.w.hi, a.w.lo), a.w);
+                    g = fusion_gamma(delta, chi_packed(qa, a.attr[o], qh, a.w.lo), a.w);
                 }
                 G[r * TN + c] = g;
             }
@@ -188,7 +189,8 @@ __global__ void __launch_bounds__(NT) topk_tile_kernel(TopkArgs a, int64_t per_s
                 if (a.chi)
                     a.chi[q * k + e] =
                         id == kNone ? (uint8_t)255
-                                    : (uint8_t)chi_packed(a.qattr[q], a.attr[id], a.w.hi, a.w.lo);
+                                    : (uint8_t)chi_packed(a.qattr[q], a.attr[id],
+                                                          a.qhi ? a.qhi[q] : a.w.hi, a.w.lo);
             } else {
                 int64_t o = (q * S + split) * (int64_t)k + e;
                 part_id[o] = id;
@@ -230,7 +232,8 @@ __global__ void topk_merge_kernel(TopkArgs a, int S, const uint32_t *__restrict_
             if (a.chi)
                 a.chi[q * k + e] = id == kNone
                                        ? (uint8_t)255
-                                       : (uint8_t)chi_packed(a.qattr[q], a.attr[id], a.w.hi, a.w.lo);
+                                       : (uint8_t)chi_packed(a.qattr[q], a.attr[id],
+                                                             a.qhi ? a.qhi[q] : a.w.hi, a.w.lo);
         }
         if (cur == best && best != ~0ull) {
             ++head;
@@ -414,6 +417,7 @@ extern "C" nhq_status nhq_brute_force_noalloc(const float *vectors,
     a.Q = queries;
     a.qstride = d;
     a.qattr = packed_query_attributes;
+    a.qhi = nullptr;
     a.nq = Q;
     a.k = k;
     a.exclude_self = 0;

@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
     float *qv = reinterpret_cast<float *>(base + L.qv);
     const int H = 1 << a.hash_bits;
     const int R = a.R;
-    const uint32_t ahi = a.w.hi, alo = a.w.lo;
+    const uint32_t alo = a.w.lo;
     // the learned stop's fp16 weights, staged once per block after the warps' areas
     __half *w16 = reinterpret_cast<__half *>(smem + (blockDim.x >> 5) * L.total);
     if (a.stop_w16 != nullptr) {
@@ -515,7 +515,8 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
 
         for (int i = lane; i < a.xstride; i += 32)
             qv[i] = i < a.d ? a.Q[q * a.qstride + i] : 0.f;
-        const uint32_t qa = pack_query_word(a.qattr + q * a.w.m, a.w);
+        uint32_t ahi;
+        const uint32_t qa = pack_query_word(a.qattr + q * a.w.m, a.w, &ahi);
         for (int i = lane; i < H / 4; i += 32)
             reinterpret_cast<uint4 *>(hash)[i] = make_uint4(kNone, kNone, kNone, kNone);
         __syncwarp();

@@ -47,11 +47,15 @@ __global__ void attribute_seeds_kernel(SearchArgs a, const uint32_t *__restrict_
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= a.nq)
         return;
-    const uint32_t qa = pack_query_word(a.qattr + q * a.w.m, a.w);
+    uint32_t qhi;
+    const uint32_t qa = pack_query_word(a.qattr + q * a.w.m, a.w, &qhi);
     const int ef = a.ef_arr ? a.ef_arr[q] : a.ef;
     const int want = ef < 32 ? ef : 32;
-    const int64_t lo = lower_bound_u32(attr_sorted, a.N, qa);
-    const int64_t hi = qa == 0xFFFFFFFFu ? a.N : lower_bound_u32(attr_sorted, a.N, qa + 1u);
+    // a query that leaves an attribute open has no tuple run: the random stream
+    const bool open = qhi != a.w.hi;
+    const int64_t lo = open ? 0 : lower_bound_u32(attr_sorted, a.N, qa);
+    const int64_t hi =
+        open ? 0 : (qa == 0xFFFFFFFFu ? a.N : lower_bound_u32(attr_sorted, a.N, qa + 1u));
     const int64_t c = hi - lo;
     if (bucket != nullptr) {
         const int bits = 64 - __clzll((unsigned long long)c + 1ull);  // 1..
@@ -90,11 +94,15 @@ __global__ void attribute_near_seeds_kernel(SearchArgs a, const uint32_t *__rest
     const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (q >= a.nq)
         return;
-    const uint32_t qa = pack_query_word(a.qattr + q * a.w.m, a.w);
+    uint32_t qhi;
+    const uint32_t qa = pack_query_word(a.qattr + q * a.w.m, a.w, &qhi);
     const int ef = a.ef_arr ? a.ef_arr[q] : a.ef;
     const int want = ef < 32 ? ef : 32;
-    const int64_t lo = lower_bound_u32(attr_sorted, a.N, qa);
-    const int64_t hi = qa == 0xFFFFFFFFu ? a.N : lower_bound_u32(attr_sorted, a.N, qa + 1u);
+    // a query that leaves an attribute open has no tuple run: the random stream
+    const bool open = qhi != a.w.hi;
+    const int64_t lo = open ? 0 : lower_bound_u32(attr_sorted, a.N, qa);
+    const int64_t hi =
+        open ? 0 : (qa == 0xFFFFFFFFu ? a.N : lower_bound_u32(attr_sorted, a.N, qa + 1u));
     const int64_t c = hi - lo;
     uint32_t *row = seeds + q * 32;
     if (lane == 0 && bucket != nullptr) {

@@ -21,6 +21,17 @@ __global__ void pack_attr_kernel(const uint8_t *__restrict__ a, int64_t n, AttrL
     }
 }
 
+__global__ void pack_query_kernel(const uint8_t *__restrict__ a, int64_t n, Fusion w,
+                                  uint32_t *__restrict__ out, uint32_t *__restrict__ hi_out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t hi;
+        out[i] = pack_query_word(a + i * w.m, w, &hi);
+        if (hi_out)
+            hi_out[i] = hi;
+    }
+}
+
 // out[j] = the largest code of attribute j over the n rows (out zeroed by the caller)
 __global__ void attr_max_kernel(const uint8_t *__restrict__ a, int64_t n, int m,
                                 unsigned int *__restrict__ out) {
@@ -97,6 +108,14 @@ cudaError_t launch_pack_attributes(const uint8_t *a, int64_t n, const AttrLayout
     if (n <= 0)
         return cudaSuccess;
     pack_attr_kernel<<<grid_for(n), 256, 0, s>>>(a, n, L, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_queries(const uint8_t *a, int64_t n, const Fusion &w, uint32_t *out,
+                                uint32_t *hi_out, cudaStream_t s) {
+    if (n <= 0)
+        return cudaSuccess;
+    pack_query_kernel<<<grid_for(n), 256, 0, s>>>(a, n, w, out, hi_out);
     return cudaGetLastError();
 }
 
@@ -182,6 +201,7 @@ Fusion make_fusion(const nhq_weights &w, const AttrLayout &L) {
     f.m = L.m;
     f.hi = L.hi;
     f.lo = L.lo;
+    f.wild = 0;
     for (int j = 0; j < kMaxAttr; ++j) {
         f.shift[j] = L.shift[j];
         f.maxc[j] = L.maxc[j];

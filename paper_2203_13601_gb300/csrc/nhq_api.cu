@@ -338,6 +338,7 @@ nhq_status nhq_knn(const nhq_index *cix, int32_t K, uint32_t *cand_ids, float *c
     a.Q = ix->X;
     a.qstride = ix->xstride;
     a.qattr = ix->attr;
+    a.qhi = nullptr;
     a.nq = ix->N;
     a.k = K;
     a.exclude_self = 1;
@@ -690,7 +691,17 @@ nhq_status nhq_brute_force(const nhq_index *cix, const float *queries,
                            const uint8_t *query_attributes, int64_t Q, int32_t k,
                            const nhq_weights *w, uint32_t *ids, float *dists, uint8_t *chi,
                            void *stream) {
+    return nhq_brute_force_wildcard(cix, queries, query_attributes, Q, k, w, 0, ids, dists, chi,
+                                    stream);
+}
+
+nhq_status nhq_brute_force_wildcard(const nhq_index *cix, const float *queries,
+                                    const uint8_t *query_attributes, int64_t Q, int32_t k,
+                                    const nhq_weights *w, int32_t wildcard, uint32_t *ids,
+                                    float *dists, uint8_t *chi, void *stream) {
     nhq_index *ix = const_cast<nhq_index *>(cix);
+    if (wildcard != 0 && wildcard != 1)
+        return fail(NHQ_ERR_ARG, "wildcard must be 0 or 1 (got %d)", wildcard);
     if (ix == nullptr)
         return fail(NHQ_ERR_ARG, "index is NULL");
     if (Q < 0)
@@ -723,15 +734,21 @@ nhq_status nhq_brute_force(const nhq_index *cix, const float *queries,
     a.k = k;
     a.exclude_self = 0;
     a.w = make_fusion(ww, ix->layout);
+    a.w.wild = wildcard;
     a.ids = (uint32_t *)st.dev(io);
     a.dists = (float *)st.dev(id);
     a.chi = (uint8_t *)st.dev(ic);
+    // query words, then (with a wildcard) their chi masks
     size_t qa_bytes = ((sizeof(uint32_t) * (size_t)Q) + 255) & ~(size_t)255;
-    size_t need = qa_bytes + topk_scratch_bytes(a, ix->sm_count);
+    const size_t words = wildcard ? 2 * qa_bytes : qa_bytes;
+    size_t need = words + topk_scratch_bytes(a, ix->sm_count);
     CKS(scratch(ix, need));
     uint32_t *qa = reinterpret_cast<uint32_t *>(ix->scratch);
-    CK(launch_pack_attributes((const uint8_t *)st.dev(ia), Q, ix->layout, qa, s));
+    uint32_t *qh = wildcard ? reinterpret_cast<uint32_t *>((char *)ix->scratch + qa_bytes) : nullptr;
+    CK(launch_pack_queries((const uint8_t *)st.dev(ia), Q, a.w, qa, qh, s));
     a.qattr = qa;
+    a.qhi = qh;
+    qa_bytes = words;
     CK(launch_topk(a, (char *)ix->scratch + qa_bytes, ix->scratch_bytes - qa_bytes, ix->sm_count,
                    s));
     return st.finish(s);
@@ -829,6 +846,8 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         return fail(NHQ_ERR_ARG, "unknown vec_dtype %d", P.vec_dtype);
     if (P.hash_bits < 0 || P.hash_bits > 16)
         return fail(NHQ_ERR_ARG, "hash_bits must be in 0..16");
+    if (P.wildcard != 0 && P.wildcard != 1)
+        return fail(NHQ_ERR_ARG, "wildcard must be 0 or 1 (got %d)", P.wildcard);
     if (P.warps_per_block < 0 || P.warps_per_block > 8)
         return fail(NHQ_ERR_ARG, "warps_per_block must be in 0..8");
     if (P.seed_mode < NHQ_SEED_RANDOM || P.seed_mode > NHQ_SEED_ATTRIBUTE_NEAR)
@@ -883,6 +902,7 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     a.nbr_attr = ix->nbr_attr;
     a.R = ix->R;
     a.w = make_fusion(ix->w, ix->layout);
+    a.w.wild = P.wildcard;
     a.Q = (const float *)st.dev(iq);
     a.qstride = ix->d;
     a.qattr = (const uint8_t *)st.dev(ia);

@@ -43,6 +43,7 @@ struct Fusion {
     int m;
     uint32_t hi, lo;  // AttrLayout::hi / lo
     uint8_t shift[kMaxAttr], maxc[kMaxAttr];
+    int wild;  // 1: a query code 255 leaves its attribute unconstrained (queries only)
 };
 
 // ---- splitmix64 (Vigna): the finaliser and the j-th output of a stream ----
@@ -69,14 +70,25 @@ __host__ __device__ __forceinline__ int chi_packed(uint32_t a, uint32_t b, uint3
 #endif
 }
 
-// A query's packed word under the layout in w (codes above maxc[j] become maxc[j] + 1).
-__device__ __forceinline__ uint32_t pack_query_word(const uint8_t *qa, const Fusion &w) {
-    uint32_t word = 0;
+// A query's packed word under the layout in w (codes above maxc[j] become maxc[j] + 1);
+// *hi = the top bits of the fields the query constrains (w.hi less the fields whose code
+// is the wildcard 255 when w.wild is set), to pass to chi_packed in place of w.hi.
+__device__ __forceinline__ uint32_t pack_query_word(const uint8_t *qa, const Fusion &w,
+                                                   uint32_t *hi) {
+    uint32_t word = 0, open = 0;
     for (int j = 0; j < w.m; ++j) {
         const uint32_t v = qa[j];
+        if (w.wild && v == 255u) {  // the field's top bit: the next field's shift - 1
+            const uint32_t next = j + 1 < w.m ? w.shift[j + 1] : 32u;
+            const uint32_t field_hi = w.hi & (next >= 32u ? 0xFFFFFFFFu : ((1u << next) - 1u)) &
+                                      ~((1u << w.shift[j]) - 1u);
+            open |= field_hi;
+            continue;
+        }
         const uint32_t c = v <= w.maxc[j] ? v : (uint32_t)w.maxc[j] + 1u;
         word |= c << w.shift[j];
     }
+    *hi = w.hi & ~open;
     return word;
 }
 
@@ -172,6 +184,9 @@ nhq_status report_error(nhq_status s, const char *message);  // nhq_api.cu
 // k_util.cu
 cudaError_t launch_pack_attributes(const uint8_t *a, int64_t n, const AttrLayout &L,
                                    uint32_t *out, cudaStream_t s);
+// query words under the layout in w and, when hi_out is not null, each query's chi mask
+cudaError_t launch_pack_queries(const uint8_t *a, int64_t n, const Fusion &w, uint32_t *out,
+                                uint32_t *hi_out, cudaStream_t s);
 // out[0..kMaxAttr) = the largest code of each of the m attributes over n rows
 cudaError_t launch_attr_max(const uint8_t *a, int64_t n, int m, unsigned int *out,
                             cudaStream_t s);
@@ -192,6 +207,7 @@ struct TopkArgs {
     const float *Q;
     int qstride;
     const uint32_t *qattr;
+    const uint32_t *qhi;  // [nq] per-query chi masks (wildcards), or null: w.hi
     int64_t nq;
     int k;
     int exclude_self;  // query q is object q (candidate sets)
