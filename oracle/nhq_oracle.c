@@ -533,7 +533,46 @@ static int pool_insert(pool_t *pool, int *n, int ef, double g, int64_t id)
  *   seed_mode 3  nearest attribute entry: P as in mode 1; the M = min(256, c) members
  *                P[floor(j * c / M)], and of them the S = min(ef, 32, M) nearest to the
  *                query by (delta^2 of the f32 rows, summed in index order, id);
- *                with c = 0, as mode 0 */
+ *                with c = 0, as mode 0
+ *   open query   (a position holding the wildcard code `wild`) under modes 1 and 3:
+ *                its completions fill every open position j with a code 0..a_j (a_j the
+ *                largest code of attribute j among the objects), the lowest open
+ *                position varying fastest; with T <= 64 completions, P = the runs of the
+ *                completions (objects equal to the completed tuple, ascending id) one
+ *                after another in completion order, c = |P|, and B follows mode 1's
+ *                rule on that P; with T > 64 or c = 0, as mode 0 */
+#define OR_MAX_COMPLETIONS 64
+
+/* the members of an open query's completion runs, in order, into out; returns their
+ * number, or -1 when the query has more than OR_MAX_COMPLETIONS completions */
+static int64_t or_open_members(const uint8_t *A, int64_t N, int m, const uint8_t *qa, int wild,
+                               const int *amax, uint8_t *comp, int64_t *out)
+{
+    int64_t T = 1;
+    for (int j = 0; j < m; ++j)
+        if ((int)qa[j] == wild) {
+            T *= amax[j] + 1;
+            if (T > OR_MAX_COMPLETIONS)
+                return -1;
+        }
+    int64_t n = 0;
+    for (int64_t t = 0; t < T; ++t) {
+        int64_t rem = t;
+        for (int j = 0; j < m; ++j) {
+            if ((int)qa[j] == wild) {
+                comp[j] = (uint8_t)(rem % (amax[j] + 1));
+                rem /= amax[j] + 1;
+            } else {
+                comp[j] = qa[j];
+            }
+        }
+        for (int64_t v = 0; v < N; ++v)
+            if (or_chi(comp, A + v * (int64_t)m, m) == 0)
+                out[n++] = v;
+    }
+    return n;
+}
+
 void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                const int64_t *nbr, int R, const float *Qv, const uint8_t *QA, int64_t nq,
                int k, int ef, int h, uint64_t seed, int64_t max_iters,
@@ -560,6 +599,13 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
     uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(R > 0 ? R : 1));
     int *rank_buf = (int *)malloc(sizeof(int) * (size_t)(R > 0 ? R : 1));
     int s1_take = h > 1 ? (R + h - 1) / h : R;
+    int *amax = (int *)calloc((size_t)(m > 0 ? m : 1), sizeof(int));
+    for (int64_t v = 0; v < N; ++v)
+        for (int j = 0; j < m; ++j)
+            if (A[v * (int64_t)m + j] > amax[j])
+                amax[j] = A[v * (int64_t)m + j];
+    uint8_t *comp = (uint8_t *)malloc((size_t)(m > 0 ? m : 1));
+    int64_t *members = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
 
     for (int64_t q = 0; q < nq; ++q) {
         const float *qv = Qv + q * (int64_t)d;
@@ -573,11 +619,22 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
         /* seed set B */
         int want = ef < 32 ? ef : 32;
         int64_t c = 0;
-        /* a query that leaves a position open has no tuple run: it takes mode 0 */
-        if ((seed_mode == 1 || seed_mode == 3) && !or_query_open(qa, m, wild))
+        const int open_q = (seed_mode == 1 || seed_mode == 3) && or_query_open(qa, m, wild);
+        int64_t c_open = open_q ? or_open_members(A, N, m, qa, wild, amax, comp, members) : 0;
+        if ((seed_mode == 1 || seed_mode == 3) && !open_q)
             for (int64_t v = 0; v < N; ++v)
                 c += or_chi(qa, A + v * (int64_t)m, m) == 0 ? 1 : 0;
-        if (seed_mode == 2) {
+        if (open_q && c_open > 0) {  /* mode 1's rule over the completion runs */
+            const int S = (int64_t)want < c_open ? want : (int)c_open;
+            for (int j = 0; j < S; ++j) {
+                const int64_t v = members[((int64_t)j * c_open) / S];
+                evaluated[v] = 1;
+                ++ndc;
+                double g = pair_gamma(qv, qa, Xs + v * (int64_t)d, A + v * (int64_t)m, d, m,
+                                      mode, wv, wl, prec, NULL, wild);
+                pool_insert(pool, &n, ef, g, v);
+            }
+        } else if (seed_mode == 2) {
             for (int j = 0; j < n_seeds; ++j) {
                 int64_t v = seeds_in[q * (int64_t)n_seeds + j];
                 if (v < 0 || v >= N || evaluated[v])
@@ -751,6 +808,9 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
         out_exp[q] = iters;
         out_status[q] = status;
     }
+    free(amax);
+    free(comp);
+    free(members);
     free(pool);
     free(before);
     free(evaluated);

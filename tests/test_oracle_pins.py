@@ -629,9 +629,37 @@ def test_search_with_open_positions(oracle_mod):
     for ef in (5, 30):
         r = O.search(w.X, w.A, G, w.Qv, QA, 5, ef, seed=3, wildcard=255)
         assert (r["ids"] == ref).all() and np.array_equal(r["gamma"], rg)
-    # an open query has no tuple run: the attribute seed rule gives it the random stream
-    nbr = np.full((30, 2), -1, np.int64)
-    a = O.search(w.X, w.A, nbr, w.Qv, QA, 5, 8, seed=3, wildcard=255, max_iters=0,
-                 seed_mode=O.SEED_ATTRIBUTE)
-    b = O.search(w.X, w.A, nbr, w.Qv, QA, 5, 8, seed=3, wildcard=255, max_iters=0)
-    assert (a["ids"][::2] == b["ids"][::2]).all()
+
+
+def test_open_query_seeds_come_from_the_completion_runs(oracle_mod):
+    # with no expansion the result is the k best seeds; the seeds of an open query are
+    # mode 1's evenly spaced picks over the runs of its completions, listed here with
+    # itertools in completion order (lowest open position fastest)
+    import itertools
+
+    O = oracle_mod
+    w = synth.int_valued(400, 24, 6, cards=(3, 4, 2), seed=59, zipf=False)
+    QA = w.QA.copy()
+    QA[:, 0] = 255
+    QA[1::2, 2] = 255
+    CONST = (1.0, 10000.0)
+    nbr = np.full((w.N, 2), -1, np.int64)
+    for ef in (8, 32):
+        r = O.search(w.X, w.A, nbr, w.Qv, QA, 5, ef, seed=3, wildcard=255, max_iters=0,
+                     weights=CONST, seed_mode=O.SEED_ATTRIBUTE, prec=O.F32)
+        amax = w.A.max(axis=0)
+        for q in range(w.nq):
+            opn = [j for j in range(w.m) if QA[q, j] == 255]
+            members = []
+            for digits in itertools.product(*[range(amax[j] + 1) for j in reversed(opn)]):
+                tup = QA[q].astype(int).copy()
+                for j, dgt in zip(reversed(opn), digits):
+                    tup[j] = dgt
+                members += np.flatnonzero((w.A == tup).all(axis=1)).tolist()
+            c = len(members)
+            S = min(ef, 32, c)
+            seeds = [members[(j * c) // S] for j in range(S)]
+            g = [O.gamma(O.delta(w.Qv[q], w.X[v], O.F32), O.chi_query(QA[q], w.A[v], 255), w.m,
+                         CONST, O.F32) for v in seeds]
+            want = [v for _, v in sorted(zip(g, seeds))][:5]
+            assert list(r["ids"][q][: len(want)]) == want, (ef, q)
