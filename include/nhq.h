@@ -123,9 +123,13 @@ typedef struct nhq_search_params {
     int32_t stop_every;      /* consult it every this many expansions (>= 1 when a model is set) */
     int32_t wildcard;        /* 1: a query code 255 places no constraint on its attribute (a
                                 partial constraint; the paper's hybrid query constrains every
-                                attribute): it never counts toward chi, and a query holding it
-                                has no tuple run, so the attribute seed modes give it the
-                                random stream of NHQ_SEED_RANDOM.  0: 255 is an ordinary code */
+                                attribute): it never counts toward chi.  Under the attribute
+                                seed modes such a query's completions (each open attribute
+                                set to 0..its largest code among the objects, the lowest
+                                attribute fastest; at most 64) give P as their runs one
+                                after another, and NHQ_SEED_ATTRIBUTE's evenly spaced rule
+                                picks B from it; more completions, or no member: the random
+                                stream of NHQ_SEED_RANDOM.  0: 255 is an ordinary code     */
 } nhq_search_params;
 
 typedef struct nhq_index nhq_index;

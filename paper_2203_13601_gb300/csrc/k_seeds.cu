@@ -40,6 +40,70 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *a, int64_t n,
     return lo;
 }
 
+constexpr int kMaxCompletions = 64;
+
+// The run [*lo, *lo + count) of the packed word `word` in the sorted attribute table.
+__device__ __forceinline__ int64_t tuple_run(const uint32_t *attr_sorted, int64_t N,
+                                             uint32_t word, int64_t *lo) {
+    const int64_t l = lower_bound_u32(attr_sorted, N, word);
+    const int64_t h = word == 0xFFFFFFFFu ? N : lower_bound_u32(attr_sorted, N, word + 1u);
+    *lo = l;
+    return h - l;
+}
+
+// Completion t of an open query: its word with every open field j set to the digit of t
+// in the mixed radix amax[j] + 1 over the open fields, the lowest field fastest.
+__device__ __forceinline__ uint32_t completion_word(const Fusion &w, uint32_t qa, uint32_t qhi,
+                                                    int64_t t) {
+    uint32_t word = qa;
+    for (int j = 0; j < w.m; ++j) {
+        if ((field_hi(w, j) & ~qhi) == 0u)
+            continue;
+        const int64_t r = (int64_t)w.amax[j] + 1;
+        word |= (uint32_t)(t % r) << w.shift[j];
+        t /= r;
+    }
+    return word;
+}
+
+// Seeds of an open query (a field left open by the wildcard) under the attribute seed
+// modes: its completions fill each open field with 0..amax[j]; with at most 64 of them,
+// P = their runs one after another in completion order and row[0..S) = P[floor(j c / S)],
+// S = min(want, c), the rest kNone.  Returns c = |P| (row untouched when c = 0), or -1
+// when there are more than 64 completions.
+__device__ int64_t open_query_seeds(const Fusion &w, uint32_t qa, uint32_t qhi,
+                                    const uint32_t *attr_sorted, const uint32_t *id_sorted,
+                                    int64_t N, int want, uint32_t *row) {
+    int64_t T = 1;
+    for (int j = 0; j < w.m; ++j)
+        if ((field_hi(w, j) & ~qhi) != 0u) {
+            T *= (int64_t)w.amax[j] + 1;
+            if (T > kMaxCompletions)
+                return -1;
+        }
+    int64_t c = 0, lo;
+    for (int64_t t = 0; t < T; ++t)
+        c += tuple_run(attr_sorted, N, completion_word(w, qa, qhi, t), &lo);
+    if (c == 0)
+        return 0;
+    const int S = (int64_t)want < c ? want : (int)c;
+    int j = 0;
+    int64_t base = 0;
+    for (int64_t t = 0; t < T && j < S; ++t) {
+        const int64_t ct = tuple_run(attr_sorted, N, completion_word(w, qa, qhi, t), &lo);
+        while (j < S) {
+            const int64_t r = ((int64_t)j * c) / S;
+            if (r >= base + ct)
+                break;
+            row[j++] = id_sorted[lo + (r - base)];
+        }
+        base += ct;
+    }
+    for (; j < 32; ++j)
+        row[j] = kNone;
+    return c;
+}
+
 __global__ void attribute_seeds_kernel(SearchArgs a, const uint32_t *__restrict__ attr_sorted,
                                        const uint32_t *__restrict__ id_sorted,
                                        uint32_t *__restrict__ seeds,
@@ -51,17 +115,22 @@ __global__ void attribute_seeds_kernel(SearchArgs a, const uint32_t *__restrict_
     const uint32_t qa = pack_query_word(a.qattr + q * a.w.m, a.w, &qhi);
     const int ef = a.ef_arr ? a.ef_arr[q] : a.ef;
     const int want = ef < 32 ? ef : 32;
-    // a query that leaves an attribute open has no tuple run: the random stream
+    uint32_t *row = seeds + q * 32;
+    // a query that leaves an attribute open takes its seeds from its completions' runs
     const bool open = qhi != a.w.hi;
-    const int64_t lo = open ? 0 : lower_bound_u32(attr_sorted, a.N, qa);
-    const int64_t hi =
-        open ? 0 : (qa == 0xFFFFFFFFu ? a.N : lower_bound_u32(attr_sorted, a.N, qa + 1u));
-    const int64_t c = hi - lo;
+    int64_t lo = 0, c = 0;
+    if (open) {
+        c = open_query_seeds(a.w, qa, qhi, attr_sorted, id_sorted, a.N, want, row);
+        c = c < 0 ? 0 : c;
+    } else {
+        c = tuple_run(attr_sorted, a.N, qa, &lo);
+    }
     if (bucket != nullptr) {
         const int bits = 64 - __clzll((unsigned long long)c + 1ull);  // 1..
         bucket[q] = (uint8_t)(bits >= 32 ? 0 : 32 - bits);
     }
-    uint32_t *row = seeds + q * 32;
+    if (open && c > 0)
+        return;  // row written
     int j = 0;
     if (c > 0) {
         const int S = (int64_t)want < c ? want : (int)c;
@@ -98,17 +167,26 @@ __global__ void attribute_near_seeds_kernel(SearchArgs a, const uint32_t *__rest
     const uint32_t qa = pack_query_word(a.qattr + q * a.w.m, a.w, &qhi);
     const int ef = a.ef_arr ? a.ef_arr[q] : a.ef;
     const int want = ef < 32 ? ef : 32;
-    // a query that leaves an attribute open has no tuple run: the random stream
-    const bool open = qhi != a.w.hi;
-    const int64_t lo = open ? 0 : lower_bound_u32(attr_sorted, a.N, qa);
-    const int64_t hi =
-        open ? 0 : (qa == 0xFFFFFFFFu ? a.N : lower_bound_u32(attr_sorted, a.N, qa + 1u));
-    const int64_t c = hi - lo;
     uint32_t *row = seeds + q * 32;
+    // a query that leaves an attribute open takes NHQ_SEED_ATTRIBUTE's seeds from its
+    // completions' runs (lane 0; the warp agrees on c)
+    const bool open = qhi != a.w.hi;
+    int64_t lo = 0, c = 0;
+    if (open) {
+        if (lane == 0) {
+            c = open_query_seeds(a.w, qa, qhi, attr_sorted, id_sorted, a.N, want, row);
+            c = c < 0 ? 0 : c;
+        }
+        c = __shfl_sync(0xFFFFFFFFu, c, 0);
+    } else {
+        c = tuple_run(attr_sorted, a.N, qa, &lo);
+    }
     if (lane == 0 && bucket != nullptr) {
         const int bits = 64 - __clzll((unsigned long long)c + 1ull);
         bucket[q] = (uint8_t)(bits >= 32 ? 0 : 32 - bits);
     }
+    if (open && c > 0)
+        return;  // row written by lane 0
     if (c == 0) {  // the random stream of NHQ_SEED_RANDOM
         if (lane == 0) {
             int j = 0;

@@ -168,6 +168,7 @@ AttrLayout byte_layout(int m) {
         L.shift[j] = (uint8_t)(8 * j);
         L.width[j] = 8;
         L.maxc[j] = 255;
+        L.amax[j] = 255;
     }
     finish_masks(&L);
     return L;
@@ -186,6 +187,7 @@ bool compact_layout(int m, const uint8_t *maxc, AttrLayout *out) {
         L.shift[j] = (uint8_t)bits;
         L.width[j] = (uint8_t)w;
         L.maxc[j] = maxc[j];
+        L.amax[j] = maxc[j];
         bits += w;
     }
     finish_masks(&L);
@@ -205,6 +207,7 @@ Fusion make_fusion(const nhq_weights &w, const AttrLayout &L) {
     for (int j = 0; j < kMaxAttr; ++j) {
         f.shift[j] = L.shift[j];
         f.maxc[j] = L.maxc[j];
+        f.amax[j] = L.amax[j];
     }
     return f;
 }

@@ -240,20 +240,24 @@ nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const ui
     if ((e = launch_copy_rows((const float *)st.dev(iv), N, d, ix->xstride, ix->X, bad, s)) !=
         cudaSuccess)
         return bail(fail_cuda(e, "copy_rows"));
+    // the largest code of each attribute: the field widths for m > 4, and the codes an
+    // open query position ranges over
+    unsigned int *amax = reinterpret_cast<unsigned int *>((char *)ix->scratch + 128);
+    unsigned int hmax[kMaxAttr];
+    if ((e = launch_attr_max((const uint8_t *)st.dev(ia), N, m, amax, s)) != cudaSuccess)
+        return bail(fail_cuda(e, "attr_max"));
+    if ((e = cudaMemcpyAsync(hmax, amax, sizeof(hmax), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return bail(fail_cuda(e, "attr_max copy"));
+    uint8_t mc[kMaxAttr] = {};
+    for (int j = 0; j < m; ++j)
+        mc[j] = (uint8_t)hmax[j];
     if (m <= 4) {
         ix->layout = byte_layout(m);
-    } else {  // fields as narrow as the largest codes allow
-        unsigned int *amax = reinterpret_cast<unsigned int *>((char *)ix->scratch + 128);
-        unsigned int hmax[kMaxAttr];
-        if ((e = launch_attr_max((const uint8_t *)st.dev(ia), N, m, amax, s)) != cudaSuccess)
-            return bail(fail_cuda(e, "attr_max"));
-        if ((e = cudaMemcpyAsync(hmax, amax, sizeof(hmax), cudaMemcpyDeviceToHost, s)) !=
-                cudaSuccess ||
-            (e = cudaStreamSynchronize(s)) != cudaSuccess)
-            return bail(fail_cuda(e, "attr_max copy"));
-        uint8_t mc[kMaxAttr];
         for (int j = 0; j < m; ++j)
-            mc[j] = (uint8_t)hmax[j];
+            ix->layout.amax[j] = mc[j];
+    } else {  // fields as narrow as the largest codes allow
         if (!compact_layout(m, mc, &ix->layout))
             return bail(fail(NHQ_ERR_ARG, "the codes of the %d attributes need more than 32 bits "
                                           "packed (each takes the bits of its largest code + 1)",

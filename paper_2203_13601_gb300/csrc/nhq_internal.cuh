@@ -32,6 +32,7 @@ struct AttrLayout {
     uint8_t shift[kMaxAttr] = {};
     uint8_t width[kMaxAttr] = {};
     uint8_t maxc[kMaxAttr] = {};
+    uint8_t amax[kMaxAttr] = {};  // the largest code of each attribute among the objects
     uint32_t hi = 0;  // the top bit of every field
     uint32_t lo = 0;  // the other bits of every field
 };
@@ -42,7 +43,7 @@ struct Fusion {
     float wv, wl;
     int m;
     uint32_t hi, lo;  // AttrLayout::hi / lo
-    uint8_t shift[kMaxAttr], maxc[kMaxAttr];
+    uint8_t shift[kMaxAttr], maxc[kMaxAttr], amax[kMaxAttr];
     int wild;  // 1: a query code 255 leaves its attribute unconstrained (queries only)
 };
 
@@ -70,6 +71,12 @@ __host__ __device__ __forceinline__ int chi_packed(uint32_t a, uint32_t b, uint3
 #endif
 }
 
+// the top bit of field j (w.hi has one bit per field, and field j ends where j + 1 starts)
+__host__ __device__ __forceinline__ uint32_t field_hi(const Fusion &w, int j) {
+    const uint32_t next = j + 1 < w.m ? w.shift[j + 1] : 32u;
+    return w.hi & (next >= 32u ? 0xFFFFFFFFu : ((1u << next) - 1u)) & ~((1u << w.shift[j]) - 1u);
+}
+
 // A query's packed word under the layout in w (codes above maxc[j] become maxc[j] + 1);
 // *hi = the top bits of the fields the query constrains (w.hi less the fields whose code
 // is the wildcard 255 when w.wild is set), to pass to chi_packed in place of w.hi.
@@ -78,11 +85,8 @@ __device__ __forceinline__ uint32_t pack_query_word(const uint8_t *qa, const Fus
     uint32_t word = 0, open = 0;
     for (int j = 0; j < w.m; ++j) {
         const uint32_t v = qa[j];
-        if (w.wild && v == 255u) {  // the field's top bit: the next field's shift - 1
-            const uint32_t next = j + 1 < w.m ? w.shift[j + 1] : 32u;
-            const uint32_t field_hi = w.hi & (next >= 32u ? 0xFFFFFFFFu : ((1u << next) - 1u)) &
-                                      ~((1u << w.shift[j]) - 1u);
-            open |= field_hi;
+        if (w.wild && v == 255u) {
+            open |= field_hi(w, j);
             continue;
         }
         const uint32_t c = v <= w.maxc[j] ? v : (uint32_t)w.maxc[j] + 1u;

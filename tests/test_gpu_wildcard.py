@@ -1,6 +1,7 @@
 """Partial attribute constraints: with the wildcard switch on, a query code 255 leaves its
-attribute unconstrained (it never counts toward chi, and an open query takes the random
-seed stream).  The paper's hybrid query constrains every attribute, so this is an
+attribute unconstrained (it never counts toward chi, and under the attribute seed modes an
+open query takes its seeds from the runs of its completions, or the random stream when it
+has more than 64).  The paper's hybrid query constrains every attribute, so this is an
 extension; every result is compared with the oracle's reading of it, bit for bit on
 integer components, for the byte layout (m = 3) and for bit fields (m = 6, 9)."""
 import numpy as np
