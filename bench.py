@@ -691,8 +691,9 @@ def wildcard_arm(a):
     """Partial constraints on the c2 workload: every query leaves one attribute open
     (code 255 with the wildcard switch on; attribute 0, 1 or 2 in turn), on the composite
     index of the headline (exact candidates, constant weights).  Ground truth: the
-    filter-mode brute force under the same rule.  For each seed rule the cheapest ef
-    reaching hybrid Recall@10 >= target, else the best recall."""
+    filter-mode brute force under the same rule.  For each seed rule (nearest attribute
+    entry, then attribute entry; the first only with --steps 1) the cheapest ef reaching
+    hybrid Recall@10 >= target, else the best recall."""
     import torch
 
     import paper_2203_13601_gb300 as nhq
@@ -732,7 +733,9 @@ def wildcard_arm(a):
         return float(np.mean(hits))
 
     by_seeds = {}
-    for sname, smode in (("attribute_entry", nhq.SEED_ATTRIBUTE),):
+    modes = (("nearest_attribute_entry", nhq.SEED_ATTRIBUTE_NEAR),
+             ("attribute_entry", nhq.SEED_ATTRIBUTE))
+    for sname, smode in modes[: 1 if a.steps == 1 else 2]:
         sweep = []
         for ef in (16, 24, 32, 48, 64, 96, 128, 200, 320, 500):
             run = lambda ef=ef: nhq.nhq_search(ix.handle, Qv, QA, k, ef, ids, dd, ch, seed=12345,

@@ -127,9 +127,10 @@ typedef struct nhq_search_params {
                                 seed modes such a query's completions (each open attribute
                                 set to 0..its largest code among the objects, the lowest
                                 attribute fastest; at most 64) give P as their runs one
-                                after another, and NHQ_SEED_ATTRIBUTE's evenly spaced rule
-                                picks B from it; more completions, or no member: the random
-                                stream of NHQ_SEED_RANDOM.  0: 255 is an ordinary code     */
+                                after another, and the seed mode's rule (evenly spaced, or
+                                nearest of 256 sampled) picks B from it; more completions,
+                                or no member: the random stream of NHQ_SEED_RANDOM.
+                                0: 255 is an ordinary code                                  */
 } nhq_search_params;
 
 typedef struct nhq_index nhq_index;

@@ -363,7 +363,7 @@ def search(X, A, nbr, Qv, QA, k, ef, h=1, seed=0, max_iters=1 << 30, weights=Non
     none).  ``vec_round`` scores candidates with X rounded to bf16 / fp8 e4m3;
     ``rerank`` re-scores the final pool with X itself before returning the first k.
     ``wildcard``: query code that leaves its position unconstrained; under the attribute
-    seed modes such a query takes mode 1's rule over the runs of its completions.
+    seed modes such a query takes the mode's rule over the runs of its completions.
     Returns a dict with ids/gamma/chi [nq,k], ndc/expansions/status [nq]."""
     X, A, nbr, Qv, QA = _f32(X), _u8(A), _i64(nbr), _f32(Qv), _u8(QA)
     if seeds is not None:

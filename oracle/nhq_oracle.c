@@ -539,8 +539,8 @@ static int pool_insert(pool_t *pool, int *n, int ef, double g, int64_t id)
  *                largest code of attribute j among the objects), the lowest open
  *                position varying fastest; with T <= 64 completions, P = the runs of the
  *                completions (objects equal to the completed tuple, ascending id) one
- *                after another in completion order, c = |P|, and B follows mode 1's
- *                rule on that P; with T > 64 or c = 0, as mode 0 */
+ *                after another in completion order, c = |P|, and B follows the rule of
+ *                mode 1 (or 3) on that P; with T > 64 or c = 0, as mode 0 */
 #define OR_MAX_COMPLETIONS 64
 
 /* the members of an open query's completion runs, in order, into out; returns their
@@ -624,7 +624,26 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
         if ((seed_mode == 1 || seed_mode == 3) && !open_q)
             for (int64_t v = 0; v < N; ++v)
                 c += or_chi(qa, A + v * (int64_t)m, m) == 0 ? 1 : 0;
-        if (open_q && c_open > 0) {  /* mode 1's rule over the completion runs */
+        if (open_q && c_open > 0 && seed_mode == 3) {  /* mode 3's rule on those runs */
+            const int M = c_open < 256 ? (int)c_open : 256;
+            rec_t *cm = (rec_t *)malloc(sizeof(rec_t) * (size_t)M);
+            for (int j = 0; j < M; ++j) {
+                const int64_t v = members[((int64_t)j * c_open) / M];
+                cm[j].g = (double)or_dist2_32(qv, X + v * (int64_t)d, d);
+                cm[j].id = v;
+            }
+            qsort(cm, (size_t)M, sizeof(rec_t), rec_cmp);
+            const int S = want < M ? want : M;
+            for (int t = 0; t < S; ++t) {
+                const int64_t v = cm[t].id;
+                evaluated[v] = 1;
+                ++ndc;
+                double g = pair_gamma(qv, qa, Xs + v * (int64_t)d, A + v * (int64_t)m, d, m,
+                                      mode, wv, wl, prec, NULL, wild);
+                pool_insert(pool, &n, ef, g, v);
+            }
+            free(cm);
+        } else if (open_q && c_open > 0) {  /* mode 1's rule on those runs */
             const int S = (int64_t)want < c_open ? want : (int)c_open;
             for (int j = 0; j < S; ++j) {
                 const int64_t v = members[((int64_t)j * c_open) / S];

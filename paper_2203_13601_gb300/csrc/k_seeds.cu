@@ -66,6 +66,18 @@ __device__ __forceinline__ uint32_t completion_word(const Fusion &w, uint32_t qa
     return word;
 }
 
+// The number of completions of an open query (-1 above kMaxCompletions).
+__device__ __forceinline__ int64_t open_completions(const Fusion &w, uint32_t qhi) {
+    int64_t T = 1;
+    for (int j = 0; j < w.m; ++j)
+        if ((field_hi(w, j) & ~qhi) != 0u) {
+            T *= (int64_t)w.amax[j] + 1;
+            if (T > kMaxCompletions)
+                return -1;
+        }
+    return T;
+}
+
 // Seeds of an open query (a field left open by the wildcard) under the attribute seed
 // modes: its completions fill each open field with 0..amax[j]; with at most 64 of them,
 // P = their runs one after another in completion order and row[0..S) = P[floor(j c / S)],
@@ -74,13 +86,9 @@ __device__ __forceinline__ uint32_t completion_word(const Fusion &w, uint32_t qa
 __device__ int64_t open_query_seeds(const Fusion &w, uint32_t qa, uint32_t qhi,
                                     const uint32_t *attr_sorted, const uint32_t *id_sorted,
                                     int64_t N, int want, uint32_t *row) {
-    int64_t T = 1;
-    for (int j = 0; j < w.m; ++j)
-        if ((field_hi(w, j) & ~qhi) != 0u) {
-            T *= (int64_t)w.amax[j] + 1;
-            if (T > kMaxCompletions)
-                return -1;
-        }
+    const int64_t T = open_completions(w, qhi);
+    if (T < 0)
+        return -1;
     int64_t c = 0, lo;
     for (int64_t t = 0; t < T; ++t)
         c += tuple_run(attr_sorted, N, completion_word(w, qa, qhi, t), &lo);
@@ -168,16 +176,35 @@ __global__ void attribute_near_seeds_kernel(SearchArgs a, const uint32_t *__rest
     const int ef = a.ef_arr ? a.ef_arr[q] : a.ef;
     const int want = ef < 32 ? ef : 32;
     uint32_t *row = seeds + q * 32;
-    // a query that leaves an attribute open takes NHQ_SEED_ATTRIBUTE's seeds from its
-    // completions' runs (lane 0; the warp agrees on c)
+    // A query that leaves an attribute open: P = its completions' runs one after another
+    // (lane l holds completions l and l + 32, at most 64); (base0, c0) and (base1, c1)
+    // are those runs' offsets in P and sizes.
     const bool open = qhi != a.w.hi;
     int64_t lo = 0, c = 0;
+    int64_t lo0 = 0, c0 = 0, base0 = 0, lo1 = 0, c1 = 0, base1 = 0;
     if (open) {
-        if (lane == 0) {
-            c = open_query_seeds(a.w, qa, qhi, attr_sorted, id_sorted, a.N, want, row);
-            c = c < 0 ? 0 : c;
+        const int64_t T = open_completions(a.w, qhi);
+        if (T > 0) {
+            if (lane < T)
+                c0 = tuple_run(attr_sorted, a.N, completion_word(a.w, qa, qhi, lane), &lo0);
+            if (lane + 32 < T)
+                c1 = tuple_run(attr_sorted, a.N, completion_word(a.w, qa, qhi, lane + 32), &lo1);
+            long long p0 = c0, p1 = c1;  // inclusive prefix sums over the lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long u0 = __shfl_up_sync(0xFFFFFFFFu, p0, o);
+                const long long u1 = __shfl_up_sync(0xFFFFFFFFu, p1, o);
+                if (lane >= o) {
+                    p0 += u0;
+                    p1 += u1;
+                }
+            }
+            const long long tot0 = __shfl_sync(0xFFFFFFFFu, p0, 31);
+            const long long tot1 = __shfl_sync(0xFFFFFFFFu, p1, 31);
+            base0 = p0 - c0;
+            base1 = tot0 + p1 - c1;
+            c = tot0 + tot1;
         }
-        c = __shfl_sync(0xFFFFFFFFu, c, 0);
     } else {
         c = tuple_run(attr_sorted, a.N, qa, &lo);
     }
@@ -185,8 +212,6 @@ __global__ void attribute_near_seeds_kernel(SearchArgs a, const uint32_t *__rest
         const int bits = 64 - __clzll((unsigned long long)c + 1ull);
         bucket[q] = (uint8_t)(bits >= 32 ? 0 : 32 - bits);
     }
-    if (open && c > 0)
-        return;  // row written by lane 0
     if (c == 0) {  // the random stream of NHQ_SEED_RANDOM
         if (lane == 0) {
             int j = 0;
@@ -210,13 +235,37 @@ __global__ void attribute_near_seeds_kernel(SearchArgs a, const uint32_t *__rest
     // 16-byte one when qstride is a multiple of 4 and the batch is 16-byte aligned
     const bool vec4 = (a.d & 3) == 0 && (a.qstride & 3) == 0 &&
                       ((reinterpret_cast<uintptr_t>(a.Q) & 15) == 0);
+    // sampled member j = lane + 32 t is P[floor(j c / M)]
+    uint32_t vid[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int j0 = lane + 32 * t;
+        vid[t] = !open && j0 < M ? id_sorted[lo + ((int64_t)j0 * c) / M] : kNone;
+        if (open) {  // the owner of each rank among the lanes' runs reads its id
+            for (int l = 0; l < 32; ++l) {
+                const int j = 32 * t + l;
+                if (j >= M)
+                    break;  // warp-uniform
+                const int64_t r = ((int64_t)j * c) / M;
+                const unsigned h0 = __ballot_sync(0xFFFFFFFFu, r >= base0 && r < base0 + c0);
+                const unsigned h1 = __ballot_sync(0xFFFFFFFFu, r >= base1 && r < base1 + c1);
+                const int src = h0 ? __ffs(h0) - 1 : __ffs(h1) - 1;
+                uint32_t v = 0;
+                if (lane == src)
+                    v = id_sorted[h0 ? lo0 + (r - base0) : lo1 + (r - base1)];
+                v = __shfl_sync(0xFFFFFFFFu, v, src);
+                if (lane == l)
+                    vid[t] = v;
+            }
+        }
+    }
     unsigned long long key[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         const int j = lane + 32 * t;
         key[t] = ~0ull;
         if (j < M) {
-            const uint32_t v = id_sorted[lo + ((int64_t)j * c) / M];
+            const uint32_t v = vid[t];
             const float *xv = a.X + (int64_t)v * a.xstride;
             float s = 0.f;
             if (vec4) {

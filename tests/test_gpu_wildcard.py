@@ -118,3 +118,23 @@ def test_wildcard_off_keeps_255_an_ordinary_code(nhq, graphs):
         torch.cuda.synchronize()
     assert (ids_i64(ids) == ref["ids"]).all()
     assert (chi.cpu().numpy().astype(np.int32) == ref["chi"]).all()
+
+
+@pytest.mark.parametrize("seed_mode", [1, 3])
+def test_search_open_queries_with_many_completions(nhq, graphs, seed_mode):
+    # attributes 1 and 2 open: 5 x 7 = 35 completions (more than one per lane), and runs
+    # of about 1,300 members, so the nearest rule samples 256 of them
+    w, gs = graphs[3]
+    wts, nbr = gs["const"]
+    QA = w.QA.copy()
+    QA[::2, 1:] = 255
+    ref = O.search(w.X, w.A, nbr, w.Qv, QA, 10, 40, seed=19, weights=wts, seed_mode=seed_mode,
+                   wildcard=255)
+    with nhq.Index.create(dev(w.X), dev(w.A), wts) as ix:
+        nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
+        ids, g, chi = empty_out(w.nq, 10)
+        nhq.nhq_search(ix.handle, dev(w.Qv), dev(QA), 10, 40, ids, g, chi, seed=19,
+                       seed_mode=seed_mode, wildcard=1)
+        torch.cuda.synchronize()
+    assert (ids_i64(ids) == ref["ids"]).all()
+    assert np.array_equal(g.cpu().numpy().astype(np.float64), ref["gamma"])

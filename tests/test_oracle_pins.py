@@ -663,3 +663,24 @@ def test_open_query_seeds_come_from_the_completion_runs(oracle_mod):
                          CONST, O.F32) for v in seeds]
             want = [v for _, v in sorted(zip(g, seeds))][:5]
             assert list(r["ids"][q][: len(want)]) == want, (ef, q)
+
+
+def test_open_query_nearest_seeds_are_the_nearest_matches(oracle_mod):
+    # mode 3 on an open query: with |P| <= 256 every member of the completion runs is
+    # ranked, so with no expansion the top-k is the exact filtered top-k of the partial
+    # constraint (itself pinned against numpy above)
+    O = oracle_mod
+    w = synth.int_valued(3000, 40, 16, cards=(3, 5, 4), seed=61)
+    QA = w.QA.copy()
+    QA[:, 0] = 255
+    CONST = (1.0, 10000.0)
+    nbr = np.full((w.N, 4), -1, np.int64)
+    r = O.search(w.X, w.A, nbr, w.Qv, QA, 10, 32, weights=CONST, max_iters=0, wildcard=255,
+                 seed_mode=O.SEED_ATTRIBUTE_NEAR)
+    ref, _, P = O.filtered_topk(w.X, w.A, w.Qv, QA, 10, prec=O.F32, wildcard=255)
+    checked = 0
+    for q in range(w.nq):
+        if 10 <= P[q] <= 256:
+            assert (r["ids"][q] == ref[q]).all(), q
+            checked += 1
+    assert checked >= 20
