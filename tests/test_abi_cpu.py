@@ -99,6 +99,12 @@ def test_argument_errors_before_cuda(lib):
                               None) == nhq.ERR_ARG
     assert lib.nhq_postfilter(1, 0, 1, None, None, None, None, None, None) == nhq.ERR_ARG
     assert lib.nhq_postfilter(1, 4, 2, None, None, None, None, None, None) == nhq.ERR_ARG
+    # the wildcard switch takes 0 or 1
+    assert lib.nhq_brute_force_wildcard(None, None, None, 1, 10, None, 2, None, None, None,
+                                        None) == nhq.ERR_ARG
+    assert "wildcard must be" in nhq.nhq_last_error()
+    assert lib.nhq_brute_force_wildcard(None, None, None, 1, 10, None, 1, None, None, None,
+                                        None) == nhq.ERR_ARG
 
 
 def test_load_rejects_missing_and_corrupt_files(lib, tmp_path):
@@ -110,6 +116,34 @@ def test_load_rejects_missing_and_corrupt_files(lib, tmp_path):
     bad.write_bytes(b"NOTANIDX" + b"\0" * 64)
     assert lib.nhq_load(str(bad).encode(), None, C.byref(out)) == nhq.ERR_IO
     assert "not an index file" in nhq.nhq_last_error()
+    # header {version, N, d, m, R, weight mode, 0, 0} and the two weights
+    def header(version, m, widths=None, shifts=None):
+        h = np.array([version, 10, 4, m, 0, 0, 0, 0], np.int32).tobytes()
+        h += np.array([1.0, 0.0], np.float32).tobytes()
+        if version == 2:
+            sh = np.zeros(32, np.uint8) if shifts is None else np.asarray(shifts, np.uint8)
+            wd = np.zeros(32, np.uint8) if widths is None else np.asarray(widths, np.uint8)
+            h += sh.tobytes() + wd.tobytes()
+        return b"NHQIDX01" + h
+    cases = {
+        "v3": header(3, 2),
+        "v1 with 5 attributes": header(1, 5),
+        "v2 with a zero-width field": header(2, 2, widths=[8] + [0] * 31,
+                                             shifts=[0, 8] + [0] * 30),
+        "v2 with a field past bit 31": header(2, 1, widths=[9] + [0] * 31,
+                                              shifts=[30] + [0] * 31),
+        "v2 with 33 attributes": header(2, 33),
+    }
+    for name, blob in cases.items():
+        f = tmp_path / "h.idx"
+        f.write_bytes(blob + b"\0" * 16)
+        assert lib.nhq_load(str(f).encode(), None, C.byref(out)) == nhq.ERR_IO, name
+        assert "not an index file" in nhq.nhq_last_error(), name
+    # a valid version-2 header over a truncated body
+    f = tmp_path / "t.idx"
+    f.write_bytes(header(2, 2, widths=[8, 8] + [0] * 30, shifts=[0, 8] + [0] * 30) + b"\0" * 8)
+    assert lib.nhq_load(str(f).encode(), None, C.byref(out)) == nhq.ERR_IO
+    assert "truncated" in nhq.nhq_last_error()
 
 
 def test_binding_type_checks():
