@@ -80,8 +80,8 @@ __host__ __device__ __forceinline__ uint32_t field_hi(const Fusion &w, int j) {
 // A query's packed word under the layout in w (codes above maxc[j] become maxc[j] + 1);
 // *hi = the top bits of the fields the query constrains (w.hi less the fields whose code
 // is the wildcard 255 when w.wild is set), to pass to chi_packed in place of w.hi.
-__device__ __forceinline__ uint32_t pack_query_word(const uint8_t *qa, const Fusion &w,
-                                                   uint32_t *hi) {
+__host__ __device__ __forceinline__ uint32_t pack_query_word(const uint8_t *qa, const Fusion &w,
+                                                            uint32_t *hi) {
     uint32_t word = 0, open = 0;
     for (int j = 0; j < w.m; ++j) {
         const uint32_t v = qa[j];
