@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--hs", default="1,2")
     ap.add_argument("--cpu-sample", type=int, default=40, help="queries in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=120.0,
+                    help="--impl reference: about this many seconds of oracle work in all")
     ap.add_argument("--fixed", default=None, help="skip the sweep: ef,h,vec (e.g. 64,1,1)")
     ap.add_argument("--seed-mode", type=int, default=1,
                     help="seed set B: 0 random (the paper's), 1 attribute entry")
@@ -183,10 +185,11 @@ def peaks():
 
 
 # ---------------------------------------------------------------- cpu baseline
-def oracle_topk_threads(w, a, n_q, cores):
+def oracle_topk_threads(w, a, n_q, cores, ex=None):
     """Seconds for the oracle's exact fused top-k of the first n_q queries, the queries
-    split into `cores` contiguous slices run by as many threads (the oracle is C called
-    through ctypes, which releases the interpreter lock during the call)."""
+    split into `cores` contiguous slices run by as many threads of `ex` (a pool of at
+    least `cores` threads, made here when None; the oracle is C called through ctypes,
+    which releases the interpreter lock during the call)."""
     from concurrent.futures import ThreadPoolExecutor
 
     import oracle
@@ -194,11 +197,19 @@ def oracle_topk_threads(w, a, n_q, cores):
     oracle.build()
     bounds = np.linspace(0, n_q, cores + 1).astype(int)
     parts = [(lo, hi) for lo, hi in zip(bounds[:-1], bounds[1:]) if hi > lo]
-    with ThreadPoolExecutor(max_workers=len(parts)) as ex:
+    X, A = np.ascontiguousarray(w.X), np.ascontiguousarray(w.A)
+
+    def run(pool):
         t0 = time.perf_counter()
-        list(ex.map(lambda p: oracle.fused_topk(w.X, w.A, w.Qv[p[0]:p[1]], w.QA[p[0]:p[1]],
-                                                a.k, weights=CONST_W, prec=oracle.F32), parts))
+        list(pool.map(lambda p: oracle.fused_topk(X, A, w.Qv[p[0]:p[1]], w.QA[p[0]:p[1]],
+                                                  a.k, weights=CONST_W, prec=oracle.F32),
+                      parts))
         return time.perf_counter() - t0
+
+    if ex is not None:
+        return run(ex)
+    with ThreadPoolExecutor(max_workers=len(parts)) as pool:
+        return run(pool)
 
 
 def cpu_baseline(w, a, n_q):
@@ -227,28 +238,37 @@ def reference_arm(a, rank, world):
     cores = os.cpu_count() or 1
     steps = max(1, a.steps)
     # calibration (untimed): one query per thread; the brute force costs the same for
-    # every query, so this sizes the per-step sample to keep the whole run near 2 minutes
+    # every query, so this sizes the per-step sample to keep the whole run near
+    # --ref-seconds (2 minutes by default)
     t1 = oracle_topk_threads(w, a, min(w.nq, cores), cores)
-    budget = 120.0 / steps
+    budget = a.ref_seconds / steps
     per_thread = int(min(max(1, a.cpu_sample // 4), max(1.0, budget / t1)))
     n_q = min(w.nq, per_thread * cores)
     frac = 1.0
-    if t1 > budget:  # even one query per thread is too long: a prefix of the objects
-        frac = max(budget / t1, 1e-3)
+    if t1 > budget:
+        # even one query per thread is too long: one query per step on one thread, over a
+        # prefix of the objects (at least 1/64 of them, so the call's fixed cost stays
+        # small beside the scan), the rate scaled by the fraction scanned
+        cores, n_q = 1, 1
+        t_one = oracle_topk_threads(w, a, 1, 1)
+        frac = min(1.0, max(budget / t_one, 1.0 / 64))
         n_obj = max(a.k, int(w.N * frac))
         frac = n_obj / w.N
         w = type(w)(w.name, w.X[:n_obj], w.A[:n_obj], w.Qv, w.QA, w.cards, w.meta)
     for _ in range(a.warmup):
         pass  # the oracle has no warm-up state
-    for _ in range(steps):
-        per.append(oracle_topk_threads(w, a, n_q, cores))
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        for _ in range(steps):
+            per.append(oracle_topk_threads(w, a, n_q, cores, ex))
     # the brute force's work is proportional to the objects scanned
     qps = n_q * len(per) / sum(per) * frac
     sample = (f"first {n_q} of the {a.nq:,} queries per step, exact fused top-{a.k} over "
               + (f"all {w.N:,} objects" if frac == 1.0 else
                  f"the first {w.N:,} objects, rate scaled by {frac:.4g} to all objects")
-              + f" (oracle brute force in C, {cores} threads over contiguous query slices, "
-              "recall 1.0)")
+              + f" (oracle brute force in C, {cores} thread{'s' if cores > 1 else ''} over "
+              "contiguous query slices, recall 1.0)")
     line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s",
             "n_gpus": a.gpus, "steps": len(per), "warmup": a.warmup,
             "ms_per_step": 1000 * float(np.mean(per)), "higher_is_better": True,
