@@ -684,3 +684,140 @@ def test_open_query_nearest_seeds_are_the_nearest_matches(oracle_mod):
             assert (r["ids"][q] == ref[q]).all(), q
             checked += 1
     assert checked >= 20
+
+
+# ------------------------------------------------------------------ seed set B (closed queries)
+_M64 = (1 << 64) - 1
+
+
+def _splitmix64_py(state, n):
+    """First n outputs of Vigna's splitmix64 from ``state``, written out in Python
+    (add the golden gamma, then the two xor-shift-multiply rounds and a final xor-shift)."""
+    out = []
+    for _ in range(n):
+        state = (state + 0x9E3779B97F4A7C15) & _M64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        out.append(z ^ (z >> 31))
+    return out
+
+
+def _mix64_py(z):
+    """The finaliser of splitmix64 applied to z (one output from state z - gamma)."""
+    return _splitmix64_py((z - 0x9E3779B97F4A7C15) & _M64, 1)[0]
+
+
+def _seed_pool_f32(Qv, QA, X, A, q, seeds, wl):
+    """(Gamma, id) of the seeds in f32 from integer arithmetic: delta^2 is an exact integer
+    below 2^24, delta = its correctly rounded square root, Gamma = 1 * delta + w_l * chi with
+    one f32 rounding (constant weights); with w_l = None the proportional form, which for
+    chi = 0 is delta itself."""
+    recs = []
+    for v in seeds:
+        d2 = int(((Qv[q].astype(np.int64) - X[v].astype(np.int64)) ** 2).sum())
+        dl = np.sqrt(np.float32(d2))
+        ch = int((A[v] != QA[q]).sum())
+        if wl is None:
+            assert ch == 0
+            g = dl
+        else:
+            g = np.float32(dl + np.float32(np.float32(wl) * np.float32(ch)))
+        recs.append((float(g), int(v)))
+    return sorted(recs)
+
+
+@pytest.mark.parametrize("weights", [None, (1.0, 10000.0)])
+def test_closed_query_attribute_entry_seeds_are_evenly_spaced_matches(oracle_mod, weights):
+    # Alg. 2's seed set B under the attribute-entry reading, for queries that constrain
+    # every attribute: P = the objects equal to the query on all attributes, ascending
+    # ids; S = min(ef, 32, |P|) seeds P[floor(j |P| / S)]; |P| = 0 falls back to the first
+    # min(ef, 32) distinct ids of splitmix64(seed ^ mix64(q)) mod N (at most 64 draws).
+    # With an empty graph and no expansion the pool is exactly B, returned by (Gamma, id).
+    O = oracle_mod
+    w = synth.int_valued(600, 40, 6, cards=(3, 4, 2), seed=63, zipf=False)
+    QA = w.QA.copy()
+    QA[::5, 1] = 7  # no object has code 7: |P| = 0 for every fifth query
+    wl = None if weights is None else weights[1]
+    nbr = np.full((w.N, 3), -1, np.int64)
+    seed = 0x5EED
+    for ef in (8, 32, 48):
+        r = O.search(w.X, w.A, nbr, w.Qv, QA, ef, ef, seed=seed, max_iters=0, weights=weights,
+                     seed_mode=O.SEED_ATTRIBUTE, prec=O.F32)
+        for q in range(w.nq):
+            P = np.flatnonzero((w.A == QA[q]).all(axis=1))
+            c = P.size
+            if c > 0:
+                S = min(ef, 32, c)
+                B = [int(P[(j * c) // S]) for j in range(S)]
+            else:
+                want, B = min(ef, 32), []
+                for x in _splitmix64_py((seed ^ _mix64_py(q)) & _M64, 64):
+                    v = x % w.N
+                    if v not in B:
+                        B.append(v)
+                    if len(B) == want:
+                        break
+            if c == 0 and wl is None:  # proportional weights, chi > 0: the set of ids
+                assert sorted(v for v in r["ids"][q] if v >= 0) == sorted(B), (ef, q)
+                continue
+            expect = _seed_pool_f32(w.Qv, QA, w.X, w.A, q, B, wl)
+            assert [v for _, v in expect] == list(r["ids"][q][:len(B)]), (ef, q)
+            assert (r["ids"][q][len(B):] == -1).all(), (ef, q)
+            assert np.array_equal(np.array([g for g, _ in expect]),
+                                  r["gamma"][q][:len(B)].astype(np.float32).astype(np.float64))
+            assert r["ndc"][q] == len(B)
+
+
+def test_nearest_attribute_entry_seeds_sample_large_match_sets(oracle_mod):
+    # the nearest-entry rule with |P| > 256: the M = 256 members P[floor(j |P| / M)] are
+    # ranked by (delta^2, id) and the min(ef, 32) first are the seeds
+    O = oracle_mod
+    w = synth.int_valued(4000, 30, 8, cards=(2, 2, 2), seed=64, zipf=False)
+    CONST = (1.0, 10000.0)
+    nbr = np.full((w.N, 3), -1, np.int64)
+    for ef in (10, 32):
+        r = O.search(w.X, w.A, nbr, w.Qv, w.QA, ef, ef, weights=CONST, max_iters=0,
+                     seed_mode=O.SEED_ATTRIBUTE_NEAR, prec=O.F32)
+        for q in range(w.nq):
+            P = np.flatnonzero((w.A == w.QA[q]).all(axis=1))
+            c = P.size
+            assert c > 256
+            sample = P[[(j * c) // 256 for j in range(256)]]
+            d2 = ((w.Qv[q].astype(np.int64) - w.X[sample].astype(np.int64)) ** 2).sum(-1)
+            B = sample[np.lexsort((sample, d2))][:min(ef, 32)]
+            expect = _seed_pool_f32(w.Qv, w.QA, w.X, w.A, q, B, 10000.0)
+            assert [v for _, v in expect] == list(r["ids"][q]), (ef, q)
+
+
+# ------------------------------------------------------------------ NPG_nsw: serial limit
+def _serial_nsw(O, X, A, R, L, weights, seed, entry):
+    """NPG_nsw as Sec. 4.3 states it, one object at a time: object v searches the graph
+    of the objects inserted before it for its L nearest (Alg. 2, k = ef = L), keeps a
+    landing-zone selection of them as N(v) (Def. 6), and every u in N(v) re-selects from
+    N(u) plus v."""
+    N = X.shape[0]
+    nbr = np.full((N, R), -1, np.int64)
+    for v in range(1, N):
+        B = O.nsw_attribute_seeds(v, v, A, seed) if entry else O.nsw_seeds(v, v, seed)
+        r = O.search(X, A, nbr, X[v:v + 1], A[v:v + 1], L, L, seeds=np.array([B]),
+                     weights=weights, prec=O.F32)
+        row, _ = O.edge_select(X, A, r["ids"], R, weights=weights, prec=O.F32, rows=[v])
+        nbr[v] = row[0]
+        for u in row[0]:
+            if u < 0:
+                continue
+            cu = np.full((1, R + 1), -1, np.int64)
+            old = [x for x in nbr[u] if x >= 0]
+            cu[0, :len(old) + 1] = old + [v]
+            nbr[u] = O.edge_select(X, A, cu, R, weights=weights, prec=O.F32, rows=[u])[0][0]
+    return nbr
+
+
+@pytest.mark.parametrize("weights,entry", [(None, 0), ((1.0, 10000.0), 1)])
+def test_nsw_single_vertex_waves_are_serial_insertion(oracle_mod, weights, entry):
+    O = oracle_mod
+    w = synth.int_valued(160, 1, 8, cards=(2, 3), seed=65)
+    got = O.build_nsw(w.X, w.A, R=6, L=12, weights=weights, seed=11, wave_max=1, entry=entry)
+    ref = _serial_nsw(O, w.X, w.A, 6, 12, weights, 11, entry)
+    assert np.array_equal(got, ref)
