@@ -237,24 +237,27 @@ def reference_arm(a, rank, world):
     per = []
     cores = os.cpu_count() or 1
     steps = max(1, a.steps)
-    # calibration (untimed): one query per thread; the brute force costs the same for
-    # every query, so this sizes the per-step sample to keep the whole run near
-    # --ref-seconds (2 minutes by default)
+    # calibration (untimed): one query per thread on every core; the brute force costs the
+    # same for every query, so this sizes the per-step sample to keep the whole run near
+    # --ref-seconds (2 minutes by default).  Every regime below keeps all cores busy, so
+    # `value` is always an all-cores rate.
     t1 = oracle_topk_threads(w, a, min(w.nq, cores), cores)
     budget = a.ref_seconds / steps
-    per_thread = int(min(max(1, a.cpu_sample // 4), max(1.0, budget / t1)))
-    n_q = min(w.nq, per_thread * cores)
     frac = 1.0
     if t1 > budget:
-        # even one query per thread is too long: one query per step on one thread, over a
-        # prefix of the objects (at least 1/64 of them, so the call's fixed cost stays
-        # small beside the scan), the rate scaled by the fraction scanned
-        cores, n_q = 1, 1
-        t_one = oracle_topk_threads(w, a, 1, 1)
-        frac = min(1.0, max(budget / t_one, 1.0 / 64))
-        n_obj = max(a.k, int(w.N * frac))
+        # even one query per thread over all objects is too long for one step: one query
+        # per thread, each over a prefix of the objects sized to the budget (at least
+        # max(k, 1024) objects, so the call's fixed cost stays small beside the scan; that
+        # floor exceeds the budget only when a step may take less than t1 * 1024 / N; every
+        # step also pays the thread pool's dispatch, about 2 ms on 8 cores), the rate scaled
+        # by the fraction scanned (brute-force work is linear in N)
+        per_thread = 1
+        n_obj = min(w.N, max(a.k, 1024, int(w.N * budget / t1)))
         frac = n_obj / w.N
         w = type(w)(w.name, w.X[:n_obj], w.A[:n_obj], w.Qv, w.QA, w.cards, w.meta)
+    else:
+        per_thread = int(min(max(1, a.cpu_sample // 4), max(1.0, budget / t1)))
+    n_q = min(w.nq, per_thread * cores)
     for _ in range(a.warmup):
         pass  # the oracle has no warm-up state
     from concurrent.futures import ThreadPoolExecutor

@@ -362,13 +362,18 @@ nhq_status nhq_search_batched(const nhq_index *index, const float *queries,
  *   and packed_query_attributes[Q] (u32 words as written by nhq_pack_attributes),
  *   queries[Q][d] f32, outputs ids/dists/chi[Q][k] (dists, chi may be NULL);
  *   every pointer must be device memory.
- * Its working memory is a fixed 16 MiB array inside the library, present on every
- * GPU that loads the library until the process exits.  The first call on a device
- * looks up that array's device address (make it before any stream capture).
+ * Its working memory is a fixed 16 MiB array inside the library.  Device memory for
+ * it is committed on each GPU when the library's code is first used there (under
+ * CUDA's lazy module loading that can be this call's first use on the device) and
+ * stays until the process exits.  The first call on a device also looks up the
+ * array's device address.  So make one call on each device at start-up -- a call
+ * with Q = 0 does only this set-up -- before the caller's own allocator reserves
+ * the device's memory and before any stream capture.
  * A call whose split lists would need more than 16 MiB (about Q * 32 * k * 8
  * bytes for small batches) returns NHQ_ERR_ARG with the required size; nothing
- * is written then.  Calls share the array: calls that overlap on the GPU (other
- * streams or host threads) race and must be serialised by the caller.
+ * is written then.  Weights follow nhq_brute_force's rules (NHQ_W_FILTER allowed).
+ * Calls share the array: calls that overlap on the GPU (other streams or host
+ * threads) race and must be serialised by the caller.
  */
 nhq_status nhq_brute_force_noalloc(const float *vectors, const uint32_t *packed_attributes,
                                    int64_t N, int32_t d, int32_t m, const float *queries,

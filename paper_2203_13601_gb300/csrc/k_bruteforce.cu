@@ -312,8 +312,13 @@ cudaError_t launch_topk(const TopkArgs &a, void *scratch, size_t scratch_bytes, 
 // start-up), or code that must not touch the allocator on its hot path.  For
 // them the split path's only scratch -- the per-slice sorted lists that
 // topk_tile_kernel writes and topk_merge_kernel reads -- lives in the
-// file-scope array below.  It is kNoAllocScratchBytes (16 MiB) on every GPU
-// that loads the library and stays there until the process exits.  Every call
+// file-scope array below.  It is kNoAllocScratchBytes (16 MiB) of device memory
+// on every GPU where this module is loaded, and stays there until the process
+// exits.  Under CUDA's lazy module loading that happens on a device's first use
+// of this file's code, possibly the first nhq_brute_force_noalloc call itself
+// (its cudaGetSymbolAddress), so callers make a first call (Q = 0 suffices) at
+// start-up, before their own allocator reserves the device's memory and before
+// any stream capture.  Every call
 // on a device shares it: each call fully rewrites the entries it later reads,
 // so nothing has to start at zero, but calls whose kernels overlap on the GPU
 // (different streams, or different host threads) race on it.
@@ -387,12 +392,13 @@ extern "C" nhq_status nhq_brute_force_noalloc(const float *vectors,
                                          "1..4, Q >= 0, k in 1..256");
     if (d % 4 != 0)
         return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: d must be a multiple of 4");
-    if (w.mode != NHQ_W_PROPORTIONAL && w.mode != NHQ_W_CONSTANT && w.mode != NHQ_W_HARMONIC &&
-        w.mode != NHQ_W_FILTER)
-        return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: unknown weight mode");
-    if (w.mode == NHQ_W_CONSTANT &&
-        (!std::isfinite(w.w_v) || !std::isfinite(w.w_l) || w.w_v < 0.f || w.w_l < 0.f))
-        return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: weights must be finite, >= 0");
+    nhq_status st = validate_weights(w, true);  // the rules of nhq_brute_force
+    if (st != NHQ_OK)
+        return st;
+    // the per-device set-up runs first, so that a call with Q = 0 can make it at start-up
+    NoAllocDevice *dv = nullptr;
+    if ((st = noalloc_setup(&dv)) != NHQ_OK)
+        return st;
     if (Q == 0)
         return NHQ_OK;
     if (!is_device_pointer(vectors) || !is_device_pointer(packed_attributes) ||
@@ -404,10 +410,6 @@ extern "C" nhq_status nhq_brute_force_noalloc(const float *vectors,
     if ((reinterpret_cast<uintptr_t>(vectors) & 15) != 0)
         return report_error(NHQ_ERR_ARG, "nhq_brute_force_noalloc: vectors must be 16-byte "
                                          "aligned");
-    NoAllocDevice *dv = nullptr;
-    nhq_status st = noalloc_setup(&dv);
-    if (st != NHQ_OK)
-        return st;
     TopkArgs a;
     a.X = vectors;
     a.xstride = d;

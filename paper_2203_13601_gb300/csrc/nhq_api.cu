@@ -181,6 +181,10 @@ nhq_status report_error(nhq_status s, const char *message) {
     g_err = message;
     return s;
 }
+// The weight rules of every entry point, for the entry points defined in other units.
+nhq_status validate_weights(const nhq_weights &w, bool allow_filter) {
+    return check_weights(w, allow_filter);
+}
 }  // namespace nhq
 
 extern "C" {

@@ -184,6 +184,8 @@ bool compact_layout(int m, const uint8_t *maxc, AttrLayout *out);
 nhq::Fusion make_fusion(const nhq_weights &w, const AttrLayout &L);
 nhq::Fusion make_fusion(const nhq_weights &w, int m);  // byte layout
 nhq_status report_error(nhq_status s, const char *message);  // nhq_api.cu
+// NHQ_OK, or NHQ_ERR_ARG with the message set, by the weight rules of nhq_brute_force
+nhq_status validate_weights(const nhq_weights &w, bool allow_filter);  // nhq_api.cu
 
 // k_util.cu
 cudaError_t launch_pack_attributes(const uint8_t *a, int64_t n, const AttrLayout &L,
