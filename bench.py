@@ -63,6 +63,12 @@ def parse():
     ap.add_argument("--seed-mode", type=int, default=1,
                     help="seed set B: 0 random (the paper's), 1 attribute entry")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned early stop")
+    ap.add_argument("--wpq", type=int, default=1, help="warps per query of the search (1, 2, 4)")
+    ap.add_argument("--cells", type=int, default=0,
+                    help="entry cells E for the learned entry point (0: the workload's default)")
+    ap.add_argument("--entry-T", type=int, default=2, help="entry cells taken per query")
+    ap.add_argument("--train-q", type=int, default=100_000,
+                    help="training queries for the learned entry point")
     ap.add_argument("--knn-dtype", type=int, default=1,
                     help="candidate build: 0 exact f32 SIMT, 1 bf16 tensor cores (exact here)")
     ap.add_argument("--learned-efs", default="16,24,32,48,64")
@@ -70,8 +76,8 @@ def parse():
     ap.add_argument("--c4-build", default="nsw", choices=["kgraph", "nsw"],
                     help="c4 workload: graph built from exact candidates or incrementally")
     ap.add_argument("--workload", default="c2",
-                    choices=["c2", "c4", "c5", "strategies", "curves", "builds", "attrdim",
-                             "wildcard"],
+                    choices=["c2", "c3", "c4", "c5", "strategies", "curves", "builds",
+                             "attrdim", "wildcard"],
                     help="c2: the headline workload (default); c4: the heterogeneous batch "
                          "(1M x 96, 100k queries with mixed k and ef) through "
                          "nhq_search_batched; c5: the 10M x 96 set (f16-valued), 50k queries; "
@@ -228,6 +234,55 @@ def cpu_baseline(w, a, n_q):
             "all_cores": {"value": n_all / dt_all, "unit": "queries/s", "cores": cores,
                           "sample": f"first {n_all} queries, {cores} threads over contiguous "
                                     "slices", "seconds": dt_all}}
+
+
+def oracle_search_threads(w, a, nbr, ef, seed_mode, n_q, cores, h=1, vec=0):
+    """Seconds for the oracle's serial Alg. 2 (the same seed rule, ef and graph as the GPU
+    search) over the first n_q queries, split into `cores` contiguous slices run by as
+    many threads (the oracle is C called through ctypes, which releases the interpreter
+    lock); returns (seconds, ids of those queries)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    oracle.build()
+    bounds = np.linspace(0, n_q, cores + 1).astype(int)
+    parts = [(lo, hi) for lo, hi in zip(bounds[:-1], bounds[1:]) if hi > lo]
+    X, A = np.ascontiguousarray(w.X), np.ascontiguousarray(w.A)
+
+    def one(pr):
+        return oracle.search(X, A, nbr, w.Qv[pr[0]:pr[1]], w.QA[pr[0]:pr[1]], a.k, ef,
+                             seed=12345, weights=CONST_W, prec=oracle.F32,
+                             seed_mode=seed_mode, h=h, vec_round=vec, rerank=vec == 2)["ids"]
+
+    with ThreadPoolExecutor(max_workers=len(parts)) as pool:
+        t0 = time.perf_counter()
+        out = list(pool.map(one, parts))
+        dt = time.perf_counter() - t0
+    return dt, np.concatenate(out, axis=0)
+
+
+def cpu_search_baseline(w, a, nbr, ef, seed_mode, gpu_ids, n_q, h=1, vec=0):
+    """The oracle's serial Alg. 2 on the bench's own graph at the chosen ef and seed rule
+    (the same algorithm as the GPU search, so the two compare like with like): one thread
+    over n_q queries, then one slice per host core.  Its ids equal the GPU's on these
+    integer-valued data (every Gamma is exact), which the line reports."""
+    n_q = max(1, min(n_q, w.nq))
+    dt1, ids1 = oracle_search_threads(w, a, nbr, ef, seed_mode, n_q, 1, h, vec)
+    cores = os.cpu_count() or 1
+    n_all = max(1, min(n_q * cores, w.nq))
+    dta, idsa = oracle_search_threads(w, a, nbr, ef, seed_mode, n_all, cores, h, vec)
+    # the single call numbers its queries as the GPU launch does (the random fallback seed
+    # depends on the row index), so its ids must equal the GPU's
+    g = gpu_ids[:n_q].astype(np.int64)
+    g[g == 0xFFFFFFFF] = -1
+    return {"value": n_q / dt1, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n_q} of the {w.nq:,} queries, serial Alg. 2 (oracle C) on the "
+                      f"bench's graph, ef {ef}, h {h}, the same seed rule and scoring copy",
+            "all_cores": {"value": n_all / dta, "unit": "queries/s", "cores": cores,
+                          "sample": f"first {n_all} queries, {cores} threads over contiguous "
+                                    "slices"},
+            "ids_equal_gpu": bool((ids1 == g).all())}
 
 
 def reference_arm(a, rank, world):
@@ -542,6 +597,216 @@ def c5_arm(a):
                    "ef": ef, "recall": sweep[-1]["recall"], "sweep": sweep,
                    "build_s": t_build, "gen_s": t_gen,
                    "queries_with_no_match": int((P == 0).sum())},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "mean_ndc": float(ndc_h.mean()), "mean_expansions": float(exp_h.mean())},
+        "clocks": clk}), flush=True)
+    ix.close()
+
+
+def train_entry(nhq, ix, w, wtr, E, k, dev, epochs=6, batch=1024, lr=2e-3):
+    """The learned entry point: cells, then the entry model trained on the cells of the
+    first results of the plain search (attribute entry, ef 64) for the training queries.
+    Returns (model, seconds, number of labelled traces)."""
+    import torch
+
+    t0 = time.perf_counter()
+    nhq.nhq_index_build_cells(ix.handle, E)
+    Qt, QAt = torch.from_numpy(wtr.Qv).to(dev), torch.from_numpy(wtr.QA).to(dev)
+    idt = torch.empty((wtr.nq, k), dtype=torch.uint32, device=dev)
+    nhq.nhq_search(ix.handle, Qt, QAt, k, 64, idt, seed=1, seed_mode=nhq.SEED_ATTRIBUTE)
+    lab = torch.empty(wtr.nq, dtype=torch.int32, device=dev)
+    nhq.nhq_entry_labels(ix.handle, idt, lab)
+    keep = lab >= 0
+    Qk, lk = Qt[keep].contiguous(), lab[keep].contiguous()
+    rms = float(np.sqrt(np.mean(np.square(wtr.Qv[:2000].astype(np.float64)))))
+    p = (np.random.default_rng(3).standard_normal(nhq.nhq_entry_param_count(w.d, E)) *
+         0.05).astype(np.float32)
+    p[0] = 1.0 / max(rms, 1e-12) / np.sqrt(w.d)  # inputs of about unit norm
+    P = torch.from_numpy(p).to(dev)
+    nhq.nhq_entry_train(P, E, Qk, lk, epochs=epochs, batch=batch, lr=lr)
+    torch.cuda.synchronize()
+    return P, time.perf_counter() - t0, int(keep.sum().item())
+
+
+def f64_error(w, ids_h, dists_h, weights, n=200):
+    """Max and mean relative error of returned Gamma values against Gamma computed in f64
+    from the f32 rows (Eq. 1 and Eq. 6), over the first n queries."""
+    errs = []
+    for q in range(min(n, ids_h.shape[0])):
+        for j in range(ids_h.shape[1]):
+            v = int(ids_h[q, j])
+            if v == 0xFFFFFFFF:
+                continue
+            dl = float(np.sqrt(np.sum((w.X[v].astype(np.float64) -
+                                       w.Qv[q].astype(np.float64)) ** 2)))
+            ch = int((w.A[v] != w.QA[q]).sum())
+            g = weights[0] * dl + weights[1] * ch
+            vec_part = weights[0] * dl  # the attribute term is exact
+            errs.append(abs(float(dists_h[q, j]) - g) / max(vec_part, 1e-30))
+    e = np.array(errs) if errs else np.zeros(1)
+    return {"max_rel": float(e.max()), "mean_rel": float(e.mean()),
+            "of": "the vector term w_v * delta"}
+
+
+def c3_arm(a):
+    """The c3-shaped set (GIST1M-shaped): N = 1M, d = 960 unit-normalised rows (1,000
+    centroids), m = 4 uniform attributes (2/5/10/50), 10,000 queries, k = 10.  Every form
+    -- scoring copy (f32; bf16; bf16 or fp8-e4m3 with the f32 re-rank), warps per query
+    (1, 2, 4), seeds by attribute entry or by the learned entry cells -- is swept for the
+    smallest ef reaching hybrid Recall@10 >= target; the fastest ("chosen") is autotuned
+    and timed beside the plain f32 form (one warp per query, attribute entry), with its
+    HBM roofline and the distance error of each scoring copy against f64 on the same
+    results."""
+    import torch
+
+    import paper_2203_13601_gb300 as nhq
+    import synth
+    from paper_2203_13601_gb300 import build as B
+
+    B.build()
+    nhq.load_library()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    w = synth.c3(N=a.n, nq=a.nq)
+    wtr = synth.c3(N=a.n, nq=a.train_q, query_stream=1)
+    t_gen = time.perf_counter() - t0
+    X, A = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.A).to(dev)
+    Qv, QA = torch.from_numpy(w.Qv).to(dev), torch.from_numpy(w.QA).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = nhq.Index.build(X, A, degree=a.R, weights=CONST_W, K=64, knn_dtype=1)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    k = a.k
+    gt = torch.empty((w.nq, k), dtype=torch.uint32, device=dev)
+    t0 = time.perf_counter()
+    nhq.nhq_brute_force(ix.handle, Qv, QA, k, gt, weights="filter")
+    torch.cuda.synchronize()
+    t_gt = time.perf_counter() - t0
+    gt_h = gt.cpu().numpy()
+    P_cnt = match_counts(w.A, w.QA)
+    E = a.cells if a.cells > 0 else 512
+    model, t_train, n_tr = train_entry(nhq, ix, w, wtr, E, k, dev)
+    ids, dd, ch = (torch.empty((w.nq, k), dtype=torch.uint32, device=dev),
+                   torch.empty((w.nq, k), dtype=torch.float32, device=dev),
+                   torch.empty((w.nq, k), dtype=torch.uint8, device=dev))
+    ndc = torch.empty(w.nq, dtype=torch.int32, device=dev)
+    exps = torch.empty(w.nq, dtype=torch.int32, device=dev)
+
+    def kw_of(form):
+        kw = dict(seed=12345, vec_dtype=form["vec"], rerank=form["rerank"],
+                  seed_mode=form["seeds"], warps_per_query=form["wpq"],
+                  warps_per_block=form.get("wpb", 0), hash_bits=form.get("bits", 0))
+        if form["seeds"] == nhq.SEED_CELL_LEARNED:
+            kw.update(entry_model=model, entry_cells=a.entry_T)
+        return kw
+
+    def run(form, ef, diag=False):
+        nhq.nhq_search(ix.handle, Qv, QA, k, ef, ids, dd, ch, ndc=ndc if diag else None,
+                       expansions=exps if diag else None, stream=stream, **kw_of(form))
+
+    def timed(form, ef, reps=5):
+        run(form, ef)
+        run(form, ef)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run(form, ef)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    efs = [int(x) for x in a.efs.split(",") if int(x) >= k]
+    names = {(0, 0): "f32", (1, 0): "bf16", (1, 1): "bf16 + f32 re-rank",
+             (2, 1): "fp8-e4m3 + f32 re-rank"}
+    forms, sweep, errors = [], [], {}
+    for (vec, rr), nm in names.items():
+        for seeds in (nhq.SEED_ATTRIBUTE, nhq.SEED_CELL_LEARNED):
+            at = None  # (ef, recall) reaching the target; it does not depend on wpq
+            for wpq in (1, 2, 4):
+                form = {"vec": vec, "rerank": rr, "seeds": seeds, "wpq": wpq}
+                if wpq == 1:
+                    for ef in efs:
+                        run(form, ef)
+                        torch.cuda.synchronize()
+                        rec, _ = hybrid_recall(ids.cpu().numpy(), w.A, w.QA, gt_h, P_cnt, k)
+                        if rec >= a.target:
+                            at = (ef, rec)
+                            break
+                if at is None:
+                    break
+                found = (at[0], at[1], timed(form, at[0]))
+                if wpq == 1 and seeds == nhq.SEED_ATTRIBUTE:
+                    errors[nm] = f64_error(w, ids.cpu().numpy(), dd.cpu().numpy(), CONST_W)
+                row = dict(form, scoring=nm, ef=found[0], recall=found[1], ms=found[2],
+                           seeds_name=["random", "attribute entry", "given",
+                                       "nearest attribute entry", "nearest cells",
+                                       "learned cells"][seeds])
+                sweep.append(row)
+                forms.append(row)
+    plain = next(r for r in forms if r["vec"] == 0 and r["seeds"] == nhq.SEED_ATTRIBUTE and
+                 r["wpq"] == 1)
+    chosen = dict(min(forms, key=lambda r: r["ms"]))
+    # the autotuner on the chosen form: warps per query, warps per block, filter size
+    tmp = torch.empty((w.nq, k), dtype=torch.uint32, device=dev)
+    kwc = kw_of(chosen)
+    wpq_t, wpb_t, bits_t, _ = nhq.nhq_autotune_search(
+        ix.handle, Qv, QA, k, chosen["ef"], tmp, seed=12345, vec_dtype=chosen["vec"],
+        rerank=chosen["rerank"], seed_mode=kwc["seed_mode"], return_wpq=True) \
+        if chosen["seeds"] != nhq.SEED_CELL_LEARNED else (chosen["wpq"], 0, 0, 0)
+    tuned = dict(chosen, wpq=wpq_t, wpb=wpb_t, bits=bits_t)
+    if timed(tuned, chosen["ef"]) < chosen["ms"]:
+        chosen = tuned
+    run(chosen, chosen["ef"], diag=True)
+    torch.cuda.synchronize()
+    ndc_h, exp_h = ndc.cpu().numpy().astype(np.float64), exps.cpu().numpy().astype(np.float64)
+    row_bytes = {0: 4, 1: 2, 2: 1}[chosen["vec"]] * w.d
+    bpq = ndc_h * (row_bytes + 4) + exp_h * a.R * 4 + w.d * 4 + k * 9
+    if chosen["rerank"]:
+        bpq = bpq + chosen["ef"] * 4 * w.d  # the re-rank reads the pool's f32 rows
+    alg_bytes = float(bpq.sum())
+    steps = max(3, min(a.steps, 100))
+    out = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    for tag, form in (("plain_f32", plain), ("chosen", chosen)):
+        for _ in range(max(3, a.warmup)):
+            run(form, form["ef"])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            run(form, form["ef"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[tag] = e0.elapsed_time(e1) / steps
+    clk = clocks.stop()
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (out["chosen"] / 1000.0) / 1e9
+    print(json.dumps({
+        "metric": f"QPS at hybrid Recall@{k} >= {a.target} on the 1M x 960 set, chosen vs "
+                  "plain f32",
+        "value": w.nq / (out["chosen"] / 1000.0), "unit": "queries/s", "n_gpus": 1,
+        "steps": steps, "warmup": a.warmup, "ms_per_step": out["chosen"],
+        "higher_is_better": True, "dtype": ["f32", "bf16", "fp8-e4m3"][chosen["vec"]],
+        "data": "synthetic",
+        "config": {"workload": f"c3-shaped: N={w.N:,} d=960 unit rows (1,000 centroids), m=4 "
+                               f"attrs 2/5/10/50 uniform, {w.nq:,} queries, k={k}, R={a.R}, "
+                               "weights w_v=1 w_l=10000",
+                   "chosen": chosen, "build_s": t_build, "gen_s": t_gen,
+                   "ground_truth_s": t_gt, "entry_cells": E, "entry_T": a.entry_T,
+                   "entry_train_s": t_train, "entry_traces": n_tr,
+                   "queries_with_no_match": int((P_cnt == 0).sum())},
+        "plain_f32": dict(plain, qps=w.nq / (out["plain_f32"] / 1000.0),
+                          ms_timed=out["plain_f32"]),
+        "chosen_beats_plain": out["chosen"] < out["plain_f32"],
+        "speedup_vs_plain": out["plain_f32"] / out["chosen"],
+        "forms": sweep,
+        "f64_error": errors,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes,
@@ -1064,6 +1329,10 @@ def main():
         if rank == 0:
             c5_arm(a)
         return
+    if a.workload == "c3":
+        if rank == 0:
+            c3_arm(a)
+        return
     if a.workload == "curves":
         if rank == 0:
             curves_arm(a)
@@ -1143,7 +1412,8 @@ def main():
                        ndc=ndc if diag else None, expansions=exps if diag else None,
                        h=h, seed=12345, vec_dtype=vec, rerank=int(vec == nhq.VEC_FP8E4M3),
                        seed_mode=a.seed_mode, stop_model=sel["model"],
-                       stop_threshold=sel["tau"], stop_min=4, stop_every=2, stream=stream)
+                       stop_threshold=sel["tau"], stop_min=4, stop_every=2, stream=stream,
+                       warps_per_query=a.wpq)
 
     def time_once(ef, h, vec, reps=2):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1313,7 +1583,8 @@ def main():
         nhq.nhq_search(ix.handle, Qh, QAh, a.k, ef, ids_h, d_h, c_h, h=h, seed=12345,
                        vec_dtype=vec, rerank=int(vec == nhq.VEC_FP8E4M3),
                        seed_mode=a.seed_mode, stop_model=sel["model"],
-                       stop_threshold=sel["tau"], stop_min=4, stop_every=2, stream=stream)
+                       stop_threshold=sel["tau"], stop_min=4, stop_every=2, stream=stream,
+                       warps_per_query=a.wpq)
 
     for _ in range(max(3, a.warmup)):
         run_host()
@@ -1362,6 +1633,16 @@ def main():
     if rank == 0 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, a, a.cpu_sample)
         line["cpu_baseline"].pop("seconds", None)
+        if not use_learned:  # the oracle has no learned stop
+            g32 = torch.empty((w.N, a.R), dtype=torch.uint32, device=dev)
+            nhq.nhq_index_get_graph(ix.handle, g32)
+            nbr = g32.cpu().numpy().astype(np.int64)
+            nbr[nbr == 0xFFFFFFFF] = -1
+            del g32
+            run(ef, h, vec)
+            torch.cuda.synchronize()
+            line["cpu_baseline"]["search"] = cpu_search_baseline(
+                w, a, nbr, ef, a.seed_mode, ids.cpu().numpy(), 4 * a.cpu_sample, h, vec)
     ix.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

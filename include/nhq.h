@@ -90,11 +90,21 @@ typedef enum nhq_seed_mode {
                                c = |P| >= 1: S = min(ef, 32, c), B = {P[floor(j*c/S)] : j < S};
                                c = 0: as NHQ_SEED_RANDOM                                     */
     NHQ_SEED_GIVEN = 2,     /* B = the valid distinct ids of seeds[q][0..n_seeds)            */
-    NHQ_SEED_ATTRIBUTE_NEAR = 3 /* P as above; of its M = min(256, c) members P[floor(j*c/M)]
+    NHQ_SEED_ATTRIBUTE_NEAR = 3, /* P as above; of its M = min(256, c) members P[floor(j*c/M)]
                                the min(ef, 32) nearest to the query by (delta^2 of the f32
                                rows summed in index order, id); c = 0 as NHQ_SEED_RANDOM.
                                For tuples spread over many clusters, where evenly spaced
                                members rarely include the query's own                       */
+    NHQ_SEED_CELL_NEAREST = 4, /* entry cells (nhq_index_build_cells): the T = entry_cells cells
+                               whose centroids are nearest to the query by (delta^2 of the f32
+                               rows summed in index order, cell); P and c as above,
+                               S = min(ef, 32, c); B = the first S members of P in those cells
+                               (nearest cell first, ascending ids within a cell), then while
+                               fewer than S the evenly spaced P[floor(j*c/S2)], j < S2 = S - |B|
+                               (an id listed twice is evaluated once); c = 0 as
+                               NHQ_SEED_RANDOM.  Closed queries only (wildcard = 0)          */
+    NHQ_SEED_CELL_LEARNED = 5  /* as NHQ_SEED_CELL_NEAREST with the T cells of largest logit
+                               (ties: smaller cell) under the entry model `entry_model`       */
 } nhq_seed_mode;
 
 /* Learned early stop (a project addition; the paper's search has no learned
@@ -104,6 +114,15 @@ typedef enum nhq_seed_mode {
 #define NHQ_MLP_INPUTS 8
 #define NHQ_MLP_HIDDEN 64
 #define NHQ_MLP_PARAMS (NHQ_MLP_INPUTS * NHQ_MLP_HIDDEN + 2 * NHQ_MLP_HIDDEN + 1)
+
+/* Learned entry point (a project addition): a 2-layer perceptron that scores the E entry
+ * cells of an index from a query vector q (d values): x = s q, NHQ_ENTRY_HIDDEN ReLU
+ * units, one logit per cell.  Parameters are one flat f32 vector of
+ * nhq_entry_param_count(d, E) values: s (a fixed input scale, not trained) |
+ * W1[d][NHQ_ENTRY_HIDDEN] (input-major) | b1 | W2[NHQ_ENTRY_HIDDEN][E] (hidden-major) | b2.
+ * Inference (the search's seed pass, nhq_entry_forward) reads fp16 weights and
+ * accumulates in f32. */
+#define NHQ_ENTRY_HIDDEN 64
 
 typedef struct nhq_search_params {
     uint64_t seed;           /* random seeds and S1 neighbour subsets derive from splitmix64(seed) */
@@ -131,6 +150,14 @@ typedef struct nhq_search_params {
                                 nearest of 256 sampled) picks B from it; more completions,
                                 or no member: the random stream of NHQ_SEED_RANDOM.
                                 0: 255 is an ordinary code                                  */
+    int32_t warps_per_query; /* 0 or 1: one warp per query; 2 or 4: that many warps share each
+                                expansion's distance evaluations (rows in flight per query
+                                grow with it, queries in flight per SM shrink); results are
+                                the same for every value                                     */
+    const float *entry_model; /* NHQ_SEED_CELL_LEARNED: device, nhq_entry_param_count(d, E) f32 */
+    int32_t entry_cells;     /* NHQ_SEED_CELL_*: T, the cells taken per query, 1..min(8, E); 0 -> 2 */
+    int32_t *cells_out;      /* NHQ_SEED_CELL_*: device [Q][T] receiving each query's cells, or
+                                NULL                                                          */
 } nhq_search_params;
 
 typedef struct nhq_index nhq_index;
@@ -265,6 +292,48 @@ nhq_status nhq_index_build(nhq_index *index, int32_t degree, const nhq_build_par
 nhq_status nhq_index_build_nsw(nhq_index *index, int32_t degree, int32_t L, int32_t wave_max,
                                int32_t rev_cap, int32_t entry, uint64_t seed, void *stream);
 
+/*
+ * Entry cells (a project addition; the paper draws the seed set B of Alg. 2 at random):
+ * E centroids, the objects floor(j N / E) for j < E; every object's cell is its nearest
+ * centroid by (delta, j) (Eq. 1 in f32, the exact top-1 of a plain-L2 brute force over the
+ * centroid rows); the objects are also ordered by (attribute word, cell, id) so that the
+ * seed modes NHQ_SEED_CELL_* find a tuple's members in a cell with one binary search.
+ * Replaces earlier cells.  Not saved by nhq_save.  Errors: E outside 1..min(N, 65535).
+ */
+nhq_status nhq_index_build_cells(nhq_index *index, int32_t E, void *stream);
+
+/* *E (may be NULL) = the number of entry cells (0 before nhq_index_build_cells) and
+ * cell_of[N] (may be NULL; device or host) = every object's cell. */
+nhq_status nhq_index_cells(const nhq_index *index, int32_t *E, uint32_t *cell_of, void *stream);
+
+/* Number of parameters of the entry model for d dimensions and E cells. */
+int64_t nhq_entry_param_count(int32_t d, int32_t E);
+
+/* Entry-model logits[n][E] of queries[n][d] with the fp16-rounded weights the search reads
+ * (f32 accumulation, the seed pass's arithmetic).  Device pointers.
+ * Errors: d < 1, E outside 1..65535. */
+nhq_status nhq_entry_forward(const float *params, int32_t d, int32_t E, const float *queries,
+                             int64_t n, float *logits, void *stream);
+
+/* Mean softmax cross-entropy over n samples (labels in 0..E-1; other labels contribute
+ * nothing) and its gradient w.r.t. the f32 parameters (grad[0], the scale's entry, is 0),
+ * written to grad[nhq_entry_param_count(d, E)] and *loss.  Device pointers. */
+nhq_status nhq_entry_grad(const float *params, int32_t d, int32_t E, const float *queries,
+                          const int32_t *labels, int64_t n, float *grad, float *loss,
+                          void *stream);
+
+/* Trains params in place with Adam (beta1 0.9, beta2 0.999; the scale is kept) on batches
+ * of `batch` consecutive samples for `epochs` passes.  Device pointers.
+ * Errors: batch outside 1..65536, epochs < 0. */
+nhq_status nhq_entry_train(float *params, int32_t d, int32_t E, const float *queries,
+                           const int32_t *labels, int64_t n, int32_t epochs, int32_t batch,
+                           float lr, void *stream);
+
+/* Training labels: labels[q] = the cell of ids[q][0] (the first result of a search), or -1
+ * where that id is 0xFFFFFFFF.  ids[n][k].  Device pointers.  Errors: no cells. */
+nhq_status nhq_entry_labels(const nhq_index *index, const uint32_t *ids, int32_t k, int64_t n,
+                            int32_t *labels, void *stream);
+
 /* build(vectors, attributes, degree, weights): nhq_index_create + nhq_index_build. */
 nhq_status nhq_build(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
                      int32_t m, int32_t degree, nhq_weights w, const nhq_build_params *params,
@@ -383,17 +452,42 @@ nhq_status nhq_brute_force_noalloc(const float *vectors, const uint32_t *packed_
 
 /*
  * Autotuner (a project addition): times nhq_search on this batch for every launch
- * shape that leaves the results unchanged -- warps per block in {2, 4, 8} and
- * visited-filter sizes 2^b for b from the smallest legal size up to two above
- * it -- with CUDA events (one warm-up and three timed runs each), and writes
- * the fastest into params->warps_per_block / params->hash_bits (the other
- * fields are used as given).  *best_ms (may be NULL) receives its time per
- * call.  Device pointers; the outputs are overwritten by the trial runs.
+ * shape that leaves the results unchanged -- warps per query in {1, 2, 4}, warps per
+ * block in {2, 4, 8} (at least the warps per query) and visited-filter sizes 2^b for b
+ * from the smallest legal size up to two above it -- with CUDA events (one warm-up and
+ * three timed runs each), and writes the fastest into params->warps_per_query /
+ * warps_per_block / hash_bits (the other fields are used as given).  *best_ms (may be
+ * NULL) receives its time per call.  Device pointers; the outputs are overwritten by the
+ * trial runs.
  */
 nhq_status nhq_autotune_search(const nhq_index *index, const float *queries,
                                const uint8_t *query_attributes, int64_t Q, int32_t k, int32_t ef,
                                nhq_search_params *params, uint32_t *ids, float *best_ms,
                                void *stream);
+
+/*
+ * Beam-width tuning (a project addition): the smallest ef of ef_list[0..n_ef)
+ * (ascending, each in k..1024) whose recall against truth[Q][k] reaches `target`, then
+ * the fastest launch shape for that ef (as nhq_autotune_search).  Recall of query q is
+ * |ids_q & truth_q| / |truth_q| with 0xFFFFFFFF entries of truth_q not counted, averaged
+ * over the queries with at least one truth entry (Eq. 3; with the filter-mode ground
+ * truth of nhq_brute_force this is the hybrid recall of Sec. 6.1).  When no ef reaches
+ * the target the largest is taken.  Writes *ef_out, *recall_out (may be NULL) and the
+ * launch-shape fields of params; *best_ms as nhq_autotune_search.  Device pointers.
+ * Errors: n_ef outside 1..64, an ef outside k..1024 or not ascending, target outside
+ * (0, 1].
+ */
+nhq_status nhq_autotune_beam(const nhq_index *index, const float *queries,
+                             const uint8_t *query_attributes, int64_t Q, int32_t k,
+                             const int32_t *ef_list, int32_t n_ef, const uint32_t *truth,
+                             float target, nhq_search_params *params, uint32_t *ids,
+                             int32_t *ef_out, float *recall_out, float *best_ms, void *stream);
+
+/* Mean recall of ids[Q][k] against truth[Q][k_truth] as nhq_autotune_beam computes it
+ * (ids beyond the first k_truth columns are not read; k_truth <= k).  Device pointers;
+ * *recall is written on the host, so the call synchronises `stream`. */
+nhq_status nhq_recall(const uint32_t *ids, int32_t k, const uint32_t *truth, int32_t k_truth,
+                      int64_t Q, float *recall, void *stream);
 
 /*
  * Captured search (a project addition): records one nhq_search call (counter

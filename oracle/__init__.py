@@ -99,6 +99,8 @@ def _L():
             lib.or_round_bf16.argtypes = [C.c_float]
             lib.or_round_e4m3.restype = C.c_float
             lib.or_round_e4m3.argtypes = [C.c_float]
+            lib.or_round_rows.restype = None
+            lib.or_round_rows.argtypes = [P, i64, i32]
             _lib = lib
     return _lib
 
@@ -199,9 +201,12 @@ def filtered_topk(X, A, Qv, QA, k, prec=F64, wildcard=None):
     return ids, dl, P
 
 
-def knn(X, A, K, weights=None, prec=F64, rows=None):
-    """Exact K nearest v != u by (Gamma, id) for every u (or the given rows)."""
+def knn(X, A, K, weights=None, prec=F64, rows=None, vec_round=0):
+    """Exact K nearest v != u by (Gamma, id) for every u (or the given rows).
+    ``vec_round`` (ROUND_BF16 / ROUND_E4M3) computes them on the rounded rows."""
     X, A = _f32(X), _u8(A)
+    if vec_round:
+        X = round_rows(X, vec_round)
     N = X.shape[0]
     if rows is None:
         rp, nr = None, N
@@ -344,7 +349,7 @@ def graph_quality(nbr, knn_ids) -> float:
 SEED_RANDOM, SEED_ATTRIBUTE, SEED_GIVEN, SEED_ATTRIBUTE_NEAR = 0, 1, 2, 3
 
 
-ROUND_NONE, ROUND_BF16, ROUND_E4M3 = 0, 1, 2
+ROUND_NONE, ROUND_BF16, ROUND_E4M3, ROUND_F16 = 0, 1, 2, 3
 
 
 def round_bf16(x) -> float:
@@ -353,6 +358,14 @@ def round_bf16(x) -> float:
 
 def round_e4m3(x) -> float:
     return float(_L().or_round_e4m3(float(x)))
+
+
+def round_rows(X, mode):
+    """A copy of X with every value rounded to bf16 (ROUND_BF16), fp8 e4m3 (ROUND_E4M3) or
+    IEEE binary16 (ROUND_F16)."""
+    Y = np.array(X, dtype=np.float32, order="C", copy=True)
+    _L().or_round_rows(_p(Y), Y.size, int(mode))
+    return Y
 
 
 def search(X, A, nbr, Qv, QA, k, ef, h=1, seed=0, max_iters=1 << 30, weights=None, prec=F32,
@@ -385,6 +398,69 @@ def search(X, A, nbr, Qv, QA, k, ef, h=1, seed=0, max_iters=1 << 30, weights=Non
                    mode, wv, wl, prec, seed_mode, sp, ns, int(vec_round), int(bool(rerank)),
                    _p(ids), _p(g), _p(ch), _p(ndc), _p(ex), _p(st), _wild(wildcard))
     return dict(ids=ids, gamma=g, chi=ch, ndc=ndc, expansions=ex, status=st)
+
+
+# ---------------------------------------------------------------- entry cells
+# Coarse cells for choosing where a search enters the graph (a project addition; the
+# paper draws the seed set B of Alg. 2 at random): E centroids, the objects with ids
+# floor(j N / E); every object belongs to the cell of its nearest centroid.
+def cell_centroids(N, E):
+    """Ids of the E centroid objects, floor(j N / E) for j < E."""
+    return np.array([(j * N) // E for j in range(E)], np.int64)
+
+
+def cells(X, E):
+    """Cell of every object: the centroid j with the smallest (delta, j), delta by Eq. 1 in
+    the canonical f32 form (the exact top-1 of the plain L2 brute force over the E
+    centroid rows)."""
+    X = _f32(X)
+    cid = cell_centroids(X.shape[0], E)
+    zeros = np.zeros((X.shape[0], 1), np.uint8)
+    ids, _, _ = fused_topk(X[cid], zeros[:E], X, zeros, 1, weights=(1.0, 0.0), prec=F32)
+    return ids[:, 0]
+
+
+def nearest_cells(X, E, Qv, T):
+    """The T cells whose centroids are nearest to each query by (delta, j), canonical f32."""
+    X = _f32(X)
+    cid = cell_centroids(X.shape[0], E)
+    Qv = _f32(Qv)
+    ids, _, _ = fused_topk(X[cid], np.zeros((E, 1), np.uint8), Qv,
+                           np.zeros((Qv.shape[0], 1), np.uint8), T, weights=(1.0, 0.0), prec=F32)
+    return ids
+
+
+def cell_seeds(A, QA, cell_of, chosen, ef, seed=0):
+    """Seed rows [nq, 32] (-1 padded) of the cell entry rule for closed queries: P = the
+    objects whose attributes all equal the query's (ascending ids), S = min(ef, 32, |P|);
+    B = the first S members of P in the chosen cells (chosen[q][0] first, ascending ids
+    within a cell), then, while fewer than S, the evenly spaced members P[floor(j |P| / S2)]
+    for j < S2 = S - |B| (repeats allowed; Alg. 2 evaluates an id once); |P| = 0: the
+    first min(ef, 32) distinct ids of splitmix64(seed ^ mix64(q)) mod N (<= 64 draws)."""
+    A, QA = np.asarray(A), np.asarray(QA)
+    N = A.shape[0]
+    out = np.full((QA.shape[0], 32), -1, np.int64)
+    for q in range(QA.shape[0]):
+        P = np.flatnonzero((A == QA[q]).all(axis=1))
+        c = P.size
+        if c == 0:
+            want, row = min(ef, 32), []
+            for x in splitmix64_stream(seed ^ mix64(q), 64):
+                v = x % N
+                if v not in row:
+                    row.append(v)
+                if len(row) == want:
+                    break
+        else:
+            S = min(ef, 32, c)
+            row = []
+            for cell in chosen[q]:
+                row += [int(v) for v in P[cell_of[P] == cell]]
+            row = row[:S]
+            S2 = S - len(row)
+            row += [int(P[(j * c) // S2]) for j in range(S2)]
+        out[q, :len(row)] = row
+    return out
 
 
 # ---------------------------------------------------------------- metrics

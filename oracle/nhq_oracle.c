@@ -173,6 +173,34 @@ float or_round_e4m3(float x)
     return (float)(x < 0 ? -r : r);
 }
 
+/* IEEE binary16: 11 significant bits for magnitudes from 2^-14, subnormals with the
+ * quantum 2^-24 below that, largest finite 65504; rounding to nearest even, and magnitudes
+ * at or above 65520 (halfway to the next binade's first value) round to infinity. */
+float or_round_f16(float x)
+{
+    double a = fabs((double)x);
+    if (a == 0.0 || isnan(x))
+        return x;
+    if (a >= 65520.0)
+        return x < 0 ? -INFINITY : INFINITY;
+    int e;
+    frexp(a, &e);          /* leading bit 2^(e-1) */
+    int lead = e - 1;
+    if (lead < -14)
+        lead = -14;        /* subnormals share the quantum of the smallest normals */
+    double quantum = ldexp(1.0, lead - 10);
+    double r = nearbyint(a / quantum) * quantum;
+    return (float)(x < 0 ? -r : r);
+}
+
+/* Rounds n values in place: mode 1 bf16, mode 2 fp8 e4m3, mode 3 f16 (the functions above). */
+void or_round_rows(float *x, int64_t n, int mode)
+{
+    for (int64_t i = 0; i < n; ++i)
+        x[i] = mode == 1 ? or_round_bf16(x[i]) : mode == 2 ? or_round_e4m3(x[i])
+                                                           : or_round_f16(x[i]);
+}
+
 /* Eq. 6 in double.  Proportional mode: w_v = 1, w_l = delta / m (Sec. 3.2). */
 double or_gamma64(double delta, int chi, int m, int mode, double wv, double wl)
 {
@@ -581,15 +609,15 @@ void or_search(const float *X, const uint8_t *A, int64_t N, int d, int m,
                int64_t *out_ids, double *out_g, int32_t *out_chi,
                int64_t *out_ndc, int64_t *out_exp, int32_t *out_status, int wild)
 {
-    /* vec_round: 0 scores with X itself, 1 with X rounded to bf16, 2 to fp8 e4m3.
+    /* vec_round: 0 scores with X itself, 1 with X rounded to bf16, 2 to fp8 e4m3, 3 to f16.
      * rerank: the final pool is re-scored with X in the chosen precision prec and
      * re-sorted by (Gamma, id) before the first k are returned. */
     const float *Xs = X;
     float *Xr = NULL;
     if (vec_round != 0) {
         Xr = (float *)malloc(sizeof(float) * (size_t)(N > 0 ? N : 1) * (size_t)d);
-        for (int64_t i = 0; i < N * (int64_t)d; ++i)
-            Xr[i] = vec_round == 1 ? or_round_bf16(X[i]) : or_round_e4m3(X[i]);
+        memcpy(Xr, X, sizeof(float) * (size_t)N * (size_t)d);
+        or_round_rows(Xr, N * (int64_t)d, vec_round);
         Xs = Xr;
     }
     pool_t *pool = (pool_t *)malloc(sizeof(pool_t) * (size_t)ef);

@@ -31,6 +31,9 @@ __all__ = [
     "nhq_mlp_train", "MLP_INPUTS", "MLP_HIDDEN", "MLP_PARAMS", "nhq_autotune_search",
     "nhq_search_graph_create", "nhq_search_graph_launch", "nhq_search_graph_free",
     "nhq_merge_topk", "nhq_postfilter", "nhq_knn_nndescent", "nhq_index_build_nsw",
+    "nhq_autotune_beam", "nhq_recall", "SEED_CELL_NEAREST", "SEED_CELL_LEARNED",
+    "ENTRY_HIDDEN", "nhq_index_build_cells", "nhq_index_cells", "nhq_entry_param_count",
+    "nhq_entry_forward", "nhq_entry_grad", "nhq_entry_train", "nhq_entry_labels",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -39,6 +42,8 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libnhq.so")
 W_PROPORTIONAL, W_CONSTANT, W_FILTER, W_HARMONIC = 0, 1, 2, 3
 VEC_F32, VEC_BF16, VEC_FP8E4M3 = 0, 1, 2
 SEED_RANDOM, SEED_ATTRIBUTE, SEED_GIVEN, SEED_ATTRIBUTE_NEAR = 0, 1, 2, 3
+SEED_CELL_NEAREST, SEED_CELL_LEARNED = 4, 5
+ENTRY_HIDDEN = 64
 MLP_INPUTS, MLP_HIDDEN = 8, 64
 MLP_PARAMS = MLP_INPUTS * MLP_HIDDEN + 2 * MLP_HIDDEN + 1
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_ITER_LIMIT, ERR_IO = range(6)
@@ -66,7 +71,9 @@ class _SearchParams(C.Structure):
                 ("vec_dtype", C.c_int32), ("rerank", C.c_int32), ("seed_mode", C.c_int32),
                 ("n_seeds", C.c_int32), ("seeds", C.c_void_p), ("stop_model", C.c_void_p),
                 ("stop_threshold", C.c_float), ("stop_min", C.c_int32),
-                ("stop_every", C.c_int32), ("wildcard", C.c_int32)]
+                ("stop_every", C.c_int32), ("wildcard", C.c_int32),
+                ("warps_per_query", C.c_int32), ("entry_model", C.c_void_p),
+                ("entry_cells", C.c_int32), ("cells_out", C.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -120,6 +127,17 @@ def load_library():
                                             P, P]),
             "nhq_autotune_search": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P,
                                         C.POINTER(C.c_float), P]),
+            "nhq_autotune_beam": (S, [P, P, P, i64, i32, P, i32, P, C.c_float,
+                                      C.POINTER(_SearchParams), P, C.POINTER(i32),
+                                      C.POINTER(C.c_float), C.POINTER(C.c_float), P]),
+            "nhq_recall": (S, [P, i32, P, i32, i64, C.POINTER(C.c_float), P]),
+            "nhq_index_build_cells": (S, [P, i32, P]),
+            "nhq_index_cells": (S, [P, C.POINTER(i32), P, P]),
+            "nhq_entry_param_count": (i64, [i32, i32]),
+            "nhq_entry_forward": (S, [P, i32, i32, P, i64, P, P]),
+            "nhq_entry_grad": (S, [P, i32, i32, P, P, i64, P, P, P]),
+            "nhq_entry_train": (S, [P, i32, i32, P, P, i64, i32, i32, C.c_float, P]),
+            "nhq_entry_labels": (S, [P, P, i32, i64, P, P]),
             "nhq_search_graph_create": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P,
                                             P, P, C.POINTER(P)]),
             "nhq_search_graph_launch": (S, [P, P]),
@@ -373,7 +391,8 @@ def nhq_brute_force_wildcard(index, queries, query_attributes, k, wildcard, ids,
 
 def _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
                    seed_mode=SEED_RANDOM, seeds=None, Q=None, stop_model=None,
-                   stop_threshold=0.5, stop_min=0, stop_every=1, wildcard=0):
+                   stop_threshold=0.5, stop_min=0, stop_every=1, wildcard=0,
+                   warps_per_query=0, entry_model=None, entry_cells=0, cells_out=None):
     """Search parameters; ``seeds`` ([Q][n] uint32, 0xFFFFFFFF = none) selects SEED_GIVEN;
     ``stop_model`` (device f32 [MLP_PARAMS]) turns on the learned early stop."""
     n_seeds, sp = 0, None
@@ -382,22 +401,26 @@ def _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, re
         n_seeds = _shape(seeds)[1]
         sp = _ptr(seeds, np.uint32, (Q, n_seeds), "seeds")
     mp = _ptr(stop_model, np.float32, (MLP_PARAMS,), "stop_model")
+    ep = _ptr(entry_model, np.float32, None, "entry_model")
+    cp = _ptr(cells_out, np.int32, None, "cells_out")
     return _SearchParams(int(seed) & (2**64 - 1), int(h), int(max_iters), int(warps_per_block),
                          int(hash_bits), int(vec_dtype), int(rerank), int(seed_mode),
                          int(n_seeds), sp, mp, float(stop_threshold), int(stop_min),
-                         int(stop_every), int(wildcard))
+                         int(stop_every), int(wildcard), int(warps_per_query), ep,
+                         int(entry_cells), cp)
 
 
 def nhq_search(index, queries, query_attributes, k, ef, ids, dists=None, chi=None, status=None,
                ndc=None, expansions=None, h=1, seed=0, max_iters=0, warps_per_block=0,
                hash_bits=0, vec_dtype=VEC_F32, rerank=0, seed_mode=SEED_RANDOM, seeds=None,
                stop_model=None, stop_threshold=0.5, stop_min=0, stop_every=1,
-               stream=None, wildcard=0) -> None:
+               stream=None, wildcard=0, warps_per_query=0, entry_model=None, entry_cells=0,
+               cells_out=None) -> None:
     Q, d = _shape(queries)
     m = _shape(query_attributes)[1]
     p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
                        seed_mode, seeds, Q, stop_model, stop_threshold, stop_min, stop_every,
-                       wildcard)
+                       wildcard, warps_per_query, entry_model, entry_cells, cells_out)
     _check(load_library().nhq_search(
         index, _ptr(queries, np.float32, (Q, d), "queries"),
         _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, ef, C.byref(p),
@@ -410,11 +433,13 @@ def nhq_search(index, queries, query_attributes, k, ef, ids, dists=None, chi=Non
 def nhq_search_batched(index, queries, query_attributes, k_arr, ef_arr, k_max, ids, dists=None,
                        chi=None, status=None, ndc=None, expansions=None, h=1, seed=0,
                        max_iters=0, warps_per_block=0, hash_bits=0, vec_dtype=VEC_F32, rerank=0,
-                       seed_mode=SEED_RANDOM, seeds=None, stream=None, wildcard=0) -> None:
+                       seed_mode=SEED_RANDOM, seeds=None, stream=None, wildcard=0,
+                       warps_per_query=0, entry_model=None, entry_cells=0) -> None:
     Q, d = _shape(queries)
     m = _shape(query_attributes)[1]
     p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
-                       seed_mode, seeds, Q, wildcard=wildcard)
+                       seed_mode, seeds, Q, wildcard=wildcard, warps_per_query=warps_per_query,
+                       entry_model=entry_model, entry_cells=entry_cells)
     _check(load_library().nhq_search_batched(
         index, _ptr(queries, np.float32, (Q, d), "queries"),
         _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q,
@@ -443,9 +468,11 @@ def nhq_brute_force_noalloc(vectors, packed_attributes, m, queries, packed_query
 
 
 def nhq_autotune_search(index, queries, query_attributes, k, ef, ids, h=1, seed=0,
-                        vec_dtype=VEC_F32, rerank=0, seed_mode=SEED_RANDOM, stream=None):
+                        vec_dtype=VEC_F32, rerank=0, seed_mode=SEED_RANDOM, stream=None,
+                        return_wpq=False):
     """Fastest result-preserving launch shape for this batch; returns
-    (warps_per_block, hash_bits, ms_per_call)."""
+    (warps_per_block, hash_bits, ms_per_call), with warps_per_query first when
+    ``return_wpq``."""
     Q, d = _shape(queries)
     m = _shape(query_attributes)[1]
     p = _search_params(seed, h, 0, 0, 0, vec_dtype, rerank, seed_mode, None, Q)
@@ -454,7 +481,93 @@ def nhq_autotune_search(index, queries, query_attributes, k, ef, ids, h=1, seed=
         index, _ptr(queries, np.float32, (Q, d), "queries"),
         _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, ef, C.byref(p),
         _ptr(ids, np.uint32, (Q, k), "ids"), C.byref(ms), _stream(stream)))
+    if return_wpq:
+        return p.warps_per_query, p.warps_per_block, p.hash_bits, ms.value
     return p.warps_per_block, p.hash_bits, ms.value
+
+
+def nhq_index_build_cells(index, E, stream=None) -> None:
+    _check(load_library().nhq_index_build_cells(index, int(E), _stream(stream)))
+
+
+def nhq_index_cells(index, cell_of=None, stream=None) -> int:
+    """Number of entry cells; fills cell_of [N] (uint32) when given."""
+    E = C.c_int32(0)
+    n = _shape(cell_of)[0] if cell_of is not None else None
+    _check(load_library().nhq_index_cells(index, C.byref(E),
+                                          _ptr(cell_of, np.uint32, (n,) if n else None,
+                                               "cell_of"), _stream(stream)))
+    return E.value
+
+
+def nhq_entry_param_count(d, E) -> int:
+    return int(load_library().nhq_entry_param_count(int(d), int(E)))
+
+
+def nhq_entry_forward(params, E, queries, logits, stream=None) -> None:
+    n, d = _shape(queries)
+    _check(load_library().nhq_entry_forward(
+        _ptr(params, np.float32, (nhq_entry_param_count(d, E),), "params"), d, int(E),
+        _ptr(queries, np.float32, (n, d), "queries"), n,
+        _ptr(logits, np.float32, (n, E), "logits"), _stream(stream)))
+
+
+def nhq_entry_grad(params, E, queries, labels, grad, loss, stream=None) -> None:
+    n, d = _shape(queries)
+    np_ = nhq_entry_param_count(d, E)
+    _check(load_library().nhq_entry_grad(
+        _ptr(params, np.float32, (np_,), "params"), d, int(E),
+        _ptr(queries, np.float32, (n, d), "queries"), _ptr(labels, np.int32, (n,), "labels"), n,
+        _ptr(grad, np.float32, (np_,), "grad"), _ptr(loss, np.float32, (1,), "loss"),
+        _stream(stream)))
+
+
+def nhq_entry_train(params, E, queries, labels, epochs=4, batch=1024, lr=1e-3,
+                    stream=None) -> None:
+    n, d = _shape(queries)
+    _check(load_library().nhq_entry_train(
+        _ptr(params, np.float32, (nhq_entry_param_count(d, E),), "params"), d, int(E),
+        _ptr(queries, np.float32, (n, d), "queries"), _ptr(labels, np.int32, (n,), "labels"), n,
+        int(epochs), int(batch), float(lr), _stream(stream)))
+
+
+def nhq_entry_labels(index, ids, labels, stream=None) -> None:
+    n, k = _shape(ids)
+    _check(load_library().nhq_entry_labels(index, _ptr(ids, np.uint32, (n, k), "ids"), k, n,
+                                           _ptr(labels, np.int32, (n,), "labels"),
+                                           _stream(stream)))
+
+
+def nhq_recall(ids, truth, stream=None) -> float:
+    """Mean recall (Eq. 3) of ids [Q, k] against truth [Q, k_truth] (device uint32,
+    0xFFFFFFFF entries of truth not counted; queries without truth skipped)."""
+    Q, k = _shape(ids)
+    kt = _shape(truth)[1]
+    r = C.c_float(0.0)
+    _check(load_library().nhq_recall(_ptr(ids, np.uint32, (Q, k), "ids"), k,
+                                     _ptr(truth, np.uint32, (Q, kt), "truth"), kt, Q,
+                                     C.byref(r), _stream(stream)))
+    return r.value
+
+
+def nhq_autotune_beam(index, queries, query_attributes, k, ef_list, truth, target, ids, h=1,
+                      seed=0, vec_dtype=VEC_F32, rerank=0, seed_mode=SEED_RANDOM, stream=None):
+    """Smallest ef of ef_list reaching ``target`` recall against truth [Q, k], then the
+    fastest launch shape for it; returns dict(ef, recall, warps_per_query,
+    warps_per_block, hash_bits, ms)."""
+    Q, d = _shape(queries)
+    m = _shape(query_attributes)[1]
+    efs = (C.c_int32 * len(ef_list))(*[int(e) for e in ef_list])
+    p = _search_params(seed, h, 0, 0, 0, vec_dtype, rerank, seed_mode, None, Q)
+    ef, rec, ms = C.c_int32(0), C.c_float(0.0), C.c_float(0.0)
+    _check(load_library().nhq_autotune_beam(
+        index, _ptr(queries, np.float32, (Q, d), "queries"),
+        _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k,
+        C.cast(efs, C.c_void_p), len(ef_list), _ptr(truth, np.uint32, (Q, k), "truth"),
+        float(target), C.byref(p), _ptr(ids, np.uint32, (Q, k), "ids"), C.byref(ef),
+        C.byref(rec), C.byref(ms), _stream(stream)))
+    return dict(ef=ef.value, recall=rec.value, warps_per_query=p.warps_per_query,
+                warps_per_block=p.warps_per_block, hash_bits=p.hash_bits, ms=ms.value)
 
 
 class SearchGraph:
@@ -467,7 +580,8 @@ class SearchGraph:
         self._p = _search_params(kw.get("seed", 0), kw.get("h", 1), kw.get("max_iters", 0),
                                  kw.get("warps_per_block", 0), kw.get("hash_bits", 0),
                                  kw.get("vec_dtype", VEC_F32), kw.get("rerank", 0),
-                                 kw["seed_mode"], None, Q, wildcard=kw.get("wildcard", 0))
+                                 kw["seed_mode"], None, Q, wildcard=kw.get("wildcard", 0),
+                                 warps_per_query=kw.get("warps_per_query", 0))
         out = C.c_void_p()
         _check(load_library().nhq_search_graph_create(
             index, _ptr(queries, np.float32, (Q, d), "queries"),

@@ -3,7 +3,8 @@
 //     split into shards with one graph each, every shard searched for every
 //     query, the lists combined by (Gamma, id));
 //   * post-filter (the "search, then filter by attributes" strategy the paper
-//     compares against): the records with chi = 0, in order.
+//     compares against): the records with chi = 0, in order;
+//   * recall of result lists against ground-truth lists (Eq. 3), for the tuner.
 //
 // One warp per query.  Every shard's list is already sorted by (Gamma, local id),
 // and adding the shard's offset keeps that order, so the merge only compares the
@@ -172,6 +173,49 @@ cudaError_t launch_merge_topk(int P, int64_t Q, int k_in, int k_out, const uint3
     if (e != cudaSuccess)
         return e;
     merge_topk_kernel<<<(unsigned)((Q + wpb - 1) / wpb), 32 * wpb, smem, s>>>(a, hpl);
+    return cudaGetLastError();
+}
+
+// Recall (Eq. 3) of one query per warp: hits = |ids_q[0..kt) & truth_q| over the valid
+// truth entries; acc[0] += hits / valid and acc[1] += 1 for queries with a valid entry.
+// Ids within a row are distinct (search and brute force never repeat one), so counting
+// the found ids that occur in the truth row counts the intersection.
+__global__ void recall_kernel(const uint32_t *__restrict__ ids, int k,
+                              const uint32_t *__restrict__ truth, int kt, int64_t Q,
+                              double *acc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= Q)
+        return;
+    const uint32_t *t = truth + q * kt;
+    const uint32_t *f = ids + q * k;
+    int hits = 0, valid = 0;
+    for (int j = lane; j < kt; j += 32) {
+        const uint32_t v = t[j];
+        if (v == kNone)
+            continue;
+        ++valid;
+        for (int i = 0; i < kt; ++i)
+            hits += f[i] == v ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        hits += __shfl_xor_sync(FULL, hits, o);
+        valid += __shfl_xor_sync(FULL, valid, o);
+    }
+    if (lane == 0 && valid > 0) {
+        atomicAdd(acc, (double)hits / (double)valid);
+        atomicAdd(acc + 1, 1.0);
+    }
+}
+
+cudaError_t launch_recall(const uint32_t *ids, int k, const uint32_t *truth, int kt, int64_t Q,
+                          double *acc, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), s);
+    if (e != cudaSuccess || Q <= 0)
+        return e;
+    const int wpb = 8;
+    recall_kernel<<<(unsigned)((Q + wpb - 1) / wpb), 32 * wpb, 0, s>>>(ids, k, truth, kt, Q, acc);
     return cudaGetLastError();
 }
 

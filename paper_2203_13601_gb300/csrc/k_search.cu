@@ -216,13 +216,16 @@ __device__ __forceinline__ void prefetch_row(const VT *X, int xstride, uint32_t 
 // lanes, two rows per team per pass (8 rows in flight per warp).  CPL > 0: each
 // lane covers at most CPL chunks of a row (EXACT: exactly CPL, no bounds test);
 // CPL == 0: a strided loop for wide rows.
+// With wpq warps per query, warp wig of the group takes the passes wig, wig + wpq, ...
+// (rows 8 wig .. 8 wig + 7 of every 8 wpq).
 template <typename VT, int CPL, bool EXACT>
 __device__ __forceinline__ void eval_dist2(const VT *__restrict__ X, int xstride, const float *qv,
-                                           const uint32_t *cid, float *d2s, int cnt, int lane) {
+                                           const uint32_t *cid, float *d2s, int cnt, int lane,
+                                           int wig = 0, int wpq = 1) {
     constexpr int PC = VecTraits<VT>::kPerChunk;
     const int team = lane / TEAM, tl = lane % TEAM;
     const int nchunk = xstride / PC;
-    for (int base = 0; base < cnt; base += 8) {
+    for (int base = 8 * wig; base < cnt; base += 8 * wpq) {
         const int j0 = base + team, j1 = base + 4 + team;
         const bool h0 = j0 < cnt, h1 = j1 < cnt;
         const VT *r0 = X + (int64_t)cid[h0 ? j0 : 0] * xstride;
@@ -449,8 +452,36 @@ __device__ __forceinline__ void clear_expanded(unsigned long long *pool, int n, 
     __syncwarp();
 }
 
+// Several warps per query (wpq > 1): the group's warp 0 (the leader) runs the search;
+// the others only share the distance passes.  For each batch of candidates the leader
+// publishes the count and the row set in the group's control words and meets the other
+// warps at the group's named barrier (1 + group index, wpq warps); all warps evaluate
+// their passes and meet again, after which the leader reads every squared distance.  A
+// negative count sends the other warps home.
+__device__ __forceinline__ void group_bar(int grp, int wpq) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(32 * wpq) : "memory");
+}
+
+template <typename VT, int CPL, bool EXACT>
+__device__ __forceinline__ void group_eval(const VT *X, int xstride, const float *qv,
+                                           const uint32_t *cid, float *d2s, int cnt, int lane,
+                                           int wpq, int grp, volatile int *ctl, int rows_f32) {
+    if (wpq == 1) {
+        eval_dist2<VT, CPL, EXACT>(X, xstride, qv, cid, d2s, cnt, lane);
+        return;
+    }
+    if (lane == 0) {
+        ctl[0] = cnt;
+        ctl[1] = rows_f32;
+    }
+    __syncwarp();
+    group_bar(grp, wpq);
+    eval_dist2<VT, CPL, EXACT>(X, xstride, qv, cid, d2s, cnt, lane, 0, wpq);
+    group_bar(grp, wpq);
+}
+
 struct WarpLayout {
-    size_t pool, sorted, d2s, cid, cchi, hash, qv, total;
+    size_t pool, sorted, d2s, cid, cchi, hash, qv, ctl, total;
 };
 
 __host__ __device__ inline WarpLayout warp_layout(int ef_cap, int hash_bits, int xstride) {
@@ -473,6 +504,8 @@ __host__ __device__ inline WarpLayout warp_layout(int ef_cap, int hash_bits, int
     L.qv = o;
     o += sizeof(float) * xstride;
     o = (o + 15) & ~(size_t)15;
+    L.ctl = o;
+    o += 16;
     L.total = o;
     return L;
 }
@@ -482,8 +515,9 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
                                                         int ef_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int wpq = a.wpq, grp = wib / wpq, wig = wib % wpq;
     const WarpLayout L = warp_layout(ef_cap, a.hash_bits, a.xstride);
-    unsigned char *base = smem + wib * L.total;
+    unsigned char *base = smem + grp * L.total;
     unsigned long long *pool = reinterpret_cast<unsigned long long *>(base + L.pool);
     unsigned long long *sorted32 = reinterpret_cast<unsigned long long *>(base + L.sorted);
     float *d2s = reinterpret_cast<float *>(base + L.d2s);
@@ -491,15 +525,30 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
     int *cchi = reinterpret_cast<int *>(base + L.cchi);
     uint32_t *hash = reinterpret_cast<uint32_t *>(base + L.hash);
     float *qv = reinterpret_cast<float *>(base + L.qv);
+    volatile int *ctl = reinterpret_cast<volatile int *>(base + L.ctl);
     const int H = 1 << a.hash_bits;
     const int R = a.R;
     const uint32_t alo = a.w.lo;
     // the learned stop's fp16 weights, staged once per block after the warps' areas
-    __half *w16 = reinterpret_cast<__half *>(smem + (blockDim.x >> 5) * L.total);
+    __half *w16 = reinterpret_cast<__half *>(smem + ((blockDim.x >> 5) / wpq) * L.total);
     if (a.stop_w16 != nullptr) {
         for (int i = threadIdx.x; i < NHQ_MLP_PARAMS; i += blockDim.x)
             w16[i] = a.stop_w16[i];
         __syncthreads();
+    }
+    if (wig != 0) {  // a helper warp of the group: distance passes only
+        for (;;) {
+            group_bar(grp, wpq);
+            const int cnt = ctl[0];
+            if (cnt < 0)
+                break;
+            if (ctl[1])
+                eval_dist2<float, 0, false>(a.X, a.xstride, qv, cid, d2s, cnt, lane, wig, wpq);
+            else
+                eval_dist2<VT, CPL, EXACT>(Xs, a.xstride, qv, cid, d2s, cnt, lane, wig, wpq);
+            group_bar(grp, wpq);
+        }
+        return;
     }
 
     for (;;) {
@@ -548,7 +597,8 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
             hcount += cnt;
             ndc += cnt;
             if (cnt > 0) {
-                eval_dist2<VT, CPL, EXACT>(Xs, a.xstride, qv, cid, d2s, cnt, lane);
+                group_eval<VT, CPL, EXACT>(Xs, a.xstride, qv, cid, d2s, cnt, lane, wpq, grp,
+                                           ctl, 0);
                 merge_round(pool, n, ef, candidate_key(lane, cnt, d2s, cid, cchi, a.w), sorted32,
                             lane);
             }
@@ -579,7 +629,8 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
             hcount += cnt;
             ndc += cnt;
             if (cnt > 0) {
-                eval_dist2<VT, CPL, EXACT>(Xs, a.xstride, qv, cid, d2s, cnt, lane);
+                group_eval<VT, CPL, EXACT>(Xs, a.xstride, qv, cid, d2s, cnt, lane, wpq, grp,
+                                           ctl, 0);
                 merge_round(pool, n, ef, candidate_key(lane, cnt, d2s, cid, cchi, a.w), sorted32,
                             lane);
             }
@@ -712,7 +763,8 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
             ndc += cnt;
             unsigned long long k0 = kInfKey, k1 = kInfKey;
             if (cnt > 0) {
-                eval_dist2<VT, CPL, EXACT>(Xs, a.xstride, qv, cid, d2s, cnt, lane);
+                group_eval<VT, CPL, EXACT>(Xs, a.xstride, qv, cid, d2s, cnt, lane, wpq, grp,
+                                           ctl, 0);
                 k0 = filter_key(candidate_key(lane, cnt, d2s, cid, cchi, a.w), pool, n, ef,
                                 rebuilt);
                 if (TWO)
@@ -773,7 +825,8 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
                     cchi[j] = chi_packed(a.attr[id], qa, ahi, alo);
                 }
                 __syncwarp();
-                eval_dist2<float, 0, false>(a.X, a.xstride, qv, cid, d2s, cb, lane);
+                group_eval<float, 0, false>(a.X, a.xstride, qv, cid, d2s, cb, lane, wpq,
+                                            grp, ctl, 1);
                 for (int j = lane; j < cb; j += 32)
                     pool[b0 + j] = candidate_key(j, cb, d2s, cid, cchi, a.w);
                 __syncwarp();
@@ -831,6 +884,12 @@ __global__ void __launch_bounds__(256, 4) search_kernel(SearchArgs a, const VT *
         }
         __syncwarp();
     }
+    if (wpq > 1) {  // no query left: release the helper warps
+        if (lane == 0)
+            ctl[0] = -1;
+        __syncwarp();
+        group_bar(grp, wpq);
+    }
 }
 
 // the smallest visited filter the rebuild rule allows (a rebuilt filter holds at most
@@ -860,7 +919,8 @@ cudaError_t launch_variant(const SearchArgs &a, const VT *X, int ef_cap, int wpb
     if (per_sm < 1)
         per_sm = 1;
     int64_t blocks = (int64_t)per_sm * sm_count;
-    const int64_t need = (a.nq + wpb - 1) / wpb;
+    const int64_t groups = wpb / a.wpq;  // queries in flight per block
+    const int64_t need = (a.nq + groups - 1) / groups;
     if (blocks > need)
         blocks = need;
     kfn<<<(unsigned)blocks, 32 * wpb, smem, s>>>(a, X, ef_cap);
@@ -910,12 +970,19 @@ cudaError_t launch_search(SearchArgs a, void *scratch, int sm_count, size_t smem
     if ((1 << a.hash_bits) < 2 * (ef_cap + a.R) + 64)
         return cudaErrorInvalidValue;
     const WarpLayout L = warp_layout(ef_cap, a.hash_bits, a.xstride);
-    int wpb = a.warps_per_block > 0 ? a.warps_per_block : 8;
-    while (wpb > 1 && L.total * wpb + 2048 > smem_optin)
-        wpb >>= 1;
-    if (L.total * wpb + 2048 > smem_optin)
+    if (a.wpq < 1)
+        a.wpq = 1;
+    if (a.wpq != 1 && a.wpq != 2 && a.wpq != 4)
         return cudaErrorInvalidValue;
-    const size_t smem = L.total * wpb + (a.stop_w16 != nullptr ? 2 * 656 : 0);
+    int wpb = a.warps_per_block > 0 ? a.warps_per_block : 8;
+    if (wpb < a.wpq)
+        wpb = a.wpq;
+    // one shared-memory area per group of wpq warps
+    while (wpb > a.wpq && L.total * (wpb / a.wpq) + 2048 > smem_optin)
+        wpb >>= 1;
+    if (L.total * (wpb / a.wpq) + 2048 > smem_optin || wpb % a.wpq != 0)
+        return cudaErrorInvalidValue;
+    const size_t smem = L.total * (wpb / a.wpq) + (a.stop_w16 != nullptr ? 2 * 656 : 0);
     if (a.vec_dtype == NHQ_VEC_BF16)
         return launch_dtype<__nv_bfloat16>(a, a.Xh, ef_cap, wpb, smem, sm_count, s);
     if (a.vec_dtype == NHQ_VEC_FP8E4M3)

@@ -295,6 +295,10 @@ void nhq_free(nhq_index *ix) {
     cudaFree(ix->normk);
     cudaFree(ix->attr_sorted);
     cudaFree(ix->id_sorted);
+    cudaFree(ix->cent);
+    cudaFree(ix->cell);
+    cudaFree(ix->cell_key);
+    cudaFree(ix->cell_id);
     cudaFree(ix->scratch);
     delete ix;
 }
@@ -678,6 +682,186 @@ nhq_status nhq_index_build_nsw(nhq_index *ix, int32_t degree, int32_t L, int32_t
     return NHQ_OK;
 }
 
+nhq_status nhq_index_build_cells(nhq_index *ix, int32_t E, void *stream) {
+    if (ix == nullptr)
+        return fail(NHQ_ERR_ARG, "index is NULL");
+    if (E < 1 || (int64_t)E > ix->N || E > 65535)
+        return fail(NHQ_ERR_ARG, "E must be in 1..min(N, 65535) (got %d)", E);
+    cudaStream_t s = as_stream(stream);
+    CK(cudaStreamSynchronize(s));
+    cudaFree(ix->cent);
+    cudaFree(ix->cell);
+    cudaFree(ix->cell_key);
+    cudaFree(ix->cell_id);
+    ix->cent = nullptr;
+    ix->cell = ix->cell_id = nullptr;
+    ix->cell_key = nullptr;
+    ix->E = 0;
+    CK(cudaMalloc(&ix->cent, sizeof(float) * (size_t)E * ix->xstride));
+    CK(cudaMalloc(&ix->cell, sizeof(uint32_t) * (size_t)ix->N));
+    CK(cudaMalloc(&ix->cell_key, sizeof(unsigned long long) * (size_t)ix->N));
+    CK(cudaMalloc(&ix->cell_id, sizeof(uint32_t) * (size_t)ix->N));
+    CKS(ensure_attribute_order(ix, s));
+    // the centroid rows and their attribute words, then every object's nearest centroid
+    // (Gamma = 1 * delta + 0 * chi: plain L2, ties to the smaller centroid index)
+    TopkArgs a;
+    a.X = ix->cent;
+    a.xstride = ix->xstride;
+    a.d = ix->d;
+    a.N = E;
+    a.Q = ix->X;
+    a.qstride = ix->xstride;
+    a.qattr = ix->attr;
+    a.qhi = nullptr;
+    a.nq = ix->N;
+    a.k = 1;
+    a.exclude_self = 0;
+    nhq_weights l2{NHQ_W_CONSTANT, 1.f, 0.f};
+    a.w = make_fusion(l2, ix->layout);
+    a.ids = ix->cell;
+    a.dists = nullptr;
+    a.chi = nullptr;
+    const size_t cattr_bytes = ((sizeof(uint32_t) * (size_t)E) + 255) & ~(size_t)255;
+    CKS(scratch(ix, cattr_bytes + topk_scratch_bytes(a, ix->sm_count)));
+    uint32_t *cattr = reinterpret_cast<uint32_t *>(ix->scratch);
+    a.attr = cattr;
+    CK(launch_gather_centroids(ix->X, ix->xstride, ix->N, E, ix->attr, ix->cent, cattr, s));
+    CK(launch_topk(a, (char *)ix->scratch + cattr_bytes, ix->scratch_bytes - cattr_bytes,
+                   ix->sm_count, s));
+    CKS(scratch(ix, cell_sort_scratch_bytes(ix->N)));
+    CK(launch_cell_sort(ix->attr, ix->cell, ix->N, ix->cell_key, ix->cell_id, ix->scratch,
+                        ix->scratch_bytes, s));
+    ix->E = E;
+    return NHQ_OK;
+}
+
+nhq_status nhq_index_cells(const nhq_index *ix, int32_t *E, uint32_t *cell_of, void *stream) {
+    if (ix == nullptr)
+        return fail(NHQ_ERR_ARG, "index is NULL");
+    if (E)
+        *E = ix->E;
+    if (cell_of != nullptr) {
+        if (ix->E == 0)
+            return fail(NHQ_ERR_ARG, "the index has no entry cells (nhq_index_build_cells)");
+        cudaStream_t s = as_stream(stream);
+        CK(cudaMemcpyAsync(cell_of, ix->cell, sizeof(uint32_t) * (size_t)ix->N, cudaMemcpyDefault,
+                           s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return NHQ_OK;
+}
+
+int64_t nhq_entry_param_count(int32_t d, int32_t E) {
+    if (d < 1 || E < 1)
+        return 0;
+    return entry_param_count(d, E);
+}
+
+static nhq_status check_entry(const float *params, int32_t d, int32_t E, const float *queries,
+                              int64_t n) {
+    if (d < 1 || d > 16384 || E < 1 || E > 65535 || n < 0)
+        return fail(NHQ_ERR_ARG, "need d in 1..16384, E in 1..65535, n >= 0");
+    if (!is_device_ptr(params) || (n > 0 && !is_device_ptr(queries)))
+        return fail(NHQ_ERR_ARG, "the entry-model calls take device pointers");
+    return NHQ_OK;
+}
+
+nhq_status nhq_entry_forward(const float *params, int32_t d, int32_t E, const float *queries,
+                             int64_t n, float *logits, void *stream) {
+    CKS(check_entry(params, d, E, queries, n));
+    if (n > 0 && !is_device_ptr(logits))
+        return fail(NHQ_ERR_ARG, "logits must be device memory");
+    cudaStream_t s = as_stream(stream);
+    const int64_t np = entry_param_count(d, E);
+    __half *w16 = nullptr;
+    CK(cudaMallocAsync(&w16, sizeof(__half) * (size_t)np, s));
+    cudaError_t e = launch_entry_to_half(params, np, w16, s);
+    if (e == cudaSuccess)
+        e = launch_entry_forward(w16, params, d, E, queries, n, logits, s);
+    cudaFreeAsync(w16, s);
+    if (e != cudaSuccess)
+        return fail_cuda(e, "nhq_entry_forward");
+    return NHQ_OK;
+}
+
+nhq_status nhq_entry_grad(const float *params, int32_t d, int32_t E, const float *queries,
+                          const int32_t *labels, int64_t n, float *grad, float *loss,
+                          void *stream) {
+    CKS(check_entry(params, d, E, queries, n));
+    if (!is_device_ptr(grad) || !is_device_ptr(loss) || (n > 0 && !is_device_ptr(labels)))
+        return fail(NHQ_ERR_ARG, "the entry-model calls take device pointers");
+    cudaStream_t s = as_stream(stream);
+    const int64_t np = entry_param_count(d, E);
+    CK(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)np, s));
+    CK(cudaMemsetAsync(loss, 0, sizeof(float), s));
+    if (n == 0)
+        return NHQ_OK;
+    const int B = 2048;
+    void *work = nullptr;
+    CK(cudaMallocAsync(&work, entry_train_chunk_bytes(B, E), s));
+    cudaError_t e = entry_grad_accumulate(params, d, E, queries, labels, n, n, B, grad, loss,
+                                          work, s);
+    cudaFreeAsync(work, s);
+    if (e != cudaSuccess)
+        return fail_cuda(e, "nhq_entry_grad");
+    return NHQ_OK;
+}
+
+nhq_status nhq_entry_train(float *params, int32_t d, int32_t E, const float *queries,
+                           const int32_t *labels, int64_t n, int32_t epochs, int32_t batch,
+                           float lr, void *stream) {
+    CKS(check_entry(params, d, E, queries, n));
+    if (batch < 1 || batch > 65536 || epochs < 0)
+        return fail(NHQ_ERR_ARG, "batch must be in 1..65536 and epochs >= 0");
+    if (n > 0 && !is_device_ptr(labels))
+        return fail(NHQ_ERR_ARG, "the entry-model calls take device pointers");
+    if (n == 0 || epochs == 0)
+        return NHQ_OK;
+    cudaStream_t s = as_stream(stream);
+    const int64_t np = entry_param_count(d, E);
+    const int B = batch < 2048 ? batch : 2048;  // chunk of one gradient pass
+    float *buf = nullptr;  // gradient, first and second moments, loss
+    void *work = nullptr;
+    CK(cudaMallocAsync(&buf, sizeof(float) * (size_t)(3 * np + 1), s));
+    cudaError_t e = cudaMallocAsync(&work, entry_train_chunk_bytes(B, E), s);
+    float *g = buf, *m = buf + np, *v = m + np, *loss = v + np;
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(m, 0, sizeof(float) * (size_t)(2 * np), s);
+    int t = 0;
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+        for (int64_t b = 0; b < n && e == cudaSuccess; b += batch) {
+            const int64_t nb = n - b < batch ? n - b : batch;
+            e = cudaMemsetAsync(g, 0, sizeof(float) * (size_t)(np + 1), s);
+            if (e == cudaSuccess)
+                e = entry_grad_accumulate(params, d, E, queries + b * d, labels + b, nb, nb, B,
+                                          g, loss, work, s);
+            ++t;
+            const float c1 = 1.f / (1.f - powf(0.9f, (float)t));
+            const float c2 = 1.f / (1.f - powf(0.999f, (float)t));
+            if (e == cudaSuccess)
+                e = launch_entry_adam(params, g, m, v, np, lr, c1, c2, s);
+        }
+    }
+    if (work)
+        cudaFreeAsync(work, s);
+    cudaFreeAsync(buf, s);
+    if (e != cudaSuccess)
+        return fail_cuda(e, "nhq_entry_train");
+    return NHQ_OK;
+}
+
+nhq_status nhq_entry_labels(const nhq_index *ix, const uint32_t *ids, int32_t k, int64_t n,
+                            int32_t *labels, void *stream) {
+    if (ix == nullptr || ix->E == 0)
+        return fail(NHQ_ERR_ARG, "the index has no entry cells (nhq_index_build_cells)");
+    if (k < 1 || n < 0)
+        return fail(NHQ_ERR_ARG, "need k >= 1, n >= 0");
+    if (n > 0 && (!is_device_ptr(ids) || !is_device_ptr(labels)))
+        return fail(NHQ_ERR_ARG, "nhq_entry_labels takes device pointers");
+    CK(launch_entry_labels(ids, k, n, ix->cell, ix->N, labels, as_stream(stream)));
+    return NHQ_OK;
+}
+
 nhq_status nhq_build(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
                      int32_t m, int32_t degree, nhq_weights w, const nhq_build_params *params,
                      void *stream, nhq_index **out) {
@@ -858,8 +1042,31 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         return fail(NHQ_ERR_ARG, "wildcard must be 0 or 1 (got %d)", P.wildcard);
     if (P.warps_per_block < 0 || P.warps_per_block > 8)
         return fail(NHQ_ERR_ARG, "warps_per_block must be in 0..8");
-    if (P.seed_mode < NHQ_SEED_RANDOM || P.seed_mode > NHQ_SEED_ATTRIBUTE_NEAR)
+    if (P.warps_per_query == 0)
+        P.warps_per_query = 1;
+    if (P.warps_per_query != 1 && P.warps_per_query != 2 && P.warps_per_query != 4)
+        return fail(NHQ_ERR_ARG, "warps_per_query must be 0, 1, 2 or 4 (got %d)",
+                    P.warps_per_query);
+    if (P.warps_per_block != 0 && P.warps_per_block % P.warps_per_query != 0)
+        return fail(NHQ_ERR_ARG, "warps_per_block must be a multiple of warps_per_query");
+    if (P.seed_mode < NHQ_SEED_RANDOM || P.seed_mode > NHQ_SEED_CELL_LEARNED)
         return fail(NHQ_ERR_ARG, "unknown seed_mode %d", P.seed_mode);
+    const bool cell_mode =
+        P.seed_mode == NHQ_SEED_CELL_NEAREST || P.seed_mode == NHQ_SEED_CELL_LEARNED;
+    if (cell_mode) {
+        if (ix->E == 0)
+            return fail(NHQ_ERR_ARG, "seed modes 4/5 need entry cells (nhq_index_build_cells)");
+        if (P.entry_cells == 0)
+            P.entry_cells = 2;
+        if (P.entry_cells < 1 || P.entry_cells > 8 || P.entry_cells > ix->E)
+            return fail(NHQ_ERR_ARG, "entry_cells must be in 1..min(8, E)");
+        if (P.wildcard != 0)
+            return fail(NHQ_ERR_ARG, "seed modes 4/5 take closed queries (wildcard = 0)");
+        if (P.seed_mode == NHQ_SEED_CELL_LEARNED && !is_device_ptr(P.entry_model))
+            return fail(NHQ_ERR_ARG, "NHQ_SEED_CELL_LEARNED needs entry_model in device memory");
+        if (P.cells_out != nullptr && !is_device_ptr(P.cells_out))
+            return fail(NHQ_ERR_ARG, "cells_out must be device memory");
+    }
     if (P.seed_mode == NHQ_SEED_GIVEN && (P.seeds == nullptr || P.n_seeds < 1 || P.n_seeds > 64))
         return fail(NHQ_ERR_ARG, "NHQ_SEED_GIVEN needs seeds and n_seeds in 1..64");
     const bool use_model = P.stop_model != nullptr && trace == nullptr;
@@ -873,7 +1080,7 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         if (!(P.stop_threshold > 0.f && P.stop_threshold < 1.f))
             return fail(NHQ_ERR_ARG, "stop_threshold must be a probability in (0, 1)");
     }
-    if (P.seed_mode == NHQ_SEED_ATTRIBUTE || P.seed_mode == NHQ_SEED_ATTRIBUTE_NEAR)
+    if (P.seed_mode == NHQ_SEED_ATTRIBUTE || P.seed_mode == NHQ_SEED_ATTRIBUTE_NEAR || cell_mode)
         CKS(ensure_attribute_order(ix, s));
     if (P.vec_dtype == NHQ_VEC_BF16 && ix->Xh == nullptr) {
         CK(cudaMalloc(&ix->Xh, sizeof(__nv_bfloat16) * (size_t)ix->N * ix->xstride));
@@ -933,11 +1140,17 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     a.expansions = (int32_t *)st.dev(ix_);
     a.warps_per_block = P.warps_per_block;
     a.hash_bits = P.hash_bits;
+    a.wpq = P.warps_per_query;
     // scratch: work counter and seeds | fp16 model | trace counter, hashes, final hashes
     const size_t off_w16 = (search_scratch_bytes(Q) + 255) & ~(size_t)255;
     const size_t off_tr = off_w16 + 2048;
     const size_t tr_bytes = trace ? 256 + sizeof(unsigned long long) * ((size_t)trace->cap + Q) : 0;
-    CKS(scratch(ix, off_tr + tr_bytes));
+    // the fp16 copy of the entry model after the trace records
+    const size_t off_entry = (off_tr + tr_bytes + 255) & ~(size_t)255;
+    const size_t entry_bytes = P.seed_mode == NHQ_SEED_CELL_LEARNED
+                                   ? sizeof(__half) * (size_t)entry_param_count(ix->d, ix->E)
+                                   : 0;
+    CKS(scratch(ix, off_entry + entry_bytes));
     a.stop_w16 = nullptr;
     a.stop_every = 0;
     a.stop_min = P.stop_min;
@@ -971,14 +1184,25 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     if (P.seed_mode == NHQ_SEED_GIVEN) {
         a.seeds = (const uint32_t *)st.dev(isd);
         a.n_seeds = P.n_seeds;
-    } else if (P.seed_mode == NHQ_SEED_ATTRIBUTE || P.seed_mode == NHQ_SEED_ATTRIBUTE_NEAR) {
+    } else if (P.seed_mode == NHQ_SEED_ATTRIBUTE || P.seed_mode == NHQ_SEED_ATTRIBUTE_NEAR ||
+               cell_mode) {
         uint32_t *sd = reinterpret_cast<uint32_t *>((char *)ix->scratch + 256);
         uint32_t *order = sd + (size_t)32 * Q;
         uint8_t *bucket = reinterpret_cast<uint8_t *>(order + Q);
-        if (P.seed_mode == NHQ_SEED_ATTRIBUTE)
+        if (P.seed_mode == NHQ_SEED_ATTRIBUTE) {
             CK(launch_attribute_seeds(a, ix->attr_sorted, ix->id_sorted, sd, bucket, s));
-        else
+        } else if (P.seed_mode == NHQ_SEED_ATTRIBUTE_NEAR) {
             CK(launch_attribute_near_seeds(a, ix->attr_sorted, ix->id_sorted, sd, bucket, s));
+        } else {
+            __half *ew16 = nullptr;
+            if (P.seed_mode == NHQ_SEED_CELL_LEARNED) {
+                ew16 = reinterpret_cast<__half *>((char *)ix->scratch + off_entry);
+                CK(launch_entry_to_half(P.entry_model, entry_param_count(ix->d, ix->E), ew16, s));
+            }
+            CK(launch_cell_seeds(a, ix->attr_sorted, ix->id_sorted, ix->cell_key, ix->cell_id,
+                                 ix->E, P.entry_cells, ix->cent, ew16, P.entry_model, P.cells_out,
+                                 sd, bucket, ix->sm_count, ix->smem_optin, s));
+        }
         CK(launch_query_order(bucket, Q, order, s));
         a.seeds = sd;
         a.n_seeds = 32;
@@ -1078,34 +1302,39 @@ nhq_status nhq_autotune_search(const nhq_index *ix, const float *queries,
     nhq_search_params best = *params;
     float best_t = 1e30f;
     bool any = false;
-    const int wpbs[3] = {2, 4, 8};
-    for (int wi = 0; wi < 3; ++wi) {
-        for (int b = bmin; b <= bmin + 2; ++b) {
-            nhq_search_params P = *params;
-            P.warps_per_block = wpbs[wi];
-            P.hash_bits = b;
-            nhq_status st = nhq_search(ix, queries, query_attributes, Q, k, ef, &P, ids, nullptr,
-                                       nullptr, nullptr, nullptr, nullptr, stream);
-            if (st == NHQ_ERR_ARG)
-                continue;  // this shape does not fit shared memory
-            if (st != NHQ_OK) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return st;
-            }
-            CK(cudaEventRecord(e0, s));
-            for (int r = 0; r < 3; ++r)
-                nhq_search(ix, queries, query_attributes, Q, k, ef, &P, ids, nullptr, nullptr,
-                           nullptr, nullptr, nullptr, stream);
-            CK(cudaEventRecord(e1, s));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            ms /= 3.f;
-            if (ms < best_t) {
-                best_t = ms;
-                best = P;
-                any = true;
+    const int wpbs[3] = {2, 4, 8}, wpqs[3] = {1, 2, 4};
+    for (int qi = 0; qi < 3; ++qi) {
+        for (int wi = 0; wi < 3; ++wi) {
+            if (wpbs[wi] < wpqs[qi])
+                continue;
+            for (int b = bmin; b <= bmin + 2; ++b) {
+                nhq_search_params P = *params;
+                P.warps_per_query = wpqs[qi];
+                P.warps_per_block = wpbs[wi];
+                P.hash_bits = b;
+                nhq_status st = nhq_search(ix, queries, query_attributes, Q, k, ef, &P, ids,
+                                           nullptr, nullptr, nullptr, nullptr, nullptr, stream);
+                if (st == NHQ_ERR_ARG)
+                    continue;  // this shape does not fit shared memory
+                if (st != NHQ_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return st;
+                }
+                CK(cudaEventRecord(e0, s));
+                for (int r = 0; r < 3; ++r)
+                    nhq_search(ix, queries, query_attributes, Q, k, ef, &P, ids, nullptr,
+                               nullptr, nullptr, nullptr, nullptr, stream);
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                ms /= 3.f;
+                if (ms < best_t) {
+                    best_t = ms;
+                    best = P;
+                    any = true;
+                }
             }
         }
     }
@@ -1113,11 +1342,69 @@ nhq_status nhq_autotune_search(const nhq_index *ix, const float *queries,
     cudaEventDestroy(e1);
     if (!any)
         return fail(NHQ_ERR_ARG, "no launch shape fits shared memory for ef = %d", ef);
+    params->warps_per_query = best.warps_per_query;
     params->warps_per_block = best.warps_per_block;
     params->hash_bits = best.hash_bits;
     if (best_ms)
         *best_ms = best_t;
     return NHQ_OK;
+}
+
+nhq_status nhq_recall(const uint32_t *ids, int32_t k, const uint32_t *truth, int32_t k_truth,
+                      int64_t Q, float *recall, void *stream) {
+    if (ids == nullptr || truth == nullptr || recall == nullptr || Q < 0 || k < 1 ||
+        k_truth < 1 || k_truth > k)
+        return fail(NHQ_ERR_ARG, "nhq_recall: need ids, truth, recall, Q >= 0, 1 <= k_truth <= k");
+    if (!is_device_ptr(ids) || !is_device_ptr(truth))
+        return fail(NHQ_ERR_ARG, "nhq_recall takes device ids and truth");
+    cudaStream_t s = as_stream(stream);
+    double *acc = nullptr;
+    CK(cudaMallocAsync(&acc, 2 * sizeof(double), s));
+    double h[2] = {0.0, 0.0};
+    cudaError_t e = launch_recall(ids, k, truth, k_truth, Q, acc, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(acc, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return fail_cuda(e, "nhq_recall");
+    *recall = h[1] > 0.0 ? (float)(h[0] / h[1]) : 0.f;
+    return NHQ_OK;
+}
+
+nhq_status nhq_autotune_beam(const nhq_index *ix, const float *queries,
+                             const uint8_t *query_attributes, int64_t Q, int32_t k,
+                             const int32_t *ef_list, int32_t n_ef, const uint32_t *truth,
+                             float target, nhq_search_params *params, uint32_t *ids,
+                             int32_t *ef_out, float *recall_out, float *best_ms, void *stream) {
+    if (ix == nullptr || params == nullptr || ids == nullptr || truth == nullptr ||
+        ef_list == nullptr || ef_out == nullptr || Q < 1)
+        return fail(NHQ_ERR_ARG, "index, params, ids, truth, ef_list, ef_out and Q >= 1 are "
+                                 "required");
+    if (n_ef < 1 || n_ef > 64)
+        return fail(NHQ_ERR_ARG, "n_ef must be in 1..64");
+    if (!(target > 0.f && target <= 1.f))
+        return fail(NHQ_ERR_ARG, "target must be in (0, 1]");
+    for (int i = 0; i < n_ef; ++i)
+        if (ef_list[i] < k || ef_list[i] > kMaxEf || (i > 0 && ef_list[i] <= ef_list[i - 1]))
+            return fail(NHQ_ERR_ARG, "ef_list must ascend within k..1024");
+    int chosen = ef_list[n_ef - 1];
+    float rec = 0.f;
+    for (int i = 0; i < n_ef; ++i) {
+        CKS(nhq_search(ix, queries, query_attributes, Q, k, ef_list[i], params, ids, nullptr,
+                       nullptr, nullptr, nullptr, nullptr, stream));
+        CKS(nhq_recall(ids, k, truth, k, Q, &rec, stream));
+        if (rec >= target || i == n_ef - 1) {
+            chosen = ef_list[i];
+            break;
+        }
+    }
+    *ef_out = chosen;
+    if (recall_out)
+        *recall_out = rec;
+    return nhq_autotune_search(ix, queries, query_attributes, Q, k, chosen, params, ids, best_ms,
+                               stream);
 }
 
 }  // extern "C"

@@ -169,6 +169,13 @@ struct nhq_index {
     int kpad = 0;                 // d rounded up to a multiple of 64
     uint32_t *attr_sorted = nullptr;  // [N] packed attributes, ascending (stable radix sort)
     uint32_t *id_sorted = nullptr;    // [N] object ids in that order
+    // entry cells (nhq_index_build_cells): E centroid rows, the cell of every object and
+    // the objects sorted by (attribute word, cell)
+    int E = 0;
+    float *cent = nullptr;                   // [E][xstride]
+    uint32_t *cell = nullptr;                // [N]
+    unsigned long long *cell_key = nullptr;  // [N] (attribute word << 16 | cell), ascending
+    uint32_t *cell_id = nullptr;             // [N] object ids in that order
     // scratch arena (grown on demand, owned by the index)
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -304,6 +311,7 @@ struct SearchArgs {
     unsigned long long *counter;  // scratch work counter (zeroed by the launcher)
     int warps_per_block;
     int hash_bits;
+    int wpq;  // warps per query (1, 2 or 4): the group shares each expansion's distance passes
 };
 size_t search_scratch_bytes(int64_t nq);
 cudaError_t launch_attribute_sort(const uint32_t *attr, int64_t N, uint32_t *attr_sorted,
@@ -359,5 +367,34 @@ cudaError_t launch_merge_topk(int P, int64_t Q, int k_in, int k_out, const uint3
                               cudaStream_t s);
 cudaError_t launch_search(SearchArgs a, void *scratch, int sm_count, size_t smem_optin,
                           cudaStream_t s);
+// k_entry.cu -- entry cells and the entry model
+int64_t entry_param_count(int d, int E);
+cudaError_t launch_gather_centroids(const float *X, int xstride, int64_t N, int E,
+                                    const uint32_t *attr, float *cent, uint32_t *cattr,
+                                    cudaStream_t s);
+size_t cell_sort_scratch_bytes(int64_t N);
+cudaError_t launch_cell_sort(const uint32_t *attr, const uint32_t *cell, int64_t N,
+                             unsigned long long *key_sorted, uint32_t *id_sorted, void *scratch,
+                             size_t scratch_bytes, cudaStream_t s);
+cudaError_t launch_entry_to_half(const float *params, int64_t n, __half *w16, cudaStream_t s);
+cudaError_t launch_cell_seeds(const SearchArgs &a, const uint32_t *attr_sorted,
+                              const uint32_t *id_sorted, const unsigned long long *cell_key,
+                              const uint32_t *cell_id, int E, int T, const float *cent,
+                              const __half *w16, const float *params, int32_t *cells_out,
+                              uint32_t *seeds, uint8_t *bucket, int sm_count, size_t smem_optin,
+                              cudaStream_t s);
+cudaError_t launch_entry_forward(const __half *w16, const float *params, int d, int E,
+                                 const float *Q, int64_t n, float *out, cudaStream_t s);
+cudaError_t launch_entry_labels(const uint32_t *ids, int k, int64_t n, const uint32_t *cell,
+                                int64_t N, int32_t *labels, cudaStream_t s);
+size_t entry_train_chunk_bytes(int B, int E);
+cudaError_t entry_grad_accumulate(const float *P, int d, int E, const float *X,
+                                  const int32_t *y, int64_t n, int64_t total, int B, float *G,
+                                  float *loss, void *work, cudaStream_t s);
+cudaError_t launch_entry_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr,
+                              float c1, float c2, cudaStream_t s);
+// acc[0] = sum over queries with a valid truth entry of |ids & truth| / valid, acc[1] = their count
+cudaError_t launch_recall(const uint32_t *ids, int k, const uint32_t *truth, int kt, int64_t Q,
+                          double *acc, cudaStream_t s);
 
 }  // namespace nhq

@@ -171,10 +171,15 @@ def int_valued(N, nq, d, cards=(3, 10, 20), n_comp=16, seed=7, zipf=True):
     return w
 
 
-def c3(N=1_000_000, nq=10_000, d=960, cards=(2, 5, 10, 50), n_comp=1_000, seed=1002):
-    """GIST1M-shaped: unit-normalised Gaussian-mixture rows, 4 uniform attributes."""
+def c3(N=1_000_000, nq=10_000, d=960, cards=(2, 5, 10, 50), n_comp=1_000, seed=1002,
+       query_stream=0):
+    """GIST1M-shaped: unit-normalised Gaussian-mixture rows, 4 uniform attributes.
+    query_stream > 0 draws the queries from another independent stream (as in c2)."""
     _check_cards(cards)
     rb, rq, ra, rqa = _rngs(seed)
+    if query_stream:
+        rq, rqa = (np.random.default_rng(x)
+                   for x in np.random.SeedSequence([seed, query_stream]).spawn(2))
     cent = rb.standard_normal((n_comp, d), dtype=np.float32)
     X, _ = gaussian_mixture(rb, N, cent, 0.5)
     Qv, _ = gaussian_mixture(rq, nq, cent, 0.5)

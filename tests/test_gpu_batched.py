@@ -42,12 +42,15 @@ def test_autotune_keeps_results_and_returns_a_legal_shape(nhq, case):
         nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 64, ids0, g0, c0, seed=1,
                        seed_mode=nhq.SEED_ATTRIBUTE)
         tmp = torch.empty((w.nq, 10), dtype=torch.uint32, device="cuda:0")
-        wpb, bits, ms = nhq.nhq_autotune_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 64, tmp,
-                                                seed=1, seed_mode=nhq.SEED_ATTRIBUTE)
-        assert wpb in (2, 4, 8) and 10 <= bits <= 16 and ms > 0
+        wpq, wpb, bits, ms = nhq.nhq_autotune_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 64,
+                                                     tmp, seed=1, seed_mode=nhq.SEED_ATTRIBUTE,
+                                                     return_wpq=True)
+        assert wpq in (1, 2, 4) and wpb in (2, 4, 8) and wpb % wpq == 0
+        assert 10 <= bits <= 16 and ms > 0
         ids1, g1, c1 = empty_out(w.nq, 10)
         nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 64, ids1, g1, c1, seed=1,
-                       seed_mode=nhq.SEED_ATTRIBUTE, warps_per_block=wpb, hash_bits=bits)
+                       seed_mode=nhq.SEED_ATTRIBUTE, warps_per_block=wpb, hash_bits=bits,
+                       warps_per_query=wpq)
         torch.cuda.synchronize()
     assert torch.equal(ids0, ids1) and torch.equal(g0, g1)
 
@@ -100,3 +103,84 @@ def test_heterogeneous_batch_on_correlated_attributes(nhq):
         swaps += int((got[q, :kq] != r["ids"][q]).sum())
         assert (got[q, kq:] == -1).all()
     assert swaps <= 4
+
+
+# ------------------------------------------------------------------ warps per query, beam width
+@pytest.mark.parametrize("d", [32, 300])
+@pytest.mark.parametrize("vec,rerank", [(0, 0), (1, 1), (2, 1)])
+def test_warps_per_query_leave_results_unchanged(nhq, d, vec, rerank):
+    # the helper warps only take distance passes: every output is the same for 1, 2, 4
+    # warps per query (d = 300 takes the strided pass of wide rows)
+    w = synth.int_valued(3000, 200, d, cards=(3, 5, 7), n_comp=20, seed=70 + d)
+    nbr, _, _ = O.build_graph(w.X, w.A, R=16, K=32, weights=CONST)
+    outs = []
+    with nhq.Index.create(dev(w.X), dev(w.A), CONST) as ix:
+        nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
+        for wpq, wpb in ((1, 8), (2, 8), (4, 8), (2, 2), (4, 4)):
+            for h, sm in ((1, nhq.SEED_ATTRIBUTE), (2, nhq.SEED_RANDOM)):
+                ids, g, c = empty_out(w.nq, 10)
+                ndc = torch.empty(w.nq, dtype=torch.int32, device="cuda:0")
+                ex = torch.empty(w.nq, dtype=torch.int32, device="cuda:0")
+                nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 40, ids, g, c, ndc=ndc,
+                               expansions=ex, h=h, seed=3, seed_mode=sm, vec_dtype=vec,
+                               rerank=rerank, warps_per_query=wpq, warps_per_block=wpb)
+                torch.cuda.synchronize()
+                outs.append(((wpq, wpb, h), [t.cpu() for t in (ids, g, c, ndc, ex)]))
+    ref = {key[2]: o for key, o in outs if key[0] == 1}
+    for key, o in outs:
+        for a, b in zip(o, ref[key[2]]):
+            assert torch.equal(a, b), key
+    # and the 4-warp form against the oracle directly
+    r = O.search(w.X, w.A, nbr, w.Qv, w.QA, 10, 40, seed=3, weights=CONST,
+                 seed_mode=O.SEED_ATTRIBUTE, vec_round=vec, rerank=bool(rerank))
+    four = dict(outs)[(4, 8, 1)]
+    assert (ids_i64(four[0]) == r["ids"]).all()
+    assert np.array_equal(four[1].numpy().astype(np.float64), r["gamma"])
+
+
+def test_warps_per_query_rejects_bad_values(nhq, case):
+    w, nbr = case
+    with nhq.Index.create(dev(w.X), dev(w.A), CONST) as ix:
+        nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
+        ids, g, c = empty_out(w.nq, 10)
+        for wpq, wpb in ((3, 0), (8, 0), (4, 2)):
+            with pytest.raises(nhq.NHQError):
+                nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 40, ids, g, c,
+                               warps_per_query=wpq, warps_per_block=wpb)
+
+
+def test_recall_matches_the_oracle_definition(nhq, case):
+    w, nbr = case
+    truth, _, P = O.filtered_topk(w.X, w.A, w.Qv, w.QA, 10, prec=O.F32)
+    with nhq.Index.create(dev(w.X), dev(w.A), CONST) as ix:
+        nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
+        for ef in (10, 20, 80):
+            ids, g, c = empty_out(w.nq, 10)
+            nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, ef, ids, g, c, seed=2)
+            r = nhq.nhq_recall(ids, dev(to_u32_graph(truth)))
+            want, _ = O.hybrid_recall(ids_i64(ids), w.A, w.QA, truth, P)
+            assert abs(r - want) < 1e-6, (ef, r, want)
+
+
+def test_autotune_beam_takes_the_smallest_ef_reaching_the_target(nhq, case):
+    w, nbr = case
+    truth, _, P = O.filtered_topk(w.X, w.A, w.Qv, w.QA, 10, prec=O.F32)
+    efs = [10, 12, 16, 24, 32, 48, 64, 128]
+    with nhq.Index.create(dev(w.X), dev(w.A), CONST) as ix:
+        nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
+        rec = {}
+        for ef in efs:
+            ids, g, c = empty_out(w.nq, 10)
+            nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, ef, ids, g, c, seed=2,
+                           seed_mode=nhq.SEED_ATTRIBUTE)
+            rec[ef] = O.hybrid_recall(ids_i64(ids), w.A, w.QA, truth, P)[0]
+        target = 0.97
+        want = next((e for e in efs if rec[e] >= target), efs[-1])
+        tmp = torch.empty((w.nq, 10), dtype=torch.uint32, device="cuda:0")
+        t = nhq.nhq_autotune_beam(ix.handle, dev(w.Qv), dev(w.QA), 10, efs,
+                                  dev(to_u32_graph(truth)), target, tmp, seed=2,
+                                  seed_mode=nhq.SEED_ATTRIBUTE)
+    assert t["ef"] == want, (t, rec)
+    assert abs(t["recall"] - rec[want]) < 1e-6
+    assert t["warps_per_query"] in (1, 2, 4) and t["warps_per_block"] in (2, 4, 8)
+    assert t["warps_per_block"] % t["warps_per_query"] == 0 and t["ms"] > 0

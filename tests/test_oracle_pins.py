@@ -373,6 +373,50 @@ def test_bf16_rounding_follows_the_format(oracle_mod):
     assert O.round_bf16(-(1 + 2**-8 + 2**-12)) == -(1 + 2**-7)
 
 
+def test_row_rounding_matches_torch_bf16_and_e4m3(oracle_mod):
+    # the array form used for candidate sets on rounded rows against an independent
+    # library conversion (torch rounds f32 to bf16 and to e4m3 to nearest, ties to even)
+    O = oracle_mod
+    rng = np.random.default_rng(66)
+    X = np.concatenate([rng.standard_normal(4000).astype(np.float32),
+                        (rng.standard_normal(2000) * 100).astype(np.float32),
+                        (rng.standard_normal(2000) * 1e-3).astype(np.float32)]).reshape(80, 100)
+    b = O.round_rows(X, O.ROUND_BF16)
+    assert np.array_equal(b, torch.from_numpy(X).to(torch.bfloat16).float().numpy())
+    assert np.array_equal(b.ravel()[:50], np.array([O.round_bf16(x) for x in X.ravel()[:50]],
+                                                   np.float32))
+    inr = np.clip(X, -440, 440)  # torch's e4m3 conversion does not saturate; stay in range
+    e = O.round_rows(inr, O.ROUND_E4M3)
+    assert np.array_equal(e, torch.from_numpy(inr).to(torch.float8_e4m3fn).float().numpy())
+
+
+def test_f16_rounding_matches_numpy_half(oracle_mod):
+    # binary16 by its definition against numpy's conversion (round to nearest even),
+    # across normals, subnormals, halfway cases and overflow
+    O = oracle_mod
+    rng = np.random.default_rng(73)
+    X = np.concatenate([rng.standard_normal(3000) * s for s in (1.0, 1e3, 3e4, 1e-5, 1e-7)]
+                       + [np.array([65504.0, 65519.0, 65520.0, 70000.0, -65520.0, 2.0 ** -24,
+                                    2.0 ** -25, 3 * 2.0 ** -26, 1 + 2.0 ** -11,
+                                    1 + 3 * 2.0 ** -11, 0.0, -0.0])]).astype(np.float32)
+    got = O.round_rows(X, O.ROUND_F16)
+    with np.errstate(over="ignore"):  # the values beyond 65504 round to infinity
+        want = X.astype(np.float16).astype(np.float32)
+    assert np.array_equal(got, want)
+    assert np.array_equal(np.signbit(got), np.signbit(want))
+
+
+def test_knn_on_rounded_rows_is_knn_of_the_rounded_copy(oracle_mod):
+    O = oracle_mod
+    w = synth.c1(N=300, nq=1, d=24, seed=67)
+    a, ga = O.knn(w.X, w.A, 8, vec_round=O.ROUND_BF16)
+    b, gb = O.knn(O.round_rows(w.X, O.ROUND_BF16), w.A, 8)
+    assert (a == b).all() and np.array_equal(ga, gb)
+    c, _ = O.knn(w.X, w.A, 8)
+    assert not np.array_equal(ga, O.knn(w.X, w.A, 8)[1])  # the rounding is not a no-op
+    assert (a[:, 0] != np.arange(300)).all() and c.shape == a.shape
+
+
 def test_e4m3_rounding_follows_the_format(oracle_mod):
     O = oracle_mod
     for x in (0.0, 1.0, 1.125, 16.0, 18.0, 448.0, -240.0, 2**-6, 2**-9, 3 * 2**-9):
@@ -821,3 +865,77 @@ def test_nsw_single_vertex_waves_are_serial_insertion(oracle_mod, weights, entry
     got = O.build_nsw(w.X, w.A, R=6, L=12, weights=weights, seed=11, wave_max=1, entry=entry)
     ref = _serial_nsw(O, w.X, w.A, 6, 12, weights, 11, entry)
     assert np.array_equal(got, ref)
+
+
+# ------------------------------------------------------------------ entry cells, entry model
+def test_cells_are_the_nearest_centroids_by_integer_delta(oracle_mod):
+    O = oracle_mod
+    w = synth.int_valued(900, 40, 12, seed=71)
+    E = 37
+    cid = O.cell_centroids(w.N, E)
+    assert list(cid[:3]) == [0, 24, 48] and len(set(cid.tolist())) == E
+    d2 = ((w.X[:, None, :].astype(np.int64) - w.X[None, cid, :].astype(np.int64)) ** 2).sum(-1)
+    want = np.array([np.lexsort((np.arange(E), r))[0] for r in d2])
+    assert (O.cells(w.X, E) == want).all()
+    assert (O.cells(w.X, E)[cid] == np.arange(E)).all() or len(set(map(tuple, w.X[cid]))) < E
+    q2 = ((w.Qv[:, None, :].astype(np.int64) - w.X[None, cid, :].astype(np.int64)) ** 2).sum(-1)
+    near = O.nearest_cells(w.X, E, w.Qv, 4)
+    for q in range(w.nq):
+        assert list(near[q]) == list(np.lexsort((np.arange(E), q2[q]))[:4])
+
+
+def test_cell_seeds_hand_case(oracle_mod):
+    O = oracle_mod
+    A = np.array([[0], [1], [0], [0], [1], [0], [0], [0]], np.uint8)
+    cell_of = np.array([2, 0, 1, 2, 1, 1, 0, 2])
+    QA = np.array([[0], [0], [1], [0]], np.uint8)
+    chosen = np.array([[1, 2], [0, 1], [2, 0], [3, 0]])
+    B = O.cell_seeds(A, QA, cell_of, chosen, ef=32)
+    # q0: P = 0 2 3 5 6 7; cell 1 -> 2 5, cell 2 -> 0 3 7; S = 6 -> all five, then P[0]
+    assert list(B[0][:6]) == [2, 5, 0, 3, 7, 0] and (B[0][6:] == -1).all()
+    # q1: cell 0 -> 6, cell 1 -> 2 5; S = 6 -> then 3 evenly spaced of P: P[0], P[2], P[4]
+    assert list(B[1][:6]) == [6, 2, 5, 0, 3, 6]
+    # q2: P = 1 4; cell 2 none, cell 0 -> 1; S = 2 -> then P[0]
+    assert list(B[2][:2]) == [1, 1] and (B[2][2:] == -1).all()
+    # a small ef limits S; cells with no member of P give nothing
+    B = O.cell_seeds(A, QA, cell_of, chosen, ef=3)
+    assert list(B[3][:3]) == [6, 0, 5] and (B[3][3:] == -1).all()  # P[0], P[3]
+    # no match: the random stream
+    B = O.cell_seeds(A, np.array([[5]], np.uint8), cell_of, np.array([[0, 1]]), ef=4, seed=9)
+    ref = []
+    for x in _splitmix64_py((9 ^ _mix64_py(0)) & _M64, 64):
+        if x % 8 not in ref:
+            ref.append(x % 8)
+        if len(ref) == 4:
+            break
+    assert list(B[0][:4]) == ref
+
+
+def test_entry_model_zero_weights_and_gradient(oracle_mod):
+    from oracle import mlp
+
+    d, E = 6, 9
+    p = np.zeros(mlp.entry_size(d, E))
+    p[0] = 0.5
+    rng = np.random.default_rng(72)
+    Q, y = rng.standard_normal((13, d)), rng.integers(0, E, 13)
+    loss, g = mlp.entry_loss_and_grad(p, Q, y, d, E)
+    assert abs(loss - math.log(E)) < 1e-12  # uniform softmax
+    # with zero weights only b2 has a gradient: mean(1/E - onehot)
+    _, _, _, _, gb2 = mlp.entry_unpack(g, d, E)
+    want = np.full(E, 1.0 / E) - np.bincount(y, minlength=E) / 13
+    assert np.allclose(gb2, want)
+    p = rng.standard_normal(p.size) * 0.3
+    p[0] = 0.7
+    loss, g = mlp.entry_loss_and_grad(p, Q, y, d, E)
+    num = np.zeros_like(p)
+    for i in range(1, p.size):
+        e = np.zeros_like(p)
+        e[i] = 1e-6
+        num[i] = (mlp.entry_loss_and_grad(p + e, Q, y, d, E)[0] -
+                  mlp.entry_loss_and_grad(p - e, Q, y, d, E)[0]) / 2e-6
+    assert np.abs(num - g).max() < 1e-7 and g[0] == 0.0
+    # forward: softmax of the logits reproduces the loss
+    t = mlp.entry_forward(p, Q, d, E)
+    lse = np.log(np.exp(t).sum(1))
+    assert abs(np.mean(lse - t[np.arange(13), y]) - loss) < 1e-12
