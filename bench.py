@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--wpq", type=int, default=1, help="warps per query of the search (1, 2, 4)")
     ap.add_argument("--cells", type=int, default=0,
                     help="entry cells E for the learned entry point (0: the workload's default)")
-    ap.add_argument("--entry-T", type=int, default=2, help="entry cells taken per query")
+    ap.add_argument("--entry-T", type=int, default=1, help="entry cells taken per query")
     ap.add_argument("--train-q", type=int, default=100_000,
                     help="training queries for the learned entry point")
     ap.add_argument("--knn-dtype", type=int, default=1,
@@ -94,6 +94,15 @@ def parse():
 def workload_name(a):
     return (f"c2-shaped: N={a.n:,} d={a.d} int-valued f32 (1,000 centroids), m=3 attrs 3/10/20 "
             f"Zipf s=1, {a.nq:,} queries, k={a.k}, R={a.R}, weights w_v=1 w_l=10000")
+
+
+def synth_c2_queries(a, nq, stream):
+    """nq training queries of the c2-shaped workload from an independent query stream."""
+    import copy
+
+    b = copy.copy(a)
+    b.nq = nq
+    return make_workload(b, query_stream=stream)
 
 
 def make_workload(a, query_stream=0):
@@ -508,9 +517,10 @@ def c4_arm(a, rank, world, local):
 
 # ---------------------------------------------------------------- the largest set
 def c5_arm(a):
-    """The c5-shaped set: N = 10M, d = 96 (values exactly representable in f16, stored
-    as f32), 4,096 centroids, m = 3 Zipf attributes (10/50/200), 50,000 queries, k = 10:
-    build time, then QPS at hybrid Recall@10 >= target over an ef sweep."""
+    """The c5-shaped set: N = 10M, d = 96 FP16 vectors (passed to the library as f16 and
+    scored from its f16 copy, 192-byte rows; every value is an f16, so the scores equal
+    f32 scores), 4,096 centroids, m = 3 Zipf attributes (10/50/200), 50,000 queries,
+    k = 10: build time, then QPS at hybrid Recall@10 >= target over an ef sweep."""
     import torch
 
     import paper_2203_13601_gb300 as nhq
@@ -524,7 +534,8 @@ def c5_arm(a):
     t0 = time.perf_counter()
     w = synth.c5()
     t_gen = time.perf_counter() - t0
-    X, A = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.A).to(dev)
+    X = torch.from_numpy(w.X.astype(np.float16)).to(dev)  # the configured FP16 input
+    A = torch.from_numpy(w.A).to(dev)
     Qv, QA = torch.from_numpy(w.Qv).to(dev), torch.from_numpy(w.QA).to(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -549,7 +560,7 @@ def c5_arm(a):
     def run(ef, diag=False):
         nhq.nhq_search(ix.handle, Qv, QA, k, ef, ids, dd, ch, ndc=ndc if diag else None,
                        expansions=exps if diag else None, seed=12345,
-                       seed_mode=nhq.SEED_ATTRIBUTE)
+                       seed_mode=nhq.SEED_ATTRIBUTE, vec_dtype=nhq.VEC_F16)
 
     sweep = []
     for ef in (16, 24, 32, 48, 64, 96):
@@ -568,7 +579,7 @@ def c5_arm(a):
     run(ef, diag=True)
     torch.cuda.synchronize()
     ndc_h, exp_h = ndc.cpu().numpy().astype(np.float64), exps.cpu().numpy().astype(np.float64)
-    alg_bytes = float((ndc_h * (4 * w.d + 4) + exp_h * a.R * 4 + w.d * 4 + k * 9).sum())
+    alg_bytes = float((ndc_h * (2 * w.d + 4) + exp_h * a.R * 4 + w.d * 4 + k * 9).sum())
     for _ in range(max(3, a.warmup)):
         run(ef)
     steps = min(a.steps, 200)
@@ -590,10 +601,11 @@ def c5_arm(a):
         "metric": f"QPS at hybrid Recall@{k} >= {a.target} on the 10M set",
         "value": w.nq * steps / (total_ms / 1000.0), "unit": "queries/s", "n_gpus": 1,
         "steps": steps, "warmup": a.warmup, "ms_per_step": total_ms / steps,
-        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "c5-shaped: N=10,000,000 d=96 (f16-representable values "
-                               "stored as f32), 4,096 centroids, m=3 attrs 10/50/200 Zipf, "
-                               "50,000 queries, k=10, R=32, weights w_v=1 w_l=10000",
+        "higher_is_better": True, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": "c5-shaped: N=10,000,000 d=96 FP16 (built from the f16 rows, "
+                               "scored from the index's f16 copy, 192-byte rows), 4,096 "
+                               "centroids, m=3 attrs 10/50/200 Zipf, 50,000 queries, k=10, "
+                               "R=32, weights w_v=1 w_l=10000",
                    "ef": ef, "recall": sweep[-1]["recall"], "sweep": sweep,
                    "build_s": t_build, "gen_s": t_gen,
                    "queries_with_no_match": int((P == 0).sum())},
@@ -1403,7 +1415,14 @@ def main():
     ndc = torch.empty(w.nq, dtype=torch.int32, device=dev)
     exps = torch.empty(w.nq, dtype=torch.int32, device=dev)
 
-    sel = {"model": None, "tau": 0.5}
+    # the learned parts chosen by the sweep below (none until then)
+    sel = {"model": None, "tau": 0.5, "stop_min": 4, "stop_every": 2, "entry": None}
+
+    def seed_kw():
+        if sel["entry"] is not None:
+            return dict(seed_mode=nhq.SEED_CELL_LEARNED, entry_model=sel["entry"],
+                        entry_cells=a.entry_T)
+        return dict(seed_mode=a.seed_mode)
 
     def run(ef, h, vec, diag=False):
         # the reduced-precision copies are re-ranked in f32 (vec 2 = fp8 needs it; bf16 is
@@ -1411,9 +1430,9 @@ def main():
         nhq.nhq_search(ix.handle, Qv, QA, a.k, ef, ids, dists, chi,
                        ndc=ndc if diag else None, expansions=exps if diag else None,
                        h=h, seed=12345, vec_dtype=vec, rerank=int(vec == nhq.VEC_FP8E4M3),
-                       seed_mode=a.seed_mode, stop_model=sel["model"],
-                       stop_threshold=sel["tau"], stop_min=4, stop_every=2, stream=stream,
-                       warps_per_query=a.wpq)
+                       stop_model=sel["model"], stop_threshold=sel["tau"],
+                       stop_min=sel["stop_min"], stop_every=sel["stop_every"], stream=stream,
+                       warps_per_query=a.wpq, **seed_kw())
 
     def time_once(ef, h, vec, reps=2):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1484,14 +1503,30 @@ def main():
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         del feats, labels, tq, F, Y
+        # the learned entry point: cells and the entry model, trained on the cells of the
+        # plain search's answers for another set of training queries
+        E = a.cells if a.cells > 0 else 256
+        wtr_e = synth_c2_queries(a, a.train_q, 2)
+        entry_model, t_entry, n_entry = train_entry(nhq, ix, w, wtr_e, E, a.k, dev, epochs=20)
         lsweep = []
+        schedules = [(4, 2), (8, 4)]
         for lef in [int(x) for x in a.learned_efs.split(",") if int(x) >= a.k]:
-            for tau in [float(x) for x in a.taus.split(",")]:
-                def run_l(lef=lef, tau=tau, diag=False):
+            combos = [(None, None, True)]  # the entry model alone
+            for (smin, severy) in schedules:
+                for tau in [float(x) for x in a.taus.split(",")]:
+                    combos += [((smin, severy), tau, False), ((smin, severy), tau, True)]
+            for sched, tau, use_entry in combos:
+                def run_l(lef=lef, tau=tau, sched=sched, use_entry=use_entry, diag=False):
+                    kw = dict(seed_mode=a.seed_mode)
+                    if use_entry:
+                        kw = dict(seed_mode=nhq.SEED_CELL_LEARNED, entry_model=entry_model,
+                                  entry_cells=a.entry_T)
                     nhq.nhq_search(ix.handle, Qv, QA, a.k, lef, ids, dists, chi, h=1,
                                    expansions=exps if diag else None, seed=12345,
-                                   seed_mode=a.seed_mode, stop_model=stop_model,
-                                   stop_threshold=tau, stop_min=4, stop_every=2, stream=stream)
+                                   stop_model=stop_model if sched else None,
+                                   stop_threshold=tau if sched else 0.5,
+                                   stop_min=sched[0] if sched else 4,
+                                   stop_every=sched[1] if sched else 2, stream=stream, **kw)
                 run_l(diag=True)
                 torch.cuda.synchronize()
                 rec, _ = hybrid_recall(ids.cpu().numpy(), w.A, w.QA, gt_h, P, a.k)
@@ -1506,13 +1541,17 @@ def main():
                 ev1.synchronize()
                 ms = ev0.elapsed_time(ev1) / 2
                 lsweep.append({"ef": lef, "tau": tau, "recall": rec, "ms": ms,
-                               "mean_expansions": mexp})
+                               "mean_expansions": mexp, "entry": use_entry,
+                               "stop": ({"stop_min": sched[0], "stop_every": sched[1]}
+                                        if sched else None)})
         ok = [x for x in lsweep if x["recall"] >= a.target]
         if ok:
             learned = min(ok, key=lambda x: x["ms"])
         ok2 = [x for x in lsweep if x["recall"] >= a.target2]
         plain2 = [x for x in sweep if x["recall"] >= a.target2 and x["vec"] == "f32"]
         learned_info = {"traces": int(ntr), "train_s": t_train, "sweep": lsweep,
+                        "entry": {"cells": E, "cells_per_query": a.entry_T,
+                                  "train_s": t_entry, "traces": n_entry},
                         "chosen": learned,
                         "at_target2": {
                             "target": a.target2,
@@ -1526,10 +1565,13 @@ def main():
     use_learned = learned is not None and learned["ms"] < best[4]
     tau = 0.5
     if use_learned:
-        ef, h, vec, rec, tau = learned["ef"], 1, nhq.VEC_F32, learned["recall"], learned["tau"]
-
-    if use_learned:
-        sel["model"], sel["tau"] = stop_model, tau
+        ef, h, vec, rec = learned["ef"], 1, nhq.VEC_F32, learned["recall"]
+        if learned["stop"] is not None:
+            tau = learned["tau"]
+            sel.update(model=stop_model, tau=tau, stop_min=learned["stop"]["stop_min"],
+                       stop_every=learned["stop"]["stop_every"])
+        if learned["entry"]:
+            sel["entry"] = entry_model
     # diagnostics at the chosen setting: NDC and expansions for the algorithmic bytes
     run(ef, h, vec, diag=True)
     torch.cuda.synchronize()
@@ -1603,10 +1645,12 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": VEC_NAMES[vec], "data": "synthetic",
         "config": {"workload": workload_name(a), "ef": ef, "h": h,
-                   "seed_set": ["random (Sec. 3.2)", "attribute entry"][a.seed_mode],
+                   "seed_set": ("learned entry cells" if sel["entry"] is not None else
+                                ["random (Sec. 3.2)", "attribute entry"][a.seed_mode]),
                    "scoring_copy": VEC_NAMES[vec] + (" + f32 re-rank" if vec == 2 else ""),
-                   "learned_stop": ({"threshold": tau, "stop_min": 4, "stop_every": 2}
-                                    if use_learned else None),
+                   "learned_stop": ({"threshold": tau, "stop_min": sel["stop_min"],
+                                     "stop_every": sel["stop_every"]}
+                                    if sel["model"] is not None else None),
                    "recall": rec,
                    "recall_kind": "hybrid Recall@10 vs filter-mode brute force",
                    "l2": "inputs larger than L2 (vectors 512 MB + adjacency 256 MB)",
@@ -1627,7 +1671,12 @@ def main():
                      "mean_expansions": float(exp_h.mean())},
         "e2e": {"value": w.nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "recall": e2e_rec},
-        "gpu_launches": a.steps * (3 if a.seed_mode in (1, 3) else 1),
+        # per step: the seed pre-pass and ordering (attribute seeds: 2 kernels; learned entry:
+        # fp16 model copy, two dense layers, seeds, ordering), the stop model's fp16 copy,
+        # the search kernel
+        "gpu_launches": a.steps * ((5 if sel["entry"] is not None else
+                                    2 if a.seed_mode in (1, 3) else 0) +
+                                   (1 if sel["model"] is not None else 0) + 1),
         "clocks": clk,
     }
     if rank == 0 and not a.no_cpu_baseline:

@@ -72,7 +72,17 @@ typedef struct nhq_weights {
  * vectors is rounded to nearest-even into the copy (FP8 saturates at +-448); the
  * query stays f32 and distances accumulate in f32.  With `rerank` the final pool
  * is re-scored with the f32 vectors and the first k of that order are returned. */
-typedef enum nhq_vec_dtype { NHQ_VEC_F32 = 0, NHQ_VEC_BF16 = 1, NHQ_VEC_FP8E4M3 = 2 } nhq_vec_dtype;
+typedef enum nhq_vec_dtype {
+    NHQ_VEC_F32 = 0,
+    NHQ_VEC_BF16 = 1,
+    NHQ_VEC_FP8E4M3 = 2,
+    NHQ_VEC_F16 = 3 /* IEEE binary16 (rounded to nearest even, overflow to +-inf) */
+} nhq_vec_dtype;
+
+/* Element type of the vectors a caller passes to nhq_index_create_typed /
+ * nhq_build_typed (the index keeps an f32 copy for every kernel; an F16 or BF16 input
+ * also becomes the index's scoring copy of that type, which is then exact). */
+typedef enum nhq_dtype { NHQ_F32 = 0, NHQ_F16 = 1, NHQ_BF16 = 2 } nhq_dtype;
 
 typedef struct nhq_build_params {
     int32_t K;           /* candidate-set size l of Sec. 4.1 (exact K nearest by Gamma); 0 -> 64 */
@@ -96,8 +106,10 @@ typedef enum nhq_seed_mode {
                                For tuples spread over many clusters, where evenly spaced
                                members rarely include the query's own                       */
     NHQ_SEED_CELL_NEAREST = 4, /* entry cells (nhq_index_build_cells): the T = entry_cells cells
-                               whose centroids are nearest to the query by (delta^2 of the f32
-                               rows summed in index order, cell); P and c as above,
+                               of largest score q.c - |c|^2/2 (f32, products summed in index
+                               order; ties: smaller cell), i.e. nearest centroids (exactly so
+                               when the arithmetic is exact, e.g. integer components); P and
+                               c as above,
                                S = min(ef, 32, c); B = the first S members of P in those cells
                                (nearest cell first, ascending ids within a cell), then while
                                fewer than S the evenly spaced P[floor(j*c/S2)], j < S2 = S - |B|
@@ -158,6 +170,11 @@ typedef struct nhq_search_params {
     int32_t entry_cells;     /* NHQ_SEED_CELL_*: T, the cells taken per query, 1..min(8, E); 0 -> 2 */
     int32_t *cells_out;      /* NHQ_SEED_CELL_*: device [Q][T] receiving each query's cells, or
                                 NULL                                                          */
+    int32_t tile_rows;       /* rows each team of 8 lanes evaluates per distance pass: 0 or 2
+                                (8 rows per warp and pass), 4 (16 rows: an expansion's
+                                candidates in one pass, fewer resident warps); rows wider than
+                                the fixed-chunk forms always take 2; results are the same on
+                                integer components, within f32 rounding otherwise         */
 } nhq_search_params;
 
 typedef struct nhq_index nhq_index;
@@ -182,6 +199,15 @@ int32_t nhq_version(void);
  */
 nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
                             int32_t m, nhq_weights w, void *stream, nhq_index **out);
+
+/* nhq_index_create for vectors of element type `dtype` (nhq_dtype): the values are
+ * widened to f32 exactly, and for NHQ_F16 / NHQ_BF16 the index's f16 / bf16 scoring copy
+ * (nhq_search_params::vec_dtype NHQ_VEC_F16 / NHQ_VEC_BF16) is those same values, so
+ * searching with it reads rows of 2 d bytes and scores exactly as f32.
+ * Errors: as nhq_index_create; dtype not an nhq_dtype. */
+nhq_status nhq_index_create_typed(const void *vectors, int32_t dtype, int64_t N, int32_t d,
+                                  const uint8_t *attributes, int32_t m, nhq_weights w,
+                                  void *stream, nhq_index **out);
 
 /* Releases the index and all its device memory.  NULL is a no-op. */
 void nhq_free(nhq_index *index);
@@ -334,6 +360,11 @@ nhq_status nhq_entry_train(float *params, int32_t d, int32_t E, const float *que
 nhq_status nhq_entry_labels(const nhq_index *index, const uint32_t *ids, int32_t k, int64_t n,
                             int32_t *labels, void *stream);
 
+/* nhq_build for vectors of element type `dtype`: nhq_index_create_typed + nhq_index_build. */
+nhq_status nhq_build_typed(const void *vectors, int32_t dtype, int64_t N, int32_t d,
+                           const uint8_t *attributes, int32_t m, int32_t degree, nhq_weights w,
+                           const nhq_build_params *params, void *stream, nhq_index **out);
+
 /* build(vectors, attributes, degree, weights): nhq_index_create + nhq_index_build. */
 nhq_status nhq_build(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
                      int32_t m, int32_t degree, nhq_weights w, const nhq_build_params *params,
@@ -452,12 +483,14 @@ nhq_status nhq_brute_force_noalloc(const float *vectors, const uint32_t *packed_
 
 /*
  * Autotuner (a project addition): times nhq_search on this batch for every launch
- * shape that leaves the results unchanged -- warps per query in {1, 2, 4}, warps per
- * block in {2, 4, 8} (at least the warps per query) and visited-filter sizes 2^b for b
- * from the smallest legal size up to two above it -- with CUDA events (one warm-up and
- * three timed runs each), and writes the fastest into params->warps_per_query /
- * warps_per_block / hash_bits (the other fields are used as given).  *best_ms (may be
- * NULL) receives its time per call.  Device pointers; the outputs are overwritten by the
+ * shape -- warps per query in {1, 2, 4}, rows per team and pass (tile_rows) in {2, 4},
+ * warps per block in {2, 4, 8} (at least the warps per query) and visited-filter sizes
+ * 2^b for b from the smallest legal size up to three above it -- with CUDA events (one
+ * warm-up and three timed runs each), and writes the fastest into
+ * params->warps_per_query / tile_rows / warps_per_block / hash_bits (the other fields
+ * are used as given).  Every shape returns the same results on integer components
+ * (tile_rows changes the f32 summation order of float rows).  *best_ms (may be NULL)
+ * receives its time per call.  Device pointers; the outputs are overwritten by the
  * trial runs.
  */
 nhq_status nhq_autotune_search(const nhq_index *index, const float *queries,

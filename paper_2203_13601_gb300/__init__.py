@@ -22,6 +22,7 @@ import numpy as np
 __all__ = [
     "NHQError", "Index", "load_library", "library_path",
     "W_PROPORTIONAL", "W_CONSTANT", "W_FILTER", "W_HARMONIC", "VEC_F32", "VEC_BF16", "VEC_FP8E4M3",
+    "VEC_F16", "F32", "F16", "BF16", "nhq_index_create_typed", "nhq_build_typed",
     "SEED_RANDOM", "SEED_ATTRIBUTE", "SEED_GIVEN", "SEED_ATTRIBUTE_NEAR",
     "nhq_last_error", "nhq_version", "nhq_index_create", "nhq_free", "nhq_index_info",
     "nhq_pack_attributes", "nhq_knn", "nhq_knn_bf16", "nhq_edge_select", "nhq_reverse_candidates",
@@ -31,7 +32,7 @@ __all__ = [
     "nhq_mlp_train", "MLP_INPUTS", "MLP_HIDDEN", "MLP_PARAMS", "nhq_autotune_search",
     "nhq_search_graph_create", "nhq_search_graph_launch", "nhq_search_graph_free",
     "nhq_merge_topk", "nhq_postfilter", "nhq_knn_nndescent", "nhq_index_build_nsw",
-    "nhq_autotune_beam", "nhq_recall", "SEED_CELL_NEAREST", "SEED_CELL_LEARNED",
+    "nhq_autotune_beam", "nhq_recall", "nhq_autotune", "SEED_CELL_NEAREST", "SEED_CELL_LEARNED",
     "ENTRY_HIDDEN", "nhq_index_build_cells", "nhq_index_cells", "nhq_entry_param_count",
     "nhq_entry_forward", "nhq_entry_grad", "nhq_entry_train", "nhq_entry_labels",
 ]
@@ -40,7 +41,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libnhq.so")
 
 W_PROPORTIONAL, W_CONSTANT, W_FILTER, W_HARMONIC = 0, 1, 2, 3
-VEC_F32, VEC_BF16, VEC_FP8E4M3 = 0, 1, 2
+VEC_F32, VEC_BF16, VEC_FP8E4M3, VEC_F16 = 0, 1, 2, 3
+F32, F16, BF16 = 0, 1, 2  # nhq_dtype of the input vectors
 SEED_RANDOM, SEED_ATTRIBUTE, SEED_GIVEN, SEED_ATTRIBUTE_NEAR = 0, 1, 2, 3
 SEED_CELL_NEAREST, SEED_CELL_LEARNED = 4, 5
 ENTRY_HIDDEN = 64
@@ -73,7 +75,8 @@ class _SearchParams(C.Structure):
                 ("stop_threshold", C.c_float), ("stop_min", C.c_int32),
                 ("stop_every", C.c_int32), ("wildcard", C.c_int32),
                 ("warps_per_query", C.c_int32), ("entry_model", C.c_void_p),
-                ("entry_cells", C.c_int32), ("cells_out", C.c_void_p)]
+                ("entry_cells", C.c_int32), ("cells_out", C.c_void_p),
+                ("tile_rows", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -100,6 +103,9 @@ def load_library():
             "nhq_last_error": (C.c_char_p, []),
             "nhq_version": (i32, []),
             "nhq_index_create": (S, [P, i64, i32, P, i32, _Weights, P, C.POINTER(P)]),
+            "nhq_index_create_typed": (S, [P, i32, i64, i32, P, i32, _Weights, P, C.POINTER(P)]),
+            "nhq_build_typed": (S, [P, i32, i64, i32, P, i32, i32, _Weights,
+                                    C.POINTER(_BuildParams), P, C.POINTER(P)]),
             "nhq_free": (None, [P]),
             "nhq_index_info": (S, [P, P, P, P, P]),
             "nhq_pack_attributes": (S, [P, i64, i32, P, P]),
@@ -230,6 +236,26 @@ def nhq_version() -> int:
     return int(load_library().nhq_version())
 
 
+def _vec_dtype_of(vectors):
+    """nhq_dtype and element type of an input array (f32, f16 or bf16)."""
+    name = str(vectors.dtype).replace("torch.", "")
+    if name == "float16":
+        return F16, np.float16
+    if name == "bfloat16":
+        return BF16, "bfloat16"
+    return F32, np.float32
+
+
+def _vec_ptr(vectors, N, d):
+    dt, _ = _vec_dtype_of(vectors)
+    if dt == F32:
+        return dt, _ptr(vectors, np.float32, (N, d), "vectors")
+    if tuple(vectors.shape) != (N, d) or not (vectors.is_contiguous() if hasattr(
+            vectors, "is_contiguous") else vectors.flags.c_contiguous):
+        raise ValueError("vectors must be a contiguous [N, d] array")
+    return dt, vectors.data_ptr() if hasattr(vectors, "data_ptr") else vectors.ctypes.data
+
+
 def nhq_index_create(vectors, attributes, weights=None, stream=None) -> int:
     N, d = _shape(vectors)
     m = _shape(attributes)[1]
@@ -237,6 +263,19 @@ def nhq_index_create(vectors, attributes, weights=None, stream=None) -> int:
     _check(load_library().nhq_index_create(_ptr(vectors, np.float32, (N, d), "vectors"), N, d,
                                            _ptr(attributes, np.uint8, (N, m), "attributes"), m,
                                            _weights(weights), _stream(stream), C.byref(out)))
+    return out.value
+
+
+def nhq_index_create_typed(vectors, attributes, weights=None, stream=None) -> int:
+    """nhq_index_create for f32, f16 or bf16 vectors (the type is taken from the array)."""
+    N, d = _shape(vectors)
+    m = _shape(attributes)[1]
+    dt, vp = _vec_ptr(vectors, N, d)
+    out = C.c_void_p()
+    _check(load_library().nhq_index_create_typed(vp, dt, N, d,
+                                                 _ptr(attributes, np.uint8, (N, m), "attributes"),
+                                                 m, _weights(weights), _stream(stream),
+                                                 C.byref(out)))
     return out.value
 
 
@@ -339,11 +378,25 @@ def nhq_build(vectors, attributes, degree, weights=None, K=64, reverse=1, revers
     m = _shape(attributes)[1]
     p = _build_params(K, reverse, reverse_cap, knn_dtype)
     out = C.c_void_p()
-    _check(load_library().nhq_build(_ptr(vectors, np.float32, (N, d), "vectors"), N, d,
-                                     _ptr(attributes, np.uint8, (N, m), "attributes"), m, degree,
-                                     _weights(weights), C.byref(p), _stream(stream),
-                                     C.byref(out)))
+    dt, vp = _vec_ptr(vectors, N, d)
+    if dt == F32:
+        _check(load_library().nhq_build(vp, N, d,
+                                         _ptr(attributes, np.uint8, (N, m), "attributes"), m,
+                                         degree, _weights(weights), C.byref(p), _stream(stream),
+                                         C.byref(out)))
+    else:
+        _check(load_library().nhq_build_typed(vp, dt, N, d,
+                                               _ptr(attributes, np.uint8, (N, m), "attributes"),
+                                               m, degree, _weights(weights), C.byref(p),
+                                               _stream(stream), C.byref(out)))
     return out.value
+
+
+def nhq_build_typed(vectors, attributes, degree, weights=None, K=64, reverse=1, reverse_cap=64,
+                    knn_dtype=0, stream=None) -> int:
+    """nhq_build for f32, f16 or bf16 vectors (the type is taken from the array)."""
+    return nhq_build(vectors, attributes, degree, weights, K, reverse, reverse_cap, knn_dtype,
+                     stream)
 
 
 def nhq_postfilter(ids, dists, chi, k_out, out_ids, out_dists, stream=None) -> None:
@@ -392,7 +445,8 @@ def nhq_brute_force_wildcard(index, queries, query_attributes, k, wildcard, ids,
 def _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
                    seed_mode=SEED_RANDOM, seeds=None, Q=None, stop_model=None,
                    stop_threshold=0.5, stop_min=0, stop_every=1, wildcard=0,
-                   warps_per_query=0, entry_model=None, entry_cells=0, cells_out=None):
+                   warps_per_query=0, entry_model=None, entry_cells=0, cells_out=None,
+                   tile_rows=0):
     """Search parameters; ``seeds`` ([Q][n] uint32, 0xFFFFFFFF = none) selects SEED_GIVEN;
     ``stop_model`` (device f32 [MLP_PARAMS]) turns on the learned early stop."""
     n_seeds, sp = 0, None
@@ -407,7 +461,7 @@ def _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, re
                          int(hash_bits), int(vec_dtype), int(rerank), int(seed_mode),
                          int(n_seeds), sp, mp, float(stop_threshold), int(stop_min),
                          int(stop_every), int(wildcard), int(warps_per_query), ep,
-                         int(entry_cells), cp)
+                         int(entry_cells), cp, int(tile_rows))
 
 
 def nhq_search(index, queries, query_attributes, k, ef, ids, dists=None, chi=None, status=None,
@@ -415,12 +469,13 @@ def nhq_search(index, queries, query_attributes, k, ef, ids, dists=None, chi=Non
                hash_bits=0, vec_dtype=VEC_F32, rerank=0, seed_mode=SEED_RANDOM, seeds=None,
                stop_model=None, stop_threshold=0.5, stop_min=0, stop_every=1,
                stream=None, wildcard=0, warps_per_query=0, entry_model=None, entry_cells=0,
-               cells_out=None) -> None:
+               cells_out=None, tile_rows=0) -> None:
     Q, d = _shape(queries)
     m = _shape(query_attributes)[1]
     p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
                        seed_mode, seeds, Q, stop_model, stop_threshold, stop_min, stop_every,
-                       wildcard, warps_per_query, entry_model, entry_cells, cells_out)
+                       wildcard, warps_per_query, entry_model, entry_cells, cells_out,
+                       tile_rows)
     _check(load_library().nhq_search(
         index, _ptr(queries, np.float32, (Q, d), "queries"),
         _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, ef, C.byref(p),
@@ -434,12 +489,13 @@ def nhq_search_batched(index, queries, query_attributes, k_arr, ef_arr, k_max, i
                        chi=None, status=None, ndc=None, expansions=None, h=1, seed=0,
                        max_iters=0, warps_per_block=0, hash_bits=0, vec_dtype=VEC_F32, rerank=0,
                        seed_mode=SEED_RANDOM, seeds=None, stream=None, wildcard=0,
-                       warps_per_query=0, entry_model=None, entry_cells=0) -> None:
+                       warps_per_query=0, entry_model=None, entry_cells=0,
+                       tile_rows=0) -> None:
     Q, d = _shape(queries)
     m = _shape(query_attributes)[1]
     p = _search_params(seed, h, max_iters, warps_per_block, hash_bits, vec_dtype, rerank,
                        seed_mode, seeds, Q, wildcard=wildcard, warps_per_query=warps_per_query,
-                       entry_model=entry_model, entry_cells=entry_cells)
+                       entry_model=entry_model, entry_cells=entry_cells, tile_rows=tile_rows)
     _check(load_library().nhq_search_batched(
         index, _ptr(queries, np.float32, (Q, d), "queries"),
         _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q,
@@ -484,6 +540,27 @@ def nhq_autotune_search(index, queries, query_attributes, k, ef, ids, h=1, seed=
     if return_wpq:
         return p.warps_per_query, p.warps_per_block, p.hash_bits, ms.value
     return p.warps_per_block, p.hash_bits, ms.value
+
+
+def nhq_autotune(index, queries, query_attributes, k, ef, ids, stream=None, **kw):
+    """nhq_autotune_search returning every tuned field: dict(warps_per_query, tile_rows,
+    warps_per_block, hash_bits, ms); ``kw`` as nhq_search (seed, h, vec_dtype, rerank,
+    seed_mode, entry_model, entry_cells, stop_model, ...)."""
+    Q, d = _shape(queries)
+    m = _shape(query_attributes)[1]
+    p = _search_params(kw.get("seed", 0), kw.get("h", 1), kw.get("max_iters", 0), 0, 0,
+                       kw.get("vec_dtype", VEC_F32), kw.get("rerank", 0),
+                       kw.get("seed_mode", SEED_RANDOM), None, Q, kw.get("stop_model"),
+                       kw.get("stop_threshold", 0.5), kw.get("stop_min", 0),
+                       kw.get("stop_every", 1), kw.get("wildcard", 0), 0,
+                       kw.get("entry_model"), kw.get("entry_cells", 0))
+    ms = C.c_float(0.0)
+    _check(load_library().nhq_autotune_search(
+        index, _ptr(queries, np.float32, (Q, d), "queries"),
+        _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q, k, ef, C.byref(p),
+        _ptr(ids, np.uint32, (Q, k), "ids"), C.byref(ms), _stream(stream)))
+    return dict(warps_per_query=p.warps_per_query, tile_rows=p.tile_rows,
+                warps_per_block=p.warps_per_block, hash_bits=p.hash_bits, ms=ms.value)
 
 
 def nhq_index_build_cells(index, E, stream=None) -> None:
@@ -567,7 +644,8 @@ def nhq_autotune_beam(index, queries, query_attributes, k, ef_list, truth, targe
         float(target), C.byref(p), _ptr(ids, np.uint32, (Q, k), "ids"), C.byref(ef),
         C.byref(rec), C.byref(ms), _stream(stream)))
     return dict(ef=ef.value, recall=rec.value, warps_per_query=p.warps_per_query,
-                warps_per_block=p.warps_per_block, hash_bits=p.hash_bits, ms=ms.value)
+                tile_rows=p.tile_rows, warps_per_block=p.warps_per_block,
+                hash_bits=p.hash_bits, ms=ms.value)
 
 
 class SearchGraph:
@@ -680,6 +758,8 @@ class Index:
 
     @classmethod
     def create(cls, vectors, attributes, weights=None, stream=None):
+        if _vec_dtype_of(vectors)[0] != F32:
+            return cls(nhq_index_create_typed(vectors, attributes, weights, stream))
         return cls(nhq_index_create(vectors, attributes, weights, stream))
 
     @classmethod

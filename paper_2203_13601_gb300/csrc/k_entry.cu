@@ -16,10 +16,17 @@
 // of the entry model (NHQ_SEED_CELL_LEARNED).
 //
 // Entry model: a 2-layer perceptron, q (d values) -> x = s q -> 64 ReLU units -> E cell
-// logits, fp16 weights and f32 accumulation at inference (one warp per query, the
-// weights staged in shared memory when they fit), f32 master weights for training
-// (softmax cross-entropy against the cell of each training query's answer, Adam).
-// Parameters, one flat f32 vector: s | W1 [d][64] | b1 [64] | W2 [64][E] | b2 [E].
+// logits, fp16 weights and f32 accumulation at inference, f32 master weights for
+// training (softmax cross-entropy against the cell of each training query's answer,
+// Adam).  Parameters, one flat f32 vector: s | W1 [d][64] | b1 [64] | W2 [64][E] | b2 [E].
+//
+// Both cell rules score every cell of every query of the batch with one register-tiled
+// dense kernel (64 x 64 output tiles, k ascending per output in one fma chain, so the
+// seed pass and nhq_entry_forward produce the same bits): the learned rule runs the two
+// layers, the nearest rule scores q.c - |c|^2 / 2 against the transposed centroids (the
+// largest score is the nearest centroid; every product and sum is exact for integer
+// components, where the order equals the (delta, cell) order).  A warp per query then
+// takes the T best scores (ties to the smaller cell) and assembles the seeds.
 #include <cub/cub.cuh>
 
 #include "nhq_internal.cuh"
@@ -90,24 +97,105 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *a, int64_t n,
     return lo;
 }
 
-// ---- inference arithmetic, shared by the seed pass and nhq_entry_forward ----
-// hidden unit j: relu(b1[j] + sum_i W1[i][j] * (s q_i)), i ascending, f32 fmaf
-__device__ __forceinline__ float entry_hidden(const __half *W, const float *q, int d, float s,
-                                              int j, const EntryLayout &L) {
-    float z = __half2float(W[L.oB1 + j]);
-    for (int i = 0; i < d; ++i)
-        z = fmaf(__half2float(W[L.oW1 + (int64_t)i * EH + j]), __fmul_rn(s, q[i]), z);
-    return fmaxf(z, 0.f);
-}
-// logit o: b2[o] + sum_h W2[h][o] * hid[h], h ascending
-__device__ __forceinline__ float entry_logit(const __half *W, const float *hid, int o, int E,
-                                             const EntryLayout &L) {
-    float t = __half2float(W[L.oB2 + o]);
+// ---- inference: Y[n][M] = act(s A[n][K] B[K][M] + bias[M]), k ascending per output ----
+__device__ __forceinline__ float as_f32(float v) { return v; }
+__device__ __forceinline__ float as_f32(__half v) { return __half2float(v); }
+
+template <typename BT>
+__global__ void __launch_bounds__(256) dense_kernel(const float *__restrict__ A, int64_t n, int K,
+                                                    int64_t lda, const BT *__restrict__ B,
+                                                    const BT *__restrict__ bias, int M,
+                                                    const float *__restrict__ scale_ptr,
+                                                    int relu, float *__restrict__ Y) {
+    __shared__ float As[32][65];  // [k][row], padded: the tile loads are free of conflicts
+    __shared__ float Bs[32][64];  // [k][col]
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = (int64_t)blockIdx.x * 64;
+    const int col0 = blockIdx.y * 64;
+    const float sc = scale_ptr != nullptr ? *scale_ptr : 1.f;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = (tid >> 5) + 8 * i, kk = tid & 31;
+            const int64_t gr = row0 + r;
+            const int gk = k0 + kk;
+            As[kk][r] = (gr < n && gk < K) ? __fmul_rn(sc, A[gr * lda + gk]) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int kk = (tid >> 6) + 4 * i, c = tid & 63;
+            const int gk = k0 + kk, gc = col0 + c;
+            Bs[kk][c] = (gk < K && gc < M) ? as_f32(B[(int64_t)gk * M + gc]) : 0.f;
+        }
+        __syncthreads();
 #pragma unroll 8
-    for (int h = 0; h < EH; ++h)
-        t = fmaf(__half2float(W[L.oW2 + (int64_t)h * E + o]), hid[h], t);
-    return t;
+        for (int kk = 0; kk < 32; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = As[kk][ty * 4 + i];
+                b[i] = Bs[kk][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = row0 + ty * 4 + i;
+        if (r >= n)
+            continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = col0 + tx * 4 + j;
+            if (c >= M)
+                continue;
+            float v = __fadd_rn(acc[i][j], as_f32(bias[c]));
+            if (relu)
+                v = fmaxf(v, 0.f);
+            Y[r * M + c] = v;
+        }
+    }
 }
+
+template <typename BT>
+cudaError_t launch_dense(const float *A, int64_t n, int K, int64_t lda, const BT *B,
+                         const BT *bias, int M, const float *scale_ptr, int relu, float *Y,
+                         cudaStream_t s) {
+    if (n <= 0)
+        return cudaSuccess;
+    const int64_t gx = (n + 63) / 64;
+    if (gx > 0x7FFFFFFF)
+        return cudaErrorInvalidValue;
+    dense_kernel<BT><<<dim3((unsigned)gx, (unsigned)((M + 63) / 64)), 256, 0, s>>>(
+        A, n, K, lda, B, bias, M, scale_ptr, relu, Y);
+    return cudaGetLastError();
+}
+
+// centroid columns for the nearest rule: cT[i][j] = cent[j][i], nh[j] = -|c_j|^2 / 2
+__global__ void centroid_columns_kernel(const float *__restrict__ cent, int xstride, int d, int E,
+                                        float *__restrict__ cT, float *__restrict__ nh) {
+    const int j = blockIdx.x;
+    for (int i = threadIdx.x; i < d; i += blockDim.x)
+        cT[(int64_t)i * E + j] = cent[(int64_t)j * xstride + i];
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int i = 0; i < d; ++i)
+            s = fmaf(cent[(int64_t)j * xstride + i], cent[(int64_t)j * xstride + i], s);
+        nh[j] = -0.5f * s;
+    }
+}
+
 // a key whose ascending order is descending logit, then ascending cell
 __device__ __forceinline__ unsigned long long logit_key(float t, int o) {
     uint32_t u = __float_as_uint(t);
@@ -133,9 +221,7 @@ struct CellSeedArgs {
     const unsigned long long *cell_key;              // (attribute word << 16 | cell), sorted
     const uint32_t *cell_id;                         // ids in that order
     int E, T;
-    const float *cent;                               // [E][xstride] (nearest mode)
-    const __half *w16;                               // entry model (learned mode) or null
-    const float *params;                             // its f32 parameters (params[0] = s)
+    const float *scores;                             // [nq][E], the larger the better
     int32_t *cells_out;                              // [nq][T] or null
     uint32_t *seeds;                                 // [nq][32]
     uint8_t *bucket;                                 // [nq] or null
@@ -143,28 +229,15 @@ struct CellSeedArgs {
 
 constexpr int kMaxT = 8;
 
-// One warp per query (persistent blocks of 8 warps).  Shared memory: the fp16 model when
-// it fits (`staged`), then per warp the query (d floats) and the hidden values (64).
-__global__ void __launch_bounds__(256) cell_seeds_kernel(CellSeedArgs c, int staged) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// One warp per query: the T best cells from the query's score row, then its seeds.
+__global__ void __launch_bounds__(256) cell_seeds_kernel(CellSeedArgs c) {
     const SearchArgs &a = c.a;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const EntryLayout L = entry_layout(a.d, c.E);
-    const __half *W = c.w16;
-    size_t off = 0;
-    if (c.w16 != nullptr && staged) {
-        __half *ws = reinterpret_cast<__half *>(smem);
-        for (int64_t i = threadIdx.x; i < L.total; i += blockDim.x)
-            ws[i] = c.w16[i];
-        W = ws;
-        off = ((size_t)L.total * sizeof(__half) + 15) & ~(size_t)15;
-    }
-    __syncthreads();
-    float *qs = reinterpret_cast<float *>(smem + off) + wib * (a.d + EH);
-    float *hid = qs + a.d;
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= a.nq)
+        return;
     const int T = c.T;
-    const float scale = c.w16 != nullptr ? c.params[0] : 0.f;
-    for (int64_t q = (int64_t)blockIdx.x * 8 + wib; q < a.nq; q += (int64_t)gridDim.x * 8) {
+    {
         uint32_t qhi;
         const uint32_t qa = pack_query_word(a.qattr + q * a.w.m, a.w, &qhi);
         const int ef = a.ef_arr ? a.ef_arr[q] : a.ef;
@@ -177,31 +250,13 @@ __global__ void __launch_bounds__(256) cell_seeds_kernel(CellSeedArgs c, int sta
             const int bits = 64 - __clzll((unsigned long long)P + 1ull);
             c.bucket[q] = (uint8_t)(bits >= 32 ? 0 : 32 - bits);
         }
-        // the chosen cells: the T smallest keys over the warp
-        for (int i = lane; i < a.d; i += 32)
-            qs[i] = a.Q[q * a.qstride + i];
-        __syncwarp();
         unsigned long long best[kMaxT];
 #pragma unroll
         for (int t = 0; t < kMaxT; ++t)
             best[t] = ~0ull;
-        if (c.w16 != nullptr) {
-            hid[lane] = entry_hidden(W, qs, a.d, scale, lane, L);
-            hid[lane + 32] = entry_hidden(W, qs, a.d, scale, lane + 32, L);
-            __syncwarp();
-            for (int o = lane; o < c.E; o += 32)
-                topT_insert(best, T, logit_key(entry_logit(W, hid, o, c.E, L), o));
-        } else {
-            for (int o = lane; o < c.E; o += 32) {
-                const float *cv = c.cent + (int64_t)o * a.xstride;
-                float s = 0.f;
-                for (int i = 0; i < a.d; ++i) {
-                    const float dd = __fsub_rn(qs[i], __ldg(cv + i));
-                    s = __fadd_rn(s, __fmul_rn(dd, dd));
-                }
-                topT_insert(best, T, ((unsigned long long)__float_as_uint(s) << 32) | (uint32_t)o);
-            }
-        }
+        const float *sr = c.scores + q * (int64_t)c.E;
+        for (int o = lane; o < c.E; o += 32)
+            topT_insert(best, T, logit_key(sr[o], o));
         int chosen[kMaxT];
         for (int t = 0; t < T; ++t) {
             unsigned long long m = best[0];
@@ -249,33 +304,7 @@ __global__ void __launch_bounds__(256) cell_seeds_kernel(CellSeedArgs c, int sta
             for (; j < 32; ++j)
                 row[j] = kNone;
         }
-        __syncwarp();
     }
-}
-
-// nhq_entry_forward: all E logits of n queries, the seed pass's arithmetic
-__global__ void __launch_bounds__(256) entry_forward_kernel(const __half *__restrict__ w16,
-                                                            const float *__restrict__ params,
-                                                            int d, int E,
-                                                            const float *__restrict__ Q,
-                                                            int64_t n, float *__restrict__ out) {
-    extern __shared__ __align__(16) float fsm[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const EntryLayout L = entry_layout(d, E);
-    float *qs = fsm + wib * (d + EH);
-    float *hid = qs + d;
-    const int64_t q = (int64_t)blockIdx.x * 8 + wib;
-    if (q >= n)
-        return;
-    const float scale = params[0];
-    for (int i = lane; i < d; i += 32)
-        qs[i] = Q[q * d + i];
-    __syncwarp();
-    hid[lane] = entry_hidden(w16, qs, d, scale, lane, L);
-    hid[lane + 32] = entry_hidden(w16, qs, d, scale, lane + 32, L);
-    __syncwarp();
-    for (int o = lane; o < E; o += 32)
-        out[q * E + o] = entry_logit(w16, hid, o, E, L);
 }
 
 __global__ void entry_to_half_kernel(const float *__restrict__ p, __half *__restrict__ h,
@@ -486,13 +515,12 @@ cudaError_t launch_entry_to_half(const float *params, int64_t n, __half *w16, cu
 
 cudaError_t launch_cell_seeds(const SearchArgs &a, const uint32_t *attr_sorted,
                               const uint32_t *id_sorted, const unsigned long long *cell_key,
-                              const uint32_t *cell_id, int E, int T, const float *cent,
-                              const __half *w16, const float *params, int32_t *cells_out,
-                              uint32_t *seeds, uint8_t *bucket, int sm_count, size_t smem_optin,
+                              const uint32_t *cell_id, int E, int T, const float *scores,
+                              int32_t *cells_out, uint32_t *seeds, uint8_t *bucket,
                               cudaStream_t s) {
     if (a.nq <= 0)
         return cudaSuccess;
-    if (T < 1 || T > kMaxT)
+    if (T < 1 || T > kMaxT || T > E)
         return cudaErrorInvalidValue;
     CellSeedArgs c;
     c.a = a;
@@ -502,42 +530,36 @@ cudaError_t launch_cell_seeds(const SearchArgs &a, const uint32_t *attr_sorted,
     c.cell_id = cell_id;
     c.E = E;
     c.T = T;
-    c.cent = cent;
-    c.w16 = w16;
-    c.params = params;
+    c.scores = scores;
     c.cells_out = cells_out;
     c.seeds = seeds;
     c.bucket = bucket;
-    const size_t per_warp = sizeof(float) * (size_t)(a.d + EH) * 8;
-    const size_t wbytes =
-        w16 ? (((size_t)entry_layout(a.d, E).total * sizeof(__half) + 15) & ~(size_t)15) : 0;
-    int staged = w16 != nullptr && wbytes + per_warp <= smem_optin;
-    const size_t smem = (staged ? wbytes : 0) + per_warp;
-    if (smem > smem_optin)
-        return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(cell_seeds_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
-    int64_t blocks = (a.nq + 7) / 8;
-    const int64_t cap = (int64_t)sm_count * (staged ? 1 : 4);  // one model copy per SM
-    if (blocks > cap)
-        blocks = cap;
-    cell_seeds_kernel<<<(unsigned)blocks, 256, smem, s>>>(c, staged);
+    cell_seeds_kernel<<<(unsigned)((a.nq + 7) / 8), 256, 0, s>>>(c);
     return cudaGetLastError();
 }
 
-cudaError_t launch_entry_forward(const __half *w16, const float *params, int d, int E,
-                                 const float *Q, int64_t n, float *out, cudaStream_t s) {
-    if (n <= 0)
-        return cudaSuccess;
-    const size_t smem = sizeof(float) * (size_t)(d + EH) * 8;
-    cudaError_t e = cudaFuncSetAttribute(entry_forward_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_centroid_columns(const float *cent, int xstride, int d, int E, float *cT,
+                                    float *nh, cudaStream_t s) {
+    centroid_columns_kernel<<<E, 128, 0, s>>>(cent, xstride, d, E, cT, nh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_entry_scores_nearest(const float *cT, const float *nh, int d, int E,
+                                        const float *Q, int64_t qstride, int64_t n, float *out,
+                                        cudaStream_t s) {
+    return launch_dense<float>(Q, n, d, qstride, cT, nh, E, nullptr, 0, out, s);
+}
+
+cudaError_t launch_entry_scores_learned(const __half *w16, const float *params, int d, int E,
+                                        const float *Q, int64_t qstride, int64_t n,
+                                        float *hidden, float *out, cudaStream_t s) {
+    const EntryLayout L = entry_layout(d, E);
+    cudaError_t e = launch_dense<__half>(Q, n, d, qstride, w16 + L.oW1, w16 + L.oB1, EH, params,
+                                         1, hidden, s);
     if (e != cudaSuccess)
         return e;
-    entry_forward_kernel<<<(unsigned)((n + 7) / 8), 256, smem, s>>>(w16, params, d, E, Q, n, out);
-    return cudaGetLastError();
+    return launch_dense<__half>(hidden, n, EH, EH, w16 + L.oW2, w16 + L.oB2, E, nullptr, 0, out,
+                                s);
 }
 
 cudaError_t launch_entry_labels(const uint32_t *ids, int k, int64_t n, const uint32_t *cell,

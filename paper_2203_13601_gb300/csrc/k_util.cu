@@ -128,6 +128,43 @@ cudaError_t launch_attr_max(const uint8_t *a, int64_t n, int m, unsigned int *ou
     return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void copy_rows_typed_kernel(const T *__restrict__ src, int64_t N, int d, int xstride,
+                                       float *__restrict__ dst, int *__restrict__ bad) {
+    int64_t total = N * (int64_t)xstride;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = i / xstride;
+        int c = (int)(i - r * xstride);
+        float v = c < d ? (float)src[r * d + c] : 0.0f;  // exact: every f16 / bf16 is an f32
+        if (!isfinite(v))
+            *bad = 1;
+        dst[i] = v;
+    }
+}
+
+__global__ void to_f16_kernel(const float *__restrict__ src, int64_t n, __half *__restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2half_rn(src[i]);
+}
+
+cudaError_t launch_copy_rows_typed(const void *src, int dtype, int64_t N, int d, int xstride,
+                                   float *dst, int *bad, cudaStream_t s) {
+    if (dtype == NHQ_F16)
+        copy_rows_typed_kernel<__half><<<grid_for(N * xstride), 256, 0, s>>>(
+            (const __half *)src, N, d, xstride, dst, bad);
+    else
+        copy_rows_typed_kernel<__nv_bfloat16><<<grid_for(N * xstride), 256, 0, s>>>(
+            (const __nv_bfloat16 *)src, N, d, xstride, dst, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_to_f16(const float *src, int64_t n, __half *dst, cudaStream_t s) {
+    to_f16_kernel<<<grid_for(n), 256, 0, s>>>(src, n, dst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_copy_rows(const float *src, int64_t N, int d, int xstride, float *dst,
                              int *bad, cudaStream_t s) {
     copy_rows_kernel<<<grid_for(N * xstride), 256, 0, s>>>(src, N, d, xstride, dst, bad);

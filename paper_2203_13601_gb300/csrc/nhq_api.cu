@@ -193,8 +193,11 @@ const char *nhq_last_error(void) { return g_err.c_str(); }
 
 int32_t nhq_version(void) { return 1; }
 
-nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
-                            int32_t m, nhq_weights w, void *stream, nhq_index **out) {
+static nhq_status index_create_impl(const void *vectors, int dtype, int64_t N, int32_t d,
+                                    const uint8_t *attributes, int32_t m, nhq_weights w,
+                                    void *stream, nhq_index **out) {
+    if (dtype != NHQ_F32 && dtype != NHQ_F16 && dtype != NHQ_BF16)
+        return fail(NHQ_ERR_ARG, "dtype must be NHQ_F32, NHQ_F16 or NHQ_BF16 (got %d)", dtype);
     if (out == nullptr)
         return fail(NHQ_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -231,7 +234,8 @@ nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const ui
     if ((e = cudaMalloc(&ix->attr, sizeof(uint32_t) * (size_t)N)) != cudaSuccess)
         return bail(fail_cuda(e, "cudaMalloc(attributes)"));
     Stager st;
-    int iv = st.add(vectors, sizeof(float) * (size_t)N * d, true);
+    const size_t esz = dtype == NHQ_F32 ? sizeof(float) : 2;
+    int iv = st.add(vectors, esz * (size_t)N * d, true);
     int ia = st.add(attributes, (size_t)N * m, true);
     nhq_status rs = st.commit(&g_stage.p, &g_stage.cap, s);
     if (rs != NHQ_OK)
@@ -241,9 +245,22 @@ nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const ui
     int *bad = reinterpret_cast<int *>(ix->scratch);
     if ((e = cudaMemsetAsync(bad, 0, sizeof(int), s)) != cudaSuccess)
         return bail(fail_cuda(e, "cudaMemsetAsync"));
-    if ((e = launch_copy_rows((const float *)st.dev(iv), N, d, ix->xstride, ix->X, bad, s)) !=
-        cudaSuccess)
+    e = dtype == NHQ_F32
+            ? launch_copy_rows((const float *)st.dev(iv), N, d, ix->xstride, ix->X, bad, s)
+            : launch_copy_rows_typed(st.dev(iv), dtype, N, d, ix->xstride, ix->X, bad, s);
+    if (e != cudaSuccess)
         return bail(fail_cuda(e, "copy_rows"));
+    // an f16 / bf16 input is also the scoring copy of its type (the round trip is exact)
+    if (dtype == NHQ_F16) {
+        if ((e = cudaMalloc(&ix->Xf, sizeof(__half) * (size_t)N * ix->xstride)) != cudaSuccess ||
+            (e = launch_rows_to_f16(ix->X, (int64_t)N * ix->xstride, ix->Xf, s)) != cudaSuccess)
+            return bail(fail_cuda(e, "f16 copy"));
+    } else if (dtype == NHQ_BF16) {
+        if ((e = cudaMalloc(&ix->Xh, sizeof(__nv_bfloat16) * (size_t)N * ix->xstride)) !=
+                cudaSuccess ||
+            (e = launch_rows_to_bf16(ix->X, (int64_t)N * ix->xstride, ix->Xh, s)) != cudaSuccess)
+            return bail(fail_cuda(e, "bf16 copy"));
+    }
     // the largest code of each attribute: the field widths for m > 4, and the codes an
     // open query position ranges over
     unsigned int *amax = reinterpret_cast<unsigned int *>((char *)ix->scratch + 128);
@@ -281,6 +298,17 @@ nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const ui
     return NHQ_OK;
 }
 
+nhq_status nhq_index_create(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
+                            int32_t m, nhq_weights w, void *stream, nhq_index **out) {
+    return index_create_impl(vectors, NHQ_F32, N, d, attributes, m, w, stream, out);
+}
+
+nhq_status nhq_index_create_typed(const void *vectors, int32_t dtype, int64_t N, int32_t d,
+                                  const uint8_t *attributes, int32_t m, nhq_weights w,
+                                  void *stream, nhq_index **out) {
+    return index_create_impl(vectors, dtype, N, d, attributes, m, w, stream, out);
+}
+
 void nhq_free(nhq_index *ix) {
     if (ix == nullptr)
         return;
@@ -288,6 +316,7 @@ void nhq_free(nhq_index *ix) {
     cudaFree(ix->X);
     cudaFree(ix->Xh);
     cudaFree(ix->X8);
+    cudaFree(ix->Xf);
     cudaFree(ix->attr);
     cudaFree(ix->nbr);
     cudaFree(ix->nbr_attr);
@@ -296,6 +325,8 @@ void nhq_free(nhq_index *ix) {
     cudaFree(ix->attr_sorted);
     cudaFree(ix->id_sorted);
     cudaFree(ix->cent);
+    cudaFree(ix->centT);
+    cudaFree(ix->cnh);
     cudaFree(ix->cell);
     cudaFree(ix->cell_key);
     cudaFree(ix->cell_id);
@@ -690,14 +721,18 @@ nhq_status nhq_index_build_cells(nhq_index *ix, int32_t E, void *stream) {
     cudaStream_t s = as_stream(stream);
     CK(cudaStreamSynchronize(s));
     cudaFree(ix->cent);
+    cudaFree(ix->centT);
+    cudaFree(ix->cnh);
     cudaFree(ix->cell);
     cudaFree(ix->cell_key);
     cudaFree(ix->cell_id);
-    ix->cent = nullptr;
+    ix->cent = ix->centT = ix->cnh = nullptr;
     ix->cell = ix->cell_id = nullptr;
     ix->cell_key = nullptr;
     ix->E = 0;
     CK(cudaMalloc(&ix->cent, sizeof(float) * (size_t)E * ix->xstride));
+    CK(cudaMalloc(&ix->centT, sizeof(float) * (size_t)E * ix->d));
+    CK(cudaMalloc(&ix->cnh, sizeof(float) * (size_t)E));
     CK(cudaMalloc(&ix->cell, sizeof(uint32_t) * (size_t)ix->N));
     CK(cudaMalloc(&ix->cell_key, sizeof(unsigned long long) * (size_t)ix->N));
     CK(cudaMalloc(&ix->cell_id, sizeof(uint32_t) * (size_t)ix->N));
@@ -726,6 +761,7 @@ nhq_status nhq_index_build_cells(nhq_index *ix, int32_t E, void *stream) {
     uint32_t *cattr = reinterpret_cast<uint32_t *>(ix->scratch);
     a.attr = cattr;
     CK(launch_gather_centroids(ix->X, ix->xstride, ix->N, E, ix->attr, ix->cent, cattr, s));
+    CK(launch_centroid_columns(ix->cent, ix->xstride, ix->d, E, ix->centT, ix->cnh, s));
     CK(launch_topk(a, (char *)ix->scratch + cattr_bytes, ix->scratch_bytes - cattr_bytes,
                    ix->sm_count, s));
     CKS(scratch(ix, cell_sort_scratch_bytes(ix->N)));
@@ -774,10 +810,15 @@ nhq_status nhq_entry_forward(const float *params, int32_t d, int32_t E, const fl
     cudaStream_t s = as_stream(stream);
     const int64_t np = entry_param_count(d, E);
     __half *w16 = nullptr;
+    float *hidden = nullptr;
     CK(cudaMallocAsync(&w16, sizeof(__half) * (size_t)np, s));
-    cudaError_t e = launch_entry_to_half(params, np, w16, s);
+    cudaError_t e = cudaMallocAsync(&hidden, sizeof(float) * NHQ_ENTRY_HIDDEN * (size_t)(n + 1), s);
     if (e == cudaSuccess)
-        e = launch_entry_forward(w16, params, d, E, queries, n, logits, s);
+        e = launch_entry_to_half(params, np, w16, s);
+    if (e == cudaSuccess)
+        e = launch_entry_scores_learned(w16, params, d, E, queries, d, n, hidden, logits, s);
+    if (hidden)
+        cudaFreeAsync(hidden, s);
     cudaFreeAsync(w16, s);
     if (e != cudaSuccess)
         return fail_cuda(e, "nhq_entry_forward");
@@ -865,8 +906,16 @@ nhq_status nhq_entry_labels(const nhq_index *ix, const uint32_t *ids, int32_t k,
 nhq_status nhq_build(const float *vectors, int64_t N, int32_t d, const uint8_t *attributes,
                      int32_t m, int32_t degree, nhq_weights w, const nhq_build_params *params,
                      void *stream, nhq_index **out) {
+    return nhq_build_typed(vectors, NHQ_F32, N, d, attributes, m, degree, w, params, stream, out);
+}
+
+nhq_status nhq_build_typed(const void *vectors, int32_t dtype, int64_t N, int32_t d,
+                           const uint8_t *attributes, int32_t m, int32_t degree, nhq_weights w,
+                           const nhq_build_params *params, void *stream, nhq_index **out) {
+    if (out == nullptr)
+        return fail(NHQ_ERR_ARG, "out is NULL");
     nhq_index *ix = nullptr;
-    CKS(nhq_index_create(vectors, N, d, attributes, m, w, stream, &ix));
+    CKS(nhq_index_create_typed(vectors, dtype, N, d, attributes, m, w, stream, &ix));
     nhq_status st = nhq_index_build(ix, degree, params, stream);
     if (st != NHQ_OK) {
         std::string keep = g_err;
@@ -1034,7 +1083,7 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     if (P.max_iters <= 0)
         P.max_iters = 1 << 20;
     if (P.vec_dtype != NHQ_VEC_F32 && P.vec_dtype != NHQ_VEC_BF16 &&
-        P.vec_dtype != NHQ_VEC_FP8E4M3)
+        P.vec_dtype != NHQ_VEC_FP8E4M3 && P.vec_dtype != NHQ_VEC_F16)
         return fail(NHQ_ERR_ARG, "unknown vec_dtype %d", P.vec_dtype);
     if (P.hash_bits < 0 || P.hash_bits > 16)
         return fail(NHQ_ERR_ARG, "hash_bits must be in 0..16");
@@ -1049,6 +1098,10 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
                     P.warps_per_query);
     if (P.warps_per_block != 0 && P.warps_per_block % P.warps_per_query != 0)
         return fail(NHQ_ERR_ARG, "warps_per_block must be a multiple of warps_per_query");
+    if (P.tile_rows == 0)
+        P.tile_rows = 2;
+    if (P.tile_rows != 2 && P.tile_rows != 4)
+        return fail(NHQ_ERR_ARG, "tile_rows must be 0, 2 or 4 (got %d)", P.tile_rows);
     if (P.seed_mode < NHQ_SEED_RANDOM || P.seed_mode > NHQ_SEED_CELL_LEARNED)
         return fail(NHQ_ERR_ARG, "unknown seed_mode %d", P.seed_mode);
     const bool cell_mode =
@@ -1086,6 +1139,10 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         CK(cudaMalloc(&ix->Xh, sizeof(__nv_bfloat16) * (size_t)ix->N * ix->xstride));
         CK(launch_rows_to_bf16(ix->X, (int64_t)ix->N * ix->xstride, ix->Xh, s));
     }
+    if (P.vec_dtype == NHQ_VEC_F16 && ix->Xf == nullptr) {
+        CK(cudaMalloc(&ix->Xf, sizeof(__half) * (size_t)ix->N * ix->xstride));
+        CK(launch_rows_to_f16(ix->X, (int64_t)ix->N * ix->xstride, ix->Xf, s));
+    }
     if (P.vec_dtype == NHQ_VEC_FP8E4M3 && ix->X8 == nullptr) {
         CK(cudaMalloc(&ix->X8, sizeof(__nv_fp8_e4m3) * (size_t)ix->N * ix->xstride));
         CK(launch_rows_to_fp8(ix->X, (int64_t)ix->N * ix->xstride, ix->X8, s));
@@ -1109,6 +1166,7 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     a.X = ix->X;
     a.Xh = ix->Xh;
     a.X8 = ix->X8;
+    a.Xf = ix->Xf;
     a.xstride = ix->xstride;
     a.d = ix->d;
     a.N = ix->N;
@@ -1141,6 +1199,7 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     a.warps_per_block = P.warps_per_block;
     a.hash_bits = P.hash_bits;
     a.wpq = P.warps_per_query;
+    a.tile_rows = P.tile_rows;
     // scratch: work counter and seeds | fp16 model | trace counter, hashes, final hashes
     const size_t off_w16 = (search_scratch_bytes(Q) + 255) & ~(size_t)255;
     const size_t off_tr = off_w16 + 2048;
@@ -1150,7 +1209,14 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
     const size_t entry_bytes = P.seed_mode == NHQ_SEED_CELL_LEARNED
                                    ? sizeof(__half) * (size_t)entry_param_count(ix->d, ix->E)
                                    : 0;
-    CKS(scratch(ix, off_entry + entry_bytes));
+    // the cell scores of every query [Q][E] and the model's hidden values [Q][64]
+    const size_t off_scores = (off_entry + entry_bytes + 255) & ~(size_t)255;
+    const size_t scores_bytes = cell_mode ? sizeof(float) * (size_t)Q * ix->E : 0;
+    const size_t off_hidden = (off_scores + scores_bytes + 255) & ~(size_t)255;
+    const size_t hidden_bytes = P.seed_mode == NHQ_SEED_CELL_LEARNED
+                                    ? sizeof(float) * (size_t)Q * NHQ_ENTRY_HIDDEN
+                                    : 0;
+    CKS(scratch(ix, off_hidden + hidden_bytes));
     a.stop_w16 = nullptr;
     a.stop_every = 0;
     a.stop_min = P.stop_min;
@@ -1194,14 +1260,19 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         } else if (P.seed_mode == NHQ_SEED_ATTRIBUTE_NEAR) {
             CK(launch_attribute_near_seeds(a, ix->attr_sorted, ix->id_sorted, sd, bucket, s));
         } else {
-            __half *ew16 = nullptr;
+            float *scores = reinterpret_cast<float *>((char *)ix->scratch + off_scores);
             if (P.seed_mode == NHQ_SEED_CELL_LEARNED) {
-                ew16 = reinterpret_cast<__half *>((char *)ix->scratch + off_entry);
+                __half *ew16 = reinterpret_cast<__half *>((char *)ix->scratch + off_entry);
+                float *hidden = reinterpret_cast<float *>((char *)ix->scratch + off_hidden);
                 CK(launch_entry_to_half(P.entry_model, entry_param_count(ix->d, ix->E), ew16, s));
+                CK(launch_entry_scores_learned(ew16, P.entry_model, ix->d, ix->E, a.Q, a.qstride,
+                                               Q, hidden, scores, s));
+            } else {
+                CK(launch_entry_scores_nearest(ix->centT, ix->cnh, ix->d, ix->E, a.Q, a.qstride,
+                                               Q, scores, s));
             }
             CK(launch_cell_seeds(a, ix->attr_sorted, ix->id_sorted, ix->cell_key, ix->cell_id,
-                                 ix->E, P.entry_cells, ix->cent, ew16, P.entry_model, P.cells_out,
-                                 sd, bucket, ix->sm_count, ix->smem_optin, s));
+                                 ix->E, P.entry_cells, scores, P.cells_out, sd, bucket, s));
         }
         CK(launch_query_order(bucket, Q, order, s));
         a.seeds = sd;
@@ -1293,7 +1364,7 @@ nhq_status nhq_autotune_search(const nhq_index *ix, const float *queries,
         return fail(NHQ_ERR_ARG, "nhq_autotune_search takes device pointers");
     cudaStream_t s = as_stream(stream);
     const int ef_cap = (ef + 31) & ~31;
-    int bmin = 10;
+    int bmin = 6;  // the smallest filter the rebuild rule allows, then three larger ones
     while ((1 << bmin) < 2 * (ef_cap + ix->R) + 64)
         ++bmin;
     cudaEvent_t e0, e1;
@@ -1303,12 +1374,14 @@ nhq_status nhq_autotune_search(const nhq_index *ix, const float *queries,
     float best_t = 1e30f;
     bool any = false;
     const int wpbs[3] = {2, 4, 8}, wpqs[3] = {1, 2, 4};
+    for (int ti = 0; ti < 2; ++ti)
     for (int qi = 0; qi < 3; ++qi) {
         for (int wi = 0; wi < 3; ++wi) {
             if (wpbs[wi] < wpqs[qi])
                 continue;
-            for (int b = bmin; b <= bmin + 2; ++b) {
+            for (int b = bmin; b <= bmin + 3 && b <= 16; ++b) {
                 nhq_search_params P = *params;
+                P.tile_rows = ti == 0 ? 2 : 4;
                 P.warps_per_query = wpqs[qi];
                 P.warps_per_block = wpbs[wi];
                 P.hash_bits = b;
@@ -1343,6 +1416,7 @@ nhq_status nhq_autotune_search(const nhq_index *ix, const float *queries,
     if (!any)
         return fail(NHQ_ERR_ARG, "no launch shape fits shared memory for ef = %d", ef);
     params->warps_per_query = best.warps_per_query;
+    params->tile_rows = best.tile_rows;
     params->warps_per_block = best.warps_per_block;
     params->hash_bits = best.hash_bits;
     if (best_ms)

@@ -160,6 +160,7 @@ struct nhq_index {
     float *X = nullptr;            // [N][xstride] f32
     __nv_bfloat16 *Xh = nullptr;   // [N][xstride] bf16 copy (built on first BF16 search)
     __nv_fp8_e4m3 *X8 = nullptr;   // [N][xstride] fp8 e4m3 copy (built on first FP8 search)
+    __half *Xf = nullptr;          // [N][xstride] f16 copy (built on first F16 search)
     nhq::AttrLayout layout;        // how attr packs the m codes
     uint32_t *attr = nullptr;      // [N] packed attributes
     uint32_t *nbr = nullptr;       // [N][R] adjacency, kNone padded
@@ -173,6 +174,8 @@ struct nhq_index {
     // the objects sorted by (attribute word, cell)
     int E = 0;
     float *cent = nullptr;                   // [E][xstride]
+    float *centT = nullptr;                  // [d][E] the centroids as columns
+    float *cnh = nullptr;                    // [E] -|c|^2 / 2
     uint32_t *cell = nullptr;                // [N]
     unsigned long long *cell_key = nullptr;  // [N] (attribute word << 16 | cell), ascending
     uint32_t *cell_id = nullptr;             // [N] object ids in that order
@@ -207,6 +210,10 @@ cudaError_t launch_copy_rows(const float *src, int64_t N, int d, int xstride, fl
                              int *nonfinite_flag, cudaStream_t s);
 cudaError_t launch_rows_to_bf16(const float *src, int64_t n_elems, __nv_bfloat16 *dst, cudaStream_t s);
 cudaError_t launch_rows_to_fp8(const float *src, int64_t n_elems, __nv_fp8_e4m3 *dst, cudaStream_t s);
+cudaError_t launch_rows_to_f16(const float *src, int64_t n_elems, __half *dst, cudaStream_t s);
+// rows of f16 / bf16 (dtype NHQ_F16 / NHQ_BF16) widened into the padded f32 layout
+cudaError_t launch_copy_rows_typed(const void *src, int dtype, int64_t N, int d, int xstride,
+                                   float *dst, int *nonfinite_flag, cudaStream_t s);
 cudaError_t launch_gather_nbr_attr(const uint32_t *nbr, const uint32_t *attr, int64_t N, int R,
                                    uint32_t *out, int *bad, cudaStream_t s);
 
@@ -267,6 +274,7 @@ struct SearchArgs {
     const float *X;
     const __nv_bfloat16 *Xh;
     const __nv_fp8_e4m3 *X8;
+    const __half *Xf;
     int xstride;
     int d;
     int64_t N;
@@ -312,6 +320,7 @@ struct SearchArgs {
     int warps_per_block;
     int hash_bits;
     int wpq;  // warps per query (1, 2 or 4): the group shares each expansion's distance passes
+    int tile_rows;  // rows per team of 8 lanes and distance pass (2 or 4)
 };
 size_t search_scratch_bytes(int64_t nq);
 cudaError_t launch_attribute_sort(const uint32_t *attr, int64_t N, uint32_t *attr_sorted,
@@ -367,6 +376,15 @@ cudaError_t launch_merge_topk(int P, int64_t Q, int k_in, int k_out, const uint3
                               cudaStream_t s);
 cudaError_t launch_search(SearchArgs a, void *scratch, int sm_count, size_t smem_optin,
                           cudaStream_t s);
+// the search launch for one scoring type (k_search_<type>.cu), sized by launch_search
+cudaError_t launch_search_f32(const SearchArgs &a, int ef_cap, int wpb, size_t smem,
+                              int sm_count, cudaStream_t s);
+cudaError_t launch_search_bf16(const SearchArgs &a, int ef_cap, int wpb, size_t smem,
+                               int sm_count, cudaStream_t s);
+cudaError_t launch_search_fp8(const SearchArgs &a, int ef_cap, int wpb, size_t smem,
+                              int sm_count, cudaStream_t s);
+cudaError_t launch_search_f16(const SearchArgs &a, int ef_cap, int wpb, size_t smem,
+                              int sm_count, cudaStream_t s);
 // k_entry.cu -- entry cells and the entry model
 int64_t entry_param_count(int d, int E);
 cudaError_t launch_gather_centroids(const float *X, int xstride, int64_t N, int E,
@@ -379,12 +397,21 @@ cudaError_t launch_cell_sort(const uint32_t *attr, const uint32_t *cell, int64_t
 cudaError_t launch_entry_to_half(const float *params, int64_t n, __half *w16, cudaStream_t s);
 cudaError_t launch_cell_seeds(const SearchArgs &a, const uint32_t *attr_sorted,
                               const uint32_t *id_sorted, const unsigned long long *cell_key,
-                              const uint32_t *cell_id, int E, int T, const float *cent,
-                              const __half *w16, const float *params, int32_t *cells_out,
-                              uint32_t *seeds, uint8_t *bucket, int sm_count, size_t smem_optin,
+                              const uint32_t *cell_id, int E, int T, const float *scores,
+                              int32_t *cells_out, uint32_t *seeds, uint8_t *bucket,
                               cudaStream_t s);
-cudaError_t launch_entry_forward(const __half *w16, const float *params, int d, int E,
-                                 const float *Q, int64_t n, float *out, cudaStream_t s);
+// cT[d][E] = the centroid rows as columns, nh[E] = -|c|^2 / 2
+cudaError_t launch_centroid_columns(const float *cent, int xstride, int d, int E, float *cT,
+                                    float *nh, cudaStream_t s);
+// out[n][E] = q.c - |c|^2 / 2 (largest for the nearest centroid)
+cudaError_t launch_entry_scores_nearest(const float *cT, const float *nh, int d, int E,
+                                        const float *Q, int64_t qstride, int64_t n, float *out,
+                                        cudaStream_t s);
+// out[n][E] = the entry model's logits (fp16 weights w16, the f32 scale params[0]);
+// hidden[n][64] is working memory
+cudaError_t launch_entry_scores_learned(const __half *w16, const float *params, int d, int E,
+                                        const float *Q, int64_t qstride, int64_t n,
+                                        float *hidden, float *out, cudaStream_t s);
 cudaError_t launch_entry_labels(const uint32_t *ids, int k, int64_t n, const uint32_t *cell,
                                 int64_t N, int32_t *labels, cudaStream_t s);
 size_t entry_train_chunk_bytes(int B, int E);

@@ -46,7 +46,7 @@ def test_autotune_keeps_results_and_returns_a_legal_shape(nhq, case):
                                                      tmp, seed=1, seed_mode=nhq.SEED_ATTRIBUTE,
                                                      return_wpq=True)
         assert wpq in (1, 2, 4) and wpb in (2, 4, 8) and wpb % wpq == 0
-        assert 10 <= bits <= 16 and ms > 0
+        assert 8 <= bits <= 16 and ms > 0  # from the legal minimum (224 slots here)
         ids1, g1, c1 = empty_out(w.nq, 10)
         nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 64, ids1, g1, c1, seed=1,
                        seed_mode=nhq.SEED_ATTRIBUTE, warps_per_block=wpb, hash_bits=bits,
@@ -184,3 +184,33 @@ def test_autotune_beam_takes_the_smallest_ef_reaching_the_target(nhq, case):
     assert abs(t["recall"] - rec[want]) < 1e-6
     assert t["warps_per_query"] in (1, 2, 4) and t["warps_per_block"] in (2, 4, 8)
     assert t["warps_per_block"] % t["warps_per_query"] == 0 and t["ms"] > 0
+
+
+@pytest.mark.parametrize("d", [32, 64, 128])
+@pytest.mark.parametrize("vec", [0, 1])
+def test_tile_rows_leave_results_unchanged(nhq, d, vec):
+    # four rows per team and pass (one pass for a typical expansion) against two: on
+    # integer components every sum is exact, so every output is the same; d = 32, 64 and
+    # 128 take the three fixed-chunk forms of the f32 rows
+    w = synth.int_valued(3000, 200, d, cards=(3, 5, 7), n_comp=20, seed=90 + d)
+    nbr, _, _ = O.build_graph(w.X, w.A, R=16, K=32, weights=CONST)
+    outs = {}
+    with nhq.Index.create(dev(w.X), dev(w.A), CONST) as ix:
+        nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
+        for tr in (2, 4):
+            for wpq in (1, 2):
+                ids, g, c = empty_out(w.nq, 10)
+                ndc = torch.empty(w.nq, dtype=torch.int32, device="cuda:0")
+                nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 48, ids, g, c, ndc=ndc,
+                               seed=3, seed_mode=nhq.SEED_ATTRIBUTE, vec_dtype=vec,
+                               tile_rows=tr, warps_per_query=wpq)
+                torch.cuda.synchronize()
+                outs[(tr, wpq)] = [t.cpu() for t in (ids, g, c, ndc)]
+        with pytest.raises(nhq.NHQError):
+            nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 48, ids, g, c, tile_rows=3)
+    for key, o in outs.items():
+        for a, b in zip(o, outs[(2, 1)]):
+            assert torch.equal(a, b), key
+    r = O.search(w.X, w.A, nbr, w.Qv, w.QA, 10, 48, seed=3, weights=CONST,
+                 seed_mode=O.SEED_ATTRIBUTE, vec_round=vec)
+    assert (ids_i64(outs[(4, 1)][0]) == r["ids"]).all()

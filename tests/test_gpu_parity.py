@@ -436,10 +436,10 @@ def test_search_given_seeds_exact(nhq, graph_case):
 
 
 # ------------------------------------------------------------------ reduced-precision scoring
-@pytest.mark.parametrize("vec,rnd", [(1, 1), (2, 2)])
+@pytest.mark.parametrize("vec,rnd", [(1, 1), (2, 2), (3, 3)])
 @pytest.mark.parametrize("rerank", [False, True])
 def test_search_reduced_precision_exact_on_integer_data(nhq, graph_case, vec, rnd, rerank):
-    # 0..255 components round to integers in bf16 and fp8 e4m3, so the scoring
+    # 0..255 components round to integers in bf16, fp8 e4m3 and f16, so the scoring
     # distances stay exact in f32 and the search must equal the oracle's bit for bit
     w, graphs = graph_case
     wts, nbr = graphs["const"]
@@ -461,7 +461,7 @@ def test_search_rerank_on_float_data(nhq):
     # be the exact f32 Gamma of the returned ids and ids equal up to near-ties
     w = synth.c3(N=3000, nq=40, d=96, cards=(2, 5), n_comp=20, seed=45)
     nbr, _, _ = O.build_graph(w.X, w.A, R=16, K=32, prec=O.F32)
-    for vec, rnd in ((1, O.ROUND_BF16), (2, O.ROUND_E4M3)):
+    for vec, rnd in ((1, O.ROUND_BF16), (2, O.ROUND_E4M3), (3, O.ROUND_F16)):
         ref = O.search(w.X, w.A, nbr, w.Qv, w.QA, 10, 48, seed=2, vec_round=rnd, rerank=True)
         with _index(nhq, w) as ix:
             nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
