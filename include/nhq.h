@@ -172,9 +172,10 @@ typedef struct nhq_search_params {
                                 NULL                                                          */
     int32_t tile_rows;       /* rows each team of 8 lanes evaluates per distance pass: 0 or 2
                                 (8 rows per warp and pass), 4 (16 rows: an expansion's
-                                candidates in one pass, fewer resident warps); rows wider than
-                                the fixed-chunk forms always take 2; results are the same on
-                                integer components, within f32 rounding otherwise         */
+                                candidates in one pass, fewer resident warps; one warp per
+                                query only); rows wider than the fixed-chunk forms always
+                                take 2; results are the same on integer components, within
+                                f32 rounding otherwise                                     */
 } nhq_search_params;
 
 typedef struct nhq_index nhq_index;
@@ -498,6 +499,14 @@ nhq_status nhq_autotune_search(const nhq_index *index, const float *queries,
                                nhq_search_params *params, uint32_t *ids, float *best_ms,
                                void *stream);
 
+/* nhq_autotune_search for a heterogeneous batch: the same launch shapes, timed on
+ * nhq_search_batched with these k_arr / ef_arr (device). */
+nhq_status nhq_autotune_batched(const nhq_index *index, const float *queries,
+                                const uint8_t *query_attributes, int64_t Q,
+                                const int32_t *k_arr, const int32_t *ef_arr, int32_t k_max,
+                                nhq_search_params *params, uint32_t *ids, float *best_ms,
+                                void *stream);
+
 /*
  * Beam-width tuning (a project addition): the smallest ef of ef_list[0..n_ef)
  * (ascending, each in k..1024) whose recall against truth[Q][k] reaches `target`, then
@@ -536,6 +545,16 @@ nhq_status nhq_search_graph_create(const nhq_index *index, const float *queries,
                                    const uint8_t *query_attributes, int64_t Q, int32_t k,
                                    int32_t ef, const nhq_search_params *params, uint32_t *ids,
                                    float *dists, uint8_t *chi, nhq_search_graph **out);
+/* The captured form of nhq_search_batched.  k_arr / ef_arr are checked once, here, and
+ * the pool is sized for the largest ef; between launches the caller may rewrite the
+ * query buffers and the per-query values in place, keeping every k in 1..k_max and every
+ * ef in k..(the largest ef at creation).  Device pointers only. */
+nhq_status nhq_search_graph_create_batched(const nhq_index *index, const float *queries,
+                                           const uint8_t *query_attributes, int64_t Q,
+                                           const int32_t *k_arr, const int32_t *ef_arr,
+                                           int32_t k_max, const nhq_search_params *params,
+                                           uint32_t *ids, float *dists, uint8_t *chi,
+                                           nhq_search_graph **out);
 nhq_status nhq_search_graph_launch(nhq_search_graph *graph, void *stream);
 void nhq_search_graph_free(nhq_search_graph *graph);
 

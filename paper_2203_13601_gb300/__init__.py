@@ -32,7 +32,8 @@ __all__ = [
     "nhq_mlp_train", "MLP_INPUTS", "MLP_HIDDEN", "MLP_PARAMS", "nhq_autotune_search",
     "nhq_search_graph_create", "nhq_search_graph_launch", "nhq_search_graph_free",
     "nhq_merge_topk", "nhq_postfilter", "nhq_knn_nndescent", "nhq_index_build_nsw",
-    "nhq_autotune_beam", "nhq_recall", "nhq_autotune", "SEED_CELL_NEAREST", "SEED_CELL_LEARNED",
+    "nhq_autotune_beam", "nhq_recall", "nhq_autotune", "nhq_autotune_batched",
+    "nhq_search_graph_create_batched", "SEED_CELL_NEAREST", "SEED_CELL_LEARNED",
     "ENTRY_HIDDEN", "nhq_index_build_cells", "nhq_index_cells", "nhq_entry_param_count",
     "nhq_entry_forward", "nhq_entry_grad", "nhq_entry_train", "nhq_entry_labels",
 ]
@@ -146,6 +147,11 @@ def load_library():
             "nhq_entry_labels": (S, [P, P, i32, i64, P, P]),
             "nhq_search_graph_create": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P,
                                             P, P, C.POINTER(P)]),
+            "nhq_search_graph_create_batched": (S, [P, P, P, i64, P, P, i32,
+                                                    C.POINTER(_SearchParams), P, P, P,
+                                                    C.POINTER(P)]),
+            "nhq_autotune_batched": (S, [P, P, P, i64, P, P, i32, C.POINTER(_SearchParams), P,
+                                         C.POINTER(C.c_float), P]),
             "nhq_search_graph_launch": (S, [P, P]),
             "nhq_search_graph_free": (None, [P]),
             "nhq_search_trace": (S, [P, P, P, i64, i32, i32, C.POINTER(_SearchParams), P, P, P,
@@ -615,6 +621,26 @@ def nhq_entry_labels(index, ids, labels, stream=None) -> None:
                                            _stream(stream)))
 
 
+def nhq_autotune_batched(index, queries, query_attributes, k_arr, ef_arr, k_max, ids,
+                         stream=None, **kw):
+    """nhq_autotune_search for a heterogeneous batch (device k_arr / ef_arr); returns
+    dict(warps_per_query, tile_rows, warps_per_block, hash_bits, ms)."""
+    Q, d = _shape(queries)
+    m = _shape(query_attributes)[1]
+    p = _search_params(kw.get("seed", 0), kw.get("h", 1), kw.get("max_iters", 0), 0, 0,
+                       kw.get("vec_dtype", VEC_F32), kw.get("rerank", 0),
+                       kw.get("seed_mode", SEED_RANDOM), None, Q,
+                       wildcard=kw.get("wildcard", 0))
+    ms = C.c_float(0.0)
+    _check(load_library().nhq_autotune_batched(
+        index, _ptr(queries, np.float32, (Q, d), "queries"),
+        _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q,
+        _ptr(k_arr, np.int32, (Q,), "k_arr"), _ptr(ef_arr, np.int32, (Q,), "ef_arr"), k_max,
+        C.byref(p), _ptr(ids, np.uint32, (Q, k_max), "ids"), C.byref(ms), _stream(stream)))
+    return dict(warps_per_query=p.warps_per_query, tile_rows=p.tile_rows,
+                warps_per_block=p.warps_per_block, hash_bits=p.hash_bits, ms=ms.value)
+
+
 def nhq_recall(ids, truth, stream=None) -> float:
     """Mean recall (Eq. 3) of ids [Q, k] against truth [Q, k_truth] (device uint32,
     0xFFFFFFFF entries of truth not counted; queries without truth skipped)."""
@@ -659,7 +685,8 @@ class SearchGraph:
                                  kw.get("warps_per_block", 0), kw.get("hash_bits", 0),
                                  kw.get("vec_dtype", VEC_F32), kw.get("rerank", 0),
                                  kw["seed_mode"], None, Q, wildcard=kw.get("wildcard", 0),
-                                 warps_per_query=kw.get("warps_per_query", 0))
+                                 warps_per_query=kw.get("warps_per_query", 0),
+                                 tile_rows=kw.get("tile_rows", 0))
         out = C.c_void_p()
         _check(load_library().nhq_search_graph_create(
             index, _ptr(queries, np.float32, (Q, d), "queries"),
@@ -686,6 +713,35 @@ class SearchGraph:
 
 def nhq_search_graph_create(*a, **kw):
     return SearchGraph(*a, **kw)
+
+
+class BatchedSearchGraph(SearchGraph):
+    """A captured nhq_search_batched call (nhq_search_graph_create_batched)."""
+
+    def __init__(self, index, queries, query_attributes, k_arr, ef_arr, k_max, ids,
+                 dists=None, chi=None, **kw):
+        Q, d = _shape(queries)
+        m = _shape(query_attributes)[1]
+        self._p = _search_params(kw.get("seed", 0), kw.get("h", 1), kw.get("max_iters", 0),
+                                 kw.get("warps_per_block", 0), kw.get("hash_bits", 0),
+                                 kw.get("vec_dtype", VEC_F32), kw.get("rerank", 0),
+                                 kw.get("seed_mode", SEED_RANDOM), None, Q,
+                                 wildcard=kw.get("wildcard", 0),
+                                 warps_per_query=kw.get("warps_per_query", 0),
+                                 tile_rows=kw.get("tile_rows", 0))
+        out = C.c_void_p()
+        _check(load_library().nhq_search_graph_create_batched(
+            index, _ptr(queries, np.float32, (Q, d), "queries"),
+            _ptr(query_attributes, np.uint8, (Q, m), "query_attributes"), Q,
+            _ptr(k_arr, np.int32, (Q,), "k_arr"), _ptr(ef_arr, np.int32, (Q,), "ef_arr"),
+            k_max, C.byref(self._p), _ptr(ids, np.uint32, (Q, k_max), "ids"),
+            _ptr(dists, np.float32, (Q, k_max), "dists"), _ptr(chi, np.uint8, (Q, k_max), "chi"),
+            C.byref(out)))
+        self.handle = out.value
+
+
+def nhq_search_graph_create_batched(*a, **kw):
+    return BatchedSearchGraph(*a, **kw)
 
 
 def nhq_search_graph_launch(graph, stream=None):

@@ -486,11 +486,11 @@ __device__ __forceinline__ void group_bar(int grp, int wpq) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(32 * wpq) : "memory");
 }
 
-template <typename VT, int CPL, bool EXACT, int RPT>
+template <typename VT, int CPL, bool EXACT, int RPT, bool GROUP>
 __device__ __forceinline__ void group_eval(const VT *X, int xstride, const float *qv,
                                            const uint32_t *cid, float *d2s, int cnt, int lane,
                                            int wpq, int grp, volatile int *ctl, int rows_f32) {
-    if (wpq == 1) {
+    if (!GROUP) {
         eval_dist2<VT, CPL, EXACT, RPT>(X, xstride, qv, cid, d2s, cnt, lane);
         return;
     }
@@ -539,13 +539,15 @@ __host__ __device__ inline WarpLayout warp_layout(int ef_cap, int hash_bits, int
 // three blocks of eight warps at d = 960), so the f32 form of that variant may use the
 // registers of three blocks (85 a thread) and keep twice the row loads in flight; the
 // narrower types keep four blocks' worth, which a smaller visited filter can fill.
-template <typename VT, int CPL, bool EXACT, bool TWO, int RPT>
+// GROUP: the form with several warps per query (wpq > 1); the one-warp form compiles
+// without the group's bookkeeping.
+template <typename VT, int CPL, bool EXACT, bool TWO, int RPT, bool GROUP>
 __global__ void __launch_bounds__(
     256, ((CPL == 0 && std::is_same<VT, float>::value) || RPT == 4) ? 3 : 4) search_kernel(SearchArgs a, const VT *__restrict__ Xs,
                                                         int ef_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int wpq = a.wpq, grp = wib / wpq, wig = wib % wpq;
+    const int wpq = GROUP ? a.wpq : 1, grp = GROUP ? wib / wpq : wib, wig = GROUP ? wib % wpq : 0;
     const WarpLayout L = warp_layout(ef_cap, a.hash_bits, a.xstride);
     unsigned char *base = smem + grp * L.total;
     unsigned long long *pool = reinterpret_cast<unsigned long long *>(base + L.pool);
@@ -566,7 +568,7 @@ __global__ void __launch_bounds__(
             w16[i] = a.stop_w16[i];
         __syncthreads();
     }
-    if (wig != 0) {  // a helper warp of the group: distance passes only
+    if (GROUP && wig != 0) {  // a helper warp of the group: distance passes only
         for (;;) {
             group_bar(grp, wpq);
             const int cnt = ctl[0];
@@ -628,8 +630,8 @@ __global__ void __launch_bounds__(
             hcount += cnt;
             ndc += cnt;
             if (cnt > 0) {
-                group_eval<VT, CPL, EXACT, RPT>(Xs, a.xstride, qv, cid, d2s, cnt, lane, wpq,
-                                                grp, ctl, 0);
+                group_eval<VT, CPL, EXACT, RPT, GROUP>(Xs, a.xstride, qv, cid, d2s, cnt, lane,
+                                                       wpq, grp, ctl, 0);
                 merge_round(pool, n, ef, candidate_key(lane, cnt, d2s, cid, cchi, a.w), sorted32,
                             lane);
             }
@@ -660,8 +662,8 @@ __global__ void __launch_bounds__(
             hcount += cnt;
             ndc += cnt;
             if (cnt > 0) {
-                group_eval<VT, CPL, EXACT, RPT>(Xs, a.xstride, qv, cid, d2s, cnt, lane, wpq,
-                                                grp, ctl, 0);
+                group_eval<VT, CPL, EXACT, RPT, GROUP>(Xs, a.xstride, qv, cid, d2s, cnt, lane,
+                                                       wpq, grp, ctl, 0);
                 merge_round(pool, n, ef, candidate_key(lane, cnt, d2s, cid, cchi, a.w), sorted32,
                             lane);
             }
@@ -794,8 +796,8 @@ __global__ void __launch_bounds__(
             ndc += cnt;
             unsigned long long k0 = kInfKey, k1 = kInfKey;
             if (cnt > 0) {
-                group_eval<VT, CPL, EXACT, RPT>(Xs, a.xstride, qv, cid, d2s, cnt, lane, wpq,
-                                                grp, ctl, 0);
+                group_eval<VT, CPL, EXACT, RPT, GROUP>(Xs, a.xstride, qv, cid, d2s, cnt, lane,
+                                                       wpq, grp, ctl, 0);
                 k0 = filter_key(candidate_key(lane, cnt, d2s, cid, cchi, a.w), pool, n, ef,
                                 rebuilt);
                 if (TWO)
@@ -856,8 +858,8 @@ __global__ void __launch_bounds__(
                     cchi[j] = chi_packed(a.attr[id], qa, ahi, alo);
                 }
                 __syncwarp();
-                group_eval<float, 0, false, 2>(a.X, a.xstride, qv, cid, d2s, cb, lane, wpq,
-                                               grp, ctl, 1);
+                group_eval<float, 0, false, 2, GROUP>(a.X, a.xstride, qv, cid, d2s, cb, lane,
+                                                      wpq, grp, ctl, 1);
                 for (int j = lane; j < cb; j += 32)
                     pool[b0 + j] = candidate_key(j, cb, d2s, cid, cchi, a.w);
                 __syncwarp();
@@ -915,7 +917,7 @@ __global__ void __launch_bounds__(
         }
         __syncwarp();
     }
-    if (wpq > 1) {  // no query left: release the helper warps
+    if (GROUP) {  // no query left: release the helper warps
         if (lane == 0)
             ctl[0] = -1;
         __syncwarp();
@@ -935,10 +937,10 @@ int auto_hash_bits(int ef_cap, int R) {
     return bits;
 }
 
-template <typename VT, int CPL, bool EXACT, bool TWO, int RPT = 2>
-cudaError_t launch_variant(const SearchArgs &a, const VT *X, int ef_cap, int wpb, size_t smem,
-                           int sm_count, cudaStream_t s) {
-    auto kfn = search_kernel<VT, CPL, EXACT, TWO, RPT>;
+template <typename VT, int CPL, bool EXACT, bool TWO, int RPT, bool GROUP>
+cudaError_t launch_kernel(const SearchArgs &a, const VT *X, int ef_cap, int wpb, size_t smem,
+                          int sm_count, cudaStream_t s) {
+    auto kfn = search_kernel<VT, CPL, EXACT, TWO, RPT, GROUP>;
     cudaError_t e =
         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
@@ -956,6 +958,18 @@ cudaError_t launch_variant(const SearchArgs &a, const VT *X, int ef_cap, int wpb
         blocks = need;
     kfn<<<(unsigned)blocks, 32 * wpb, smem, s>>>(a, X, ef_cap);
     return cudaGetLastError();
+}
+
+// one warp per query, or a group (four rows per team take one warp per query only)
+template <typename VT, int CPL, bool EXACT, bool TWO, int RPT = 2>
+cudaError_t launch_variant(const SearchArgs &a, const VT *X, int ef_cap, int wpb, size_t smem,
+                           int sm_count, cudaStream_t s) {
+    if (a.wpq == 1)
+        return launch_kernel<VT, CPL, EXACT, TWO, RPT, false>(a, X, ef_cap, wpb, smem,
+                                                               sm_count, s);
+    if (RPT != 2)
+        return cudaErrorInvalidValue;
+    return launch_kernel<VT, CPL, EXACT, TWO, 2, true>(a, X, ef_cap, wpb, smem, sm_count, s);
 }
 
 template <typename VT, bool TWO>

@@ -1102,6 +1102,8 @@ static nhq_status search_common(const nhq_index *cix, const float *queries,
         P.tile_rows = 2;
     if (P.tile_rows != 2 && P.tile_rows != 4)
         return fail(NHQ_ERR_ARG, "tile_rows must be 0, 2 or 4 (got %d)", P.tile_rows);
+    if (P.tile_rows == 4 && P.warps_per_query != 1)
+        return fail(NHQ_ERR_ARG, "tile_rows 4 takes one warp per query");
     if (P.seed_mode < NHQ_SEED_RANDOM || P.seed_mode > NHQ_SEED_CELL_LEARNED)
         return fail(NHQ_ERR_ARG, "unknown seed_mode %d", P.seed_mode);
     const bool cell_mode =
@@ -1354,15 +1356,14 @@ nhq_status nhq_search_batched(const nhq_index *ix, const float *queries,
                          params, ids, dists, chi, status, ndc, expansions, stream);
 }
 
-nhq_status nhq_autotune_search(const nhq_index *ix, const float *queries,
-                               const uint8_t *query_attributes, int64_t Q, int32_t k, int32_t ef,
-                               nhq_search_params *params, uint32_t *ids, float *best_ms,
-                               void *stream) {
-    if (ix == nullptr || params == nullptr || ids == nullptr || Q < 1)
-        return fail(NHQ_ERR_ARG, "index, params, ids and Q >= 1 are required");
-    if (!is_device_ptr(queries) || !is_device_ptr(query_attributes) || !is_device_ptr(ids))
-        return fail(NHQ_ERR_ARG, "nhq_autotune_search takes device pointers");
-    cudaStream_t s = as_stream(stream);
+}  // extern "C"
+
+// Times run(P) for every launch shape (rows per team, warps per query, warps per block,
+// visited-filter size from the smallest legal one) with CUDA events, one warm-up and
+// three timed calls each, and writes the fastest shape into params.
+template <typename Run>
+static nhq_status autotune_shapes(const nhq_index *ix, int ef, nhq_search_params *params,
+                                  float *best_ms, cudaStream_t s, Run run) {
     const int ef_cap = (ef + 31) & ~31;
     int bmin = 6;  // the smallest filter the rebuild rule allows, then three larger ones
     while ((1 << bmin) < 2 * (ef_cap + ix->R) + 64)
@@ -1373,40 +1374,39 @@ nhq_status nhq_autotune_search(const nhq_index *ix, const float *queries,
     nhq_search_params best = *params;
     float best_t = 1e30f;
     bool any = false;
-    const int wpbs[3] = {2, 4, 8}, wpqs[3] = {1, 2, 4};
-    for (int ti = 0; ti < 2; ++ti)
-    for (int qi = 0; qi < 3; ++qi) {
-        for (int wi = 0; wi < 3; ++wi) {
-            if (wpbs[wi] < wpqs[qi])
-                continue;
-            for (int b = bmin; b <= bmin + 3 && b <= 16; ++b) {
-                nhq_search_params P = *params;
-                P.tile_rows = ti == 0 ? 2 : 4;
-                P.warps_per_query = wpqs[qi];
-                P.warps_per_block = wpbs[wi];
-                P.hash_bits = b;
-                nhq_status st = nhq_search(ix, queries, query_attributes, Q, k, ef, &P, ids,
-                                           nullptr, nullptr, nullptr, nullptr, nullptr, stream);
-                if (st == NHQ_ERR_ARG)
-                    continue;  // this shape does not fit shared memory
-                if (st != NHQ_OK) {
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
-                    return st;
-                }
-                CK(cudaEventRecord(e0, s));
-                for (int r = 0; r < 3; ++r)
-                    nhq_search(ix, queries, query_attributes, Q, k, ef, &P, ids, nullptr,
-                               nullptr, nullptr, nullptr, nullptr, stream);
-                CK(cudaEventRecord(e1, s));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                ms /= 3.f;
-                if (ms < best_t) {
-                    best_t = ms;
-                    best = P;
-                    any = true;
+    const int wpbs[3] = {2, 4, 8}, wpqs[3] = {1, 2, 4}, rows[2] = {2, 4};
+    for (int tr : rows) {
+        for (int wpq : wpqs) {
+            for (int wpb : wpbs) {
+                if (wpb < wpq)
+                    continue;
+                for (int b = bmin; b <= bmin + 3 && b <= 16; ++b) {
+                    nhq_search_params P = *params;
+                    P.tile_rows = tr;
+                    P.warps_per_query = wpq;
+                    P.warps_per_block = wpb;
+                    P.hash_bits = b;
+                    nhq_status st = run(P);
+                    if (st == NHQ_ERR_ARG)
+                        continue;  // this shape does not fit shared memory
+                    if (st != NHQ_OK) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return st;
+                    }
+                    CK(cudaEventRecord(e0, s));
+                    for (int r = 0; r < 3; ++r)
+                        run(P);
+                    CK(cudaEventRecord(e1, s));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    ms /= 3.f;
+                    if (ms < best_t) {
+                        best_t = ms;
+                        best = P;
+                        any = true;
+                    }
                 }
             }
         }
@@ -1422,6 +1422,48 @@ nhq_status nhq_autotune_search(const nhq_index *ix, const float *queries,
     if (best_ms)
         *best_ms = best_t;
     return NHQ_OK;
+}
+
+extern "C" {
+
+nhq_status nhq_autotune_search(const nhq_index *ix, const float *queries,
+                               const uint8_t *query_attributes, int64_t Q, int32_t k, int32_t ef,
+                               nhq_search_params *params, uint32_t *ids, float *best_ms,
+                               void *stream) {
+    if (ix == nullptr || params == nullptr || ids == nullptr || Q < 1)
+        return fail(NHQ_ERR_ARG, "index, params, ids and Q >= 1 are required");
+    if (!is_device_ptr(queries) || !is_device_ptr(query_attributes) || !is_device_ptr(ids))
+        return fail(NHQ_ERR_ARG, "nhq_autotune_search takes device pointers");
+    return autotune_shapes(ix, ef, params, best_ms, as_stream(stream),
+                           [&](const nhq_search_params &P) {
+                               return nhq_search(ix, queries, query_attributes, Q, k, ef, &P,
+                                                 ids, nullptr, nullptr, nullptr, nullptr,
+                                                 nullptr, stream);
+                           });
+}
+
+nhq_status nhq_autotune_batched(const nhq_index *ix, const float *queries,
+                                const uint8_t *query_attributes, int64_t Q,
+                                const int32_t *k_arr, const int32_t *ef_arr, int32_t k_max,
+                                nhq_search_params *params, uint32_t *ids, float *best_ms,
+                                void *stream) {
+    if (ix == nullptr || params == nullptr || ids == nullptr || Q < 1 || k_arr == nullptr ||
+        ef_arr == nullptr)
+        return fail(NHQ_ERR_ARG, "index, params, ids, k_arr, ef_arr and Q >= 1 are required");
+    if (!is_device_ptr(queries) || !is_device_ptr(query_attributes) || !is_device_ptr(ids) ||
+        !is_device_ptr(k_arr) || !is_device_ptr(ef_arr))
+        return fail(NHQ_ERR_ARG, "nhq_autotune_batched takes device pointers");
+    std::vector<int32_t> he((size_t)Q);
+    cudaStream_t s = as_stream(stream);
+    CK(cudaMemcpyAsync(he.data(), ef_arr, sizeof(int32_t) * Q, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int ef_max = 1;
+    for (int32_t e : he)
+        ef_max = e > ef_max ? e : ef_max;
+    return autotune_shapes(ix, ef_max, params, best_ms, s, [&](const nhq_search_params &P) {
+        return nhq_search_batched(ix, queries, query_attributes, Q, k_arr, ef_arr, k_max, &P,
+                                  ids, nullptr, nullptr, nullptr, nullptr, nullptr, stream);
+    });
 }
 
 nhq_status nhq_recall(const uint32_t *ids, int32_t k, const uint32_t *truth, int32_t k_truth,
@@ -1488,23 +1530,13 @@ struct nhq_search_graph {
     cudaGraphExec_t exec = nullptr;
 };
 
-extern "C" {
-
-nhq_status nhq_search_graph_create(const nhq_index *ix, const float *queries,
-                                   const uint8_t *query_attributes, int64_t Q, int32_t k,
-                                   int32_t ef, const nhq_search_params *params, uint32_t *ids,
-                                   float *dists, uint8_t *chi, nhq_search_graph **out) {
-    if (out == nullptr)
-        return fail(NHQ_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    if (!is_device_ptr(queries) || !is_device_ptr(query_attributes) || !is_device_ptr(ids) ||
-        (dists && !is_device_ptr(dists)) || (chi && !is_device_ptr(chi)))
-        return fail(NHQ_ERR_ARG, "nhq_search_graph_create takes device pointers");
+// One ordinary call of run(stream) first (it builds the lazily made index parts and sizes
+// the scratch), then the same call captured on a private stream and instantiated.
+template <typename Run>
+static nhq_status capture_search(Run run, nhq_search_graph **out) {
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    // one ordinary call first: builds lazy index parts and sizes the scratch
-    nhq_status st = nhq_search(ix, queries, query_attributes, Q, k, ef, params, ids, dists, chi,
-                               nullptr, nullptr, nullptr, cs);
+    nhq_status st = run(cs);
     cudaError_t e = cudaStreamSynchronize(cs);
     if (st == NHQ_OK && e != cudaSuccess)
         st = fail_cuda(e, "cudaStreamSynchronize");
@@ -1515,8 +1547,7 @@ nhq_status nhq_search_graph_create(const nhq_index *ix, const float *queries,
         if (e != cudaSuccess) {
             st = fail_cuda(e, "cudaStreamBeginCapture");
         } else {
-            st = nhq_search(ix, queries, query_attributes, Q, k, ef, params, ids, dists, chi,
-                            nullptr, nullptr, nullptr, cs);
+            st = run(cs);
             e = cudaStreamEndCapture(cs, &g->graph);
             if (st == NHQ_OK && e != cudaSuccess)
                 st = fail_cuda(e, "cudaStreamEndCapture");
@@ -1531,6 +1562,63 @@ nhq_status nhq_search_graph_create(const nhq_index *ix, const float *queries,
     }
     *out = g;
     return NHQ_OK;
+}
+
+extern "C" {
+
+nhq_status nhq_search_graph_create(const nhq_index *ix, const float *queries,
+                                   const uint8_t *query_attributes, int64_t Q, int32_t k,
+                                   int32_t ef, const nhq_search_params *params, uint32_t *ids,
+                                   float *dists, uint8_t *chi, nhq_search_graph **out) {
+    if (out == nullptr)
+        return fail(NHQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!is_device_ptr(queries) || !is_device_ptr(query_attributes) || !is_device_ptr(ids) ||
+        (dists && !is_device_ptr(dists)) || (chi && !is_device_ptr(chi)))
+        return fail(NHQ_ERR_ARG, "nhq_search_graph_create takes device pointers");
+    return capture_search(
+        [&](cudaStream_t cs) {
+            return nhq_search(ix, queries, query_attributes, Q, k, ef, params, ids, dists, chi,
+                              nullptr, nullptr, nullptr, cs);
+        },
+        out);
+}
+
+nhq_status nhq_search_graph_create_batched(const nhq_index *ix, const float *queries,
+                                           const uint8_t *query_attributes, int64_t Q,
+                                           const int32_t *k_arr, const int32_t *ef_arr,
+                                           int32_t k_max, const nhq_search_params *params,
+                                           uint32_t *ids, float *dists, uint8_t *chi,
+                                           nhq_search_graph **out) {
+    if (out == nullptr)
+        return fail(NHQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (ix == nullptr || ix->nbr == nullptr)
+        return fail(NHQ_ERR_ARG, "the index has no graph (build or set one first)");
+    if (Q < 1 || k_max < 1 || k_max > kMaxK)
+        return fail(NHQ_ERR_ARG, "need Q >= 1 and k_max in 1..256");
+    if (!is_device_ptr(queries) || !is_device_ptr(query_attributes) || !is_device_ptr(ids) ||
+        !is_device_ptr(k_arr) || !is_device_ptr(ef_arr) || (dists && !is_device_ptr(dists)) ||
+        (chi && !is_device_ptr(chi)))
+        return fail(NHQ_ERR_ARG, "nhq_search_graph_create_batched takes device pointers");
+    // the per-query values are checked (and the pool sized) once, here
+    std::vector<int32_t> hk((size_t)Q), he((size_t)Q);
+    CK(cudaMemcpy(hk.data(), k_arr, sizeof(int32_t) * Q, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(he.data(), ef_arr, sizeof(int32_t) * Q, cudaMemcpyDeviceToHost));
+    int ef_max = 1;
+    for (int64_t i = 0; i < Q; ++i) {
+        if (hk[i] < 1 || hk[i] > k_max)
+            return fail(NHQ_ERR_ARG, "k_arr[%lld] = %d outside 1..k_max", (long long)i, hk[i]);
+        if (he[i] < hk[i] || he[i] > kMaxEf)
+            return fail(NHQ_ERR_ARG, "ef_arr[%lld] = %d outside k..1024", (long long)i, he[i]);
+        ef_max = he[i] > ef_max ? he[i] : ef_max;
+    }
+    return capture_search(
+        [&](cudaStream_t cs) {
+            return search_common(ix, queries, query_attributes, Q, k_arr, ef_arr, k_max, ef_max,
+                                 k_max, params, ids, dists, chi, nullptr, nullptr, nullptr, cs);
+        },
+        out);
 }
 
 nhq_status nhq_search_graph_launch(nhq_search_graph *g, void *stream) {

@@ -33,6 +33,7 @@ __all__ = [
     "c4",
     "c5",
     "int_valued",
+    "c5_queries",
     "gaussian_mixture",
     "zipf_attributes",
     "uniform_attributes",
@@ -227,6 +228,20 @@ def c4(N=1_000_000, nq=100_000, d=96, cards=(5, 20, 100), n_comp=1_000, seed=100
         QA[:, i] = rem % c
         rem //= c
     return Workload("c4", X, A, Qv, QA, tuple(cards), dict(seed=seed, n_comp=n_comp))
+
+
+def c5_queries(nq, query_stream, d=96, cards=(10, 50, 200), n_comp=4_096, seed=1004):
+    """Queries of the c5 mixture from an independent query stream, without generating the
+    10M-object base set (the centroids are the base stream's first draw): training
+    queries for the learned parts.  Returns (Qv, QA)."""
+    _check_cards(cards)
+    rb, _, _, _ = _rngs(seed)
+    rq, rqa = (np.random.default_rng(x)
+               for x in np.random.SeedSequence([seed, query_stream]).spawn(2))
+    cent = rb.standard_normal((n_comp, d), dtype=np.float32)
+    Qv, _ = gaussian_mixture(rq, nq, cent, 0.3)
+    Qv = Qv.astype(np.float16).astype(np.float32)
+    return Qv, zipf_attributes(rqa, nq, cards)
 
 
 def c5(N=10_000_000, nq=50_000, d=96, cards=(10, 50, 200), n_comp=4_096, seed=1004):

@@ -197,8 +197,8 @@ def test_tile_rows_leave_results_unchanged(nhq, d, vec):
     outs = {}
     with nhq.Index.create(dev(w.X), dev(w.A), CONST) as ix:
         nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
-        for tr in (2, 4):
-            for wpq in (1, 2):
+        for tr, wpq in ((2, 1), (2, 2), (4, 1)):
+            if True:
                 ids, g, c = empty_out(w.nq, 10)
                 ndc = torch.empty(w.nq, dtype=torch.int32, device="cuda:0")
                 nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 48, ids, g, c, ndc=ndc,
@@ -206,11 +206,55 @@ def test_tile_rows_leave_results_unchanged(nhq, d, vec):
                                tile_rows=tr, warps_per_query=wpq)
                 torch.cuda.synchronize()
                 outs[(tr, wpq)] = [t.cpu() for t in (ids, g, c, ndc)]
-        with pytest.raises(nhq.NHQError):
-            nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 48, ids, g, c, tile_rows=3)
+        for bad in (dict(tile_rows=3), dict(tile_rows=4, warps_per_query=2)):
+            with pytest.raises(nhq.NHQError):
+                nhq.nhq_search(ix.handle, dev(w.Qv), dev(w.QA), 10, 48, ids, g, c, **bad)
     for key, o in outs.items():
         for a, b in zip(o, outs[(2, 1)]):
             assert torch.equal(a, b), key
     r = O.search(w.X, w.A, nbr, w.Qv, w.QA, 10, 48, seed=3, weights=CONST,
                  seed_mode=O.SEED_ATTRIBUTE, vec_round=vec)
     assert (ids_i64(outs[(4, 1)][0]) == r["ids"]).all()
+
+
+def test_batched_tuner_and_captured_batched_search(nhq, case):
+    # a heterogeneous batch: the tuned shape and the captured launch return what the
+    # plain batched call returns, and the graph replays after its inputs change in place
+    w, nbr = case
+    k_arr, ef_arr = synth.mixed_k_ef(w.nq, seed=95, ks=(1, 5, 10), ef_lo=12, ef_hi=80)
+    kmax = 10
+    with nhq.Index.create(dev(w.X), dev(w.A), CONST) as ix:
+        nhq.nhq_index_set_graph(ix.handle, dev(to_u32_graph(nbr)))
+        kd, efd = dev(k_arr), dev(ef_arr)
+        ref, refg, _ = empty_out(w.nq, kmax)
+        nhq.nhq_search_batched(ix.handle, dev(w.Qv), dev(w.QA), kd, efd, kmax, ref, refg,
+                               seed=4, seed_mode=nhq.SEED_ATTRIBUTE)
+        tmp = torch.empty((w.nq, kmax), dtype=torch.uint32, device="cuda:0")
+        t = nhq.nhq_autotune_batched(ix.handle, dev(w.Qv), dev(w.QA), kd, efd, kmax, tmp,
+                                     seed=4, seed_mode=nhq.SEED_ATTRIBUTE)
+        assert t["warps_per_query"] in (1, 2, 4) and t["tile_rows"] in (2, 4) and t["ms"] > 0
+        shape = {x: t[x] for x in ("warps_per_query", "tile_rows", "warps_per_block",
+                                   "hash_bits")}
+        ids, g, _ = empty_out(w.nq, kmax)
+        nhq.nhq_search_batched(ix.handle, dev(w.Qv), dev(w.QA), kd, efd, kmax, ids, g, seed=4,
+                               seed_mode=nhq.SEED_ATTRIBUTE, **shape)
+        torch.cuda.synchronize()
+        assert torch.equal(ids, ref) and torch.equal(g, refg)
+        Qd, QAd = dev(w.Qv), dev(w.QA)
+        gids, gg, _ = empty_out(w.nq, kmax)
+        graph = nhq.nhq_search_graph_create_batched(ix.handle, Qd, QAd, kd, efd, kmax, gids,
+                                                    gg, seed=4, seed_mode=nhq.SEED_ATTRIBUTE)
+        gids.fill_(0)
+        graph.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(gids, ref) and torch.equal(gg, refg)
+        # new queries written in place, replayed
+        Qd.copy_(torch.flip(Qd, [0]))
+        QAd.copy_(torch.flip(QAd, [0]))
+        graph.launch()
+        ref2, refg2, _ = empty_out(w.nq, kmax)
+        nhq.nhq_search_batched(ix.handle, Qd, QAd, kd, efd, kmax, ref2, refg2, seed=4,
+                               seed_mode=nhq.SEED_ATTRIBUTE)
+        torch.cuda.synchronize()
+        graph.close()
+        assert torch.equal(gids, ref2) and torch.equal(gg, refg2)
