@@ -598,14 +598,19 @@ def c5_arm(a):
     model, t_train, n_tr = train_entry(nhq, ix, w, wtr, E, k, dev, epochs=6)
     del Qt, QAt, wtr
 
-    def run(form, ef, diag=False):
-        kw = dict(seed_mode=nhq.SEED_ATTRIBUTE)
+    shapes = {}  # tuned launch shape per form
+
+    def form_kw(form):
         if form == "learned":
-            kw = dict(seed_mode=nhq.SEED_CELL_LEARNED, entry_model=model,
-                      entry_cells=a.entry_T)
+            return dict(seed_mode=nhq.SEED_CELL_LEARNED, entry_model=model,
+                        entry_cells=a.entry_T)
+        return dict(seed_mode=nhq.SEED_ATTRIBUTE)
+
+    def run(form, ef, diag=False):
         nhq.nhq_search(ix.handle, Qv, QA, k, ef, ids, dd, ch, ndc=ndc if diag else None,
                        expansions=exps if diag else None, seed=12345,
-                       vec_dtype=nhq.VEC_F16, stream=stream, **kw)
+                       vec_dtype=nhq.VEC_F16, stream=stream, **form_kw(form),
+                       **shapes.get(form, {}))
 
     def timed(form, ef, reps):
         for _ in range(2):
@@ -632,6 +637,19 @@ def c5_arm(a):
             if rec >= a.target:
                 found[form] = sweeps[form][-1]
                 break
+    # the autotuner on each form at its ef; the tuned shape is kept where it is faster
+    tuned = {}
+    for f in found:
+        t = nhq.nhq_autotune(ix.handle, Qv, QA, k, found[f]["ef"], ids, seed=12345,
+                             vec_dtype=nhq.VEC_F16, **form_kw(f))
+        shape = {x: t[x] for x in ("warps_per_query", "tile_rows", "warps_per_block",
+                                   "hash_bits")}
+        before = timed(f, found[f]["ef"], 5)
+        shapes[f] = shape
+        after = timed(f, found[f]["ef"], 5)
+        if after >= before:
+            shapes.pop(f)
+        tuned[f] = dict(t, default_ms=before, tuned_ms=after, used=f in shapes)
     chosen = min(found, key=lambda f: found[f]["ms"])
     ef = found[chosen]["ef"]
     run(chosen, ef, diag=True)
@@ -663,6 +681,7 @@ def c5_arm(a):
                              "train_s": t_train}},
         "sweeps": sweeps,
         "timed_ms": timed_ms,
+        "autotune": tuned,
         "qps": {f: w.nq / (timed_ms[f] / 1000.0) for f in timed_ms},
         "learned_vs_plain": (timed_ms["plain"] / timed_ms["learned"]
                              if "learned" in timed_ms and "plain" in timed_ms else None),

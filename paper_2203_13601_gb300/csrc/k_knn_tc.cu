@@ -588,8 +588,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int j = j4 * 4 + q;
-                            const float d2 =
-                                fmaxf((nu + nc[q]) - 2.f * __uint_as_float(v[j]), 0.f);
+                            // unclamped: a rounding below zero passes as it would at
+                            // zero (the survivor's exact key decides)
+                            const float d2 = (nu + nc[q]) - 2.f * __uint_as_float(v[j]);
                             v[j] = __float_as_uint(d2);
                             pass |= (d2 <= Lb ? 1u : 0u) << j;
                         }
@@ -605,8 +606,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int j = j4 * 4 + q;
-                            const float d2 =
-                                fmaxf((nu + nc[q]) - 2.f * __uint_as_float(v[j]), 0.f);
+                            const float d2 = (nu + nc[q]) - 2.f * __uint_as_float(v[j]);
                             v[j] = __float_as_uint(d2);
                             const int ch = chi_level(chi_packed(au, ac[q], a.w.hi, a.w.lo));
                             pass |= (d2 <= lt[ch * BM] ? 1u : 0u) << j;
@@ -618,8 +618,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
                         if ((pass >> j) & 1u)
-                            stg[ns++] = make_uint2(v[j], (uint32_t)(c0 + j));
+                            stg[ns++] = make_uint2(
+                                __float_as_uint(fmaxf(__uint_as_float(v[j]), 0.f)),
+                                (uint32_t)(c0 + j));
                 }
+                bool touched = false;  // the heap changed: refresh the bounds after the chunk
                 for (int s2 = 0; s2 < ns; ++s2) {
                     const uint2 e = stg[s2];
                     const int c = (int)e.y;
@@ -638,13 +641,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             hp[K + 1] = 0ull;
                             for (int h = K / 2; h >= 1; --h)
                                 heap_sift(hp, K, h, hp[h]);
-                            update_lim();
+                            thr = hp[1];
+                            touched = true;
                         }
                     } else {  // replace the largest of the K records
                         heap_sift(hp, K, 1, key);
-                        update_lim();
+                        thr = hp[1];
+                        touched = true;
                     }
                 }
+                // the bounds are only a filter: the staler (looser) ones used within the
+                // chunk let through records the key test then rejects
+                if (touched)
+                    update_lim();
             }
             tc_fence_before();
             mbar_arrive(bar(TEMPTY0 + b));

@@ -99,6 +99,10 @@ __host__ __device__ __forceinline__ uint32_t pack_query_word(const uint8_t *qa, 
 // Gamma (Eq. 6) from delta and chi, each operation rounded once (round-to-nearest),
 // so it equals the canonical f32 evaluation of the formula.
 __device__ __forceinline__ float fusion_gamma(float delta, int chi, const Fusion &w) {
+    // chi = 0: the attribute term is +0 and delta >= 0, so the sum is the vector term
+    // exactly (this skips the rounded division of the proportional form)
+    if (chi == 0 && w.mode != NHQ_W_HARMONIC)
+        return w.mode == NHQ_W_CONSTANT ? __fmul_rn(w.wv, delta) : delta;
     if (w.mode == NHQ_W_PROPORTIONAL) {
         float wl = __fdiv_rn(delta, (float)w.m);
         return __fadd_rn(delta, __fmul_rn(wl, (float)chi));

@@ -166,12 +166,37 @@ def test_learned_stop_gains_over_plain_search(nhq):
                        stop_min=4, stop_every=2)
         gt = torch.empty((nte, k), dtype=torch.uint32, device="cuda:0")
         nhq.nhq_brute_force(ix.handle, Qte, QAte, k, gt, weights="filter")
+
+        # the time of both forms on this batch (CUDA events, 20 launches each)
+        def timed(**kw):
+            for _ in range(3):
+                nhq.nhq_search(ix.handle, Qte, QAte, k, ef, ids0, g0, c0,
+                               seed_mode=nhq.SEED_ATTRIBUTE, **kw)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record()
+            for _ in range(20):
+                nhq.nhq_search(ix.handle, Qte, QAte, k, ef, ids0, g0, c0,
+                               seed_mode=nhq.SEED_ATTRIBUTE, **kw)
+            a1.record()
+            a1.synchronize()
+            return a0.elapsed_time(a1) / 20
+
+        ms_plain = timed()
+        ms_learned = timed(stop_model=p, stop_threshold=0.95, stop_min=4, stop_every=2)
         torch.cuda.synchronize()
     gt_i, i0, i1 = ids_i64(gt), ids_i64(ids0), ids_i64(ids1)
     rec0 = np.mean([len(set(a) & set(b[b >= 0])) / max(1, (b >= 0).sum()) for a, b in zip(i0, gt_i)])
     rec1 = np.mean([len(set(a) & set(b[b >= 0])) / max(1, (b >= 0).sum()) for a, b in zip(i1, gt_i)])
     e0, e1 = ex0.float().mean().item(), ex1.float().mean().item()
-    print(f"plain: recall {rec0:.4f}, expansions {e0:.1f}; learned: recall {rec1:.4f}, "
-          f"expansions {e1:.1f}")
+    print(f"plain: recall {rec0:.4f}, expansions {e0:.1f}, {ms_plain:.4f} ms; learned: "
+          f"recall {rec1:.4f}, expansions {e1:.1f}, {ms_learned:.4f} ms "
+          f"({ms_plain / ms_learned:.2f}x)")
     assert e1 < 0.85 * e0          # at least 15% fewer expansions
     assert rec1 > rec0 - 0.01      # for at most 0.01 of recall
+    # Time: the gain in expansions does not turn into a gain in time (the model costs a
+    # 641-parameter evaluation every second expansion, and a batch's time follows its
+    # slowest queries more than its mean expansion count; on the 1M sets the learned stop
+    # is not faster at the 0.95 point).  The times are printed above; the test only
+    # bounds the cost of the model, at most 1.5x the plain search.
+    assert ms_learned < 1.5 * ms_plain, (ms_plain, ms_learned)
