@@ -1746,7 +1746,10 @@ def main():
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms, "mean_ndc": float(ndc_h.mean()),
-                     "mean_expansions": float(exp_h.mean())},
+                     "mean_expansions": float(exp_h.mean()),
+                     "step_ms": {"min": float(np.min(step_ms)),
+                                 "median": float(np.median(step_ms)),
+                                 "max": float(np.max(step_ms))}},
         "e2e": {"value": w.nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "recall": e2e_rec},
         # per step: the seed pre-pass and ordering (attribute seeds: 2 kernels; learned entry:

@@ -55,6 +55,11 @@ constexpr uint32_t RING_BYTES = 6 * BOX_BYTES;
 constexpr int MAX_STAGES = 4;
 constexpr uint32_t TMEM_COLS = 2 * BN;
 constexpr long long kWaitLimit = 1ll << 26;
+// survivors of the filter wait in a queue of QCAP records per row and enter the row's heap
+// in flushes that every lane of the warp runs at once (a flush when some lane's queue is
+// half full, every FLUSH_TILES kept tiles, and at the end)
+constexpr int QCAP = 16;
+constexpr int FLUSH_TILES = 4;
 
 struct TcArgs {
     const float *norms;     // |x|^2 of the bf16-rounded rows, sorted order
@@ -218,13 +223,15 @@ __device__ __forceinline__ int next_kept(const int *decided, const uint32_t *bit
 }
 
 struct TcSmem {  // byte offsets in the dynamic shared memory (after 1024-byte alignment)
-    uint32_t heaps, stage, limtab, meta, bits, bars, misc, total;
+    uint32_t heaps, drow, queue, qchi, limtab, meta, bits, bars, misc, total;
 };
 __host__ __device__ inline TcSmem tc_smem_layout(int ntiles) {
     TcSmem L;
     L.heaps = RING_BYTES;
-    L.stage = L.heaps + 8u * BM * LSTRIDE;                         // [BM][33] uint2
-    L.limtab = L.stage + 8u * BM * 33;                             // [5][BM] f32
+    L.drow = L.heaps + 8u * BM * LSTRIDE;                          // [BM][33] f32
+    L.queue = L.drow + 4u * BM * 33;                               // [QCAP][BM] u64
+    L.qchi = L.queue + 8u * QCAP * BM;                             // [QCAP][BM] u8
+    L.limtab = L.qchi + 1u * QCAP * BM;                            // [5][BM] f32
     L.meta = L.limtab + 4u * 5 * BM;                               // per epilogue warp: norm, attr, id [BN]
     L.bits = L.meta + 4u * 3 * 4 * BN;                             // skip bit per tile
     L.bars = L.bits + ((4u * (uint32_t)((ntiles + 31) / 32) + 15u) & ~15u);
@@ -242,7 +249,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const TcSmem L = tc_smem_layout(ntiles);
     unsigned char *ring = sm;
     unsigned long long *heaps = reinterpret_cast<unsigned long long *>(sm + L.heaps);
-    uint2 *stage = reinterpret_cast<uint2 *>(sm + L.stage);
+    float *drows = reinterpret_cast<float *>(sm + L.drow);
+    unsigned long long *queue = reinterpret_cast<unsigned long long *>(sm + L.queue);
+    unsigned char *qchi = sm + L.qchi;
     float *limtab = reinterpret_cast<float *>(sm + L.limtab);
     unsigned char *meta = sm + L.meta;
     uint32_t *skipbits = reinterpret_cast<uint32_t *>(sm + L.bits);
@@ -423,10 +432,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (resA)
             ok = mbar_wait(bar(AFULL), 0, a.err, 6);
         for (int i = 0; ok; ++i) {
-            i = next_kept(decided, skipbits, i, ntiles, a.err, 7);
-            if (i < 0) {
-                ok = false;
-                break;
+            if (skip_on) {  // otherwise every tile is kept
+                i = next_kept(decided, skipbits, i, ntiles, a.err, 7);
+                if (i < 0) {
+                    ok = false;
+                    break;
+                }
             }
             if (i >= ntiles)
                 break;
@@ -473,7 +484,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const float nu = row_ok ? a.norms[u] : 0.f;
         const uint32_t au = row_ok ? a.attr[u] : 0u;
         unsigned long long *hp = heaps + r * LSTRIDE;
-        uint2 *stg = stage + r * (32 + 1);  // survivors of one 32-column chunk
+        float *drow = drows + r * 33;          // delta^2 of the current 32-column chunk
+        unsigned long long *qk = queue + r;    // queued records (delta^2 bits, id), stride BM
+        unsigned char *qc = qchi + r;          // their chi, stride BM
+        int qn = 0;                            // queued records of this row
         // this warp's copy of the tile's column metadata
         float *mnorm = reinterpret_cast<float *>(meta) + ew * 3 * BN;
         uint32_t *mattr = reinterpret_cast<uint32_t *>(mnorm + BN);
@@ -514,18 +528,69 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 limtab[cc * BM + r] = tt < 0.f ? -1.f : tt * tt;
             }
         };
+        // the queued records enter the heap: exact Gamma (Eq. 6) and key test, then the
+        // bounds once for the whole flush
+        auto flush = [&]() {
+            bool touched = false;
+            for (int e = 0; e < qn; ++e) {
+                const unsigned long long rec = qk[e * BM];
+                const float g = fusion_gamma(__fsqrt_rn(__uint_as_float((uint32_t)(rec >> 32))),
+                                             (int)qc[e * BM], a.w);
+                const unsigned long long key =
+                    ((unsigned long long)__float_as_uint(g) << 32) | (uint32_t)rec;
+                if (key >= thr)
+                    continue;
+                if (cnt < K) {  // filling: unordered, heapified once full
+                    hp[1 + cnt] = key;
+                    if (++cnt == K) {
+                        hp[K + 1] = 0ull;
+                        for (int h = K / 2; h >= 1; --h)
+                            heap_sift(hp, K, h, hp[h]);
+                        thr = hp[1];
+                        touched = true;
+                    }
+                } else {  // replace the largest of the K records
+                    heap_sift(hp, K, 1, key);
+                    thr = hp[1];
+                    touched = true;
+                }
+            }
+            qn = 0;
+            if (touched)
+                update_lim();
+        };
         const uint32_t lane_base = (uint32_t)(ew * 32) << 16;
         const float *lt = limtab + r;
         bool ok = true;
         int p = 0;
-        for (int i = 0;; ++i) {
-            i = next_kept(decided, skipbits, i, ntiles, a.err, 8);
-            ok = i >= 0;
-            if (!__all_sync(0xFFFFFFFFu, ok)) {
-                ok = false;
-                break;
+        // a tile's column metadata in registers until it is stored to this warp's copy
+        float rn[4];
+        uint32_t rat[4], rid[4];
+        auto load_meta = [&](int ii) {
+            const int64_t cb = (int64_t)tile_at(ii) * BN;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t col = cb + lane + 32 * k;
+                const bool in = col < a.N;
+                rn[k] = in ? __ldg(a.norms + col) : 0.f;
+                rat[k] = in ? __ldg(a.attr + col) : 0u;
+                rid[k] = in ? __ldg(a.perm + col) : 0u;
             }
-            i = __shfl_sync(0xFFFFFFFFu, i, 0);  // every lane saw the same published bits
+        };
+        // without tile skipping every tile is kept: there are no decisions to wait for,
+        // and the next tile's metadata loads while this one is filtered
+        if (!skip_on)
+            load_meta(0);
+        for (int i = 0;; ++i) {
+            if (skip_on) {
+                i = next_kept(decided, skipbits, i, ntiles, a.err, 8);
+                ok = i >= 0;
+                if (!__all_sync(0xFFFFFFFFu, ok)) {
+                    ok = false;
+                    break;
+                }
+                i = __shfl_sync(0xFFFFFFFFu, i, 0);  // every lane saw the same published bits
+            }
             if (i >= ntiles)
                 break;
             const int t = tile_at(i);
@@ -533,18 +598,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t tph = (uint32_t)(p >> 1) & 1u;
             ++p;
             const int64_t cbase = (int64_t)t * BN;
-            // the tile's column metadata: loads issued before the accumulator wait,
-            // stored to this warp's copy after it
-            float rn[4];
-            uint32_t rat[4], rid[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t col = cbase + lane + 32 * k;
-                const bool in = col < a.N;
-                rn[k] = in ? __ldg(a.norms + col) : 0.f;
-                rat[k] = in ? __ldg(a.attr + col) : 0u;
-                rid[k] = in ? __ldg(a.perm + col) : 0u;
-            }
+            // with skipping, the loads are issued here, before the accumulator wait
+            if (skip_on)
+                load_meta(i);
             ok = mbar_wait(bar(TFULL0 + b), tph, a.err, 5);
             __syncwarp();  // every lane is done with the previous tile's metadata
 #pragma unroll
@@ -558,6 +614,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 ok = false;
                 break;
             }
+            if (!skip_on && i + 1 < ntiles)
+                load_meta(i + 1);
             tc_fence_after();
             const int nvalid = a.N - cbase < BN ? (int)(a.N - cbase) : BN;
             const uint32_t tf = mattr[0], tl = mattr[nvalid - 1];
@@ -566,20 +624,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int ch_min = (au >= tf && au <= tl) ? 0 : (uni ? ch_t : 1);
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 // the bounds only tighten: a row whose bound for the smallest chi of
-                // this tile is negative rejects every column of it
-                const bool dead = !row_ok || lt[ch_min * BM] < 0.f;
+                // this tile is negative rejects every column of it (negative bounds
+                // arise only under constant weights, where tiles are skipped)
+                const bool dead = !row_ok || (skip_on && lt[ch_min * BM] < 0.f);
                 if (__all_sync(0xFFFFFFFFu, dead))
                     break;
                 uint32_t v[32];
                 tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + c0), v);
-                if (dead)
-                    continue;
-                // branch-free filter in two phases, all shared-memory loads before any
-                // store: a pass mask of the columns within the bound of their chi,
-                // then the passing columns are appended to the stage
+                // branch-free filter: a pass mask of the columns within the bound of their
+                // chi (a dead row passes none and stays with the warp for its votes)
                 uint32_t pass = 0;
                 const float4 *cn4 = reinterpret_cast<const float4 *>(mnorm + c0);
-                if (uni) {
+                if (dead) {
+                } else if (uni) {
                     const float Lb = lt[ch_t * BM];
 #pragma unroll
                     for (int j4 = 0; j4 < 8; ++j4) {
@@ -613,51 +670,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     }
                 }
-                int ns = 0;
                 if (pass != 0u) {
+                    // the chunk's delta^2 values (8-column groups that hold a pass) go to
+                    // this row's line; the passing columns join the queue
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if ((pass >> j) & 1u)
-                            stg[ns++] = make_uint2(
-                                __float_as_uint(fmaxf(__uint_as_float(v[j]), 0.f)),
-                                (uint32_t)(c0 + j));
-                }
-                bool touched = false;  // the heap changed: refresh the bounds after the chunk
-                for (int s2 = 0; s2 < ns; ++s2) {
-                    const uint2 e = stg[s2];
-                    const int c = (int)e.y;
-                    const int64_t col = cbase + c;
-                    if (col >= a.N || col == u)
-                        continue;
-                    const int ch = chi_packed(au, mattr[c], a.w.hi, a.w.lo);
-                    const float g = fusion_gamma(__fsqrt_rn(__uint_as_float(e.x)), ch, a.w);
-                    const unsigned long long key =
-                        ((unsigned long long)__float_as_uint(g) << 32) | mid[c];
-                    if (key >= thr)
-                        continue;
-                    if (cnt < K) {  // filling: unordered, heapified once full
-                        hp[1 + cnt] = key;
-                        if (++cnt == K) {
-                            hp[K + 1] = 0ull;
-                            for (int h = K / 2; h >= 1; --h)
-                                heap_sift(hp, K, h, hp[h]);
-                            thr = hp[1];
-                            touched = true;
+                    for (int g8 = 0; g8 < 4; ++g8) {
+                        if ((pass >> (8 * g8)) & 0xFFu) {
+#pragma unroll
+                            for (int j = 8 * g8; j < 8 * g8 + 8; ++j)
+                                drow[j] = __uint_as_float(v[j]);
                         }
-                    } else {  // replace the largest of the K records
-                        heap_sift(hp, K, 1, key);
-                        thr = hp[1];
-                        touched = true;
+                    }
+                    for (uint32_t pm = pass; pm != 0u; pm &= pm - 1u) {
+                        const int j = __ffs((int)pm) - 1;
+                        const int c = c0 + j;
+                        const int64_t col = cbase + c;
+                        if (col >= a.N || col == u)
+                            continue;
+                        if (qn == QCAP)
+                            flush();  // this lane alone: a dense chunk
+                        qk[qn * BM] =
+                            ((unsigned long long)__float_as_uint(fmaxf(drow[j], 0.f)) << 32) |
+                            mid[c];
+                        qc[qn * BM] = (unsigned char)chi_packed(au, mattr[c], a.w.hi, a.w.lo);
+                        ++qn;
                     }
                 }
-                // the bounds are only a filter: the staler (looser) ones used within the
-                // chunk let through records the key test then rejects
-                if (touched)
-                    update_lim();
+                // every lane flushes together once some queue is half full
+                if (__any_sync(0xFFFFFFFFu, qn >= QCAP / 2))
+                    flush();
             }
+            // and every FLUSH_TILES kept tiles, so that the bounds (and the scheduler's
+            // skip decisions) follow the heaps
+            if ((p % FLUSH_TILES) == 0 && __any_sync(0xFFFFFFFFu, qn > 0))
+                flush();
             tc_fence_before();
             mbar_arrive(bar(TEMPTY0 + b));
         }
+        flush();
         if (row_ok) {
             // heap sort: pop the largest into the last open output slot of the
             // object's own (original) row
