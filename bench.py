@@ -191,6 +191,54 @@ def recorded_traffic(ef, h, vec, seed_mode, n, nq, learned):
     return float(rec["dram_bytes_per_launch"]) if same else None
 
 
+def fp32_simt_peak(dev):
+    """Measured FP32 throughput of the SIMT units: cuBLAS SGEMM with TF32 off (8192^3),
+    TFLOP/s; the denominator of the brute force's ALU roofline."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        n = 8192
+        g = torch.Generator(device=dev).manual_seed(0)
+        x = torch.randn((n, n), device=dev, generator=g)
+        y = torch.randn((n, n), device=dev, generator=g)
+        for _ in range(2):
+            torch.mm(x, y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            torch.mm(x, y)
+        e1.record()
+        e1.synchronize()
+        return 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) / 1000.0) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def brute_force_roofline(nhq, ix, Qv, QA, k, n, d, dev, stream):
+    """The brute-force fused top-k (every query against every object, constant weights)
+    timed with CUDA events on its stream: 3 flops per (query, object, dimension) (the
+    difference and its fused square-add) against the measured SGEMM rate."""
+    nq = Qv.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.uint32, device=dev)
+    nhq.nhq_brute_force(ix.handle, Qv, QA, k, ids, weights=CONST_W, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    e0.record(stream)
+    for _ in range(reps):
+        nhq.nhq_brute_force(ix.handle, Qv, QA, k, ids, weights=CONST_W, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    achieved = 3.0 * nq * n * d / (ms / 1000.0) / 1e12
+    peak = fp32_simt_peak(dev)
+    nominal = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA flops x max clock
+    return {"bound": "alu", "ms": ms, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_kind": "cuBLAS SGEMM with TF32 off, measured",
+            "nominal_fp32_peak": nominal, "frac_of_nominal": achieved / nominal,
+            "flops_per_pair_dim": 3, "queries": nq, "objects": n}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -1760,6 +1808,8 @@ def main():
                                    (1 if sel["model"] is not None else 0) + 1),
         "clocks": clk,
     }
+    if rank == 0:
+        line["brute_force"] = brute_force_roofline(nhq, ix, Qv, QA, a.k, a.n, a.d, dev, stream)
     if rank == 0 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, a, a.cpu_sample)
         line["cpu_baseline"].pop("seconds", None)

@@ -21,12 +21,15 @@
 //                       bf16 boxes of 128 rows x 64 dims; with d <= 128 the row
 //                       operand is loaded once and stays resident
 //   warp 1 (one lane)   tcgen05.mma kind::f16, M = 128, N = 128, K = 16, f32
-//                       accumulators in two TMEM buffers of 128 columns
-//   warps 4..7          epilogue: tcgen05.ld of its 32 lanes (= rows), delta^2 and
-//                       chi of every pair against a per-row table of delta^2
-//                       bounds by chi (branch-free), then for the few survivors
-//                       exact Gamma (Eq. 6) and a per-row max-heap of the K best
-//                       records in shared memory (sorted once at the end)
+//                       accumulators in four TMEM buffers of 128 columns
+//   warps 2..9          epilogue, two groups of four warps taking the kept tiles
+//                       alternately: tcgen05.ld of the warp's 32 lanes (= rows),
+//                       delta^2 and chi of every pair against a per-row table of
+//                       delta^2 bounds by chi (branch-free); the survivors wait in
+//                       a per-row queue of the group and enter, with exact Gamma
+//                       (Eq. 6), the row's max-heap of the K best records in
+//                       shared memory (shared by the groups under a per-row lock,
+//                       sorted once at the end)
 // A tile is skipped when every row's bound for the smallest chi the tile can
 // have with it is negative: in the constant and filter weightings a row whose K
 // records all match its tuple rejects every other tuple.  The bounds only
@@ -47,18 +50,19 @@ constexpr int KMAX = 64;
 // u64 entries per row heap: slot 0 unused, 1..K the heap, K+1 a zero sentinel (so a
 // node's two children are one aligned 16-byte pair); even, so every row is 16-byte aligned
 constexpr int LSTRIDE = KMAX + 2;
-constexpr int NTHREADS = 256;
+constexpr int NTHREADS = 320;
 constexpr uint32_t BOX_BYTES = BM * BK * 2;  // one operand box: 16 KB
 // operand ring of 6 boxes: 3 stages of (A, B) boxes, or with d <= 128 the resident
 // A boxes (2) and 4 single-box B stages
 constexpr uint32_t RING_BYTES = 6 * BOX_BYTES;
 constexpr int MAX_STAGES = 4;
-constexpr uint32_t TMEM_COLS = 2 * BN;
+constexpr int NBUF = 4;  // accumulator buffers in TMEM (two per epilogue group)
+constexpr uint32_t TMEM_COLS = NBUF * BN;
 constexpr long long kWaitLimit = 1ll << 26;
 // survivors of the filter wait in a queue of QCAP records per row and enter the row's heap
 // in flushes that every lane of the warp runs at once (a flush when some lane's queue is
 // half full, every FLUSH_TILES kept tiles, and at the end)
-constexpr int QCAP = 16;
+constexpr int QCAP = 12;
 constexpr int FLUSH_TILES = 4;
 
 struct TcArgs {
@@ -183,6 +187,24 @@ __device__ __forceinline__ void heap_sift(unsigned long long *hp, int n, int i,
     hp[i] = key;
 }
 
+// v[j] for a runtime j by a tree of selects (the array stays in registers)
+__device__ __forceinline__ uint32_t pick32(const uint32_t (&v)[32], int j) {
+    uint32_t t16[16], t8[8], t4[4], t2[2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        t16[i] = (j & 16) ? v[i + 16] : v[i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        t8[i] = (j & 8) ? t16[i + 8] : t16[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        t4[i] = (j & 4) ? t8[i + 4] : t8[i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        t2[i] = (j & 2) ? t4[i + 2] : t4[i];
+    return (j & 1) ? t2[1] : t2[0];
+}
+
 // row of the bound table for a chi: the table holds chi = 0..4; Gamma grows with chi,
 // so the bound of chi = 4 also holds (more loosely) for every larger chi
 __device__ __forceinline__ int chi_level(int chi) { return chi < 4 ? chi : 4; }
@@ -223,19 +245,20 @@ __device__ __forceinline__ int next_kept(const int *decided, const uint32_t *bit
 }
 
 struct TcSmem {  // byte offsets in the dynamic shared memory (after 1024-byte alignment)
-    uint32_t heaps, drow, queue, qchi, limtab, meta, bits, bars, misc, total;
+    uint32_t heaps, queue, qchi, rowcnt, rowlock, limtab, meta, bits, bars, misc, total;
 };
 __host__ __device__ inline TcSmem tc_smem_layout(int ntiles) {
     TcSmem L;
     L.heaps = RING_BYTES;
-    L.drow = L.heaps + 8u * BM * LSTRIDE;                          // [BM][33] f32
-    L.queue = L.drow + 4u * BM * 33;                               // [QCAP][BM] u64
-    L.qchi = L.queue + 8u * QCAP * BM;                             // [QCAP][BM] u8
-    L.limtab = L.qchi + 1u * QCAP * BM;                            // [5][BM] f32
+    L.queue = L.heaps + 8u * BM * LSTRIDE;                         // [2][QCAP][BM] u64
+    L.qchi = L.queue + 8u * 2 * QCAP * BM;                         // [2][QCAP][BM] u8
+    L.rowcnt = L.qchi + 1u * 2 * QCAP * BM;                        // [BM] records per heap
+    L.rowlock = L.rowcnt + 4u * BM;                                // [BM] heap locks
+    L.limtab = L.rowlock + 4u * BM;                                // [5][BM] f32
     L.meta = L.limtab + 4u * 5 * BM;                               // per epilogue warp: norm, attr, id [BN]
-    L.bits = L.meta + 4u * 3 * 4 * BN;                             // skip bit per tile
+    L.bits = L.meta + 4u * 3 * 8 * BN;                             // skip bit per tile
     L.bars = L.bits + ((4u * (uint32_t)((ntiles + 31) / 32) + 15u) & ~15u);
-    L.misc = L.bars + 8u * 16;                                     // decided counter, TMEM address
+    L.misc = L.bars + 8u * 32;                                     // decided counter, TMEM address
     L.total = L.misc + 16;
     return L;
 }
@@ -249,9 +272,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const TcSmem L = tc_smem_layout(ntiles);
     unsigned char *ring = sm;
     unsigned long long *heaps = reinterpret_cast<unsigned long long *>(sm + L.heaps);
-    float *drows = reinterpret_cast<float *>(sm + L.drow);
     unsigned long long *queue = reinterpret_cast<unsigned long long *>(sm + L.queue);
     unsigned char *qchi = sm + L.qchi;
+    int *rowcnt = reinterpret_cast<int *>(sm + L.rowcnt);
+    int *rowlock = reinterpret_cast<int *>(sm + L.rowlock);
     float *limtab = reinterpret_cast<float *>(sm + L.limtab);
     unsigned char *meta = sm + L.meta;
     uint32_t *skipbits = reinterpret_cast<uint32_t *>(sm + L.bits);
@@ -270,8 +294,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int t0 = (int)blockIdx.x;  // the diagonal tile comes first
     auto tile_at = [&](int i) { return t0 + i < ntiles ? t0 + i : t0 + i - ntiles; };
     auto bar = [&](int i) { return smem_u32(bars + i); };
-    const int FULL0 = 0, EMPTY0 = MAX_STAGES, TFULL0 = 2 * MAX_STAGES, TEMPTY0 = TFULL0 + 2,
-              AFULL = TEMPTY0 + 2, DONE = AFULL + 1;
+    const int FULL0 = 0, EMPTY0 = MAX_STAGES, TFULL0 = 2 * MAX_STAGES, TEMPTY0 = TFULL0 + NBUF,
+              AFULL = TEMPTY0 + NBUF, DONE = AFULL + 1;
     // whole tiles are rejected only where a negative bound is possible
     const bool skip_on = a.w.mode == NHQ_W_CONSTANT;
 
@@ -279,14 +303,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         skipbits[i] = 0u;
     for (int i = threadIdx.x; i < 5 * BM; i += NTHREADS)
         limtab[i] = __int_as_float(0x7f800000);
+    for (int i = threadIdx.x; i < BM; i += NTHREADS) {
+        rowcnt[i] = 0;
+        rowlock[i] = 0;
+    }
     if (threadIdx.x == 0) {
         for (int q = 0; q < MAX_STAGES; ++q) {
             mbar_init(bar(FULL0 + q), 1);
             mbar_init(bar(EMPTY0 + q), 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NBUF; ++b) {
             mbar_init(bar(TFULL0 + b), 1);
-            mbar_init(bar(TEMPTY0 + b), BM);
+            mbar_init(bar(TEMPTY0 + b), BM);  // the 128 threads of one epilogue group
         }
         mbar_init(bar(AFULL), 1);
         mbar_init(bar(DONE), 1);
@@ -441,8 +469,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             if (i >= ntiles)
                 break;
-            const int b = p & 1;
-            const uint32_t tph = (uint32_t)(p >> 1) & 1u;
+            const int b = p % NBUF;
+            const uint32_t tph = (uint32_t)(p / NBUF) & 1u;
             ++p;
             ok = mbar_wait(bar(TEMPTY0 + b), tph ^ 1u, a.err, 2);
             if (!ok)
@@ -475,26 +503,30 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             umma_commit(bar(DONE));
             mbar_wait(bar(DONE), 0, a.err, 4);
         }
-    } else if (warp >= 4) {
-        // ---------------- epilogue: thread r owns row row0 + r (sorted position)
-        const int ew = warp - 4;
-        const int r = ew * 32 + lane;
+    } else if (warp >= 2) {
+        // ---------------- epilogue: two groups of four warps (g = (warp - 2) / 4) take
+        // the kept tiles alternately (the k-th kept tile: group k mod 2, accumulator
+        // buffer k mod NBUF).  Thread (warp, lane) serves row r = 32 (warp mod 4) + lane
+        // (sorted position), warp mod 4 being the warp's TMEM lane quarter, so each row
+        // has one thread in each group; the row's heap is shared, and a flush into it
+        // holds the row's lock.
+        const int g = (warp - 2) >> 2;
+        const int ew = warp - 2;  // this warp's copy of the tile metadata
+        const int r = (warp & 3) * 32 + lane;
         const int64_t u = row0 + r;
         const bool row_ok = u < a.N;
         const float nu = row_ok ? a.norms[u] : 0.f;
         const uint32_t au = row_ok ? a.attr[u] : 0u;
         unsigned long long *hp = heaps + r * LSTRIDE;
-        float *drow = drows + r * 33;          // delta^2 of the current 32-column chunk
-        unsigned long long *qk = queue + r;    // queued records (delta^2 bits, id), stride BM
-        unsigned char *qc = qchi + r;          // their chi, stride BM
-        int qn = 0;                            // queued records of this row
-        // this warp's copy of the tile's column metadata
+        unsigned long long *qk = queue + g * QCAP * BM + r;  // this group's queue of the row
+        unsigned char *qc = qchi + g * QCAP * BM + r;        // their chi, stride BM
+        volatile int *hcnt = rowcnt + r;                      // records in the row's heap
+        int *hlock = rowlock + r;
+        int qn = 0;  // records in this group's queue of the row
         float *mnorm = reinterpret_cast<float *>(meta) + ew * 3 * BN;
         uint32_t *mattr = reinterpret_cast<uint32_t *>(mnorm + BN);
         uint32_t *mid = mattr + BN;
         const int K = a.K;
-        int cnt = 0;
-        unsigned long long thr = kInfKey;
         // delta^2 bound of chi = c for this row at limtab[c * BM + r]: a record with
         // this chi and a larger delta^2 cannot reach the row's current K-th record
         // (Gamma grows with delta and with chi); -1 where no delta can
@@ -506,8 +538,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                          ? (a.w.wl > 0.f ? (c == 0 ? 1.f : a.w.wl * (float)c) : (float)c)
                          : (float)a.w.m / (float)(a.w.m + c);
         const float inv_wv = a.w.wv > 0.f ? 1.f / a.w.wv : 0.f;
-        auto update_lim = [&]() {
-            thr = hp[1];
+        auto update_lim = [&](unsigned long long thr) {  // thr: the row's K-th record
             // with slack 1e-5: the f32 roundings of Gamma and of these bounds stay far inside it
             const float gt = __uint_as_float((uint32_t)(thr >> 32)) * 1.00001f;
 #pragma unroll
@@ -528,16 +559,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 limtab[cc * BM + r] = tt < 0.f ? -1.f : tt * tt;
             }
         };
-        // the queued records enter the heap: exact Gamma (Eq. 6) and key test, then the
-        // bounds once for the whole flush
+        // The queued records enter the heap under the row's lock: exact Gamma (Eq. 6) and
+        // the key test, then the bounds once for the whole flush.  The lock's other user
+        // is this row's thread of the other group, which holds it only for a flush (no
+        // waits inside), so the bounded acquisition ends; a failure is recorded.
         auto flush = [&]() {
+            if (qn == 0)
+                return;
+            bool locked = false;
+            for (long long it = 0; it < kWaitLimit; ++it) {
+                if (atomicCAS(hlock, 0, 1) == 0) {
+                    locked = true;
+                    break;
+                }
+                if ((it & 1023) == 1023 && *reinterpret_cast<volatile int *>(a.err) != 0)
+                    break;
+            }
+            if (!locked) {
+                atomicCAS(a.err, 0, 9);
+                qn = 0;
+                return;
+            }
+            __threadfence_block();
+            int cnt = *hcnt;
+            unsigned long long thr = cnt == K ? hp[1] : kInfKey;
             bool touched = false;
             for (int e = 0; e < qn; ++e) {
                 const unsigned long long rec = qk[e * BM];
-                const float g = fusion_gamma(__fsqrt_rn(__uint_as_float((uint32_t)(rec >> 32))),
-                                             (int)qc[e * BM], a.w);
+                const float gm = fusion_gamma(__fsqrt_rn(__uint_as_float((uint32_t)(rec >> 32))),
+                                              (int)qc[e * BM], a.w);
                 const unsigned long long key =
-                    ((unsigned long long)__float_as_uint(g) << 32) | (uint32_t)rec;
+                    ((unsigned long long)__float_as_uint(gm) << 32) | (uint32_t)rec;
                 if (key >= thr)
                     continue;
                 if (cnt < K) {  // filling: unordered, heapified once full
@@ -555,32 +607,36 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     touched = true;
                 }
             }
-            qn = 0;
+            *hcnt = cnt;
             if (touched)
-                update_lim();
+                update_lim(thr);
+            __threadfence_block();
+            atomicExch(hlock, 0);
+            qn = 0;
         };
-        const uint32_t lane_base = (uint32_t)(ew * 32) << 16;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         const float *lt = limtab + r;
         bool ok = true;
-        int p = 0;
+        int k = -1;  // index of the current tile in the kept sequence
+        int p = 0;   // tiles this group processed
         // a tile's column metadata in registers until it is stored to this warp's copy
         float rn[4];
         uint32_t rat[4], rid[4];
         auto load_meta = [&](int ii) {
             const int64_t cb = (int64_t)tile_at(ii) * BN;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t col = cb + lane + 32 * k;
+            for (int kk = 0; kk < 4; ++kk) {
+                const int64_t col = cb + lane + 32 * kk;
                 const bool in = col < a.N;
-                rn[k] = in ? __ldg(a.norms + col) : 0.f;
-                rat[k] = in ? __ldg(a.attr + col) : 0u;
-                rid[k] = in ? __ldg(a.perm + col) : 0u;
+                rn[kk] = in ? __ldg(a.norms + col) : 0.f;
+                rat[kk] = in ? __ldg(a.attr + col) : 0u;
+                rid[kk] = in ? __ldg(a.perm + col) : 0u;
             }
         };
-        // without tile skipping every tile is kept: there are no decisions to wait for,
-        // and the next tile's metadata loads while this one is filtered
-        if (!skip_on)
-            load_meta(0);
+        // without tile skipping every tile is kept (k = i): there are no decisions to wait
+        // for, and this group's next tile's metadata loads while this one is filtered
+        if (!skip_on && g < ntiles)
+            load_meta(g);
         for (int i = 0;; ++i) {
             if (skip_on) {
                 i = next_kept(decided, skipbits, i, ntiles, a.err, 8);
@@ -593,9 +649,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             if (i >= ntiles)
                 break;
+            ++k;
+            if ((k & 1) != g)
+                continue;  // the other group's tile
             const int t = tile_at(i);
-            const int b = p & 1;
-            const uint32_t tph = (uint32_t)(p >> 1) & 1u;
+            const int b = k % NBUF;
+            const uint32_t tph = (uint32_t)(k / NBUF) & 1u;
             ++p;
             const int64_t cbase = (int64_t)t * BN;
             // with skipping, the loads are issued here, before the accumulator wait
@@ -604,18 +663,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ok = mbar_wait(bar(TFULL0 + b), tph, a.err, 5);
             __syncwarp();  // every lane is done with the previous tile's metadata
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                mnorm[lane + 32 * k] = rn[k];
-                mattr[lane + 32 * k] = rat[k];
-                mid[lane + 32 * k] = rid[k];
+            for (int kk = 0; kk < 4; ++kk) {
+                mnorm[lane + 32 * kk] = rn[kk];
+                mattr[lane + 32 * kk] = rat[kk];
+                mid[lane + 32 * kk] = rid[kk];
             }
             __syncwarp();  // metadata visible; tcgen05.ld below needs the warp converged
             if (!__all_sync(0xFFFFFFFFu, ok)) {
                 ok = false;
                 break;
             }
-            if (!skip_on && i + 1 < ntiles)
-                load_meta(i + 1);
+            if (!skip_on && i + 2 < ntiles)
+                load_meta(i + 2);
             tc_fence_after();
             const int nvalid = a.N - cbase < BN ? (int)(a.N - cbase) : BN;
             const uint32_t tf = mattr[0], tl = mattr[nvalid - 1];
@@ -670,45 +729,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     }
                 }
-                if (pass != 0u) {
-                    // the chunk's delta^2 values (8-column groups that hold a pass) go to
-                    // this row's line; the passing columns join the queue
-#pragma unroll
-                    for (int g8 = 0; g8 < 4; ++g8) {
-                        if ((pass >> (8 * g8)) & 0xFFu) {
-#pragma unroll
-                            for (int j = 8 * g8; j < 8 * g8 + 8; ++j)
-                                drow[j] = __uint_as_float(v[j]);
-                        }
-                    }
-                    for (uint32_t pm = pass; pm != 0u; pm &= pm - 1u) {
-                        const int j = __ffs((int)pm) - 1;
-                        const int c = c0 + j;
-                        const int64_t col = cbase + c;
-                        if (col >= a.N || col == u)
-                            continue;
-                        if (qn == QCAP)
-                            flush();  // this lane alone: a dense chunk
-                        qk[qn * BM] =
-                            ((unsigned long long)__float_as_uint(fmaxf(drow[j], 0.f)) << 32) |
-                            mid[c];
-                        qc[qn * BM] = (unsigned char)chi_packed(au, mattr[c], a.w.hi, a.w.lo);
-                        ++qn;
-                    }
+                // the passing columns join this group's queue of the row (delta^2 picked
+                // from the registers by the column's index)
+                for (uint32_t pm = pass; pm != 0u; pm &= pm - 1u) {
+                    const int j = __ffs((int)pm) - 1;
+                    const int c = c0 + j;
+                    const int64_t col = cbase + c;
+                    if (col >= a.N || col == u)
+                        continue;
+                    if (qn == QCAP)
+                        flush();  // this lane alone: a dense chunk
+                    const float d2 = __uint_as_float(pick32(v, j));
+                    qk[qn * BM] =
+                        ((unsigned long long)__float_as_uint(fmaxf(d2, 0.f)) << 32) | mid[c];
+                    qc[qn * BM] = (unsigned char)chi_packed(au, mattr[c], a.w.hi, a.w.lo);
+                    ++qn;
                 }
                 // every lane flushes together once some queue is half full
                 if (__any_sync(0xFFFFFFFFu, qn >= QCAP / 2))
                     flush();
             }
-            // and every FLUSH_TILES kept tiles, so that the bounds (and the scheduler's
-            // skip decisions) follow the heaps
+            // and every FLUSH_TILES tiles of the group, so that the bounds (and the
+            // scheduler's skip decisions) follow the heaps
             if ((p % FLUSH_TILES) == 0 && __any_sync(0xFFFFFFFFu, qn > 0))
                 flush();
             tc_fence_before();
             mbar_arrive(bar(TEMPTY0 + b));
         }
         flush();
-        if (row_ok) {
+        // both groups have flushed (named barrier 1 over the eight epilogue warps); group
+        // 0 writes the rows
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        const int cnt = *hcnt;
+        if (g == 0 && row_ok) {
             // heap sort: pop the largest into the last open output slot of the
             // object's own (original) row
             const int64_t orow = (int64_t)a.perm[u] * K;
