@@ -194,6 +194,8 @@ def recorded_traffic(ef, h, vec, seed_mode, n, nq, learned):
 def fp32_simt_peak(dev):
     """Measured FP32 throughput of the SIMT units: cuBLAS SGEMM with TF32 off (8192^3),
     TFLOP/s; the denominator of the brute force's ALU roofline."""
+    import torch
+
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
@@ -219,6 +221,8 @@ def brute_force_roofline(nhq, ix, Qv, QA, k, n, d, dev, stream):
     """The brute-force fused top-k (every query against every object, constant weights)
     timed with CUDA events on its stream: 3 flops per (query, object, dimension) (the
     difference and its fused square-add) against the measured SGEMM rate."""
+    import torch
+
     nq = Qv.shape[0]
     ids = torch.empty((nq, k), dtype=torch.uint32, device=dev)
     nhq.nhq_brute_force(ix.handle, Qv, QA, k, ids, weights=CONST_W, stream=stream)

@@ -23,6 +23,7 @@ namespace {
 constexpr int TQ = 32;   // queries per CTA
 constexpr int TN = 128;  // objects per tile
 constexpr int DC = 32;   // dimensions per staged chunk
+constexpr int DS = DC + 4;  // staged row stride: 16-byte aligned rows, read as float4
 constexpr int NT = 256;  // threads per CTA
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
@@ -34,9 +35,9 @@ __global__ void __launch_bounds__(NT) topk_tile_kernel(TopkArgs a, int64_t per_s
                                                        uint32_t *__restrict__ part_id,
                                                        float *__restrict__ part_g) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float(*Qs)[DC + 1] = reinterpret_cast<float(*)[DC + 1]>(smem);
-    float(*Xs)[DC + 1] = reinterpret_cast<float(*)[DC + 1]>(smem + sizeof(float) * TQ * (DC + 1));
-    float *G = reinterpret_cast<float *>(smem + sizeof(float) * (TQ + TN) * (DC + 1));
+    float(*Qs)[DS] = reinterpret_cast<float(*)[DS]>(smem);
+    float(*Xs)[DS] = reinterpret_cast<float(*)[DS]>(smem + sizeof(float) * TQ * DS);
+    float *G = reinterpret_cast<float *>(smem + sizeof(float) * (TQ + TN) * DS);
     float *Lg = G + TQ * TN;
     uint32_t *Li = reinterpret_cast<uint32_t *>(Lg + TQ * a.k);
 
@@ -72,19 +73,31 @@ __global__ void __launch_bounds__(NT) topk_tile_kernel(TopkArgs a, int64_t per_s
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (o < n_end && col < a.xstride)
                     v = *reinterpret_cast<const float4 *>(a.X + o * a.xstride + col);
-                Xs[r][4 * c4 + 0] = v.x;
-                Xs[r][4 * c4 + 1] = v.y;
-                Xs[r][4 * c4 + 2] = v.z;
-                Xs[r][4 * c4 + 3] = v.w;
+                *reinterpret_cast<float4 *>(&Xs[r][4 * c4]) = v;
             }
             __syncthreads();
-#pragma unroll 8
-            for (int c = 0; c < DC; ++c) {
-                float a0 = Qs[ty][c], a1 = Qs[ty + 16][c];
+            // four dimensions per shared-memory load; each pair still sums its squared
+            // differences one dimension at a time, in dimension order
+#pragma unroll 1
+            for (int c = 0; c < DC; c += 4) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(&Qs[ty][c]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&Qs[ty + 16][c]);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    float b = Xs[tx + 16 * j][c];
-                    float t0 = a0 - b, t1 = a1 - b;
+                    const float4 b = *reinterpret_cast<const float4 *>(&Xs[tx + 16 * j][c]);
+                    float t0 = a0.x - b.x, t1 = a1.x - b.x;
+                    acc[0][j] = fmaf(t0, t0, acc[0][j]);
+                    acc[1][j] = fmaf(t1, t1, acc[1][j]);
+                    t0 = a0.y - b.y;
+                    t1 = a1.y - b.y;
+                    acc[0][j] = fmaf(t0, t0, acc[0][j]);
+                    acc[1][j] = fmaf(t1, t1, acc[1][j]);
+                    t0 = a0.z - b.z;
+                    t1 = a1.z - b.z;
+                    acc[0][j] = fmaf(t0, t0, acc[0][j]);
+                    acc[1][j] = fmaf(t1, t1, acc[1][j]);
+                    t0 = a0.w - b.w;
+                    t1 = a1.w - b.w;
                     acc[0][j] = fmaf(t0, t0, acc[0][j]);
                     acc[1][j] = fmaf(t1, t1, acc[1][j]);
                 }
@@ -255,7 +268,7 @@ int choose_splits(const TopkArgs &a, int sm_count) {
 }
 
 size_t tile_smem(int k) {
-    return sizeof(float) * (TQ + TN) * (DC + 1) + sizeof(float) * TQ * TN +
+    return sizeof(float) * (TQ + TN) * DS + sizeof(float) * TQ * TN +
            (sizeof(float) + sizeof(uint32_t)) * (size_t)TQ * k;
 }
 
