@@ -263,6 +263,9 @@ __host__ __device__ inline TcSmem tc_smem_layout(int ntiles) {
     return L;
 }
 
+// MODE: the weighting (NHQ_W_CONSTANT, NHQ_W_PROPORTIONAL or NHQ_W_HARMONIC), fixed at
+// compile time so that each form carries only its own Gamma and bound code
+template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     knn_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int FULL0 = 0, EMPTY0 = MAX_STAGES, TFULL0 = 2 * MAX_STAGES, TEMPTY0 = TFULL0 + NBUF,
               AFULL = TEMPTY0 + NBUF, DONE = AFULL + 1;
     // whole tiles are rejected only where a negative bound is possible
-    const bool skip_on = a.w.mode == NHQ_W_CONSTANT;
+    constexpr bool skip_on = MODE == NHQ_W_CONSTANT;
 
     for (int i = threadIdx.x; i < (ntiles + 31) / 32; i += NTHREADS)
         skipbits[i] = 0u;
@@ -533,21 +536,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         float fac[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c)
-            fac[c] = a.w.mode == NHQ_W_CONSTANT   ? a.w.wl * (float)c
-                     : a.w.mode == NHQ_W_HARMONIC // the attribute term h of the harmonic mean
+            fac[c] = MODE == NHQ_W_CONSTANT   ? a.w.wl * (float)c
+                     : MODE == NHQ_W_HARMONIC // the attribute term h of the harmonic mean
                          ? (a.w.wl > 0.f ? (c == 0 ? 1.f : a.w.wl * (float)c) : (float)c)
                          : (float)a.w.m / (float)(a.w.m + c);
         const float inv_wv = a.w.wv > 0.f ? 1.f / a.w.wv : 0.f;
+        Fusion wf = a.w;  // the weights with the mode as a constant
+        wf.mode = MODE;
         auto update_lim = [&](unsigned long long thr) {  // thr: the row's K-th record
             // with slack 1e-5: the f32 roundings of Gamma and of these bounds stay far inside it
             const float gt = __uint_as_float((uint32_t)(thr >> 32)) * 1.00001f;
 #pragma unroll
             for (int cc = 0; cc < 5; ++cc) {
                 float tt;
-                if (a.w.mode == NHQ_W_CONSTANT) {
+                if constexpr (MODE == NHQ_W_CONSTANT) {
                     tt = a.w.wv > 0.f ? (gt - fac[cc]) * inv_wv
                                       : (gt >= fac[cc] ? __int_as_float(0x7f800000) : -1.f);
-                } else if (a.w.mode == NHQ_W_HARMONIC) {
+                } else if constexpr (MODE == NHQ_W_HARMONIC) {
                     // Gamma = 2 delta h / (delta + h) < 2 h for every delta: no bound while
                     // gt >= 2 h; below that, delta <= gt h / (2 h - gt)
                     const float h = fac[cc];
@@ -587,7 +592,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int e = 0; e < qn; ++e) {
                 const unsigned long long rec = qk[e * BM];
                 const float gm = fusion_gamma(__fsqrt_rn(__uint_as_float((uint32_t)(rec >> 32))),
-                                              (int)qc[e * BM], a.w);
+                                              (int)qc[e * BM], wf);
                 const unsigned long long key =
                     ((unsigned long long)__float_as_uint(gm) << 32) | (uint32_t)rec;
                 if (key >= thr)
@@ -882,13 +887,18 @@ cudaError_t launch_knn_tc(const __nv_bfloat16 *Xk, int kpad, const float *norms,
         e = cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess)
         return e;
-    if (smem > (size_t)smax)  // one skip bit per tile: N up to about 2.3e7
+    if (smem > (size_t)smax)  // one skip bit per tile: N up to about 2.2e7
         return cudaErrorInvalidValue;
-    e =
-        cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    void (*kfn)(const CUtensorMap, TcArgs) =
+        w.mode == NHQ_W_CONSTANT   ? knn_tc_kernel<NHQ_W_CONSTANT>
+        : w.mode == NHQ_W_HARMONIC ? knn_tc_kernel<NHQ_W_HARMONIC>
+                                   : knn_tc_kernel<NHQ_W_PROPORTIONAL>;
+    if (w.mode != NHQ_W_CONSTANT && w.mode != NHQ_W_HARMONIC && w.mode != NHQ_W_PROPORTIONAL)
+        return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    knn_tc_kernel<<<(unsigned)ntiles, NTHREADS, smem, s>>>(tmap, a);
+    kfn<<<(unsigned)ntiles, NTHREADS, smem, s>>>(tmap, a);
     return cudaGetLastError();
 }
 
