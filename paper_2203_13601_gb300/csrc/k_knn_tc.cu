@@ -652,116 +652,123 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 i = __shfl_sync(0xFFFFFFFFu, i, 0);  // every lane saw the same published bits
             }
-            if (i >= ntiles)
-                break;
-            ++k;
-            if ((k & 1) != g)
-                continue;  // the other group's tile
-            const int t = tile_at(i);
-            const int b = k % NBUF;
-            const uint32_t tph = (uint32_t)(k / NBUF) & 1u;
-            ++p;
-            const int64_t cbase = (int64_t)t * BN;
-            // with skipping, the loads are issued here, before the accumulator wait
-            if (skip_on)
-                load_meta(i);
-            ok = mbar_wait(bar(TFULL0 + b), tph, a.err, 5);
-            __syncwarp();  // every lane is done with the previous tile's metadata
+            const bool last = i >= ntiles;  // no tile left: the final flush
+            if (!last) {
+                ++k;
+                if ((k & 1) != g)
+                    continue;  // the other group's tile
+                const int t = tile_at(i);
+                const int b = k % NBUF;
+                const uint32_t tph = (uint32_t)(k / NBUF) & 1u;
+                ++p;
+                const int64_t cbase = (int64_t)t * BN;
+                // with skipping, the loads are issued here, before the accumulator wait
+                if (skip_on)
+                    load_meta(i);
+                ok = mbar_wait(bar(TFULL0 + b), tph, a.err, 5);
+                __syncwarp();  // every lane is done with the previous tile's metadata
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                mnorm[lane + 32 * kk] = rn[kk];
-                mattr[lane + 32 * kk] = rat[kk];
-                mid[lane + 32 * kk] = rid[kk];
-            }
-            __syncwarp();  // metadata visible; tcgen05.ld below needs the warp converged
-            if (!__all_sync(0xFFFFFFFFu, ok)) {
-                ok = false;
-                break;
-            }
-            if (!skip_on && i + 2 < ntiles)
-                load_meta(i + 2);
-            tc_fence_after();
-            const int nvalid = a.N - cbase < BN ? (int)(a.N - cbase) : BN;
-            const uint32_t tf = mattr[0], tl = mattr[nvalid - 1];
-            const bool uni = tf == tl;  // one tuple in the whole tile (sorted order)
-            const int ch_t = chi_level(chi_packed(au, tf, a.w.hi, a.w.lo));
-            const int ch_min = (au >= tf && au <= tl) ? 0 : (uni ? ch_t : 1);
-            for (int c0 = 0; c0 < BN; c0 += 32) {
-                // the bounds only tighten: a row whose bound for the smallest chi of
-                // this tile is negative rejects every column of it (negative bounds
-                // arise only under constant weights, where tiles are skipped)
-                const bool dead = !row_ok || (skip_on && lt[ch_min * BM] < 0.f);
-                if (__all_sync(0xFFFFFFFFu, dead))
+                for (int kk = 0; kk < 4; ++kk) {
+                    mnorm[lane + 32 * kk] = rn[kk];
+                    mattr[lane + 32 * kk] = rat[kk];
+                    mid[lane + 32 * kk] = rid[kk];
+                }
+                __syncwarp();  // metadata visible; tcgen05.ld below needs the warp converged
+                if (!__all_sync(0xFFFFFFFFu, ok)) {
+                    ok = false;
                     break;
-                uint32_t v[32];
-                tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + c0), v);
-                // branch-free filter: a pass mask of the columns within the bound of their
-                // chi (a dead row passes none and stays with the warp for its votes)
-                uint32_t pass = 0;
-                const float4 *cn4 = reinterpret_cast<const float4 *>(mnorm + c0);
-                if (dead) {
-                } else if (uni) {
-                    const float Lb = lt[ch_t * BM];
+                }
+                if (!skip_on && i + 2 < ntiles)
+                    load_meta(i + 2);
+                tc_fence_after();
+                const int nvalid = a.N - cbase < BN ? (int)(a.N - cbase) : BN;
+                const uint32_t tf = mattr[0], tl = mattr[nvalid - 1];
+                const bool uni = tf == tl;  // one tuple in the whole tile (sorted order)
+                const int ch_t = chi_level(chi_packed(au, tf, a.w.hi, a.w.lo));
+                const int ch_min = (au >= tf && au <= tl) ? 0 : (uni ? ch_t : 1);
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    // the bounds only tighten: a row whose bound for the smallest chi of
+                    // this tile is negative rejects every column of it (negative bounds
+                    // arise only under constant weights, where tiles are skipped)
+                    const bool dead = !row_ok || (skip_on && lt[ch_min * BM] < 0.f);
+                    if (__all_sync(0xFFFFFFFFu, dead))
+                        break;
+                    uint32_t v[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + c0), v);
+                    // branch-free filter: a pass mask of the columns within the bound of their
+                    // chi (a dead row passes none and stays with the warp for its votes)
+                    uint32_t pass = 0;
+                    const float4 *cn4 = reinterpret_cast<const float4 *>(mnorm + c0);
+                    if (dead) {
+                    } else if (uni) {
+                        const float Lb = lt[ch_t * BM];
 #pragma unroll
-                    for (int j4 = 0; j4 < 8; ++j4) {
-                        const float4 n4 = cn4[j4];
-                        const float nc[4] = {n4.x, n4.y, n4.z, n4.w};
+                        for (int j4 = 0; j4 < 8; ++j4) {
+                            const float4 n4 = cn4[j4];
+                            const float nc[4] = {n4.x, n4.y, n4.z, n4.w};
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int j = j4 * 4 + q;
-                            // unclamped: a rounding below zero passes as it would at
-                            // zero (the survivor's exact key decides)
-                            const float d2 = (nu + nc[q]) - 2.f * __uint_as_float(v[j]);
-                            v[j] = __float_as_uint(d2);
-                            pass |= (d2 <= Lb ? 1u : 0u) << j;
+                            for (int q = 0; q < 4; ++q) {
+                                const int j = j4 * 4 + q;
+                                // unclamped: a rounding below zero passes as it would at
+                                // zero (the survivor's exact key decides)
+                                const float d2 = (nu + nc[q]) - 2.f * __uint_as_float(v[j]);
+                                v[j] = __float_as_uint(d2);
+                                pass |= (d2 <= Lb ? 1u : 0u) << j;
+                            }
+                        }
+                    } else {
+                        const uint4 *ca4 = reinterpret_cast<const uint4 *>(mattr + c0);
+#pragma unroll
+                        for (int j4 = 0; j4 < 8; ++j4) {
+                            const float4 n4 = cn4[j4];
+                            const uint4 at4 = ca4[j4];
+                            const float nc[4] = {n4.x, n4.y, n4.z, n4.w};
+                            const uint32_t ac[4] = {at4.x, at4.y, at4.z, at4.w};
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int j = j4 * 4 + q;
+                                const float d2 = (nu + nc[q]) - 2.f * __uint_as_float(v[j]);
+                                v[j] = __float_as_uint(d2);
+                                const int ch = chi_level(chi_packed(au, ac[q], a.w.hi, a.w.lo));
+                                pass |= (d2 <= lt[ch * BM] ? 1u : 0u) << j;
+                            }
                         }
                     }
-                } else {
-                    const uint4 *ca4 = reinterpret_cast<const uint4 *>(mattr + c0);
-#pragma unroll
-                    for (int j4 = 0; j4 < 8; ++j4) {
-                        const float4 n4 = cn4[j4];
-                        const uint4 at4 = ca4[j4];
-                        const float nc[4] = {n4.x, n4.y, n4.z, n4.w};
-                        const uint32_t ac[4] = {at4.x, at4.y, at4.z, at4.w};
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int j = j4 * 4 + q;
-                            const float d2 = (nu + nc[q]) - 2.f * __uint_as_float(v[j]);
-                            v[j] = __float_as_uint(d2);
-                            const int ch = chi_level(chi_packed(au, ac[q], a.w.hi, a.w.lo));
-                            pass |= (d2 <= lt[ch * BM] ? 1u : 0u) << j;
+                    // the passing columns join this group's queue of the row (delta^2 picked
+                    // from the registers by the column's index); every lane flushes together
+                    // once some queue is half full, or full with columns of the chunk left
+                    // (one call site, so the flush is compiled twice in all, not four times)
+                    uint32_t pm = pass;
+                    for (;;) {
+                        for (; pm != 0u && qn < QCAP; pm &= pm - 1u) {
+                            const int j = __ffs((int)pm) - 1;
+                            const int c = c0 + j;
+                            const int64_t col = cbase + c;
+                            if (col >= a.N || col == u)
+                                continue;
+                            const float d2 = __uint_as_float(pick32(v, j));
+                            qk[qn * BM] =
+                                ((unsigned long long)__float_as_uint(fmaxf(d2, 0.f)) << 32) | mid[c];
+                            qc[qn * BM] = (unsigned char)chi_packed(au, mattr[c], a.w.hi, a.w.lo);
+                            ++qn;
                         }
+                        if (!__any_sync(0xFFFFFFFFu, qn >= QCAP / 2 || pm != 0u))
+                            break;
+                        flush();
                     }
                 }
-                // the passing columns join this group's queue of the row (delta^2 picked
-                // from the registers by the column's index)
-                for (uint32_t pm = pass; pm != 0u; pm &= pm - 1u) {
-                    const int j = __ffs((int)pm) - 1;
-                    const int c = c0 + j;
-                    const int64_t col = cbase + c;
-                    if (col >= a.N || col == u)
-                        continue;
-                    if (qn == QCAP)
-                        flush();  // this lane alone: a dense chunk
-                    const float d2 = __uint_as_float(pick32(v, j));
-                    qk[qn * BM] =
-                        ((unsigned long long)__float_as_uint(fmaxf(d2, 0.f)) << 32) | mid[c];
-                    qc[qn * BM] = (unsigned char)chi_packed(au, mattr[c], a.w.hi, a.w.lo);
-                    ++qn;
-                }
-                // every lane flushes together once some queue is half full
-                if (__any_sync(0xFFFFFFFFu, qn >= QCAP / 2))
-                    flush();
+                tc_fence_before();
+                mbar_arrive(bar(TEMPTY0 + b));
+                // and every FLUSH_TILES tiles of the group, so that the bounds (and the
+                // scheduler's skip decisions) follow the heaps; at the end, the rest
+                if ((p % FLUSH_TILES) != 0)
+                    continue;
             }
-            // and every FLUSH_TILES tiles of the group, so that the bounds (and the
-            // scheduler's skip decisions) follow the heaps
-            if ((p % FLUSH_TILES) == 0 && __any_sync(0xFFFFFFFFu, qn > 0))
+            if (__any_sync(0xFFFFFFFFu, qn > 0))
                 flush();
-            tc_fence_before();
-            mbar_arrive(bar(TEMPTY0 + b));
+            if (last)
+                break;
         }
-        flush();
         // both groups have flushed (named barrier 1 over the eight epilogue warps); group
         // 0 writes the rows
         asm volatile("bar.sync 1, 256;" ::: "memory");
