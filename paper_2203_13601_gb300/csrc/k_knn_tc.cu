@@ -674,6 +674,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     mid[lane + 32 * kk] = rid[kk];
                 }
                 __syncwarp();  // metadata visible; tcgen05.ld below needs the warp converged
+                // the tile's largest |v|^2 (norms are >= 0, so their bits order like them)
+                const float ncmax = __uint_as_float(__reduce_max_sync(
+                    0xFFFFFFFFu,
+                    __float_as_uint(fmaxf(fmaxf(rn[0], rn[1]), fmaxf(rn[2], rn[3])))));
                 if (!__all_sync(0xFFFFFFFFu, ok)) {
                     ok = false;
                     break;
@@ -701,7 +705,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const float4 *cn4 = reinterpret_cast<const float4 *>(mnorm + c0);
                     if (dead) {
                     } else if (uni) {
+                        // delta^2 = |u|^2 + |v|^2 - 2 u.v <= Lb tested as u.v >= |v|^2 / 2 + h,
+                        // h = (|u|^2 - Lb) / 2 lowered by 2^-20 (|u|^2 + max |v|^2 + |Lb|):
+                        // sixteen times the f32 rounding of either form, so every pair
+                        // within the bound passes (a few more do, and fail the exact key
+                        // test); two operations per pair instead of three
                         const float Lb = lt[ch_t * BM];
+                        const float marg = 9.5367431640625e-07f * (nu + ncmax + fabsf(Lb));
+                        const float h = 0.5f * (nu - Lb) - marg;
 #pragma unroll
                         for (int j4 = 0; j4 < 8; ++j4) {
                             const float4 n4 = cn4[j4];
@@ -709,11 +720,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                             for (int q = 0; q < 4; ++q) {
                                 const int j = j4 * 4 + q;
-                                // unclamped: a rounding below zero passes as it would at
-                                // zero (the survivor's exact key decides)
-                                const float d2 = (nu + nc[q]) - 2.f * __uint_as_float(v[j]);
-                                v[j] = __float_as_uint(d2);
-                                pass |= (d2 <= Lb ? 1u : 0u) << j;
+                                const float dot = __uint_as_float(v[j]);
+                                pass |= (dot >= fmaf(0.5f, nc[q], h) ? 1u : 0u) << j;
                             }
                         }
                     } else {
@@ -727,8 +735,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                             for (int q = 0; q < 4; ++q) {
                                 const int j = j4 * 4 + q;
-                                const float d2 = (nu + nc[q]) - 2.f * __uint_as_float(v[j]);
-                                v[j] = __float_as_uint(d2);
+                                const float d2 =
+                                    __fmaf_rn(-2.f, __uint_as_float(v[j]), __fadd_rn(nu, nc[q]));
                                 const int ch = chi_level(chi_packed(au, ac[q], a.w.hi, a.w.lo));
                                 pass |= (d2 <= lt[ch * BM] ? 1u : 0u) << j;
                             }
@@ -746,7 +754,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             const int64_t col = cbase + c;
                             if (col >= a.N || col == u)
                                 continue;
-                            const float d2 = __uint_as_float(pick32(v, j));
+                            // the pair's delta^2 as the filters define it (unclamped there: a
+                            // rounding below zero passes as it would at zero)
+                            const float d2 = __fmaf_rn(-2.f, __uint_as_float(pick32(v, j)),
+                                                       __fadd_rn(nu, mnorm[c]));
                             qk[qn * BM] =
                                 ((unsigned long long)__float_as_uint(fmaxf(d2, 0.f)) << 32) | mid[c];
                             qc[qn * BM] = (unsigned char)chi_packed(au, mattr[c], a.w.hi, a.w.lo);

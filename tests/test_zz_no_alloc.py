@@ -4,8 +4,10 @@ It serves callers that cannot allocate device memory when they call the
 library (their device memory belongs to another allocator or a pool reserved
 at start-up, or their hot path must not touch an allocator), so its working
 memory is a fixed array compiled into the library.  These tests call it
-through the C ABI and check it against nhq_brute_force on the same inputs,
-twice in a row (the fixed array keeps the previous call's contents), check
+through the C ABI and check it against the oracle's exact top-k (Def. 2 with
+Eq. 6; for the filter weighting the hybrid ground truth of Sec. 6.1) and against
+nhq_brute_force on the same inputs, twice in a row (the fixed array keeps the
+previous call's contents), check
 that the second call changes the device's free memory by nothing, and check
 that a batch needing more than the fixed array is refused without writing
 anything.  This file is collected last on purpose.
@@ -13,6 +15,7 @@ anything.  This file is collected last on purpose.
 import numpy as np
 import pytest
 
+import oracle as O
 import synth
 from helpers import dev, ids_i64
 
@@ -88,6 +91,20 @@ def test_noalloc_matches_brute_force_twice(nhq, N, nq, k, weights):
         assert torch.equal(g, ref_g)
     # the second call allocated nothing on the device
     assert torch.cuda.mem_get_info()[0] == free[1]
+    # and both equal the oracle's exact answer (integer components: Gamma exact in f32)
+    O.build()
+    ids = ids_i64(outs[1][0])
+    if weights == "filter":
+        want, dl, _ = O.filtered_topk(w.X, w.A, w.Qv, w.QA, k, prec=O.F32)
+        assert (ids == want).all()
+        g = outs[1][1].cpu().numpy().astype(np.float64)
+        fin = want >= 0
+        assert np.array_equal(g[fin], dl[fin])
+    else:
+        want, wg, wc = O.fused_topk(w.X, w.A, w.Qv, w.QA, k, weights=weights, prec=O.F32)
+        assert (ids == want).all()
+        assert np.array_equal(outs[1][1].cpu().numpy().astype(np.float64), wg)
+        assert (outs[1][2].cpu().numpy().astype(np.int64) == wc).all()
 
 
 def test_noalloc_refuses_a_batch_beyond_its_fixed_memory(nhq):
