@@ -63,7 +63,7 @@ constexpr long long kWaitLimit = 1ll << 26;
 // in flushes that every lane of the warp runs at once (a flush when some lane's queue is
 // half full, every FLUSH_TILES kept tiles, and at the end)
 constexpr int QCAP = 12;
-constexpr int FLUSH_TILES = 4;
+constexpr int FLUSH_TILES = 16;
 
 struct TcArgs {
     const float *norms;     // |x|^2 of the bf16-rounded rows, sorted order
