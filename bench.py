@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--target", type=float, default=0.95)
     ap.add_argument("--target2", type=float, default=0.98,
                     help="a second recall level at which the forms are also compared")
-    ap.add_argument("--efs", default="10,12,16,20,24,32,40,48,64,80,96,128,160,200,256,320,400,500")
+    ap.add_argument("--efs", default="10,12,16,20,22,23,24,32,40,48,64,80,96,128,160,200,256,320,400,500")
     ap.add_argument("--hs", default="1,2")
     ap.add_argument("--cpu-sample", type=int, default=40, help="queries in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
